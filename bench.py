@@ -1,0 +1,365 @@
+"""Benchmark of the overlap-and-layout hot path on one GB300 (or N independent replicas).
+
+One step = the whole path over one seeded synthetic read set: build A and At from the reads
+(canonical k-mers, Bloom pass, exact count, reliable filter), C = A At over the overlap semiring,
+and the transitive reduction of the overlap graph R (Algorithm 1). The workload is the
+bacterial-scale read set (5 Mbp genome with 50 repeat copies, 30x, 10 kbp mean, 15% errors,
+k = 17, reliable range [2, 20], >= 2 shared k-mers, fuzz 1000).
+
+value  = A A^T semiring products (sum_j nnz(At_j)^2) per second over whole steps, inputs resident
+         in HBM, L2 flushed (256 MB write) between steps.
+e2e    = the same through sg_pipeline_host: reads and R copied from pinned host memory, C and S
+         copied back, every step.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A·Aᵀ semiring products/s & TR edges/s (bit-exact); batched vs plain; p99"
+UNIT = "products/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--workload", default="bacterial-5Mbp-30x")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline
+def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
+    """Bytes the method must move per launch of `kernel` (kernel table)."""
+    if kernel == "bloom_insert":
+        # every base read once, one 8-byte filter word touched per k-mer window
+        return sz["total"] + 8.0 * sz["windows"]
+    if kernel in ("cand_count", "cand_emit"):
+        extra = 16.0 * sz["cand"] if kernel == "cand_emit" else 0.0
+        return sz["total"] + 8.0 * sz["windows"] + extra
+    if kernel == "spgemm_numeric":
+        return 8.0 * sz["nnzA"] + 8.0 * sz["products"] + (8.0 + 8.0 * sz["S"]) * sz["nnzC"] + 8.0 * (sz["n"] + 1)
+    if kernel == "spgemm_symbolic":
+        return 8.0 * sz["nnzA"] + 4.0 * sz["products"] + 8.0 * (sz["n"] + 1)
+    if kernel == "tr_minplus_mark":
+        return 9.0 * sz["nnzR"] + 9.0 * sz["tr_products"] + 1.0 * sz["nnzR"] + 8.0 * sz["n"]
+    return None
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    import numpy as np
+    import torch
+
+    import paper_2010_10055_gb300 as sg
+    import synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = synth.WORKLOADS[args.workload]
+    w = synth.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})  # independent replica per rank
+    d = synth.make(w)
+    n = int(d["offsets"].size - 1)
+    total = int(d["seq"].size)
+    seq = torch.from_numpy(d["seq"]).cuda()
+    off = torch.from_numpy(d["offsets"]).cuda()
+    R = sg.DeviceGraph.from_numpy(d["R"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+        C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+        S, it = sg.transitive_reduce(R, w.fuzz)
+        return km, C, S, it
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        out = step()
+        del out
+    torch.cuda.synchronize()
+    # sizes for the units and the roofline (from the last warm-up step)
+    km, C, S, it = step()
+    at_rp = km.At.to_numpy()["row_ptr"]
+    a = np.diff(at_rp).astype(np.int64)
+    products = int((a * a).sum())
+    deg = np.diff(d["R"]["row_ptr"]).astype(np.int64)
+    tr_products = int(deg[d["R"]["col"]].sum()) if d["R"]["col"].size else 0
+    sz = dict(n=n, total=total, windows=max(total - (w.k - 1) * n, 0), nnzA=km.A.nnz, products=products,
+              nnzC=C.nnz, S=w.max_seeds, nnzR=R.nnz, tr_products=tr_products, nnzS=S.nnz, rounds=it, m=km.m)
+    del km, C, S
+
+    # ---- timed region: K steps, per-step events, L2 flushed in between
+    clocks = ClockSampler(local)
+    sg.prof_reset()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = sg.launch_count()
+    sg.prof_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    tr_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+        C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+        tr_ev[i][0].record(stream)
+        S, it = sg.transitive_reduce(R, w.fuzz)
+        tr_ev[i][1].record(stream)
+        ev[i][1].record(stream)
+        del km, C, S
+    torch.cuda.synchronize()
+    sg.prof_enable(False)
+    launches = sg.launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a0.elapsed_time(a1) for a0, a1 in ev]
+    tr_ms = [a0.elapsed_time(a1) for a0, a1 in tr_ev]
+    total_ms = sum(step_ms)
+    prof = sg.prof_collect()
+    if world > 1:
+        t = torch.tensor([total_ms, float(products), float(sum(tr_ms)), float(R.nnz)], dtype=torch.float64,
+                         device="cuda")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        total_ms_all = float(mx[0])
+        products_all = float(sm[1])
+        tr_ms_max = float(sm[2]) / world
+        edges_all = float(sm[3])
+    else:
+        total_ms_all, products_all, tr_ms_max, edges_all = total_ms, float(products), sum(tr_ms), float(R.nnz)
+    value = products_all * args.steps / (total_ms_all / 1e3)
+
+    # ---- roofline of the dominant kernel
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_src = "measured"
+    except Exception:
+        peak_src = "fallback"
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ktot = sum(v[1] for v in prof.values()) or 1.0
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if dom:
+        name, (cnt, ms) = dom
+        ab = algorithmic_bytes(name, sz)
+        avg_ms = ms / max(cnt, 1)
+        ach = (ab / (avg_ms / 1e3) / 1e9) if ab else None
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": (ach / hbm) if ach else None, "traffic": None, "peak_source": peak_src,
+                "launch_ms": avg_ms, "share": ms / ktot}
+    kernels = {k: {"launches": c, "ms_per_step": ms / args.steps, "share": ms / ktot}
+               for k, (c, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(sg, d, w, args)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w.name, "reads": n, "bases": total, "k": w.k, "reliable": [w.lo, w.hi],
+                       "min_shared": w.min_shared, "max_seeds": w.max_seeds, "fuzz": w.fuzz,
+                       "m": sz["m"], "nnz_A": sz["nnzA"], "products": products, "nnz_C": sz["nnzC"],
+                       "nnz_R": sz["nnzR"], "nnz_S": sz["nnzS"], "tr_rounds": sz["rounds"],
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "tr_edges_per_s": edges_all * args.steps / (tr_ms_max / 1e3) if tr_ms_max else None,
+            "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
+            "e2e": e2e, "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": launches}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, scale=0.1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(sg, d, w, args):
+    """Products/s through sg_pipeline_host: pinned host inputs in, C and S out, every step."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    L = sg.lib()
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+           dict(seq=d["seq"], off=d["offsets"], rp=d["R"]["row_ptr"], col=d["R"]["col"],
+                suf=d["R"]["suffix"].view(np.int32), dir=d["R"]["dir"]).items()}
+    job = sg.PipelineJob.make(pin["seq"].data_ptr(), pin["off"].data_ptr(), int(d["offsets"].size - 1),
+                              int(d["seq"].size), w, pin["rp"].data_ptr(), pin["col"].data_ptr(),
+                              pin["suf"].data_ptr(), pin["dir"].data_ptr(), int(d["R"]["col"].size))
+    arena = ctypes.c_void_p()
+    sg._check(L.sg_host_arena_create(ctypes.byref(arena)), "host_arena_create")
+    res = sg.PipelineResult()
+    stream = torch.cuda.current_stream()
+    st = ctypes.c_void_p(stream.cuda_stream)
+    try:
+        for _ in range(max(args.warmup, 1)):
+            sg._check(L.sg_pipeline_host(ctypes.byref(job), arena, ctypes.byref(res), st), "pipeline_host")
+        times = []
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sg._check(L.sg_pipeline_host(ctypes.byref(job), arena, ctypes.byref(res), st), "pipeline_host")
+            times.append(time.perf_counter() - t0)
+        h2d = sum(int(t.numel() * t.element_size()) for t in pin.values())
+        nrow = int(d["offsets"].size)  # n + 1 row pointers for C and for S
+        d2h = 8 * nrow * 2 + res.nnz_c * (8 + 8 * res.max_seeds) + res.nnz_s * 9 + 8
+        return {"value": float(res.products) * args.steps / sum(times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(times) / args.steps,
+                "nnz_C": int(res.nnz_c), "nnz_S": int(res.nnz_s)}
+    finally:
+        L.sg_host_arena_destroy(arena)
+
+
+def cpu_baseline(w, scale: float):
+    """The oracle, as it stands (single host thread), on the same workload shape at `scale` of
+    the genome: products/s over the three operations."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    ws = w.scaled(scale)
+    d = synth.make(ws)
+    t0 = time.perf_counter()
+    km = oracle.build_kmer_matrix(d["seq"], d["offsets"], ws.k, ws.lo, ws.hi)
+    oracle.overlap_spgemm(km["A"], km["At"], ws.min_shared, ws.max_seeds)
+    oracle.transitive_reduce(d["R"], ws.fuzz)
+    dt = time.perf_counter() - t0
+    a = np.diff(km["At"]["row_ptr"]).astype(np.int64)
+    prod = int((a * a).sum())
+    return {"value": prod / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{ws.name} at {scale:g} of the genome ({ws.G} bp, {d['offsets'].size - 1} reads), "
+                      f"{dt:.1f} s for build_kmer_matrix + overlap_spgemm + transitive_reduce"}
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed on the host cores as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+
+    w = synth.WORKLOADS[args.workload]
+    scale = 0.04
+    ws = w.scaled(scale)
+    d = synth.make(ws)
+
+    def one():
+        km = oracle.build_kmer_matrix(d["seq"], d["offsets"], ws.k, ws.lo, ws.hi)
+        oracle.overlap_spgemm(km["A"], km["At"], ws.min_shared, ws.max_seeds)
+        oracle.transitive_reduce(d["R"], ws.fuzz)
+        return km
+
+    for _ in range(args.warmup):
+        one()
+    times = []
+    km = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        km = one()
+        times.append(time.perf_counter() - t0)
+    a = np.diff(km["At"]["row_ptr"]).astype(np.int64)
+    prod = int((a * a).sum())
+    value = prod * args.steps / sum(times)
+    sample = f"{ws.name} at {scale:g} of the genome ({ws.G} bp, {d['offsets'].size - 1} reads) per step"
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                      "data": "synthetic", "impl": "reference",
+                      "config": {"workload": w.name, "parallelism": "host, 1 thread"},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * sgraph.h -- C ABI of the GB300 (sm_103a) library for the overlap-and-layout hot path of
+ * diBELLA 2D, "Parallel String Graph Construction and Transitive Reduction for De Novo Genome
+ * Assembly" (arXiv 2010.10055).
+ *
+ * Three operations, each one call, each run entirely by the library's own CUDA kernels:
+ *   sg_build_kmer_matrix   reads -> A (reads x reliable k-mers) and its transpose
+ *                          (Algorithm 2 steps KmerCounter, GenerateA, Transpose; Sec. IV-C, IV-D)
+ *   sg_overlap_spgemm      C = A A^T over the overlap semiring (Algorithm 2 step "C <- A A^T";
+ *                          Sec. IV-D)
+ *   sg_transitive_reduce   S = TransitiveReduction(R) (Algorithm 1 with the MinPlus semiring of
+ *                          Algorithm 3; Sec. IV-E)
+ * plus sg_minplus_square, the single N = R^2 product of Algorithm 1 exposed on its own.
+ *
+ * Conventions shared by every call
+ *  - Pointers named d_* and the array members of the CSR structs are DEVICE pointers (the
+ *    current CUDA device); the structs themselves and the scalars live on the host.
+ *  - Inputs are borrowed and never modified.
+ *  - Outputs are allocated by the library with stream-ordered allocation (cudaMallocAsync) on
+ *    the caller's stream, or with the allocator installed by sg_set_allocator, and are released
+ *    with the matching sg_free_* call. On any error every output pointer is left NULL and no
+ *    memory stays allocated.
+ *  - All work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream). Each
+ *    compute call validates its device inputs on the device and synchronises the stream to read
+ *    that verdict and its output sizes back, so outputs are complete when it returns.
+ *  - Errors: a non-SG_OK status; sg_last_error() describes it (per host thread). There is no
+ *    CPU fallback: if the GPU cannot run the call, it fails.
+ *  - Sizes are int64. Row pointers are int64, column indices int32 (so n and m < 2^31).
+ */
+#ifndef SGRAPH_H
+#define SGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *sg_stream_t; /* cudaStream_t */
+
+typedef enum {
+    SG_OK = 0,
+    SG_ERR_INVALID = 1,  /* an argument or input array breaks the documented contract */
+    SG_ERR_OOM = 2,      /* device (or host staging) allocation failed */
+    SG_ERR_CUDA = 3,     /* a CUDA runtime call failed; sg_last_error() has the CUDA message */
+    SG_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    SG_ERR_BUDGET = 5,   /* a job does not fit the memory budget it was given */
+    SG_ERR_OVERFLOW = 6  /* an intermediate exceeded a documented limit (e.g. nnz >= 2^31 per row) */
+} sg_status;
+
+/* Sparse matrix in CSR with a 32-bit payload: A (n x m) and At (m x n).
+ * val = pos | strand << 31: pos = 0-based start of the k-mer in the read, strand = 1 when the
+ * read holds the reverse complement of the canonical k-mer. Columns ascend within each row. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    int64_t *row_ptr; /* [n_rows + 1] */
+    int32_t *col;     /* [nnz] */
+    uint32_t *val;    /* [nnz] */
+} sg_csr_u32;
+
+/* Candidate overlap matrix C (n x n). count = number of shared reliable k-mers. Seed arrays are
+ * slot-major, [max_seeds][nnz]: seed_i[s*nnz+e] = position of the s-th seed k-mer in read i (the
+ * row), seed_k[s*nnz+e] = its position in read k (the column) | (strand_i xor strand_k) << 31.
+ * Seeds are the shared k-mers with the smallest column index of A, ascending; unused slots hold
+ * 0xFFFFFFFF. No diagonal entries; columns ascend within each row. */
+typedef struct {
+    int64_t n, nnz;
+    int32_t max_seeds;
+    int64_t *row_ptr; /* [n + 1] */
+    int32_t *col;     /* [nnz] */
+    uint32_t *count;  /* [nnz] */
+    uint32_t *seed_i; /* [max_seeds * nnz] */
+    uint32_t *seed_k; /* [max_seeds * nnz] */
+} sg_overlap_csr;
+
+/* Bidirected overlap / string graph R or S (n x n). Entry (i, k) is the walk i -> k:
+ * suffix = overhang of read k beyond read i (< 2^30); dir = 2 * o_i + o_k where o = 0 when the
+ * read is traversed as given and 1 when traversed reverse-complemented (Sec. II, Fig. 1).
+ * No diagonal entries; columns strictly ascend within each row. */
+typedef struct {
+    int64_t n, nnz;
+    int64_t *row_ptr; /* [n + 1] */
+    int32_t *col;     /* [nnz] */
+    uint32_t *suffix; /* [nnz] */
+    uint8_t *dir;     /* [nnz] */
+} sg_graph_csr;
+
+/* Transitive-reduction semiring readings (Algorithm 3 keeps one min per entry; the paper does
+ * not say which orientation that min carries when walks with different end orientations tie). */
+enum {
+    SG_TR_DIRMATCH = 0, /* N_ik = min over valid walks i->j->k whose end orientations match d_ik */
+    SG_TR_LITERAL = 1   /* N_ik = lexicographic min of (sum, composite dir) over valid walks; the
+                           end-orientation check is applied to that one min afterwards */
+};
+
+/*
+ * Reads -> A and At (Sec. II canonical k-mers; Sec. IV-C k-mer counting and reliable range;
+ * Sec. IV-D "A_ij stores the position of the j-th k-mer in the i-th sequence").
+ *   d_seq      [total_len] ASCII bases of all reads back to back. Only 'A','C','G','T' form
+ *              k-mers; a window holding any other byte is skipped.
+ *   d_offsets  [n_reads + 1] int64; read i is d_seq[d_offsets[i] .. d_offsets[i+1]);
+ *              d_offsets[0] = 0, non-decreasing, d_offsets[n_reads] = total_len, each read
+ *              shorter than 2^31.
+ *   k          odd, 1..31 (odd k: no k-mer equals its reverse complement).
+ *   lo, hi     a canonical k-mer is reliable iff lo <= (occurrences over all windows) <= hi;
+ *              1 <= lo <= hi. (The paper drops singletons and k-mers seen at least d times:
+ *              lo = 2, hi = d - 1.)
+ * Outputs: *A (n_reads x m), *At (m x n_reads), *d_kmer_codes [m] = canonical 2k-bit code of each
+ * column (first base in the most significant bits, A=0 C=1 G=2 T=3); columns are numbered by
+ * ascending code. A_ij = pos | strand << 31 at the LOWEST position of k-mer j in read i.
+ * Errors: SG_ERR_INVALID for bad k/lo/hi/n_reads or inconsistent offsets (checked on the device),
+ * SG_ERR_OOM, SG_ERR_CUDA.
+ */
+sg_status sg_build_kmer_matrix(const uint8_t *d_seq, const int64_t *d_offsets, int64_t n_reads,
+                               int64_t total_len, int32_t k, uint32_t lo, uint32_t hi,
+                               sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **d_kmer_codes,
+                               sg_stream_t stream);
+
+/*
+ * C = A At over the overlap semiring (Sec. IV-D: multiply = take the positions of the k-mer in
+ * both reads; add = count the shared k-mer and keep up to max_seeds positions).
+ *   A, At      as produced by sg_build_kmer_matrix (At must be the transpose of A, rows of both
+ *              sorted by column).
+ *   min_shared entries of C with count < min_shared are dropped (>= 1).
+ *   max_seeds  0..8 seed slots per entry.
+ * Output *C as documented at sg_overlap_csr. C is symmetric in pattern and count.
+ * Errors: SG_ERR_INVALID (shape mismatch, bad scalars), SG_ERR_OOM, SG_ERR_CUDA.
+ */
+sg_status sg_overlap_spgemm(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared,
+                            int32_t max_seeds, sg_overlap_csr *C, sg_stream_t stream);
+
+/*
+ * N = R^2 over the MinPlus semiring of Algorithm 3 (add = min, multiply = R_ij + R_jk when the
+ * walk i->j->k is valid, i.e. the two heads at j point opposite ways, Sec. II and IV-E),
+ * evaluated on the pattern of R only (Algorithm 1 compares M and N only where both exist).
+ *   d_N    [R->nnz] caller-allocated; N for entry e of R, 0xFFFFFFFF when no walk qualifies.
+ *   d_Ndir [R->nnz] caller-allocated; the composite dir of the minimising walk (LITERAL), or the
+ *          entry's own dir (DIRMATCH). May be NULL.
+ * R must satisfy the sg_graph_csr contract (checked on the device; SG_ERR_INVALID otherwise).
+ */
+sg_status sg_minplus_square(const sg_graph_csr *R, int32_t mode, uint32_t *d_N, uint8_t *d_Ndir,
+                            sg_stream_t stream);
+
+/*
+ * Algorithm 1: repeat { N = R^2 (Algorithm 3); v = rowmax(R) + fuzz; I = (v_i >= N_ik, with the
+ * end-orientation rule); R = R minus I } until nnz(R) stops changing; S = R.
+ *   fuzz        < 2^30 (the scalar x of Sec. IV-E).
+ *   mode        SG_TR_DIRMATCH or SG_TR_LITERAL.
+ *   *iterations rounds run, including the last round that removed nothing.
+ * Output *S keeps the surviving entries of R with their values, in R's order.
+ * Errors: SG_ERR_INVALID (R breaks the sg_graph_csr contract, fuzz or mode out of range),
+ * SG_ERR_OOM, SG_ERR_CUDA.
+ */
+sg_status sg_transitive_reduce(const sg_graph_csr *R, uint32_t fuzz, int32_t mode, sg_graph_csr *S,
+                               int32_t *iterations, sg_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
+ * The whole path on HOST buffers: Algorithm 2 from the reads to S (KmerCounter, GenerateA,
+ * Transpose, C = A A^T, TransitiveReduction; the alignment/prune steps that turn C into R are not
+ * part of this library, so R is an input). Copies the inputs to the device, runs the three
+ * operations above, and copies C, S and the sizes back.
+ */
+typedef struct {
+    const uint8_t *seq;       /* [total_len] host, ASCII bases */
+    const int64_t *offsets;   /* [n_reads + 1] host */
+    int64_t n_reads, total_len;
+    int32_t k;                /* as sg_build_kmer_matrix */
+    uint32_t lo, hi;
+    uint32_t min_shared;      /* as sg_overlap_spgemm */
+    int32_t max_seeds;
+    const int64_t *r_row_ptr; /* host R over the same n_reads reads; NULL skips the reduction */
+    const int32_t *r_col;
+    const uint32_t *r_suffix;
+    const uint8_t *r_dir;
+    int64_t r_nnz;
+    uint32_t fuzz;            /* as sg_transitive_reduce */
+    int32_t tr_mode;
+} sg_pipeline_job;
+
+/* Host results. The arrays point into the arena passed to sg_pipeline_host and stay valid until
+ * that arena's next use or its destruction. Layouts as sg_overlap_csr (c_*) and sg_graph_csr (s_*).
+ * products = sum over k-mers j of nnz(At_j)^2, the number of semiring multiplications in A A^T. */
+typedef struct {
+    int64_t m, nnz_a, nnz_c, nnz_s;
+    int32_t iterations, max_seeds;
+    uint64_t products;
+    int64_t *c_row_ptr;
+    int32_t *c_col;
+    uint32_t *c_count, *c_seed_i, *c_seed_k;
+    int64_t *s_row_ptr;
+    int32_t *s_col;
+    uint32_t *s_suffix;
+    uint8_t *s_dir;
+} sg_pipeline_result;
+
+/* Grow-only pinned host + device staging owned by one caller (not thread-safe). */
+typedef struct sg_host_arena sg_host_arena;
+sg_status sg_host_arena_create(sg_host_arena **arena);
+void sg_host_arena_destroy(sg_host_arena *arena);
+/* Errors: as the three operations, plus SG_ERR_OOM when staging cannot grow. Synchronises. */
+sg_status sg_pipeline_host(const sg_pipeline_job *job, sg_host_arena *arena, sg_pipeline_result *out,
+                           sg_stream_t stream);
+
+/* Release outputs (stream-ordered on `stream`); the struct is zeroed. NULL-safe. */
+void sg_free_csr_u32(sg_csr_u32 *m, sg_stream_t stream);
+void sg_free_overlap(sg_overlap_csr *c, sg_stream_t stream);
+void sg_free_graph(sg_graph_csr *g, sg_stream_t stream);
+void sg_free(void *d_ptr, sg_stream_t stream);
+
+/* Description of the last non-OK status returned on this host thread. */
+const char *sg_last_error(void);
+
+/* Optional device allocator (e.g. a framework's caching allocator). alloc returns NULL on
+ * failure. Pass NULLs to restore cudaMallocAsync / cudaFreeAsync. Not thread-safe to change
+ * while calls are running. */
+typedef void *(*sg_alloc_fn)(size_t bytes, sg_stream_t stream, void *ctx);
+typedef void (*sg_free_fn)(void *ptr, sg_stream_t stream, void *ctx);
+void sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx);
+
+/* Test hook: make the n-th device allocation from now fail (n >= 1); 0 disables. */
+void sg_debug_fail_alloc_after(int64_t n);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t sg_launch_count(void);
+
+/* Per-kernel CUDA-event timing. While enabled, each kernel launch is bracketed by two events on
+ * its stream. sg_prof_collect synchronises on the recorded events and folds them into per-name
+ * totals, readable with sg_prof_entry(idx, ...) for idx < sg_prof_collect()'s return value. */
+void sg_prof_enable(int on);
+void sg_prof_reset(void);
+int sg_prof_collect(void);
+int sg_prof_entry(int idx, const char **name, int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGRAPH_H */

@@ -1,0 +1,443 @@
+"""sgraph -- GB300 (sm_103a) library for the overlap-and-layout hot path of diBELLA 2D
+(arXiv 2010.10055): the reads x k-mers matrix A, C = A A^T over the overlap semiring, and the
+transitive reduction of the bidirected overlap graph (Algorithms 1 and 3).
+
+This module is the thin Python binding of the C ABI in ``include/sgraph.h``: it marshals torch
+tensors (device memory, current stream) into the C calls and exposes the library-allocated
+outputs as zero-copy torch tensors. Every step of the computation runs in the library's CUDA
+kernels; there is no CPU path. If ``libsgraph.so`` is missing, calls raise ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgraph.so")
+
+SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_TIMEOUT, SG_ERR_BUDGET, SG_ERR_OVERFLOW = range(7)
+DIRMATCH, LITERAL = 0, 1
+INF = 0xFFFFFFFF
+
+EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",
+           "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy",
+           "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_launch_count", "sg_prof_enable",
+           "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
+
+
+class SgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sgraph status {status}: {msg}")
+        self.status = status
+
+
+class CsrU32(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class OverlapCsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("max_seeds", ctypes.c_int32),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("seed_i", ctypes.c_void_p), ("seed_k", ctypes.c_void_p)]
+
+
+class GraphCsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("suffix", ctypes.c_void_p), ("dir", ctypes.c_void_p)]
+
+
+class PipelineJob(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n_reads", ctypes.c_int64),
+                ("total_len", ctypes.c_int64), ("k", ctypes.c_int32), ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32),
+                ("min_shared", ctypes.c_uint32), ("max_seeds", ctypes.c_int32), ("r_row_ptr", ctypes.c_void_p),
+                ("r_col", ctypes.c_void_p), ("r_suffix", ctypes.c_void_p), ("r_dir", ctypes.c_void_p),
+                ("r_nnz", ctypes.c_int64), ("fuzz", ctypes.c_uint32), ("tr_mode", ctypes.c_int32)]
+
+    @staticmethod
+    def make(seq, offsets, n, total, w, r_row_ptr=None, r_col=None, r_suffix=None, r_dir=None, r_nnz=0,
+             tr_mode=0):
+        """Job from host addresses and a parameter set with k, lo, hi, min_shared, max_seeds, fuzz."""
+        return PipelineJob(seq, offsets, int(n), int(total), int(w.k), int(w.lo), int(w.hi), int(w.min_shared),
+                           int(w.max_seeds), r_row_ptr, r_col, r_suffix, r_dir, int(r_nnz), int(w.fuzz),
+                           int(tr_mode))
+
+
+class PipelineResult(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("nnz_a", ctypes.c_int64), ("nnz_c", ctypes.c_int64),
+                ("nnz_s", ctypes.c_int64), ("iterations", ctypes.c_int32), ("max_seeds", ctypes.c_int32),
+                ("products", ctypes.c_uint64), ("c_row_ptr", ctypes.c_void_p), ("c_col", ctypes.c_void_p),
+                ("c_count", ctypes.c_void_p), ("c_seed_i", ctypes.c_void_p), ("c_seed_k", ctypes.c_void_p),
+                ("s_row_ptr", ctypes.c_void_p), ("s_col", ctypes.c_void_p), ("s_suffix", ctypes.c_void_p),
+                ("s_dir", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded C library (loads it on first use; raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2010_10055_gb300.build_lib`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+        L.sg_build_kmer_matrix.restype = ctypes.c_int
+        L.sg_build_kmer_matrix.argtypes = [vp, vp, i64, i64, i32, u32, u32, ctypes.POINTER(CsrU32),
+                                           ctypes.POINTER(CsrU32), ctypes.POINTER(vp), vp]
+        L.sg_overlap_spgemm.restype = ctypes.c_int
+        L.sg_overlap_spgemm.argtypes = [ctypes.POINTER(CsrU32), ctypes.POINTER(CsrU32), u32, i32,
+                                        ctypes.POINTER(OverlapCsr), vp]
+        L.sg_minplus_square.restype = ctypes.c_int
+        L.sg_minplus_square.argtypes = [ctypes.POINTER(GraphCsr), i32, vp, vp, vp]
+        L.sg_transitive_reduce.restype = ctypes.c_int
+        L.sg_transitive_reduce.argtypes = [ctypes.POINTER(GraphCsr), u32, i32, ctypes.POINTER(GraphCsr),
+                                           ctypes.POINTER(i32), vp]
+        L.sg_free_csr_u32.argtypes = [ctypes.POINTER(CsrU32), vp]
+        L.sg_free_overlap.argtypes = [ctypes.POINTER(OverlapCsr), vp]
+        L.sg_free_graph.argtypes = [ctypes.POINTER(GraphCsr), vp]
+        L.sg_free.argtypes = [vp, vp]
+        L.sg_last_error.restype = ctypes.c_char_p
+        L.sg_debug_fail_alloc_after.argtypes = [i64]
+        L.sg_launch_count.restype = ctypes.c_uint64
+        L.sg_prof_enable.argtypes = [ctypes.c_int]
+        L.sg_prof_collect.restype = ctypes.c_int
+        L.sg_prof_entry.restype = ctypes.c_int
+        L.sg_prof_entry.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i64),
+                                    ctypes.POINTER(ctypes.c_double)]
+        L.sg_host_arena_create.restype = ctypes.c_int
+        L.sg_host_arena_create.argtypes = [ctypes.POINTER(vp)]
+        L.sg_host_arena_destroy.argtypes = [vp]
+        L.sg_pipeline_host.restype = ctypes.c_int
+        L.sg_pipeline_host.argtypes = [ctypes.POINTER(PipelineJob), vp, ctypes.POINTER(PipelineResult), vp]
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != SG_OK:
+        raise SgError(status, f"{what}: {lib().sg_last_error().decode(errors='replace')}")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class _DevView:
+    """A library-owned device array, viewable as a torch tensor without copying."""
+
+    def __init__(self, ptr, n, typestr, owner):
+        self.__cuda_array_interface__ = dict(shape=(int(n),), typestr=typestr, data=(int(ptr or 0), False),
+                                             version=3, strides=None, stream=None)
+        self.owner = owner
+
+
+# unsigned 32/64-bit arrays are exposed with the signed torch dtype of the same width
+_TS = {"i8": "<i8", "i4": "<i4", "u4": "<i4", "u1": "|u1", "u8": "<i8"}
+_NP = {"i8": np.int64, "i4": np.int32, "u4": np.uint32, "u1": np.uint8, "u8": np.uint64}
+
+
+def _view(ptr, n, kind, owner):
+    import torch
+    if n == 0:
+        dt = {"i8": torch.int64, "i4": torch.int32, "u4": torch.int32, "u1": torch.uint8, "u8": torch.int64}[kind]
+        return torch.empty(0, dtype=dt, device="cuda")
+    return torch.as_tensor(_DevView(ptr, n, _TS[kind], owner), device="cuda")
+
+
+def _host(t, kind):
+    return t.cpu().numpy().view(_NP[kind])
+
+
+class _Owned:
+    """Owns one output struct; frees it (stream-ordered) when released or collected."""
+    _free_name = ""
+
+    def __init__(self, struct, stream):
+        self.s = struct
+        self._stream = stream
+        self._alive = True
+
+    def free(self):
+        if self._alive and _lib is not None:
+            getattr(_lib, self._free_name)(ctypes.byref(self.s), self._stream)
+        self._alive = False
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class CsrMatrix(_Owned):
+    """A or At (CSR, 32-bit values pos | strand << 31)."""
+    _free_name = "sg_free_csr_u32"
+
+    @property
+    def shape(self):
+        return (int(self.s.n_rows), int(self.s.n_cols))
+
+    @property
+    def nnz(self):
+        return int(self.s.nnz)
+
+    KINDS = dict(row_ptr="i8", col="i4", val="u4")
+
+    def tensors(self):
+        return dict(row_ptr=_view(self.s.row_ptr, self.s.n_rows + 1, "i8", self),
+                    col=_view(self.s.col, self.s.nnz, "i4", self),
+                    val=_view(self.s.val, self.s.nnz, "u4", self))
+
+    def to_numpy(self):
+        d = {k: _host(v, self.KINDS[k]) for k, v in self.tensors().items()}
+        d["n_rows"], d["n_cols"] = self.shape
+        return d
+
+
+class KmerMatrix:
+    """Result of build_kmer_matrix: A, At and the canonical code of every column."""
+
+    def __init__(self, A: CsrMatrix, At: CsrMatrix, codes_ptr, m, stream):
+        self.A, self.At = A, At
+        self._codes = codes_ptr
+        self.m = m
+        self._stream = stream
+
+    def codes(self):
+        """Column codes (uint64 bit patterns in an int64 tensor)."""
+        return _view(self._codes, self.m, "u8", self)
+
+    def free(self):
+        self.A.free()
+        self.At.free()
+        if self._codes and _lib is not None:
+            _lib.sg_free(self._codes, self._stream)
+        self._codes = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def to_numpy(self):
+        return dict(A=self.A.to_numpy(), At=self.At.to_numpy(), codes=_host(self.codes(), "u8"))
+
+
+class Overlap(_Owned):
+    """C = A At over the overlap semiring."""
+    _free_name = "sg_free_overlap"
+
+    @property
+    def nnz(self):
+        return int(self.s.nnz)
+
+    KINDS = dict(row_ptr="i8", col="i4", count="u4", seed_i="u4", seed_k="u4")
+
+    def tensors(self):
+        S, nnz = int(self.s.max_seeds), int(self.s.nnz)
+        return dict(row_ptr=_view(self.s.row_ptr, self.s.n + 1, "i8", self),
+                    col=_view(self.s.col, nnz, "i4", self),
+                    count=_view(self.s.count, nnz, "u4", self),
+                    seed_i=_view(self.s.seed_i, S * nnz, "u4", self).view(S, nnz),
+                    seed_k=_view(self.s.seed_k, S * nnz, "u4", self).view(S, nnz))
+
+    def to_numpy(self):
+        d = {k: _host(v, self.KINDS[k]) for k, v in self.tensors().items()}
+        d["n"] = int(self.s.n)
+        return d
+
+
+class Graph(_Owned):
+    """A bidirected overlap / string graph in CSR (suffix uint32, dir uint8)."""
+    _free_name = "sg_free_graph"
+
+    @property
+    def nnz(self):
+        return int(self.s.nnz)
+
+    KINDS = dict(row_ptr="i8", col="i4", suffix="u4", dir="u1")
+
+    def tensors(self):
+        nnz = int(self.s.nnz)
+        return dict(row_ptr=_view(self.s.row_ptr, self.s.n + 1, "i8", self),
+                    col=_view(self.s.col, nnz, "i4", self),
+                    suffix=_view(self.s.suffix, nnz, "u4", self),
+                    dir=_view(self.s.dir, nnz, "u1", self))
+
+    def to_numpy(self):
+        d = {k: _host(v, self.KINDS[k]) for k, v in self.tensors().items()}
+        d["n"] = int(self.s.n)
+        return d
+
+
+# ------------------------------------------------------------------------------- calls
+def build_kmer_matrix(seq, offsets, k: int = 17, lo: int = 2, hi: int = 8, stream=None) -> KmerMatrix:
+    """Reads -> A, At (see sg_build_kmer_matrix). seq: uint8 CUDA tensor of ASCII bases;
+    offsets: int64 CUDA tensor [n+1]."""
+    L = lib()
+    st = _stream(stream)
+    A, At, codes = CsrU32(), CsrU32(), ctypes.c_void_p()
+    n = int(offsets.numel()) - 1
+    rc = L.sg_build_kmer_matrix(_ptr(seq), _ptr(offsets), n, int(seq.numel()), int(k), int(lo), int(hi),
+                                ctypes.byref(A), ctypes.byref(At), ctypes.byref(codes), st)
+    _check(rc, "build_kmer_matrix")
+    a, at = CsrMatrix(A, st), CsrMatrix(At, st)
+    return KmerMatrix(a, at, codes.value, int(A.n_cols), st)
+
+
+def overlap_spgemm(km: KmerMatrix, min_shared: int = 2, max_seeds: int = 2, stream=None) -> Overlap:
+    """C = A At over the overlap semiring (see sg_overlap_spgemm)."""
+    L = lib()
+    st = _stream(stream)
+    C = OverlapCsr()
+    _check(L.sg_overlap_spgemm(ctypes.byref(km.A.s), ctypes.byref(km.At.s), int(min_shared), int(max_seeds),
+                               ctypes.byref(C), st), "overlap_spgemm")
+    return Overlap(C, st)
+
+
+class DeviceGraph:
+    """A caller-owned graph (torch tensors) to pass as R."""
+
+    def __init__(self, n, row_ptr, col, suffix, dir):
+        self.n, self.row_ptr, self.col, self.suffix, self.dir = int(n), row_ptr, col, suffix, dir
+        self.s = GraphCsr(self.n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr() if col.numel() else 0,
+                          suffix.data_ptr() if suffix.numel() else 0, dir.data_ptr() if dir.numel() else 0)
+
+    @property
+    def nnz(self):
+        return int(self.col.numel())
+
+    @staticmethod
+    def from_numpy(R: dict, device="cuda") -> "DeviceGraph":
+        import torch
+        return DeviceGraph(R["n"], torch.from_numpy(np.ascontiguousarray(R["row_ptr"], np.int64)).to(device),
+                           torch.from_numpy(np.ascontiguousarray(R["col"], np.int32)).to(device),
+                           torch.from_numpy(np.ascontiguousarray(R["suffix"], np.uint32).view(np.int32)).to(device),
+                           torch.from_numpy(np.ascontiguousarray(R["dir"], np.uint8)).to(device))
+
+
+def _graph_struct(R):
+    if isinstance(R, (DeviceGraph, Graph)):
+        return R.s
+    raise TypeError("R must be a DeviceGraph or a Graph returned by this library")
+
+
+def transitive_reduce(R, fuzz: int = 0, mode: int = DIRMATCH, stream=None):
+    """Algorithm 1: returns (S as Graph, iterations)."""
+    L = lib()
+    st = _stream(stream)
+    S, it = GraphCsr(), ctypes.c_int32()
+    _check(L.sg_transitive_reduce(ctypes.byref(_graph_struct(R)), int(fuzz), int(mode), ctypes.byref(S),
+                                  ctypes.byref(it), st), "transitive_reduce")
+    return Graph(S, st), int(it.value)
+
+
+def minplus_square(R, mode: int = DIRMATCH, stream=None):
+    """N = R^2 over Algorithm 3's semiring on the pattern of R: (N, Ndir) CUDA tensors; N holds
+    uint32 bit patterns in an int32 tensor (0xFFFFFFFF = no qualifying walk)."""
+    import torch
+    L = lib()
+    st = _stream(stream)
+    s = _graph_struct(R)
+    N = torch.empty(max(int(s.nnz), 1), dtype=torch.int32, device="cuda")  # uint32 bit patterns
+    D = torch.empty(max(int(s.nnz), 1), dtype=torch.uint8, device="cuda")
+    _check(L.sg_minplus_square(ctypes.byref(s), int(mode), _ptr(N), _ptr(D), st), "minplus_square")
+    return N[: int(s.nnz)], D[: int(s.nnz)]
+
+
+# ----------------------------------------------------------------------------- tooling
+def launch_count() -> int:
+    return int(lib().sg_launch_count())
+
+
+def prof_enable(on: bool = True):
+    lib().sg_prof_enable(1 if on else 0)
+
+
+def prof_reset():
+    lib().sg_prof_reset()
+
+
+def prof_collect() -> dict:
+    """{kernel name: (launches, total ms)} for the launches recorded since the last reset."""
+    L = lib()
+    n = L.sg_prof_collect()
+    out = {}
+    for i in range(n):
+        name, cnt, ms = ctypes.c_char_p(), ctypes.c_int64(), ctypes.c_double()
+        if L.sg_prof_entry(i, ctypes.byref(name), ctypes.byref(cnt), ctypes.byref(ms)):
+            out[name.value.decode()] = (int(cnt.value), float(ms.value))
+    return out
+
+
+def debug_fail_alloc_after(n: int):
+    lib().sg_debug_fail_alloc_after(int(n))
+
+
+# ------------------------------------------------------------------ host-buffer pipeline
+class HostPipeline:
+    """The whole path on host (numpy) buffers through sg_pipeline_host, with its own arena."""
+
+    def __init__(self):
+        self.arena = ctypes.c_void_p()
+        _check(lib().sg_host_arena_create(ctypes.byref(self.arena)), "host_arena_create")
+
+    def close(self):
+        if self.arena and _lib is not None:
+            _lib.sg_host_arena_destroy(self.arena)
+        self.arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, seq, offsets, params, R=None, tr_mode=DIRMATCH, stream=None) -> dict:
+        """Returns numpy copies of C, S and the sizes. `params` has k, lo, hi, min_shared,
+        max_seeds and fuzz attributes."""
+        seq = np.ascontiguousarray(seq, np.uint8)
+        offsets = np.ascontiguousarray(offsets, np.int64)
+        keep = [seq, offsets]
+        rargs = (None, None, None, None, 0)
+        if R is not None:
+            rr = (np.ascontiguousarray(R["row_ptr"], np.int64), np.ascontiguousarray(R["col"], np.int32),
+                  np.ascontiguousarray(R["suffix"], np.uint32), np.ascontiguousarray(R["dir"], np.uint8))
+            keep += list(rr)
+            rargs = tuple(a.ctypes.data for a in rr) + (int(rr[1].size),)
+        job = PipelineJob.make(seq.ctypes.data if seq.size else None, offsets.ctypes.data, offsets.size - 1,
+                               seq.size, params, *rargs, tr_mode=tr_mode)
+        res = PipelineResult()
+        _check(lib().sg_pipeline_host(ctypes.byref(job), self.arena, ctypes.byref(res), _stream(stream)),
+               "pipeline_host")
+        n = offsets.size - 1
+
+        def arr(ptr, count, dtype):
+            if count == 0 or not ptr:
+                return np.zeros(0, dtype)
+            return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(np.ctypeslib.as_ctypes_type(dtype))),
+                                         shape=(count,)).copy()
+
+        S_ = int(res.max_seeds)
+        out = dict(m=int(res.m), nnz_a=int(res.nnz_a), products=int(res.products), iterations=int(res.iterations),
+                   C=dict(n=n, row_ptr=arr(res.c_row_ptr, n + 1, np.int64), col=arr(res.c_col, res.nnz_c, np.int32),
+                          count=arr(res.c_count, res.nnz_c, np.uint32),
+                          seed_i=arr(res.c_seed_i, res.nnz_c * S_, np.uint32).reshape(S_, -1),
+                          seed_k=arr(res.c_seed_k, res.nnz_c * S_, np.uint32).reshape(S_, -1)))
+        if R is not None:
+            out["S"] = dict(n=n, row_ptr=arr(res.s_row_ptr, n + 1, np.int64), col=arr(res.s_col, res.nnz_s, np.int32),
+                            suffix=arr(res.s_suffix, res.nnz_s, np.uint32), dir=arr(res.s_dir, res.nnz_s, np.uint8))
+        return out

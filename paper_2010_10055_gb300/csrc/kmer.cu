@@ -1,0 +1,415 @@
+// kmer.cu -- reads -> A (reads x reliable k-mers) and At, on the GPU.
+//
+// Sec. II: a k-mer's canonical form is the smaller of its code and its reverse complement's.
+// Sec. IV-C: k-mers are counted in two phases -- a Bloom filter sees every k-mer, and only
+// k-mers it has already seen go on to be counted exactly -- and a k-mer is kept when its
+// frequency lies in the reliable range [lo, hi].
+// Sec. IV-D: A_ij holds the position of k-mer j in read i (here: pos | strand << 31 at the
+// lowest such position).
+//
+// Pipeline (all on `stream`):
+//  1. bloom_insert   every window's canonical code is OR-ed into the blocked Bloom filter B1
+//                    (all probe bits in one 64-bit word, so "already present" is decided by one
+//                    atomic); a code found present is OR-ed into B2 ("seen at least twice").
+//  2. cand_count     per thread, the windows whose code tests positive in B2. Every occurrence
+//                    of a k-mer with frequency >= 2 passes (false positives only add singletons,
+//                    which the exact count below drops). Skipped when lo == 1.
+//  3. cand_emit      writes (code, read << 32 | pos | strand << 31) at scanned offsets, so the
+//                    candidates stay in (read, pos) order.
+//  4. radix sort by code (stable, 2k bits): equal codes form segments in (read, pos) order.
+//  5. segments -> exact frequency (segment length) -> reliable flag -> column = rank of the
+//     reliable code; within a reliable segment the first entry of each read is its lowest
+//     position: those entries are At's row, already sorted by read.
+//  6. A = At transposed by a stable radix sort on the read id (columns stay ascending).
+#include "prim.cuh"
+
+namespace sg {
+
+constexpr int KM_NT = 256;
+constexpr int KM_W = 32;                  // windows per thread
+constexpr int KM_CHUNK = KM_NT * KM_W;    // windows per block
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {  // murmur3 fmix64
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33;
+    return x;
+}
+
+struct Bloom {
+    unsigned long long *words;
+    uint64_t nwords;  // < 2^32
+    uint64_t seed;
+    __device__ __forceinline__ void probe(uint64_t code, uint64_t *idx, unsigned long long *mask) const {
+        uint64_t h = mix64(code ^ seed);
+        *idx = ((h >> 32) * nwords) >> 32;
+        *mask = (1ull << (h & 63)) | (1ull << ((h >> 6) & 63)) | (1ull << ((h >> 12) & 63)) |
+                (1ull << ((h >> 18) & 63));
+    }
+};
+
+// Visits the windows [c0 + t*KM_W, c0 + (t+1)*KM_W) of thread t in position order, calling
+// f(code, strand, read, pos) for each window of k A/C/G/T bases inside one read.
+template <class F>
+__device__ __forceinline__ void for_each_window(const uint8_t *__restrict__ sm, int64_t c0, int64_t total,
+                                                const int64_t *__restrict__ off, int64_t n, int k,
+                                                F &&f) {
+    const int64_t qs = c0 + (int64_t)threadIdx.x * KM_W;
+    if (qs >= total) return;
+    int64_t qe = qs + KM_W + k - 1;  // exclusive
+    if (qe > total) qe = total;
+    // read containing qs: last r with off[r] <= qs
+    int64_t lo = 0, hi = n;  // invariant: off[lo] <= qs < off[hi] (off[n] = total > qs)
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= qs) lo = mid; else hi = mid;
+    }
+    int64_t r = lo, next = off[r + 1];
+    const uint64_t mask = (k == 32) ? ~0ull : ((1ull << (2 * k)) - 1);
+    const int rs = 2 * (k - 1);
+    uint64_t fw = 0, rc = 0;
+    int run = 0;
+    for (int64_t q = qs; q < qe; q++) {
+        while (q >= next) {  // crossed into the next read (skips empty reads)
+            r++;
+            next = off[r + 1];
+            run = 0;
+        }
+        uint8_t c = sm[q - c0];
+        bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
+        uint32_t t = (c >> 1) & 3u;
+        uint32_t b = t ^ (t >> 1);  // A=0 C=1 G=2 T=3
+        fw = ((fw << 2) | b) & mask;
+        rc = (rc >> 2) | ((uint64_t)(3u - b) << rs);
+        run = ok ? run + 1 : 0;
+        if (run >= k && q - k + 1 >= qs) {
+            uint64_t code = fw < rc ? fw : rc;
+            uint32_t strand = rc < fw ? 1u : 0u;
+            f(code, strand, r, (uint32_t)(q - k + 1 - off[r]));
+        }
+    }
+}
+
+__device__ __forceinline__ void load_chunk(uint8_t *sm, const uint8_t *__restrict__ seq, int64_t c0,
+                                           int64_t total, int k) {
+    int64_t len = (int64_t)KM_CHUNK + k - 1;
+    if (c0 + len > total) len = total - c0;
+    for (int64_t i = threadIdx.x; i < len; i += KM_NT) sm[i] = seq[c0 + i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint8_t *__restrict__ seq, int64_t total,
+                                                            const int64_t *__restrict__ off, int64_t n, int k,
+                                                            Bloom b1, Bloom b2) {
+    __shared__ uint8_t sm[KM_CHUNK + 32];
+    int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
+    load_chunk(sm, seq, c0, total, k);
+    for_each_window(sm, c0, total, off, n, k, [&](uint64_t code, uint32_t, int64_t, uint32_t) {
+        uint64_t i1;
+        unsigned long long m1;
+        b1.probe(code, &i1, &m1);
+        unsigned long long old = atomicOr(b1.words + i1, m1);
+        if ((old & m1) == m1) {
+            uint64_t i2;
+            unsigned long long m2;
+            b2.probe(code, &i2, &m2);
+            if ((b2.words[i2] & m2) != m2) atomicOr(b2.words + i2, m2);
+        }
+    });
+}
+
+// use_bloom == 0 keeps every window (lo == 1: singletons may be reliable).
+__global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint8_t *__restrict__ seq, int64_t total,
+                                                          const int64_t *__restrict__ off, int64_t n, int k,
+                                                          Bloom b2, int use_bloom, uint32_t *__restrict__ cnt) {
+    __shared__ uint8_t sm[KM_CHUNK + 32];
+    int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
+    load_chunk(sm, seq, c0, total, k);
+    uint32_t c = 0;
+    for_each_window(sm, c0, total, off, n, k, [&](uint64_t code, uint32_t, int64_t, uint32_t) {
+        if (use_bloom) {
+            uint64_t i2;
+            unsigned long long m2;
+            b2.probe(code, &i2, &m2);
+            if ((b2.words[i2] & m2) != m2) return;
+        }
+        c++;
+    });
+    cnt[(int64_t)blockIdx.x * KM_NT + threadIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint8_t *__restrict__ seq, int64_t total,
+                                                         const int64_t *__restrict__ off, int64_t n, int k,
+                                                         Bloom b2, int use_bloom,
+                                                         const int64_t *__restrict__ pos_of_thread,
+                                                         uint64_t *__restrict__ keys, uint64_t *__restrict__ vals) {
+    __shared__ uint8_t sm[KM_CHUNK + 32];
+    int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
+    load_chunk(sm, seq, c0, total, k);
+    int64_t w = pos_of_thread[(int64_t)blockIdx.x * KM_NT + threadIdx.x];
+    for_each_window(sm, c0, total, off, n, k, [&](uint64_t code, uint32_t strand, int64_t r, uint32_t pos) {
+        if (use_bloom) {
+            uint64_t i2;
+            unsigned long long m2;
+            b2.probe(code, &i2, &m2);
+            if ((b2.words[i2] & m2) != m2) return;
+        }
+        keys[w] = code;
+        vals[w] = ((uint64_t)r << 32) | pos | (strand << 31);
+        w++;
+    });
+}
+
+__global__ void validate_offsets_kernel(const int64_t *__restrict__ off, int64_t n, int64_t total,
+                                        uint32_t *__restrict__ err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    int64_t a = off[i];
+    bool bad = false;
+    if (i == 0 && a != 0) bad = true;
+    if (i == n && a != total) bad = true;
+    if (i < n) {
+        int64_t b = off[i + 1];
+        if (b < a || b - a >= ((int64_t)1 << 31)) bad = true;
+    }
+    if (bad) atomicOr(err, (uint32_t)DEV_INVALID);
+}
+
+// head[i] = 1 where a new code starts.
+__global__ void seg_head_kernel(const uint64_t *__restrict__ key, int64_t nc, uint32_t *__restrict__ head) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) head[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+}
+
+// seg_start[s] = first index of segment s; seg_start[nseg] = nc.
+__global__ void seg_start_kernel(const uint32_t *__restrict__ head, const int64_t *__restrict__ seg_excl,
+                                 int64_t nc, int64_t *__restrict__ seg_start) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc && head[i]) seg_start[seg_excl[i]] = i;
+    if (i == nc - 1) seg_start[seg_excl[nc]] = nc;
+}
+
+__global__ void seg_reliable_kernel(const int64_t *__restrict__ seg_start, const int64_t *__restrict__ nseg_p,
+                                    uint32_t lo, uint32_t hi, uint32_t *__restrict__ rel) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nseg = *nseg_p;
+    if (s >= nseg) {  // slots past the last segment still feed the scan below: make them 0
+        rel[s] = 0u;
+        return;
+    }
+    int64_t len = seg_start[s + 1] - seg_start[s];
+    rel[s] = (len >= (int64_t)lo && len <= (int64_t)hi) ? 1u : 0u;
+}
+
+// keep[i]: i lies in a reliable segment and is the first (lowest position) entry of its read.
+__global__ void keep_kernel(const uint32_t *__restrict__ head, const int64_t *__restrict__ seg_excl,
+                            const uint32_t *__restrict__ rel, const uint64_t *__restrict__ val, int64_t nc,
+                            uint32_t *__restrict__ keep) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    int64_t s = seg_excl[i] + head[i] - 1;
+    bool first = head[i] || ((val[i] >> 32) != (val[i - 1] >> 32));
+    keep[i] = (rel[s] && first) ? 1u : 0u;
+}
+
+// Writes At's entries, its row pointers, the column codes, and the (read, col|val) pairs that
+// are sorted into A.
+__global__ void emit_at_kernel(const uint32_t *__restrict__ head, const int64_t *__restrict__ seg_excl,
+                               const uint32_t *__restrict__ rel, const int64_t *__restrict__ col_of_seg,
+                               const uint32_t *__restrict__ keep, const int64_t *__restrict__ out_pos,
+                               const uint64_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t nc,
+                               int64_t m, int64_t nnz, int32_t *__restrict__ at_col, uint32_t *__restrict__ at_val,
+                               int64_t *__restrict__ at_rp, uint64_t *__restrict__ codes,
+                               uint32_t *__restrict__ a_key, uint64_t *__restrict__ a_val) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) at_rp[m] = nnz;
+    if (i >= nc) return;
+    int64_t s = seg_excl[i] + head[i] - 1;
+    if (head[i] && rel[s]) {
+        int64_t j = col_of_seg[s];
+        at_rp[j] = out_pos[i];
+        codes[j] = key[i];
+    }
+    if (keep[i]) {
+        int64_t o = out_pos[i];
+        uint32_t r = (uint32_t)(val[i] >> 32), v = (uint32_t)val[i];
+        at_col[o] = (int32_t)r;
+        at_val[o] = v;
+        a_key[o] = r;
+        a_val[o] = ((uint64_t)col_of_seg[s] << 32) | v;
+    }
+}
+
+// Row pointers of A from the read ids of its entries, sorted ascending.
+__global__ void rowptr_from_sorted_kernel(const uint32_t *__restrict__ rows, int64_t nnz, int64_t n,
+                                          int64_t *__restrict__ rp) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > nnz) return;
+    int64_t prev = (e == 0) ? -1 : (int64_t)rows[e - 1];
+    int64_t cur = (e == nnz) ? n : (int64_t)rows[e];
+    for (int64_t r = prev + 1; r <= cur; r++) rp[r] = e;
+}
+
+__global__ void split_pairs_kernel(const uint64_t *__restrict__ pv, int64_t nnz, int32_t *__restrict__ col,
+                                   uint32_t *__restrict__ val) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    uint64_t x = pv[e];
+    col[e] = (int32_t)(x >> 32);
+    val[e] = (uint32_t)x;
+}
+
+static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
+
+static sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t total, int k,
+                            uint32_t lo, uint32_t hi, sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **codes_out,
+                            cudaStream_t s, Scratch &sc) {
+    const int NT = 256;
+    uint32_t *err = sc.get<uint32_t>(1);
+    if (!err) return SG_ERR_OOM;
+    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    SG_LAUNCH("validate_offsets", validate_offsets_kernel, blocks_for(n + 1, NT), NT, 0, s, off, n, total, err);
+
+    const int64_t nblk = blocks_for(total, KM_CHUNK);
+    const int use_bloom = lo >= 2 ? 1 : 0;
+    Bloom b1{nullptr, 0, 0x9e3779b97f4a7c15ULL}, b2{nullptr, 0, 0xc2b2ae3d27d4eb4fULL};
+    if (use_bloom && total > 0) {
+        // B1: 8 bits per window; B2 ("seen twice"): 2 bits per window.
+        b1.nwords = (uint64_t)(total / 8) + 1024;
+        b2.nwords = (uint64_t)(total / 32) + 1024;
+        if (b1.nwords >= (1ull << 32)) b1.nwords = (1ull << 32) - 1;
+        if (b2.nwords >= (1ull << 32)) b2.nwords = (1ull << 32) - 1;
+        b1.words = sc.get<unsigned long long>(b1.nwords);
+        b2.words = sc.get<unsigned long long>(b2.nwords);
+        if (!b1.words || !b2.words) return SG_ERR_OOM;
+        SG_CUDA_TRY(cudaMemsetAsync(b1.words, 0, b1.nwords * 8, s));
+        SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, b2.nwords * 8, s));
+    }
+    // offsets are validated before any kernel that walks them
+    uint32_t herr = 0;
+    SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));
+    if (herr) {
+        set_error("build_kmer_matrix: offsets are not a valid partition of the sequence");
+        return SG_ERR_INVALID;
+    }
+    if (use_bloom)
+        SG_LAUNCH("bloom_insert", bloom_insert_kernel, nblk, KM_NT, 0, s, seq, total, off, n, k, b1, b2);
+    uint32_t *tcnt = sc.get<uint32_t>(nblk * KM_NT + 1);
+    int64_t *tpos = sc.get<int64_t>(nblk * KM_NT + 1);
+    if (!tcnt || !tpos) return SG_ERR_OOM;
+    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, seq, total, off, n, k, b2, use_bloom, tcnt);
+    SG_TRY(exclusive_scan<uint32_t>(tcnt, tpos, nblk * KM_NT, s));
+    int64_t nc = 0;
+    SG_CUDA_TRY(read_back(&nc, tpos + nblk * KM_NT, sizeof(int64_t), s));
+
+    uint64_t *key0 = sc.get<uint64_t>(nc), *val0 = sc.get<uint64_t>(nc);
+    uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
+    if (!key0 || !val0 || !key1 || !val1) return SG_ERR_OOM;
+    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, seq, total, off, n, k, b2, use_bloom,
+              (const int64_t *)tpos, key0, val0);
+    bool alt = false;
+    SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, 2 * k, &alt, s)));
+    const uint64_t *key = alt ? key1 : key0;
+    const uint64_t *val = alt ? val1 : val0;
+
+    uint32_t *head = sc.get<uint32_t>(nc + 1);
+    int64_t *seg_excl = sc.get<int64_t>(nc + 1);
+    int64_t *seg_start = sc.get<int64_t>(nc + 1);
+    uint32_t *rel = sc.get<uint32_t>(nc + 1);
+    int64_t *col_of_seg = sc.get<int64_t>(nc + 1);
+    uint32_t *keep = sc.get<uint32_t>(nc + 1);
+    int64_t *out_pos = sc.get<int64_t>(nc + 1);
+    if (!head || !seg_excl || !seg_start || !rel || !col_of_seg || !keep || !out_pos) return SG_ERR_OOM;
+    SG_LAUNCH("seg_head", seg_head_kernel, blocks_for(nc, NT), NT, 0, s, key, nc, head);
+    SG_TRY(exclusive_scan<uint32_t>(head, seg_excl, nc, s));
+    SG_LAUNCH("seg_start", seg_start_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, nc, seg_start);
+    // number of segments lives on the device at seg_excl[nc]; launch over the upper bound nc
+    SG_LAUNCH("seg_reliable", seg_reliable_kernel, blocks_for(nc, NT), NT, 0, s, seg_start, seg_excl + nc, lo,
+              hi, rel);
+    SG_TRY(exclusive_scan<uint32_t>(rel, col_of_seg, nc, s));
+    SG_LAUNCH("keep", keep_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, rel, val, nc, keep);
+    SG_TRY(exclusive_scan<uint32_t>(keep, out_pos, nc, s));
+    int64_t sizes[2] = {0, 0};  // m, nnz
+    // m = reliable segments = col_of_seg[nc] (rel is 0 past the last segment)
+    SG_CUDA_TRY(cudaMemcpyAsync(&sizes[0], col_of_seg + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaMemcpyAsync(&sizes[1], out_pos + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t m = sizes[0], nnz = sizes[1];
+    if (m >= ((int64_t)1 << 31)) {
+        set_error("build_kmer_matrix: %lld reliable k-mers exceed the int32 column range", (long long)m);
+        return SG_ERR_OVERFLOW;
+    }
+
+    // outputs
+    SG_ALLOC(At->row_ptr, int64_t, m + 1, s);
+    SG_ALLOC(At->col, int32_t, nnz, s);
+    SG_ALLOC(At->val, uint32_t, nnz, s);
+    SG_ALLOC(A->row_ptr, int64_t, n + 1, s);
+    SG_ALLOC(A->col, int32_t, nnz, s);
+    SG_ALLOC(A->val, uint32_t, nnz, s);
+    SG_ALLOC(*codes_out, uint64_t, m, s);
+    At->n_rows = m; At->n_cols = n; At->nnz = nnz;
+    A->n_rows = n; A->n_cols = m; A->nnz = nnz;
+
+    uint32_t *ak0 = sc.get<uint32_t>(nnz), *ak1 = sc.get<uint32_t>(nnz);
+    uint64_t *av0 = sc.get<uint64_t>(nnz), *av1 = sc.get<uint64_t>(nnz);
+    if (!ak0 || !ak1 || !av0 || !av1) return SG_ERR_OOM;
+    SG_LAUNCH("emit_at", emit_at_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, head, seg_excl, rel, col_of_seg,
+              keep, out_pos, key, val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0, av0);
+    int rbits = 0;
+    while (rbits < 32 && ((int64_t)1 << rbits) < n) rbits++;
+    bool aalt = false;
+    SG_TRY((radix_sort_pairs<uint32_t, uint64_t>(ak0, av0, ak1, av1, nnz, rbits, &aalt, s)));
+    const uint32_t *arow = aalt ? ak1 : ak0;
+    const uint64_t *apv = aalt ? av1 : av0;
+    SG_LAUNCH("rowptr_from_sorted", rowptr_from_sorted_kernel, blocks_for(nnz + 1, NT), NT, 0, s, arow, nnz, n,
+              A->row_ptr);
+    SG_LAUNCH("split_pairs", split_pairs_kernel, blocks_for(nnz, NT), NT, 0, s, apv, nnz, A->col, A->val);
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    return SG_OK;
+}
+
+}  // namespace sg
+
+extern "C" sg_status sg_build_kmer_matrix(const uint8_t *d_seq, const int64_t *d_offsets, int64_t n_reads,
+                                          int64_t total_len, int32_t k, uint32_t lo, uint32_t hi,
+                                          sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **d_kmer_codes,
+                                          sg_stream_t stream) {
+    if (!A || !At || !d_kmer_codes) {
+        sg::set_error("build_kmer_matrix: NULL output struct");
+        return SG_ERR_INVALID;
+    }
+    *A = sg_csr_u32{};
+    *At = sg_csr_u32{};
+    *d_kmer_codes = nullptr;
+    if (k < 1 || k > 31 || (k & 1) == 0 || lo < 1 || lo > hi || n_reads < 0 || n_reads >= ((int64_t)1 << 31) ||
+        total_len < 0 || !d_offsets || (total_len > 0 && !d_seq)) {
+        sg::set_error("build_kmer_matrix: invalid arguments (k=%d lo=%u hi=%u n=%lld total=%lld)", k, lo, hi,
+                      (long long)n_reads, (long long)total_len);
+        return SG_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sg_status st;
+    {
+        sg::Scratch sc(s);
+        st = sg::build_impl(d_seq, d_offsets, n_reads, total_len, k, lo, hi, A, At, d_kmer_codes, s, sc);
+    }
+    if (st != SG_OK) {
+        sg_free_csr_u32(A, stream);
+        sg_free_csr_u32(At, stream);
+        sg::dfree(*d_kmer_codes, s);
+        *d_kmer_codes = nullptr;
+    }
+    return st;
+}
+
+extern "C" void sg_free_csr_u32(sg_csr_u32 *m, sg_stream_t stream) {
+    if (!m) return;
+    cudaStream_t s = (cudaStream_t)stream;
+    sg::dfree(m->row_ptr, s);
+    sg::dfree(m->col, s);
+    sg::dfree(m->val, s);
+    *m = sg_csr_u32{};
+}

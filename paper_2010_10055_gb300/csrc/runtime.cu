@@ -1,0 +1,167 @@
+// runtime.cu -- error strings, allocation, launch counting and per-kernel event timing.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sg {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static sg_alloc_fn g_alloc = nullptr;
+static sg_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+static std::atomic<int64_t> g_fail_after{0};
+
+void *dalloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    int64_t f = g_fail_after.load();
+    if (f > 0) {
+        if (g_fail_after.fetch_sub(1) == 1) {
+            set_error("device allocation of %zu bytes failed (injected)", bytes);
+            return nullptr;
+        }
+    }
+    void *p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, (sg_stream_t)s, g_alloc_ctx);
+        if (!p) set_error("device allocation of %zu bytes failed (user allocator)", bytes);
+        return p;
+    }
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(void *p, cudaStream_t s) {
+    if (!p) return;
+    if (g_free) {
+        g_free(p, (sg_stream_t)s, g_alloc_ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+cudaError_t read_back(void *host, const void *dev, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+// ---------------------------------------------------------------- launch accounting
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_prof_on{0};
+struct PendingEvent { std::string name; cudaEvent_t a, b; };
+static std::mutex g_prof_mu;
+static std::vector<PendingEvent> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+struct ProfTotal { int64_t launches = 0; double ms = 0.0; };
+static std::map<std::string, ProfTotal> g_totals;
+static std::vector<std::pair<std::string, ProfTotal>> g_snapshot;
+
+static cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+LaunchScope::LaunchScope(const char *n, cudaStream_t s) : name(n), stream(s), slot(-1) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_prof_on.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        PendingEvent pe{name, take_event(), take_event()};
+        cudaEventRecord(pe.a, s);
+        g_pending.push_back(pe);
+        slot = (int)g_pending.size() - 1;
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (slot >= 0) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        cudaEventRecord(g_pending[slot].b, stream);
+    }
+}
+
+}  // namespace sg
+
+extern "C" {
+
+const char *sg_last_error(void) { return sg::g_err; }
+
+void sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx) {
+    sg::g_alloc = alloc;
+    sg::g_free = release;
+    sg::g_alloc_ctx = ctx;
+}
+
+void sg_debug_fail_alloc_after(int64_t n) { sg::g_fail_after.store(n > 0 ? n : 0); }
+
+void sg_free(void *d_ptr, sg_stream_t stream) { sg::dfree(d_ptr, (cudaStream_t)stream); }
+
+uint64_t sg_launch_count(void) { return sg::g_launches.load(); }
+
+void sg_prof_enable(int on) { sg::g_prof_on.store(on ? 1 : 0); }
+
+void sg_prof_reset(void) {
+    std::lock_guard<std::mutex> lk(sg::g_prof_mu);
+    for (auto &p : sg::g_pending) {
+        sg::g_event_pool.push_back(p.a);
+        sg::g_event_pool.push_back(p.b);
+    }
+    sg::g_pending.clear();
+    sg::g_totals.clear();
+    sg::g_snapshot.clear();
+}
+
+int sg_prof_collect(void) {
+    std::lock_guard<std::mutex> lk(sg::g_prof_mu);
+    for (auto &p : sg::g_pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto &t = sg::g_totals[p.name];
+            t.launches += 1;
+            t.ms += ms;
+        }
+        sg::g_event_pool.push_back(p.a);
+        sg::g_event_pool.push_back(p.b);
+    }
+    sg::g_pending.clear();
+    sg::g_snapshot.assign(sg::g_totals.begin(), sg::g_totals.end());
+    return (int)sg::g_snapshot.size();
+}
+
+int sg_prof_entry(int idx, const char **name, int64_t *launches, double *total_ms) {
+    std::lock_guard<std::mutex> lk(sg::g_prof_mu);
+    if (idx < 0 || idx >= (int)sg::g_snapshot.size()) return 0;
+    *name = sg::g_snapshot[idx].first.c_str();
+    *launches = sg::g_snapshot[idx].second.launches;
+    *total_ms = sg::g_snapshot[idx].second.ms;
+    return 1;
+}
+
+}  // extern "C"

@@ -1,0 +1,400 @@
+// tr.cu -- transitive reduction of the bidirected overlap graph R (Algorithm 1, Sec. IV-E) with
+// the MinPlus semiring of Algorithm 3, on the GPU.
+//
+// One round, for every row i in one thread block:
+//   N_ik = min over j of R_ij + R_jk, over walks i->j->k that are valid (the two heads at j
+//          point opposite ways: in(d_ij) == out(d_jk), Sec. II) -- only for k with R_ik present,
+//          since Algorithm 1 compares M and N only where both exist;
+//   v_i  = max_k R_ik + fuzz                                   (Reduce(Row, max), Apply(+x));
+//   I_ik = N_ik exists, its end orientations equal d_ik (rules (b), (c) of Sec. II), and
+//          v_i >= N_ik                                        (M >= N with M = DimApply(Row, v));
+//   R    = R minus I                                          (R o not I).
+// The round's result is a keep flag per entry; a stable compaction builds the next R. Rounds
+// repeat until nnz(R) does not change.
+//
+// Direction encoding: d = 2 * o_first + o_second (o = 1: the read is traversed reverse-
+// complemented). in(d) = d & 1, out(d) = d >> 1; the walk's composite dir is
+// 2 * out(d_ij) + in(d_jk). N is kept as (sum << 2 | composite) in one 64-bit word so that
+// DIRMATCH (composite must equal d_ik before the min) and LITERAL (lexicographic min of
+// (sum, composite), checked after) share one atomicMin.
+#include "prim.cuh"
+
+namespace sg {
+
+constexpr int TR_NT = 128;
+constexpr int TR_SMEM_ROW = 1024;  // rows up to this degree stage their entries in shared memory
+constexpr unsigned long long TR_NONE = ~0ull;
+
+struct TrGraph {
+    const int64_t *rp;
+    const int32_t *col;
+    const uint32_t *suf;
+    const uint8_t *dir;
+    int64_t n;
+};
+
+__global__ void validate_graph_kernel(TrGraph g, int64_t nnz, uint32_t *__restrict__ err) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row > g.n) return;
+    if (row == g.n) {
+        if (lane == 0 && (g.rp[g.n] != nnz || g.rp[0] != 0)) atomicOr(err, (uint32_t)DEV_INVALID);
+        return;
+    }
+    int64_t r0 = g.rp[row], r1 = g.rp[row + 1];
+    if (r1 < r0 || r0 < 0 || r1 > nnz) {
+        if (lane == 0) atomicOr(err, (uint32_t)DEV_INVALID);
+        return;
+    }
+    bool bad = false;
+    for (int64_t e = r0 + lane; e < r1; e += 32) {
+        int32_t c = g.col[e];
+        if (c < 0 || c >= g.n || c == row) bad = true;
+        if (e > r0 && g.col[e - 1] >= c) bad = true;
+        if (g.suf[e] >= (1u << 30) || g.dir[e] > 3) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, (uint32_t)DEV_INVALID);
+}
+
+// index of k in the sorted cols[0..deg), or -1
+__device__ __forceinline__ int64_t find_col(const int32_t *cols, int64_t deg, int32_t k) {
+    int64_t lo = 0, hi = deg;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (cols[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < deg && cols[lo] == k) ? lo : -1;
+}
+
+// One block per row. GMEM: the row is read in place from global memory and the per-entry
+// minima live in `gbest` (indexed by entry); otherwise the row is staged in shared memory.
+template <bool GMEM>
+__global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const int32_t *__restrict__ rows,
+                                                            int64_t nrows, int mode, uint32_t fuzz,
+                                                            unsigned long long *__restrict__ gbest,
+                                                            int64_t *__restrict__ gpre,
+                                                            uint8_t *__restrict__ keep, int64_t *__restrict__ kept,
+                                                            uint32_t *__restrict__ outN, uint8_t *__restrict__ outD) {
+    __shared__ int32_t s_col[GMEM ? 1 : TR_SMEM_ROW];
+    __shared__ uint32_t s_suf[GMEM ? 1 : TR_SMEM_ROW];
+    __shared__ uint8_t s_dir[GMEM ? 1 : TR_SMEM_ROW];
+    __shared__ unsigned long long s_best[GMEM ? 1 : TR_SMEM_ROW];
+    __shared__ int64_t s_pre[GMEM ? 1 : TR_SMEM_ROW + 1];
+    __shared__ int64_t s_tmp[TR_NT / 32 + 1];
+    __shared__ uint32_t s_red[TR_NT / 32];
+    __shared__ int64_t s_kept[TR_NT / 32];
+    for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
+        const int32_t i = rows[rb];
+        const int64_t r0 = g.rp[i], r1 = g.rp[i + 1], deg = r1 - r0;
+        const int32_t *col = GMEM ? g.col + r0 : s_col;
+        const uint32_t *suf = GMEM ? g.suf + r0 : s_suf;
+        const uint8_t *dir = GMEM ? g.dir + r0 : s_dir;
+        unsigned long long *best = GMEM ? gbest + r0 : s_best;
+        int64_t *pre = GMEM ? gpre + r0 + i : s_pre;  // deg + 1 slots per row
+        // stage row i and the exclusive prefix of its neighbours' degrees
+        uint32_t vmax = 0;
+        int64_t run = 0;
+        for (int64_t base = 0; base < deg; base += TR_NT) {
+            int64_t a = base + threadIdx.x;
+            int64_t dj = 0;
+            if (a < deg) {
+                int32_t j = g.col[r0 + a];
+                uint32_t sv = g.suf[r0 + a];
+                if (!GMEM) {
+                    s_col[a] = j;
+                    s_suf[a] = sv;
+                    s_dir[a] = g.dir[r0 + a];
+                }
+                best[a] = TR_NONE;
+                vmax = sv > vmax ? sv : vmax;
+                dj = g.rp[j + 1] - g.rp[j];
+            }
+            int64_t tot;
+            int64_t ex = block_exclusive_scan<TR_NT>(dj, s_tmp, &tot);
+            if (a < deg) pre[a] = run + ex;
+            run += tot;
+        }
+        if (threadIdx.x == 0) pre[deg] = run;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            uint32_t y = __shfl_xor_sync(0xffffffffu, vmax, o);
+            vmax = y > vmax ? y : vmax;
+        }
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = vmax;
+        __syncthreads();
+        const int64_t P = pre[deg];
+        // N = R^2 on the pattern of row i
+        for (int64_t p = threadIdx.x; p < P; p += TR_NT) {
+            int64_t lo = 0, hi = deg;  // entry a with pre[a] <= p < pre[a + 1]
+            while (hi - lo > 1) {
+                int64_t mid = (lo + hi) >> 1;
+                if (pre[mid] <= p) lo = mid; else hi = mid;
+            }
+            const int64_t a = lo;
+            const int32_t j = col[a];
+            const int64_t b = g.rp[j] + (p - pre[a]);
+            const int32_t k = g.col[b];
+            if (k == i) continue;
+            const int64_t t = find_col(col, deg, k);
+            if (t < 0) continue;
+            const uint32_t dij = dir[a], djk = g.dir[b];
+            if ((dij & 1u) != (djk >> 1)) continue;  // heads at j must point opposite ways
+            const uint32_t comp = (dij & 2u) | (djk & 1u);
+            if (mode == SG_TR_DIRMATCH && comp != dir[t]) continue;
+            const unsigned long long key = ((unsigned long long)(suf[a] + g.suf[b]) << 2) | comp;
+            atomicMin(best + t, key);
+        }
+        __syncthreads();
+        uint32_t vm = 0;
+        for (int w = 0; w < TR_NT / 32; w++) vm = s_red[w] > vm ? s_red[w] : vm;
+        const uint64_t v = (uint64_t)vm + fuzz;  // M_ik for every k of row i
+        int64_t mykept = 0;
+        for (int64_t t = threadIdx.x; t < deg; t += TR_NT) {
+            const unsigned long long bt = best[t];
+            const uint32_t d = dir[t];
+            const bool has = bt != TR_NONE;
+            const uint64_t N = bt >> 2;
+            const bool transitive = has && (uint32_t)(bt & 3u) == d && v >= N;
+            if (keep) keep[r0 + t] = transitive ? 0 : 1;
+            mykept += transitive ? 0 : 1;
+            if (outN) outN[r0 + t] = has ? (uint32_t)N : 0xFFFFFFFFu;
+            if (outD) outD[r0 + t] = has ? (uint8_t)(bt & 3u) : (uint8_t)d;
+        }
+        if (kept) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mykept += __shfl_xor_sync(0xffffffffu, mykept, o);
+            if ((threadIdx.x & 31) == 0) s_kept[threadIdx.x >> 5] = mykept;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int64_t a = 0;
+                for (int w = 0; w < TR_NT / 32; w++) a += s_kept[w];
+                kept[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// rows of each kind: 0 = empty, 1 = staged in shared memory, 2 = global memory
+__global__ void tr_bin_kernel(const int64_t *__restrict__ rp, int64_t n, unsigned long long *__restrict__ counts,
+                              int8_t *__restrict__ kind) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t d = rp[i + 1] - rp[i];
+    int8_t c = d == 0 ? 0 : (d <= TR_SMEM_ROW ? 1 : 2);
+    kind[i] = c;
+    atomicAdd(counts + c, 1ull);
+}
+
+__global__ void tr_fill_kernel(const int8_t *__restrict__ kind, int64_t n, unsigned long long *__restrict__ cursor,
+                               int64_t base_big, int32_t *__restrict__ rows) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = kind[i];
+    if (c == 0) return;
+    unsigned long long p = atomicAdd(cursor + c, 1ull);
+    rows[(c == 1 ? 0 : base_big) + (int64_t)p] = (int32_t)i;
+}
+
+// Stable compaction of kept entries: one warp per row.
+__global__ void tr_compact_kernel(TrGraph g, const uint8_t *__restrict__ keep, const int64_t *__restrict__ nrp,
+                                  int32_t *__restrict__ ocol, uint32_t *__restrict__ osuf,
+                                  uint8_t *__restrict__ odir) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= g.n) return;
+    int64_t r0 = g.rp[row], r1 = g.rp[row + 1], w = nrp[row];
+    for (int64_t base = r0; base < r1; base += 32) {
+        int64_t e = base + lane;
+        bool kp = e < r1 && keep[e];
+        uint32_t bal = __ballot_sync(0xffffffffu, kp);
+        if (kp) {
+            int64_t o = w + __popc(bal & ((1u << lane) - 1u));
+            ocol[o] = g.col[e];
+            osuf[o] = g.suf[e];
+            odir[o] = g.dir[e];
+        }
+        w += __popc(bal);
+    }
+}
+
+static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
+
+static sg_status validate(const TrGraph &g, int64_t nnz, Scratch &sc, cudaStream_t s) {
+    uint32_t *err = sc.get<uint32_t>(1);
+    if (!err) return SG_ERR_OOM;
+    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    SG_LAUNCH("validate_graph", validate_graph_kernel, blocks_for((g.n + 1) * 32, 256), 256, 0, s, g, nnz, err);
+    uint32_t h = 0;
+    SG_CUDA_TRY(read_back(&h, err, sizeof(uint32_t), s));
+    if (h) {
+        set_error("graph does not satisfy the CSR contract (sorted unique columns, no diagonal, suffix < 2^30, dir <= 3)");
+        return SG_ERR_INVALID;
+    }
+    return SG_OK;
+}
+
+// Buffers reused by every round (sized for the input graph; later rounds only shrink).
+struct TrWork {
+    unsigned long long *counts;  // [6]: rows per kind, then fill cursors
+    int8_t *kind;                // [n]
+    int32_t *rows;               // [n]
+    unsigned long long *gbest;   // [nnz] per-entry minima of global-memory rows
+    int64_t *gpre;               // [nnz + n + 1] neighbour-degree prefixes of global-memory rows
+};
+
+static sg_status tr_work_alloc(TrWork *w, int64_t n, int64_t nnz, Scratch &sc) {
+    w->counts = sc.get<unsigned long long>(6);
+    w->kind = sc.get<int8_t>(n + 1);
+    w->rows = sc.get<int32_t>(n + 1);
+    w->gbest = sc.get<unsigned long long>(nnz + 1);
+    w->gpre = sc.get<int64_t>(nnz + n + 1);
+    return (w->counts && w->kind && w->rows && w->gbest && w->gpre) ? SG_OK : SG_ERR_OOM;
+}
+
+// One round over graph g: keep flags + per-row kept counts (and optionally N / Ndir).
+static sg_status minplus_round(const TrGraph &g, int64_t nnz, int mode, uint32_t fuzz, uint8_t *keep,
+                               int64_t *kept, uint32_t *outN, uint8_t *outD, const TrWork &w, cudaStream_t s) {
+    const int64_t n = g.n;
+    unsigned long long *counts = w.counts;
+    int8_t *kind = w.kind;
+    int32_t *rows = w.rows;
+    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, 6 * sizeof(unsigned long long), s));
+    if (kept) SG_CUDA_TRY(cudaMemsetAsync(kept, 0, (n + 1) * sizeof(int64_t), s));
+    SG_LAUNCH("tr_bin", tr_bin_kernel, blocks_for(n, 256), 256, 0, s, g.rp, n, counts, kind);
+    unsigned long long hc[3];
+    SG_CUDA_TRY(read_back(hc, counts, sizeof(hc), s));
+    SG_LAUNCH("tr_fill", tr_fill_kernel, blocks_for(n, 256), 256, 0, s, kind, n, counts + 3, (int64_t)hc[1], rows);
+    const int grid_cap = 152 * 16;
+    if (hc[1]) {
+        int grid = (int)(hc[1] < (unsigned long long)grid_cap ? hc[1] : grid_cap);
+        SG_LAUNCH("tr_minplus_mark", minplus_mark_kernel<false>, grid, TR_NT, 0, s, g, rows, (int64_t)hc[1], mode,
+                  fuzz, (unsigned long long *)nullptr, (int64_t *)nullptr, keep, kept, outN, outD);
+    }
+    if (hc[2]) {
+        unsigned long long *gbest = w.gbest;
+        int64_t *gpre = w.gpre;
+        int grid = (int)(hc[2] < (unsigned long long)grid_cap ? hc[2] : grid_cap);
+        SG_LAUNCH("tr_minplus_mark_gmem", minplus_mark_kernel<true>, grid, TR_NT, 0, s, g, rows + hc[1],
+                  (int64_t)hc[2], mode, fuzz, gbest, gpre, keep, kept, outN, outD);
+    }
+    return SG_OK;
+}
+
+static void free_graph_arrays(sg_graph_csr *x, cudaStream_t s) {
+    dfree(x->row_ptr, s);
+    dfree(x->col, s);
+    dfree(x->suffix, s);
+    dfree(x->dir, s);
+    *x = sg_graph_csr{};
+}
+
+static sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *S, int32_t *iters,
+                         cudaStream_t s) {
+    const int64_t n = R->n;
+    Scratch sc(s);
+    TrGraph g{R->row_ptr, R->col, R->suffix, R->dir, n};
+    SG_TRY(validate(g, R->nnz, sc, s));
+    uint8_t *keep = sc.get<uint8_t>(R->nnz);
+    int64_t *kept = sc.get<int64_t>(n + 1);
+    if (!keep || !kept) return SG_ERR_OOM;
+    TrWork wk;
+    SG_TRY(tr_work_alloc(&wk, n, R->nnz, sc));
+    sg_graph_csr cur{};  // library-owned current graph (empty = still the input)
+    int64_t cur_nnz = R->nnz;
+    int32_t it = 0;
+    for (;;) {
+        it++;
+        sg_status rs = minplus_round(g, cur_nnz, mode, fuzz, keep, kept, nullptr, nullptr, wk, s);
+        if (rs != SG_OK) { free_graph_arrays(&cur, s); return rs; }
+        sg_graph_csr nx{};
+        nx.n = n;
+        nx.row_ptr = (int64_t *)dalloc((n + 1) * sizeof(int64_t), s);
+        if (!nx.row_ptr) { free_graph_arrays(&cur, s); return SG_ERR_OOM; }
+        sg_status st = exclusive_scan<int64_t>(kept, nx.row_ptr, n, s);
+        int64_t nnz2 = 0;
+        if (st == SG_OK && read_back(&nnz2, nx.row_ptr + n, sizeof(int64_t), s) != cudaSuccess) {
+            set_error("transitive_reduce: reading nnz back failed");
+            st = SG_ERR_CUDA;
+        }
+        if (st != SG_OK) { free_graph_arrays(&nx, s); free_graph_arrays(&cur, s); return st; }
+        if (nnz2 == cur_nnz) {  // nothing removed: done
+            dfree(nx.row_ptr, s);
+            break;
+        }
+        nx.nnz = nnz2;
+        nx.col = (int32_t *)dalloc(nnz2 * sizeof(int32_t), s);
+        nx.suffix = (uint32_t *)dalloc(nnz2 * sizeof(uint32_t), s);
+        nx.dir = (uint8_t *)dalloc(nnz2, s);
+        if (!nx.col || !nx.suffix || !nx.dir) { free_graph_arrays(&nx, s); free_graph_arrays(&cur, s); return SG_ERR_OOM; }
+        SG_LAUNCH("tr_compact", tr_compact_kernel, blocks_for(n * 32, 256), 256, 0, s, g, keep, nx.row_ptr, nx.col,
+                  nx.suffix, nx.dir);
+        free_graph_arrays(&cur, s);
+        cur = nx;
+        cur_nnz = nnz2;
+        g = TrGraph{cur.row_ptr, cur.col, cur.suffix, cur.dir, n};
+    }
+    if (!cur.row_ptr) {  // first round removed nothing: S is a copy of R
+        cur.n = n;
+        cur.nnz = R->nnz;
+        cur.row_ptr = (int64_t *)dalloc((n + 1) * sizeof(int64_t), s);
+        cur.col = (int32_t *)dalloc(R->nnz * sizeof(int32_t), s);
+        cur.suffix = (uint32_t *)dalloc(R->nnz * sizeof(uint32_t), s);
+        cur.dir = (uint8_t *)dalloc(R->nnz, s);
+        if (!cur.row_ptr || !cur.col || !cur.suffix || !cur.dir) { free_graph_arrays(&cur, s); return SG_ERR_OOM; }
+        SG_CUDA_TRY(cudaMemcpyAsync(cur.row_ptr, R->row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        if (R->nnz) {
+            SG_CUDA_TRY(cudaMemcpyAsync(cur.col, R->col, R->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            SG_CUDA_TRY(cudaMemcpyAsync(cur.suffix, R->suffix, R->nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+            SG_CUDA_TRY(cudaMemcpyAsync(cur.dir, R->dir, R->nnz, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    *S = cur;
+    *iters = it;
+    return SG_OK;
+}
+
+static bool graph_args_ok(const sg_graph_csr *R) {
+    return R && R->n >= 0 && R->n < ((int64_t)1 << 31) && R->nnz >= 0 && R->row_ptr &&
+           (R->nnz == 0 || (R->col && R->suffix && R->dir));
+}
+
+}  // namespace sg
+
+extern "C" sg_status sg_transitive_reduce(const sg_graph_csr *R, uint32_t fuzz, int32_t mode, sg_graph_csr *S,
+                                          int32_t *iterations, sg_stream_t stream) {
+    if (!S || !iterations) {
+        sg::set_error("transitive_reduce: NULL output");
+        return SG_ERR_INVALID;
+    }
+    *S = sg_graph_csr{};
+    *iterations = 0;
+    if (!sg::graph_args_ok(R) || fuzz >= (1u << 30) || (mode != SG_TR_DIRMATCH && mode != SG_TR_LITERAL)) {
+        sg::set_error("transitive_reduce: invalid arguments");
+        return SG_ERR_INVALID;
+    }
+    return sg::tr_impl(R, fuzz, mode, S, iterations, (cudaStream_t)stream);
+}
+
+extern "C" sg_status sg_minplus_square(const sg_graph_csr *R, int32_t mode, uint32_t *d_N, uint8_t *d_Ndir,
+                                       sg_stream_t stream) {
+    if (!sg::graph_args_ok(R) || (mode != SG_TR_DIRMATCH && mode != SG_TR_LITERAL) || (R->nnz > 0 && !d_N)) {
+        sg::set_error("minplus_square: invalid arguments");
+        return SG_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sg::Scratch sc(s);
+    sg::TrGraph g{R->row_ptr, R->col, R->suffix, R->dir, R->n};
+    SG_TRY(sg::validate(g, R->nnz, sc, s));
+    sg::TrWork wk;
+    SG_TRY(sg::tr_work_alloc(&wk, R->n, R->nnz, sc));
+    SG_TRY(sg::minplus_round(g, R->nnz, mode, 0, nullptr, nullptr, d_N, d_Ndir, wk, s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    return SG_OK;
+}
+
+extern "C" void sg_free_graph(sg_graph_csr *x, sg_stream_t stream) {
+    if (!x) return;
+    sg::free_graph_arrays(x, (cudaStream_t)stream);
+}
