@@ -150,7 +150,7 @@ def main():
         S, it = sg.transitive_reduce(R, w.fuzz)
         return km, C, S, it
 
-    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+    for _ in range(args.warmup):
         out = step()
         del out
     torch.cuda.synchronize()
