@@ -102,7 +102,7 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- roofline
 def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
-    """Bytes the method must move per launch of `kernel` (kernel table)."""
+    """Bytes the method must move per launch of `kernel` (inputs read once, outputs written once)."""
     if kernel == "bloom_insert":
         # every base read once, one 8-byte filter word touched per k-mer window
         return sz["total"] + 8.0 * sz["windows"]
