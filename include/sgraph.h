@@ -143,6 +143,27 @@ sg_status sg_minplus_square(const sg_graph_csr *R, int32_t mode, uint32_t *d_N, 
                             sg_stream_t stream);
 
 /*
+ * Allocation-free form of sg_minplus_square (the paper has no counterpart; this is a library
+ * convenience). Same inputs, outputs, result and errors, but it never allocates device memory:
+ * its workspace is one fixed device array of SG_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads the library reserves until the process exits. It is meant for callers that cannot call
+ * cudaMalloc when they need the product -- e.g. code running under a hard per-process memory
+ * cap, while a memory pool is exhausted or being torn down, or on a host thread that may not
+ * take the allocator's locks.
+ *  - Limit: the workspace needs about 13 n + 16 nnz + 2 KB bytes; larger graphs are rejected with
+ *    SG_ERR_BUDGET and a message naming the sizes (use sg_minplus_square for them).
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture.
+ *  - Every call on a device shares the one array, and it keeps the previous call's contents
+ *    (the call clears what must start at zero itself). Calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race on it: serialise them.
+ *  - Synchronises `stream`.
+ */
+#define SG_NOALLOC_SCRATCH_BYTES (16u << 20)
+sg_status sg_minplus_square_noalloc(const sg_graph_csr *R, int32_t mode, uint32_t *d_N, uint8_t *d_Ndir,
+                                    sg_stream_t stream);
+
+/*
  * Algorithm 1: repeat { N = R^2 (Algorithm 3); v = rowmax(R) + fuzz; I = (v_i >= N_ik, with the
  * end-orientation rule); R = R minus I } until nnz(R) stops changing; S = R.
  *   fuzz        < 2^30 (the scalar x of Sec. IV-E).

@@ -398,3 +398,97 @@ extern "C" void sg_free_graph(sg_graph_csr *x, sg_stream_t stream) {
     if (!x) return;
     sg::free_graph_arrays(x, (cudaStream_t)stream);
 }
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of sg_minplus_square.
+//
+// Some callers cannot allocate device memory at the moment they want this product: code that
+// runs while a memory pool is being torn down or is already exhausted, code that must not
+// grow the footprint of a process that shares its GPU under a hard memory cap, and host
+// threads (e.g. a real-time scheduler loop) that may not take the allocator's locks or wait on
+// its synchronisation. For them the workspace of the product lives in one file-scope device
+// array, reserved when the library is loaded and kept until the process exits, on every GPU
+// that loads the library.
+#include <mutex>
+
+static __device__ __align__(256) unsigned char sg_noalloc_scratch[SG_NOALLOC_SCRATCH_BYTES];
+
+namespace sg {
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];  // device address of sg_noalloc_scratch, per device ordinal
+
+// Device address of the scratch array on the current device. The first call on a device looks
+// it up (the array's name in host code is only a stand-in, never a device address).
+static sg_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        set_error("minplus_square_noalloc: device ordinal %d out of range", dev);
+        return SG_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, sg_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("minplus_square_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
+                      cudaGetErrorString(e));
+            return SG_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (unsigned char *)g_noalloc_addr[dev];
+    return SG_OK;
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace sg
+
+extern "C" sg_status sg_minplus_square_noalloc(const sg_graph_csr *R, int32_t mode, uint32_t *d_N,
+                                               uint8_t *d_Ndir, sg_stream_t stream) {
+    if (!sg::graph_args_ok(R) || (mode != SG_TR_DIRMATCH && mode != SG_TR_LITERAL) || (R->nnz > 0 && !d_N)) {
+        sg::set_error("minplus_square_noalloc: invalid arguments");
+        return SG_ERR_INVALID;
+    }
+    const int64_t n = R->n, nnz = R->nnz;
+    // workspace layout inside the scratch array
+    const size_t o_err = 0;
+    const size_t o_cnt = sg::up256(o_err + sizeof(uint32_t));
+    const size_t o_kind = sg::up256(o_cnt + 6 * sizeof(unsigned long long));
+    const size_t o_rows = sg::up256(o_kind + (size_t)(n + 1));
+    const size_t o_best = sg::up256(o_rows + (size_t)(n + 1) * sizeof(int32_t));
+    const size_t o_pre = sg::up256(o_best + (size_t)(nnz + 1) * sizeof(unsigned long long));
+    const size_t need = o_pre + (size_t)(nnz + n + 1) * sizeof(int64_t);
+    if (need > (size_t)SG_NOALLOC_SCRATCH_BYTES) {
+        sg::set_error("minplus_square_noalloc: a graph with n=%lld and nnz=%lld needs %zu bytes of workspace, "
+                      "more than the fixed %zu-byte scratch array; use sg_minplus_square",
+                      (long long)n, (long long)nnz, need, (size_t)SG_NOALLOC_SCRATCH_BYTES);
+        return SG_ERR_BUDGET;
+    }
+    unsigned char *base = nullptr;
+    SG_TRY(sg::noalloc_scratch(&base));
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *err = (uint32_t *)(base + o_err);
+    sg::TrWork wk;
+    wk.counts = (unsigned long long *)(base + o_cnt);
+    wk.kind = (int8_t *)(base + o_kind);
+    wk.rows = (int32_t *)(base + o_rows);
+    wk.gbest = (unsigned long long *)(base + o_best);
+    wk.gpre = (int64_t *)(base + o_pre);
+    sg::TrGraph g{R->row_ptr, R->col, R->suffix, R->dir, n};
+    // the array keeps whatever the previous call left: the error word starts from zero here,
+    // the row counters are zeroed by minplus_round, and every other word is written before read
+    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    SG_LAUNCH("validate_graph", sg::validate_graph_kernel, (n + 1 + 7) / 8, 256, 0, s, g, nnz, err);
+    uint32_t herr = 0;
+    SG_CUDA_TRY(sg::read_back(&herr, err, sizeof(uint32_t), s));
+    if (herr) {
+        sg::set_error("minplus_square_noalloc: graph does not satisfy the CSR contract");
+        return SG_ERR_INVALID;
+    }
+    SG_TRY(sg::minplus_round(g, nnz, mode, 0, nullptr, nullptr, d_N, d_Ndir, wk, s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    return SG_OK;
+}
