@@ -177,6 +177,49 @@ sg_status sg_transitive_reduce(const sg_graph_csr *R, uint32_t fuzz, int32_t mod
                                int32_t *iterations, sg_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Batched form: many independent read sets in one pass. The sets are laid end to end as one
+ * block-diagonal problem (set b's reads are rows read_off[b] .. read_off[b+1] of A, C and S; its
+ * k-mers are columns col_off[b] .. col_off[b+1] of A, ordered by code within the set), so each
+ * set's slice of the results equals what the three calls above give for that set alone --
+ * indices in the slice are offset by read_off[b] (rows of A, C, S; columns of C, S, At) and
+ * col_off[b] (columns of A, rows of At) -- while the batch runs as one sequence of launches.
+ */
+typedef struct {
+    const uint8_t *d_seq;      /* device, as sg_build_kmer_matrix */
+    const int64_t *d_offsets;  /* device [n_reads + 1] */
+    int64_t n_reads, total_len;
+    uint32_t lo, hi;           /* this set's reliable range */
+    const sg_graph_csr *R;     /* device graph over this set's reads, or NULL (no reduction) */
+} sg_batch_item;
+
+typedef struct {
+    int32_t k;                 /* shared by all sets */
+    uint32_t min_shared;
+    int32_t max_seeds;
+    uint32_t fuzz;
+    int32_t tr_mode;
+} sg_batch_params;
+
+typedef struct {
+    int32_t n_items;
+    int64_t *read_off;         /* host [n_items + 1] */
+    int64_t *col_off;          /* host [n_items + 1] */
+    int32_t *iterations;       /* host [n_items]: rounds the set alone would take (0 without R) */
+    int32_t iterations_all;    /* rounds run for the whole batch */
+    sg_csr_u32 A, At;          /* device, union */
+    uint64_t *d_kmer_codes;    /* device [A.n_cols], codes without the set prefix */
+    sg_overlap_csr C;          /* device, union (column indices are union read ids) */
+    sg_graph_csr S;            /* device, union; empty when no item has R */
+} sg_batch_result;
+
+/* Errors: SG_ERR_INVALID (an item or the parameters break the contract, e.g. an R column outside
+ * its own set), SG_ERR_OVERFLOW (more than 2^31 reads, or set prefix + 2k > 64 bits), SG_ERR_OOM,
+ * SG_ERR_CUDA. Synchronises. Release with sg_free_batch. */
+sg_status sg_run_batch(const sg_batch_item *items, int32_t n_items, const sg_batch_params *params,
+                       sg_batch_result *out, sg_stream_t stream);
+void sg_free_batch(sg_batch_result *r, sg_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
  * The whole path on HOST buffers: Algorithm 2 from the reads to S (KmerCounter, GenerateA,
  * Transpose, C = A A^T, TransitiveReduction; the alignment/prune steps that turn C into R are not
  * part of this library, so R is an input). Copies the inputs to the device, runs the three
@@ -249,6 +292,8 @@ uint64_t sg_launch_count(void);
  * its stream. sg_prof_collect synchronises on the recorded events and folds them into per-name
  * totals, readable with sg_prof_entry(idx, ...) for idx < sg_prof_collect()'s return value. */
 void sg_prof_enable(int on);
+/* Time only kernels whose name starts with name_prefix (NULL or "" = all). */
+void sg_prof_select(const char *name_prefix);
 void sg_prof_reset(void);
 int sg_prof_collect(void);
 int sg_prof_entry(int idx, const char **name, int64_t *launches, double *total_ms);

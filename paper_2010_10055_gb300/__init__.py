@@ -24,7 +24,7 @@ INF = 0xFFFFFFFF
 EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",
            "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
-           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_launch_count", "sg_prof_enable",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_launch_count", "sg_prof_enable", "sg_prof_select",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
 
 
@@ -105,6 +105,7 @@ def lib():
         L.sg_debug_fail_alloc_after.argtypes = [i64]
         L.sg_launch_count.restype = ctypes.c_uint64
         L.sg_prof_enable.argtypes = [ctypes.c_int]
+        L.sg_prof_select.argtypes = [ctypes.c_char_p]
         L.sg_prof_collect.restype = ctypes.c_int
         L.sg_prof_entry.restype = ctypes.c_int
         L.sg_prof_entry.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i64),
@@ -365,6 +366,11 @@ def launch_count() -> int:
 
 def prof_enable(on: bool = True):
     lib().sg_prof_enable(1 if on else 0)
+
+
+def prof_select(prefix: str | None = None):
+    """Time only kernels whose name starts with `prefix` (None = all)."""
+    lib().sg_prof_select(prefix.encode() if prefix else None)
 
 
 def prof_reset():

@@ -30,11 +30,11 @@ struct LaunchScope {
 // Scoped set of temporary device buffers, released in reverse order on scope exit.
 struct Scratch {
     cudaStream_t s;
-    void *ptrs[64];
+    void *ptrs[128];
     int n = 0;
     explicit Scratch(cudaStream_t st) : s(st) {}
     template <class T> T *get(size_t count) {
-        if (n == 64) { set_error("internal: scratch table full"); return nullptr; }
+        if (n == 128) { set_error("internal: scratch table full"); return nullptr; }
         void *p = dalloc(count * sizeof(T), s);
         if (p) ptrs[n++] = p;
         return (T *)p;
@@ -44,6 +44,10 @@ struct Scratch {
 
 // Copy one device value to the host and wait for it.
 cudaError_t read_back(void *host, const void *dev, size_t bytes, cudaStream_t s);
+
+// Whether a launch grid has any blocks.
+inline bool grid_ok(int64_t g) { return g > 0; }
+inline bool grid_ok(dim3 g) { return g.x > 0 && g.y > 0 && g.z > 0; }
 
 // The device-side error word used by validation kernels (one per call, zeroed first).
 enum : uint32_t { DEV_OK = 0, DEV_INVALID = 1, DEV_OVERFLOW = 2 };
@@ -64,7 +68,7 @@ enum : uint32_t { DEV_OK = 0, DEV_INVALID = 1, DEV_OVERFLOW = 2 };
 // from the enclosing function if the launch is rejected.
 #define SG_LAUNCH(name, kernel, grid, block, smem, stream, ...)                                 \
     do {                                                                                        \
-        if ((grid) > 0) {                                                                       \
+        if (sg::grid_ok(grid)) {                                                                \
             sg::LaunchScope ls_(name, stream);                                                  \
             kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                         \
         }                                                                                       \

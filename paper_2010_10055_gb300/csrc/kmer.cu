@@ -21,99 +21,154 @@
 //     reliable code; within a reliable segment the first entry of each read is its lowest
 //     position: those entries are At's row, already sorted by read.
 //  6. A = At transposed by a stable radix sort on the read id (columns stay ascending).
-#include "prim.cuh"
+#include <type_traits>
+
+#include "ops.cuh"
 
 namespace sg {
 
 constexpr int KM_NT = 256;
 constexpr int KM_W = 32;                  // windows per thread
 constexpr int KM_CHUNK = KM_NT * KM_W;    // windows per block
+constexpr uint64_t KM_SLICE_BYTES = 48ull << 20;  // B1 bytes updated per Bloom launch (L2-resident)
 
-__device__ __forceinline__ uint64_t mix64(uint64_t x) {  // murmur3 fmix64
-    x ^= x >> 33;
-    x *= 0xff51afd7ed558ccdULL;
-    x ^= x >> 33;
-    x *= 0xc4ceb9fe1a85ec53ULL;
-    x ^= x >> 33;
-    return x;
+// 32-bit mix of a 64-bit k-mer code (multiply-xorshift finaliser).
+__device__ __forceinline__ uint32_t hash32(uint64_t code, uint32_t seed) {
+    uint32_t h = (uint32_t)code * 0x9E3779B1u + seed;
+    h ^= (uint32_t)(code >> 32) * 0x85EBCA77u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
 }
 
+// Blocked Bloom filter: a key sets 4 bits of one 32-bit word, so whether all of them were
+// already set is decided by the single atomicOr that sets them.
 struct Bloom {
-    unsigned long long *words;
-    uint64_t nwords;  // < 2^32
-    uint64_t seed;
-    __device__ __forceinline__ void probe(uint64_t code, uint64_t *idx, unsigned long long *mask) const {
-        uint64_t h = mix64(code ^ seed);
-        *idx = ((h >> 32) * nwords) >> 32;
-        *mask = (1ull << (h & 63)) | (1ull << ((h >> 6) & 63)) | (1ull << ((h >> 12) & 63)) |
-                (1ull << ((h >> 18) & 63));
+    uint32_t *words;
+    uint32_t nwords;
+    uint32_t seed;
+    __device__ __forceinline__ void probe(uint64_t code, uint32_t *idx, uint32_t *mask) const {
+        const uint32_t h = hash32(code, seed);
+        *idx = __umulhi(h, nwords);
+        const uint32_t g = h * 0x85EBCA6Bu;  // bit positions from a second mix
+        *mask = (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u)) |
+                (1u << ((g >> 12) & 31u));
+    }
+};
+
+// Per-thread cursor over the job map (reads are visited in increasing order).
+struct JobCursor {
+    JobMap m;
+    int64_t jb = 0, jlo = 0, jhi = -1;
+    __device__ __forceinline__ uint64_t key(uint64_t code, int64_t r) {
+        if (!m.ro) return code;
+        if (r < jlo || r >= jhi) {  // last job b with ro[b] <= r
+            int64_t lo = 0, hi = m.njobs;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (m.ro[mid] <= r) lo = mid; else hi = mid;
+            }
+            jb = lo;
+            jlo = m.ro[lo];
+            jhi = m.ro[lo + 1];
+        }
+        return ((uint64_t)jb << m.kbits) | code;
     }
 };
 
 // Visits the windows [c0 + t*KM_W, c0 + (t+1)*KM_W) of thread t in position order, calling
-// f(code, strand, read, pos) for each window of k A/C/G/T bases inside one read.
-template <class F>
+// f(code, strand, read, pos) for each window of k A/C/G/T bases inside one read. K > 0 makes k a
+// compile-time constant (K == 0: k taken from k_rt). Indices inside the block are 32-bit.
+template <int K, class F>
 __device__ __forceinline__ void for_each_window(const uint8_t *__restrict__ sm, int64_t c0, int64_t total,
-                                                const int64_t *__restrict__ off, int64_t n, int k,
+                                                const int64_t *__restrict__ off, int64_t n, int k_rt,
                                                 F &&f) {
-    const int64_t qs = c0 + (int64_t)threadIdx.x * KM_W;
-    if (qs >= total) return;
-    int64_t qe = qs + KM_W + k - 1;  // exclusive
-    if (qe > total) qe = total;
+    const int k = K > 0 ? K : k_rt;
+    const int ls = threadIdx.x * KM_W;
+    const int64_t qs = c0 + ls;
+    if (qs >= total || n <= 0) return;
+    int le = ls + KM_W + k - 1;  // exclusive, local to the block
+    if (c0 + le > total) le = (int)(total - c0);
     // read containing qs: last r with off[r] <= qs
     int64_t lo = 0, hi = n;  // invariant: off[lo] <= qs < off[hi] (off[n] = total > qs)
     while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
+        const int64_t mid = (lo + hi) >> 1;
         if (off[mid] <= qs) lo = mid; else hi = mid;
     }
-    int64_t r = lo, next = off[r + 1];
-    const uint64_t mask = (k == 32) ? ~0ull : ((1ull << (2 * k)) - 1);
+    int64_t r = lo;
+    int64_t rbase = off[r] - c0;  // start of read r relative to the block
+    int64_t nx = off[r + 1] - c0;
+    int next = nx > (int64_t)0x7fffffff ? 0x7fffffff : (int)nx;
+    const uint64_t mask = (1ull << (2 * k)) - 1;
     const int rs = 2 * (k - 1);
     uint64_t fw = 0, rc = 0;
     int run = 0;
-    for (int64_t q = qs; q < qe; q++) {
-        while (q >= next) {  // crossed into the next read (skips empty reads)
+    for (int q = ls; q < le; q++) {
+        // crossed into the next read (skips empty reads); r + 1 < n keeps every access in
+        // bounds even when the offsets turn out to be invalid (reported after this pass)
+        while (q >= next && r + 1 < n) {
             r++;
-            next = off[r + 1];
+            rbase = off[r] - c0;
+            nx = off[r + 1] - c0;
+            next = nx > (int64_t)0x7fffffff ? 0x7fffffff : (int)nx;
             run = 0;
         }
-        uint8_t c = sm[q - c0];
-        bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
-        uint32_t t = (c >> 1) & 3u;
-        uint32_t b = t ^ (t >> 1);  // A=0 C=1 G=2 T=3
+        const uint32_t c = sm[q];
+        const bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
+        const uint32_t t = (c >> 1) & 3u;
+        const uint32_t b = t ^ (t >> 1);  // A=0 C=1 G=2 T=3
         fw = ((fw << 2) | b) & mask;
         rc = (rc >> 2) | ((uint64_t)(3u - b) << rs);
         run = ok ? run + 1 : 0;
-        if (run >= k && q - k + 1 >= qs) {
-            uint64_t code = fw < rc ? fw : rc;
-            uint32_t strand = rc < fw ? 1u : 0u;
-            f(code, strand, r, (uint32_t)(q - k + 1 - off[r]));
+        if (run >= k && q - k + 1 >= ls) {
+            const uint64_t code = fw < rc ? fw : rc;
+            const uint32_t strand = rc < fw ? 1u : 0u;
+            f(code, strand, r, (uint32_t)(q - k + 1 - rbase));
         }
     }
 }
 
+// Stages the block's bases in shared memory. The reads stream through once per pass, so they
+// are loaded evict-first (ld.global.cs) to keep the filters resident in L2; 16-byte loads when
+// the chunk start is 16-byte aligned.
 __device__ __forceinline__ void load_chunk(uint8_t *sm, const uint8_t *__restrict__ seq, int64_t c0,
                                            int64_t total, int k) {
     int64_t len = (int64_t)KM_CHUNK + k - 1;
     if (c0 + len > total) len = total - c0;
-    for (int64_t i = threadIdx.x; i < len; i += KM_NT) sm[i] = seq[c0 + i];
+    int64_t done = 0;
+    if ((((uintptr_t)(seq + c0)) & 15) == 0) {
+        const int64_t nv = len >> 4;
+        const uint4 *src = reinterpret_cast<const uint4 *>(seq + c0);
+        uint4 *dst = reinterpret_cast<uint4 *>(sm);
+        for (int64_t i = threadIdx.x; i < nv; i += KM_NT) dst[i] = __ldcs(src + i);
+        done = nv << 4;
+    }
+    for (int64_t i = done + threadIdx.x; i < len; i += KM_NT) sm[i] = __ldcs(seq + c0 + i);
     __syncthreads();
 }
 
+// One launch per slice [w_lo, w_hi) of B1's words: every launch walks all windows but only the
+// k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2.
+template <int K>
 __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint8_t *__restrict__ seq, int64_t total,
                                                             const int64_t *__restrict__ off, int64_t n, int k,
-                                                            Bloom b1, Bloom b2) {
-    __shared__ uint8_t sm[KM_CHUNK + 32];
+                                                            Bloom b1, Bloom b2, uint32_t w_lo, uint32_t w_hi,
+                                                            JobMap jm) {
+    __shared__ __align__(16) uint8_t sm[KM_CHUNK + 48];
     int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
     load_chunk(sm, seq, c0, total, k);
-    for_each_window(sm, c0, total, off, n, k, [&](uint64_t code, uint32_t, int64_t, uint32_t) {
-        uint64_t i1;
-        unsigned long long m1;
+    JobCursor jc{jm};
+    for_each_window<K>(sm, c0, total, off, n, k, [&](uint64_t code0, uint32_t, int64_t r, uint32_t) {
+        const uint64_t code = jc.key(code0, r);
+        uint32_t i1, m1;
         b1.probe(code, &i1, &m1);
-        unsigned long long old = atomicOr(b1.words + i1, m1);
+        if (i1 < w_lo || i1 >= w_hi) return;  // another slice's launch handles this k-mer
+        const uint32_t old = atomicOr(b1.words + i1, m1);
         if ((old & m1) == m1) {
-            uint64_t i2;
-            unsigned long long m2;
+            uint32_t i2, m2;
             b2.probe(code, &i2, &m2);
             if ((b2.words[i2] & m2) != m2) atomicOr(b2.words + i2, m2);
         }
@@ -121,17 +176,20 @@ __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint8_t *__re
 }
 
 // use_bloom == 0 keeps every window (lo == 1: singletons may be reliable).
+template <int K>
 __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint8_t *__restrict__ seq, int64_t total,
                                                           const int64_t *__restrict__ off, int64_t n, int k,
-                                                          Bloom b2, int use_bloom, uint32_t *__restrict__ cnt) {
-    __shared__ uint8_t sm[KM_CHUNK + 32];
+                                                          Bloom b2, int use_bloom, uint32_t *__restrict__ cnt,
+                                                          JobMap jm) {
+    __shared__ __align__(16) uint8_t sm[KM_CHUNK + 48];
     int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
     load_chunk(sm, seq, c0, total, k);
     uint32_t c = 0;
-    for_each_window(sm, c0, total, off, n, k, [&](uint64_t code, uint32_t, int64_t, uint32_t) {
+    JobCursor jc{jm};
+    for_each_window<K>(sm, c0, total, off, n, k, [&](uint64_t code0, uint32_t, int64_t r, uint32_t) {
+        const uint64_t code = jc.key(code0, r);
         if (use_bloom) {
-            uint64_t i2;
-            unsigned long long m2;
+            uint32_t i2, m2;
             b2.probe(code, &i2, &m2);
             if ((b2.words[i2] & m2) != m2) return;
         }
@@ -140,19 +198,22 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint8_t *__rest
     cnt[(int64_t)blockIdx.x * KM_NT + threadIdx.x] = c;
 }
 
+template <int K>
 __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint8_t *__restrict__ seq, int64_t total,
                                                          const int64_t *__restrict__ off, int64_t n, int k,
                                                          Bloom b2, int use_bloom,
                                                          const int64_t *__restrict__ pos_of_thread,
-                                                         uint64_t *__restrict__ keys, uint64_t *__restrict__ vals) {
-    __shared__ uint8_t sm[KM_CHUNK + 32];
+                                                         uint64_t *__restrict__ keys, uint64_t *__restrict__ vals,
+                                                         JobMap jm) {
+    __shared__ __align__(16) uint8_t sm[KM_CHUNK + 48];
     int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
     load_chunk(sm, seq, c0, total, k);
     int64_t w = pos_of_thread[(int64_t)blockIdx.x * KM_NT + threadIdx.x];
-    for_each_window(sm, c0, total, off, n, k, [&](uint64_t code, uint32_t strand, int64_t r, uint32_t pos) {
+    JobCursor jc{jm};
+    for_each_window<K>(sm, c0, total, off, n, k, [&](uint64_t code0, uint32_t strand, int64_t r, uint32_t pos) {
+        const uint64_t code = jc.key(code0, r);
         if (use_bloom) {
-            uint64_t i2;
-            unsigned long long m2;
+            uint32_t i2, m2;
             b2.probe(code, &i2, &m2);
             if ((b2.words[i2] & m2) != m2) return;
         }
@@ -191,13 +252,20 @@ __global__ void seg_start_kernel(const uint32_t *__restrict__ head, const int64_
     if (i == nc - 1) seg_start[seg_excl[nc]] = nc;
 }
 
+// lohi (batches): the reliable range of each job, [2 * job] = lo, [2 * job + 1] = hi.
 __global__ void seg_reliable_kernel(const int64_t *__restrict__ seg_start, const int64_t *__restrict__ nseg_p,
-                                    uint32_t lo, uint32_t hi, uint32_t *__restrict__ rel) {
+                                    uint32_t lo, uint32_t hi, const uint64_t *__restrict__ key,
+                                    const uint32_t *__restrict__ lohi, int kbits, uint32_t *__restrict__ rel) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nseg = *nseg_p;
     if (s >= nseg) {  // slots past the last segment still feed the scan below: make them 0
         rel[s] = 0u;
         return;
+    }
+    if (lohi) {
+        const uint64_t job = key[seg_start[s]] >> kbits;
+        lo = lohi[2 * job];
+        hi = lohi[2 * job + 1];
     }
     int64_t len = seg_start[s + 1] - seg_start[s];
     rel[s] = (len >= (int64_t)lo && len <= (int64_t)hi) ? 1u : 0u;
@@ -222,7 +290,8 @@ __global__ void emit_at_kernel(const uint32_t *__restrict__ head, const int64_t 
                                const uint64_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t nc,
                                int64_t m, int64_t nnz, int32_t *__restrict__ at_col, uint32_t *__restrict__ at_val,
                                int64_t *__restrict__ at_rp, uint64_t *__restrict__ codes,
-                               uint32_t *__restrict__ a_key, uint64_t *__restrict__ a_val) {
+                               uint32_t *__restrict__ a_key, uint64_t *__restrict__ a_val, int kbits,
+                               unsigned long long *__restrict__ job_ncols) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) at_rp[m] = nnz;
     if (i >= nc) return;
@@ -230,7 +299,8 @@ __global__ void emit_at_kernel(const uint32_t *__restrict__ head, const int64_t 
     if (head[i] && rel[s]) {
         int64_t j = col_of_seg[s];
         at_rp[j] = out_pos[i];
-        codes[j] = key[i];
+        codes[j] = kbits < 64 ? key[i] & ((1ull << kbits) - 1) : key[i];
+        if (job_ncols) atomicAdd(job_ncols + (key[i] >> kbits), 1ull);
     }
     if (keep[i]) {
         int64_t o = out_pos[i];
@@ -263,9 +333,23 @@ __global__ void split_pairs_kernel(const uint64_t *__restrict__ pv, int64_t nnz,
 
 static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
 
-static sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t total, int k,
-                            uint32_t lo, uint32_t hi, sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **codes_out,
-                            cudaStream_t s, Scratch &sc) {
+// Runs f with k as a compile-time constant for the common k (17 is the paper's), else 0.
+template <class F>
+static sg_status dispatch_k(int k, F &&f) {
+    switch (k) {
+        case 17: return f(std::integral_constant<int, 17>{});
+        case 21: return f(std::integral_constant<int, 21>{});
+        case 31: return f(std::integral_constant<int, 31>{});
+        default: return f(std::integral_constant<int, 0>{});
+    }
+}
+
+// jm.ro == nullptr: one read set with range [lo, hi]. Otherwise a batch: lohi (device) holds
+// each job's range and job_ncols (device, zeroed, njobs entries) receives each job's column count.
+sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t total, int k,
+                     uint32_t lo, uint32_t hi, sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **codes_out,
+                     cudaStream_t s, Scratch &sc, JobMap jm, const uint32_t *lohi,
+                     unsigned long long *job_ncols) {
     const int NT = 256;
     uint32_t *err = sc.get<uint32_t>(1);
     if (!err) return SG_ERR_OOM;
@@ -274,43 +358,62 @@ static sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, i
 
     const int64_t nblk = blocks_for(total, KM_CHUNK);
     const int use_bloom = lo >= 2 ? 1 : 0;
-    Bloom b1{nullptr, 0, 0x9e3779b97f4a7c15ULL}, b2{nullptr, 0, 0xc2b2ae3d27d4eb4fULL};
+    Bloom b1{nullptr, 0, 0x9e3779b9u}, b2{nullptr, 0, 0x7f4a7c15u};
     if (use_bloom && total > 0) {
-        // B1: 8 bits per window; B2 ("seen twice"): 2 bits per window.
-        b1.nwords = (uint64_t)(total / 8) + 1024;
-        b2.nwords = (uint64_t)(total / 32) + 1024;
-        if (b1.nwords >= (1ull << 32)) b1.nwords = (1ull << 32) - 1;
-        if (b2.nwords >= (1ull << 32)) b2.nwords = (1ull << 32) - 1;
-        b1.words = sc.get<unsigned long long>(b1.nwords);
-        b2.words = sc.get<unsigned long long>(b2.nwords);
+        // B1: 8 bits per window; B2 ("seen twice"): 2 bits per window; 32-bit words
+        const int64_t w1 = total / 4 + 1024, w2 = total / 16 + 1024;
+        b1.nwords = (uint32_t)(w1 < 0xFFFFFFF0LL ? w1 : 0xFFFFFFF0LL);
+        b2.nwords = (uint32_t)(w2 < 0xFFFFFFF0LL ? w2 : 0xFFFFFFF0LL);
+        b1.words = sc.get<uint32_t>(b1.nwords);
+        b2.words = sc.get<uint32_t>(b2.nwords);
         if (!b1.words || !b2.words) return SG_ERR_OOM;
-        SG_CUDA_TRY(cudaMemsetAsync(b1.words, 0, b1.nwords * 8, s));
-        SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, b2.nwords * 8, s));
+        SG_CUDA_TRY(cudaMemsetAsync(b1.words, 0, (size_t)b1.nwords * 4, s));
+        SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, (size_t)b2.nwords * 4, s));
     }
-    // offsets are validated before any kernel that walks them
-    uint32_t herr = 0;
-    SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));
-    if (herr) {
-        set_error("build_kmer_matrix: offsets are not a valid partition of the sequence");
-        return SG_ERR_INVALID;
+    if (use_bloom) {
+        // slices of at most KM_SLICE_BYTES of B1, so each launch's atomics stay in L2
+        const uint64_t slice_words = KM_SLICE_BYTES / 4;
+        const uint64_t nsl = (b1.nwords + slice_words - 1) / slice_words;
+        for (uint64_t q = 0; q < nsl; q++) {
+            const uint32_t lo_w = (uint32_t)((uint64_t)b1.nwords * q / nsl);
+            const uint32_t hi_w = (uint32_t)((uint64_t)b1.nwords * (q + 1) / nsl);
+            SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total,
+                          off, n, k, b1, b2, lo_w, hi_w, jm);
+                return SG_OK;
+            }));
+        }
     }
-    if (use_bloom)
-        SG_LAUNCH("bloom_insert", bloom_insert_kernel, nblk, KM_NT, 0, s, seq, total, off, n, k, b1, b2);
     uint32_t *tcnt = sc.get<uint32_t>(nblk * KM_NT + 1);
     int64_t *tpos = sc.get<int64_t>(nblk * KM_NT + 1);
     if (!tcnt || !tpos) return SG_ERR_OOM;
-    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, seq, total, off, n, k, b2, use_bloom, tcnt);
+    SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
+        SG_LAUNCH("cand_count", cand_count_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n, k, b2,
+                  use_bloom, tcnt, jm);
+        return SG_OK;
+    }));
     SG_TRY(exclusive_scan<uint32_t>(tcnt, tpos, nblk * KM_NT, s));
     int64_t nc = 0;
+    uint32_t herr = 0;
+    SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SG_CUDA_TRY(read_back(&nc, tpos + nblk * KM_NT, sizeof(int64_t), s));
+    if (herr) {  // the passes above stayed in bounds; their results are discarded
+        set_error("build_kmer_matrix: offsets are not a valid partition of the sequence");
+        return SG_ERR_INVALID;
+    }
 
     uint64_t *key0 = sc.get<uint64_t>(nc), *val0 = sc.get<uint64_t>(nc);
     uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
     if (!key0 || !val0 || !key1 || !val1) return SG_ERR_OOM;
-    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, seq, total, off, n, k, b2, use_bloom,
-              (const int64_t *)tpos, key0, val0);
+    SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
+        SG_LAUNCH("cand_emit", cand_emit_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n, k, b2,
+                  use_bloom, (const int64_t *)tpos, key0, val0, jm);
+        return SG_OK;
+    }));
     bool alt = false;
-    SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, 2 * k, &alt, s)));
+    int job_bits = 0;
+    while (jm.ro && ((int64_t)1 << job_bits) < jm.njobs) job_bits++;
+    SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, 2 * k + job_bits, &alt, s)));
     const uint64_t *key = alt ? key1 : key0;
     const uint64_t *val = alt ? val1 : val0;
 
@@ -327,7 +430,7 @@ static sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, i
     SG_LAUNCH("seg_start", seg_start_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, nc, seg_start);
     // number of segments lives on the device at seg_excl[nc]; launch over the upper bound nc
     SG_LAUNCH("seg_reliable", seg_reliable_kernel, blocks_for(nc, NT), NT, 0, s, seg_start, seg_excl + nc, lo,
-              hi, rel);
+              hi, key, lohi, 2 * k, rel);
     SG_TRY(exclusive_scan<uint32_t>(rel, col_of_seg, nc, s));
     SG_LAUNCH("keep", keep_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, rel, val, nc, keep);
     SG_TRY(exclusive_scan<uint32_t>(keep, out_pos, nc, s));
@@ -357,7 +460,8 @@ static sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, i
     uint64_t *av0 = sc.get<uint64_t>(nnz), *av1 = sc.get<uint64_t>(nnz);
     if (!ak0 || !ak1 || !av0 || !av1) return SG_ERR_OOM;
     SG_LAUNCH("emit_at", emit_at_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, head, seg_excl, rel, col_of_seg,
-              keep, out_pos, key, val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0, av0);
+              keep, out_pos, key, val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0, av0, 2 * k,
+              job_ncols);
     int rbits = 0;
     while (rbits < 32 && ((int64_t)1 << rbits) < n) rbits++;
     bool aalt = false;
@@ -367,7 +471,6 @@ static sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, i
     SG_LAUNCH("rowptr_from_sorted", rowptr_from_sorted_kernel, blocks_for(nnz + 1, NT), NT, 0, s, arow, nnz, n,
               A->row_ptr);
     SG_LAUNCH("split_pairs", split_pairs_kernel, blocks_for(nnz, NT), NT, 0, s, apv, nnz, A->col, A->val);
-    SG_CUDA_TRY(cudaStreamSynchronize(s));
     return SG_OK;
 }
 
@@ -385,7 +488,7 @@ extern "C" sg_status sg_build_kmer_matrix(const uint8_t *d_seq, const int64_t *d
     *At = sg_csr_u32{};
     *d_kmer_codes = nullptr;
     if (k < 1 || k > 31 || (k & 1) == 0 || lo < 1 || lo > hi || n_reads < 0 || n_reads >= ((int64_t)1 << 31) ||
-        total_len < 0 || !d_offsets || (total_len > 0 && !d_seq)) {
+        total_len < 0 || !d_offsets || (total_len > 0 && !d_seq) || (n_reads == 0 && total_len != 0)) {
         sg::set_error("build_kmer_matrix: invalid arguments (k=%d lo=%u hi=%u n=%lld total=%lld)", k, lo, hi,
                       (long long)n_reads, (long long)total_len);
         return SG_ERR_INVALID;
@@ -394,7 +497,8 @@ extern "C" sg_status sg_build_kmer_matrix(const uint8_t *d_seq, const int64_t *d
     sg_status st;
     {
         sg::Scratch sc(s);
-        st = sg::build_impl(d_seq, d_offsets, n_reads, total_len, k, lo, hi, A, At, d_kmer_codes, s, sc);
+        st = sg::build_impl(d_seq, d_offsets, n_reads, total_len, k, lo, hi, A, At, d_kmer_codes, s, sc,
+                            sg::JobMap{nullptr, 1, 2 * k}, nullptr, nullptr);
     }
     if (st != SG_OK) {
         sg_free_csr_u32(A, stream);

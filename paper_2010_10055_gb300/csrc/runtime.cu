@@ -27,6 +27,40 @@ static sg_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;
 static std::atomic<int64_t> g_fail_after{0};
 
+// The library's own stream-ordered pool on each device. Its release threshold is unbounded, so
+// memory freed at the end of one call is reused by the next instead of being unmapped at every
+// synchronisation (the default pool's threshold of 0 returns it to the driver each time). The
+// pool belongs to this process and disappears with it.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[256];
+static bool g_pool_tried[256];
+
+static cudaMemPool_t library_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_tried[dev]) {
+        g_pool_tried[dev] = true;
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            g_pools[dev] = pool;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return g_pools[dev];
+}
+
 void *dalloc(size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
     int64_t f = g_fail_after.load();
@@ -42,7 +76,8 @@ void *dalloc(size_t bytes, cudaStream_t s) {
         if (!p) set_error("device allocation of %zu bytes failed (user allocator)", bytes);
         return p;
     }
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
@@ -69,6 +104,7 @@ cudaError_t read_back(void *host, const void *dev, size_t bytes, cudaStream_t s)
 // ---------------------------------------------------------------- launch accounting
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<int> g_prof_on{0};
+static std::string g_prof_prefix;  // only kernels whose name starts with this are timed
 struct PendingEvent { std::string name; cudaEvent_t a, b; };
 static std::mutex g_prof_mu;
 static std::vector<PendingEvent> g_pending;
@@ -92,6 +128,7 @@ LaunchScope::LaunchScope(const char *n, cudaStream_t s) : name(n), stream(s), sl
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (g_prof_on.load(std::memory_order_relaxed)) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_prof_prefix.empty() && strncmp(name, g_prof_prefix.c_str(), g_prof_prefix.size()) != 0) return;
         PendingEvent pe{name, take_event(), take_event()};
         cudaEventRecord(pe.a, s);
         g_pending.push_back(pe);
@@ -125,6 +162,11 @@ void sg_free(void *d_ptr, sg_stream_t stream) { sg::dfree(d_ptr, (cudaStream_t)s
 uint64_t sg_launch_count(void) { return sg::g_launches.load(); }
 
 void sg_prof_enable(int on) { sg::g_prof_on.store(on ? 1 : 0); }
+
+void sg_prof_select(const char *name_prefix) {
+    std::lock_guard<std::mutex> lk(sg::g_prof_mu);
+    sg::g_prof_prefix = name_prefix ? name_prefix : "";
+}
 
 void sg_prof_reset(void) {
     std::lock_guard<std::mutex> lk(sg::g_prof_mu);

@@ -6,150 +6,39 @@
 // Every update below is commutative (a count increment and an insertion into a "smallest S"
 // list), so any parallel order gives the same C bit for bit.
 //
-// Passes:
-//  1. row_work    w_i = sum over j in row i of (nnz(At_j) - 1): products of row i, diagonal excluded.
-//  2. bin rows by hash-table size (power of two >= 2 * min(w_i, n - 1)).
-//  3. symbolic    per row, a hash table keyed by the partner read k with a count per key; records
-//                 nnz_i = #{k : count >= min_shared} and distinct_i = #{k}.
-//  4. scan nnz_i -> C.row_ptr; re-bin rows by 2 * distinct_i.
-//  5. numeric     per row, a hash table (key, count, S seed words). A seed word is
-//                 (index of j within row i) << 32 | At value, so its numeric order is the order
-//                 of j; inserting into the S-slot list is a chain of atomicMin's that pushes the
-//                 loser down. Entries with count >= min_shared are compacted, bitonic-sorted by k
-//                 and written to C; seed positions are resolved from A's row.
-// Tables live in shared memory (one block per row) up to a size limit, else in a global pool.
-#include "prim.cuh"
+// Passes (one thread block per row of C, rows binned by table size):
+//  1. row_work   w_i = sum over j in row i of (nnz(At_j) - 1): products of row i, diagonal excluded.
+//  2. symbolic   a hash table keyed by the partner read k, with a count per key, sized from a
+//                guess (w_i / 2 slots: partners are far fewer than products because every true
+//                overlap shares many k-mers). A row whose table fills past 3/4 is marked and
+//                redone with 2 * min(w_i, n - 1) slots in a per-block global slice.
+//                Records nnz_i = #{k : count >= min_shared} and distinct_i = #{k}.
+//  3. scan nnz_i -> C.row_ptr; numeric classes from distinct_i (exact table sizes).
+//  4. numeric    hash table (key, count, S seed words). A seed word is
+//                (index of j within row i) << 32 | At value, so its numeric order is the order
+//                of j; inserting into the S-slot list is a chain of atomicMin's that pushes the
+//                loser down. Entries with count >= min_shared are compacted, bitonic-sorted by
+//                k and written to C; seed positions are resolved from A's row.
+// Products of a row are enumerated warp by warp: a warp takes 32 consecutive entries of A's row,
+// scans their At row lengths in registers, and walks the flattened product list 32 at a time,
+// each lane finding its entry with a 5-step shuffle search.
+#include "ops.cuh"
 
 namespace sg {
 
-constexpr int SP_NT = 256;
-constexpr int SP_NT_BIG = 512;
-constexpr int SP_CH = 1024;  // A entries staged per chunk
 constexpr int SP_MAX_SEEDS = 8;
 constexpr uint64_t SEED_NONE = ~0ull;
+constexpr int SP_NCLS = 4;        // shared-memory classes per pass
+constexpr int SP_GRID = 152 * 8;  // blocks per class launch (grid-stride over the class's rows)
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t k, int log2T) {
     return ((uint32_t)k * 2654435761u) >> (32 - log2T);
 }
 
-// Find or insert key k; returns its slot. T = 1 << log2T, never full (load <= 1/2).
-__device__ __forceinline__ uint32_t table_slot(int32_t *keys, int32_t k, int log2T) {
-    const uint32_t msk = (1u << log2T) - 1u;
-    uint32_t h = hash_slot(k, log2T);
-    for (;;) {
-        int32_t cur = ((volatile int32_t *)keys)[h];
-        if (cur == k) return h;
-        if (cur == -1) {
-            int32_t old = atomicCAS(keys + h, -1, k);
-            if (old == -1 || old == k) return h;
-        }
-        h = (h + 1) & msk;
-    }
-}
-
-__global__ void row_work_kernel(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
-                                const int64_t *__restrict__ t_rp, int64_t n, int64_t *__restrict__ work) {
-    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    int64_t w = 0;
-    for (int64_t a = a_rp[row] + lane; a < a_rp[row + 1]; a += 32) {
-        int32_t j = a_col[a];
-        w += t_rp[j + 1] - t_rp[j] - 1;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (lane == 0) work[row] = w;
-}
-
-// Bin classes: log2 of the table size. Classes 0..NB-1 are shared-memory bins with table sizes
-// 2^min_log2[c]..; the last class is the global-memory bin.
-struct Bins {
-    static constexpr int NB = 5;  // 4 smem classes + 1 global
-    int log2T[NB - 1];            // table size of each smem class
-    int nsmem;                    // smem classes in use (the rest go global)
-};
-
-// bin[i] = class of row i (or -1 when the row has no products); counts[c]++; for the global
-// class, gsize[i] = table slots needed.
-__global__ void bin_kernel(const int64_t *__restrict__ ub, int64_t n, int64_t cap, Bins bins,
-                           int32_t *__restrict__ bin, unsigned long long *__restrict__ counts,
-                           int64_t *__restrict__ gsize) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t u = ub[i] < cap ? ub[i] : cap;
-    int b = -1;
-    int64_t g = 0;
-    if (u > 0) {
-        int l = 0;
-        while (((int64_t)1 << l) < 2 * u) l++;
-        b = bins.nsmem;
-        for (int c = 0; c < bins.nsmem; c++)
-            if (l <= bins.log2T[c]) { b = c; break; }
-        if (b == bins.nsmem) g = (int64_t)1 << l;
-        atomicAdd(counts + b, 1ull);
-    }
-    bin[i] = b;
-    gsize[i] = g;
-}
-
-__global__ void bin_fill_kernel(const int32_t *__restrict__ bin, int64_t n, const int64_t *__restrict__ base,
-                                unsigned long long *__restrict__ cursor, int32_t *__restrict__ rows) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int b = bin[i];
-    if (b < 0) return;
-    unsigned long long p = atomicAdd(cursor + b, 1ull);
-    rows[base[b] + (int64_t)p] = (int32_t)i;
-}
-
-// Staging of one chunk of row i of A: the columns, At row starts, and the exclusive prefix of
-// At row lengths. Returns the number of products of the chunk.
-template <int NT>
-__device__ __forceinline__ int64_t stage_chunk(const int64_t *__restrict__ t_rp, const int32_t *__restrict__ a_col,
-                                               int64_t a0, int cnt, int32_t *s_j, int64_t *s_beg,
-                                               int64_t *s_pre, int64_t *s_tmp) {
-    int64_t len = 0;
-    int64_t beg = 0;
-    int32_t j = 0;
-    // each thread owns SP_CH / NT consecutive entries
-    constexpr int PER = SP_CH / NT;
-    int64_t loc[PER];
-    int64_t sum = 0;
-#pragma unroll
-    for (int q = 0; q < PER; q++) {
-        int c = threadIdx.x * PER + q;
-        len = 0;
-        if (c < cnt) {
-            j = a_col[a0 + c];
-            beg = t_rp[j];
-            len = t_rp[j + 1] - beg;
-            s_j[c] = j;
-            s_beg[c] = beg;
-        }
-        loc[q] = sum;
-        sum += len;
-    }
-    int64_t total;
-    int64_t pre = block_exclusive_scan<NT>(sum, s_tmp, &total);
-#pragma unroll
-    for (int q = 0; q < PER; q++) {
-        int c = threadIdx.x * PER + q;
-        if (c < cnt) s_pre[c] = pre + loc[q];
-    }
-    if (threadIdx.x == 0) s_pre[cnt] = total;
-    __syncthreads();
-    return total;
-}
-
-// index c in [0, cnt) with s_pre[c] <= p < s_pre[c + 1]
-__device__ __forceinline__ int find_chunk_entry(const int64_t *s_pre, int cnt, int64_t p) {
-    int lo = 0, hi = cnt;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (s_pre[mid] <= p) lo = mid; else hi = mid;
-    }
-    return lo;
+__host__ __device__ __forceinline__ int64_t pow2_at_least(int64_t x) {
+    int64_t t = 1;
+    while (t < x) t <<= 1;
+    return t;
 }
 
 struct SpArgs {
@@ -159,59 +48,192 @@ struct SpArgs {
     const int64_t *t_rp;
     const int32_t *t_col;
     const uint32_t *t_val;
+    const int64_t *a_beg;     // per A entry (i, j): start of At row j
+    const uint32_t *a_len;    // per A entry: length of At row j
+    const uint64_t *t_pair;   // At entries as (val << 32 | col): one sector per product
     int64_t n;
     uint32_t min_shared;
     int S;
     uint32_t *err;  // DEV_OVERFLOW if the numeric pass ever disagrees with the symbolic sizes
 };
 
+// One warp per row: w_i, and for every entry (i, j) the start and length of At row j, so that
+// the two passes stream these instead of gathering At's row pointers at random.
+__global__ void row_work_kernel(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
+                                const int64_t *__restrict__ t_rp, int64_t n, int64_t *__restrict__ work,
+                                int64_t *__restrict__ a_beg, uint32_t *__restrict__ a_len) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    int64_t w = 0;
+    for (int64_t a = a_rp[row] + lane; a < a_rp[row + 1]; a += 32) {
+        const int32_t j = a_col[a];
+        const int64_t b = t_rp[j], e = t_rp[j + 1];
+        a_beg[a] = b;
+        a_len[a] = (uint32_t)(e - b);
+        w += e - b - 1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) work[row] = w;
+}
+
+// Row classes: a row whose table needs at most 2^log2T[c] slots goes to class c; larger rows go
+// to the global class (index ncls). lists[c * n + x] = rows of class c; counts[c] = its size.
+struct Classes {
+    int log2T[SP_NCLS];
+    int ncls;
+};
+
+__global__ void classify_kernel(const int64_t *__restrict__ need, int64_t n, Classes cl,
+                                unsigned long long *__restrict__ counts, int32_t *__restrict__ lists) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t u = need[i];
+    if (u <= 0) return;
+    int c = cl.ncls;
+    for (int q = 0; q < cl.ncls; q++)
+        if (u <= ((int64_t)1 << cl.log2T[q])) { c = q; break; }
+    unsigned long long p = atomicAdd(counts + c, 1ull);
+    lists[(int64_t)c * n + (int64_t)p] = (int32_t)i;
+}
+
+// symbolic table request: nextpow2(max(64, w / 2)), capped at the exact bound 2 * min(w, n - 1)
+__global__ void sym_need_kernel(const int64_t *__restrict__ work, int64_t n, int64_t *__restrict__ need) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t w = work[i];
+    if (w <= 0) { need[i] = 0; return; }
+    int64_t exact = pow2_at_least(2 * (w < n - 1 ? w : n - 1));
+    int64_t guess = pow2_at_least(w / 2 > 64 ? w / 2 : 64);
+    need[i] = guess < exact ? guess : exact;
+}
+
+// numeric table request: nextpow2(2 * distinct), at least 64
+__global__ void num_need_kernel(const int64_t *__restrict__ dist, int64_t n, int64_t *__restrict__ need) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t d = dist[i];
+    need[i] = d > 0 ? pow2_at_least(2 * d > 64 ? 2 * d : 64) : 0;
+}
+
+// ------------------------------------------------------------------- product enumeration
+// Calls f(k, vk, idx) for every product of row i: k = partner read (k != i), vk = the At value
+// (PAIR only), idx = index of the A entry within row i. Stops (per warp) once *stop is nonzero.
+template <bool PAIR, class F>
+__device__ __forceinline__ void for_each_product(const SpArgs &g, int32_t i, int64_t r0, int64_t r1,
+                                                 const volatile int *stop, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t a0 = r0 + (int64_t)warp * 32; a0 < r1; a0 += (int64_t)nwarps * 32) {
+        if (stop && *stop) return;
+        const int64_t a = a0 + lane;
+        int64_t beg = 0, len = 0;
+        if (a < r1) {
+            beg = g.a_beg[a];
+            len = g.a_len[a];
+        }
+        int64_t inc = len;  // inclusive scan of the lengths across the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int64_t excl = inc - len;
+        const int64_t total = __shfl_sync(0xffffffffu, inc, 31);
+        for (int64_t base = 0; base < total; base += 32) {
+            const int64_t p = base + lane;
+            int owner = 0;  // largest lane whose exclusive prefix is <= p
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int64_t v = __shfl_sync(0xffffffffu, excl, (owner + s) & 31);
+                if (owner + s < 32 && v <= p) owner += s;
+            }
+            const int64_t ob = __shfl_sync(0xffffffffu, beg, owner);
+            const int64_t oe = __shfl_sync(0xffffffffu, excl, owner);
+            if (p < total) {
+                const int64_t b = ob + (p - oe);
+                if (PAIR) {
+                    const uint64_t pr = g.t_pair[b];
+                    const int32_t k = (int32_t)(uint32_t)pr;
+                    if (k != i) f(k, (uint32_t)(pr >> 32), a0 - r0 + owner);
+                } else {
+                    const int32_t k = g.t_col[b];
+                    if (k != i) f(k, 0u, a0 - r0 + owner);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------- symbolic
-template <int NT, bool GMEM>
-__global__ void __launch_bounds__(NT) symbolic_kernel(SpArgs g, const int32_t *__restrict__ rows, int64_t nrows,
-                                                     int log2T, int32_t *__restrict__ gpool,
-                                                     const int64_t *__restrict__ goff, int64_t *__restrict__ nnz_row,
-                                                     int64_t *__restrict__ distinct_row) {
-    extern __shared__ __align__(16) unsigned char sp_raw[];
-    int32_t *s_j = (int32_t *)sp_raw;
-    int64_t *s_beg = (int64_t *)(s_j + SP_CH);
-    int64_t *s_pre = s_beg + SP_CH;
-    int64_t *s_tmp = s_pre + SP_CH + 2;
-    int32_t *tab = (int32_t *)(s_tmp + 32);  // keys [T] then counts [T]
-    __shared__ int32_t s_red[2 * (NT / 32)];
+// Table in shared memory (GSLICE == false, 2^log2T slots, may overflow) or in this block's slice
+// of a global pool (GSLICE == true, 2 * min(w_i, n - 1) slots rounded up: never overflows).
+template <bool GSLICE>
+__global__ void __launch_bounds__(512) symbolic_kernel(SpArgs g, const int32_t *__restrict__ rows,
+                                                      const unsigned long long *__restrict__ nrows_p, int log2T,
+                                                      const int64_t *__restrict__ work, int32_t *__restrict__ gpool,
+                                                      int64_t slice, int32_t *__restrict__ ovf_list,
+                                                      unsigned long long *__restrict__ ovf_count,
+                                                      int64_t *__restrict__ nnz_row, int64_t *__restrict__ distinct_row) {
+    extern __shared__ __align__(16) int32_t sym_tab[];
+    __shared__ int s_ins, s_ovf;
+    __shared__ int32_t s_red[2 * 16];
+    const int64_t nrows = (int64_t)*nrows_p;
     for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
         const int32_t i = rows[rb];
         int lT = log2T;
-        int32_t *keys;
-        if (GMEM) {
-            const int64_t T = goff[i + 1] - goff[i];  // a power of two
-            keys = gpool + 2 * goff[i];
+        int32_t *keys = sym_tab;
+        if (GSLICE) {
+            const int64_t w = work[i];
+            const int64_t T = pow2_at_least(2 * (w < g.n - 1 ? w : g.n - 1));
             lT = 0;
             while (((int64_t)1 << lT) < T) lT++;
-        } else {
-            keys = tab;
+            keys = gpool + (int64_t)blockIdx.x * slice;
         }
         const int32_t T = 1 << lT;
         uint32_t *cnt = (uint32_t *)(keys + T);
-        for (int x = threadIdx.x; x < T; x += NT) {
+        const int cap = GSLICE ? T : (T >> 1) + (T >> 2);
+        for (int x = threadIdx.x; x < T; x += blockDim.x) {
             keys[x] = -1;
             cnt[x] = 0;
         }
+        if (threadIdx.x == 0) {
+            s_ins = 0;
+            s_ovf = 0;
+        }
         __syncthreads();
-        const int64_t r0 = g.a_rp[i], r1 = g.a_rp[i + 1];
-        for (int64_t a0 = r0; a0 < r1; a0 += SP_CH) {
-            int cntc = (int)((r1 - a0) < SP_CH ? (r1 - a0) : SP_CH);
-            int64_t P = stage_chunk<NT>(g.t_rp, g.a_col, a0, cntc, s_j, s_beg, s_pre, s_tmp);
-            for (int64_t p = threadIdx.x; p < P; p += NT) {
-                int c = find_chunk_entry(s_pre, cntc, p);
-                int32_t k = g.t_col[s_beg[c] + (p - s_pre[c])];
-                if (k == i) continue;
-                uint32_t h = table_slot(keys, k, lT);
-                atomicAdd(cnt + h, 1u);
+        const uint32_t msk = (uint32_t)T - 1u;
+        for_each_product<false>(g, i, g.a_rp[i], g.a_rp[i + 1], GSLICE ? nullptr : &s_ovf,
+                                [&](int32_t k, uint32_t, int64_t) {
+            uint32_t h = hash_slot(k, lT);
+            for (int probe = 0; probe < T; probe++) {
+                int32_t cur = ((volatile int32_t *)keys)[h];
+                if (cur == -1) {
+                    const int32_t old = atomicCAS(keys + h, -1, k);
+                    if (old == -1) {
+                        if (atomicAdd(&s_ins, 1) >= cap) s_ovf = 1;
+                        atomicAdd(cnt + h, 1u);
+                        return;
+                    }
+                    cur = old;
+                }
+                if (cur == k) {
+                    atomicAdd(cnt + h, 1u);
+                    return;
+                }
+                h = (h + 1) & msk;
             }
+            s_ovf = 1;  // went round the whole table
+        });
+        __syncthreads();
+        if (s_ovf) {  // table too small for this row: the global-slice pass redoes it
+            if (threadIdx.x == 0) ovf_list[atomicAdd(ovf_count, 1ull)] = i;
             __syncthreads();
+            continue;
         }
         int32_t nz = 0, dist = 0;
-        for (int x = threadIdx.x; x < T; x += NT) {
+        for (int x = threadIdx.x; x < T; x += blockDim.x) {
             if (keys[x] != -1) {
                 dist++;
                 if (cnt[x] >= g.min_shared) nz++;
@@ -229,7 +251,7 @@ __global__ void __launch_bounds__(NT) symbolic_kernel(SpArgs g, const int32_t *_
         __syncthreads();
         if (threadIdx.x == 0) {
             int64_t a = 0, b = 0;
-            for (int w = 0; w < NT / 32; w++) {
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
                 a += s_red[2 * w];
                 b += s_red[2 * w + 1];
             }
@@ -241,94 +263,91 @@ __global__ void __launch_bounds__(NT) symbolic_kernel(SpArgs g, const int32_t *_
 }
 
 // ----------------------------------------------------------------------------- numeric
-template <int NT, bool GMEM>
-__global__ void __launch_bounds__(NT) numeric_kernel(SpArgs g, const int32_t *__restrict__ rows, int64_t nrows,
-                                                    int log2T, int tab_off, unsigned char *__restrict__ gpool,
-                                                    const int64_t *__restrict__ goff,
-                                                    const int64_t *__restrict__ c_rp, int32_t *__restrict__ c_col,
-                                                    uint32_t *__restrict__ c_cnt, uint32_t *__restrict__ c_si,
-                                                    uint32_t *__restrict__ c_sk, int64_t c_nnz) {
-    extern __shared__ __align__(16) unsigned char sp_raw[];
-    // chunk staging region (reused as the output sort buffer once accumulation is done)
-    int32_t *s_j = (int32_t *)sp_raw;
-    int64_t *s_beg = (int64_t *)(s_j + SP_CH);
-    int64_t *s_pre = s_beg + SP_CH;
-    int64_t *s_tmp = s_pre + SP_CH + 2;
-    unsigned char *tab_smem = sp_raw + tab_off;  // tab_off >= staging bytes and >= T/2 * 8
-    __shared__ int s_ctr[1];
+// One table of T slots: seeds [T][S] u64 | keys [T] i32 | counts [T] u32 | sort buffer [T/2] u64,
+// in shared memory (GSLICE == false) or in this block's global slice.
+__host__ __device__ inline size_t num_table_bytes(int64_t T, int S) {
+    return (size_t)T * (8 * (size_t)S + 8) + (size_t)(T / 2) * 8;
+}
+
+template <bool GSLICE>
+__global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
+                                                     const unsigned long long *__restrict__ nrows_p, int log2T,
+                                                     const int64_t *__restrict__ need, unsigned char *__restrict__ gpool,
+                                                     int64_t slice_bytes, const int64_t *__restrict__ c_rp,
+                                                     int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
+                                                     uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
+                                                     int64_t c_nnz) {
+    extern __shared__ __align__(16) unsigned char num_raw[];
+    __shared__ int s_ctr;
     const int S = g.S;
+    const int64_t nrows = (int64_t)*nrows_p;
     for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
         const int32_t i = rows[rb];
         int lT = log2T;
-        unsigned char *tb;
-        uint64_t *obuf;
-        if (GMEM) {
-            int64_t T = goff[i + 1] - goff[i];
+        unsigned char *tb = num_raw;
+        if (GSLICE) {
+            const int64_t T = need[i];
             lT = 0;
             while (((int64_t)1 << lT) < T) lT++;
-            // per slot: 8 (key, count) + 8 S (seeds) + 8 (sort buffer of T/2 u64, padded to keep
-            // every row 8-byte aligned)
-            tb = gpool + goff[i] * (int64_t)(16 + 8 * S);
-            obuf = (uint64_t *)(tb + ((int64_t)1 << lT) * (8 + 8 * S));
-        } else {
-            tb = tab_smem;
-            obuf = (uint64_t *)sp_raw;
+            tb = gpool + (int64_t)blockIdx.x * slice_bytes;
         }
         const int32_t T = 1 << lT;
-        uint64_t *seeds = (uint64_t *)tb;                 // [T][S]
+        uint64_t *seeds = (uint64_t *)tb;
         int32_t *keys = (int32_t *)(seeds + (int64_t)T * S);
         uint32_t *cnt = (uint32_t *)(keys + T);
-        for (int x = threadIdx.x; x < T; x += NT) {
+        uint64_t *obuf = (uint64_t *)(cnt + T);
+        for (int x = threadIdx.x; x < T; x += blockDim.x) {
             keys[x] = -1;
             cnt[x] = 0;
         }
-        for (int x = threadIdx.x; x < T * S; x += NT) seeds[x] = SEED_NONE;
-        if (threadIdx.x == 0) s_ctr[0] = 0;
+        for (int x = threadIdx.x; x < T * S; x += blockDim.x) seeds[x] = SEED_NONE;
+        if (threadIdx.x == 0) s_ctr = 0;
         __syncthreads();
         const int64_t r0 = g.a_rp[i], r1 = g.a_rp[i + 1];
-        for (int64_t a0 = r0; a0 < r1; a0 += SP_CH) {
-            int cntc = (int)((r1 - a0) < SP_CH ? (r1 - a0) : SP_CH);
-            int64_t P = stage_chunk<NT>(g.t_rp, g.a_col, a0, cntc, s_j, s_beg, s_pre, s_tmp);
-            for (int64_t p = threadIdx.x; p < P; p += NT) {
-                int c = find_chunk_entry(s_pre, cntc, p);
-                int64_t b = s_beg[c] + (p - s_pre[c]);
-                int32_t k = g.t_col[b];
-                if (k == i) continue;
-                uint32_t h = table_slot(keys, k, lT);
-                atomicAdd(cnt + h, 1u);
-                if (S > 0) {
-                    // seed word: (index of j within row i) << 32 | value of At_jk
-                    unsigned long long v = ((unsigned long long)(a0 - r0 + c) << 32) | g.t_val[b];
-                    unsigned long long *sl = (unsigned long long *)(seeds + (int64_t)h * S);
-                    for (int q = 0; q < S; q++) {
-                        unsigned long long old = atomicMin(sl + q, v);
-                        if (old > v) v = old;  // the larger one moves on to the next slot
-                        if (v == SEED_NONE) break;
-                    }
+        const uint32_t msk = (uint32_t)T - 1u;
+        for_each_product<true>(g, i, r0, r1, nullptr, [&](int32_t k, uint32_t vk, int64_t idx) {
+            uint32_t h = hash_slot(k, lT);
+            for (;;) {  // T >= 2 * distinct_i: a free slot or k is always found
+                int32_t cur = ((volatile int32_t *)keys)[h];
+                if (cur == -1) {
+                    const int32_t old = atomicCAS(keys + h, -1, k);
+                    if (old == -1 || old == k) break;
+                    cur = old;
+                }
+                if (cur == k) break;
+                h = (h + 1) & msk;
+            }
+            atomicAdd(cnt + h, 1u);
+            if (S > 0) {
+                unsigned long long v = ((unsigned long long)idx << 32) | vk;
+                unsigned long long *sl = (unsigned long long *)(seeds + (int64_t)h * S);
+                for (int q = 0; q < S; q++) {
+                    const unsigned long long old = atomicMin(sl + q, v);
+                    if (old > v) v = old;  // the larger one moves on to the next slot
+                    if (v == SEED_NONE) break;
                 }
             }
-            __syncthreads();
-        }
-        // compact entries with count >= min_shared as (k << 32 | slot)
-        for (int x = threadIdx.x; x < T; x += NT) {
+        });
+        __syncthreads();
+        for (int x = threadIdx.x; x < T; x += blockDim.x) {
             if (keys[x] != -1 && cnt[x] >= g.min_shared) {
-                int p = atomicAdd(s_ctr, 1);
+                const int p = atomicAdd(&s_ctr, 1);
                 obuf[p] = ((uint64_t)(uint32_t)keys[x] << 32) | (uint32_t)x;
             }
         }
         __syncthreads();
-        const int nv = s_ctr[0];
+        const int nv = s_ctr;
         int P2 = 1;
         while (P2 < nv) P2 <<= 1;
-        for (int x = nv + threadIdx.x; x < P2; x += NT) obuf[x] = ~0ull;
+        for (int x = nv + threadIdx.x; x < P2; x += blockDim.x) obuf[x] = ~0ull;
         __syncthreads();
         for (int kk = 2; kk <= P2; kk <<= 1) {
             for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                for (int x = threadIdx.x; x < P2; x += NT) {
-                    int y = x ^ jj;
+                for (int x = threadIdx.x; x < P2; x += blockDim.x) {
+                    const int y = x ^ jj;
                     if (y > x) {
-                        uint64_t a = obuf[x], b = obuf[y];
-                        bool up = (x & kk) == 0;
+                        const uint64_t a = obuf[x], b = obuf[y];
+                        const bool up = (x & kk) == 0;
                         if ((a > b) == up) {
                             obuf[x] = b;
                             obuf[y] = a;
@@ -342,18 +361,18 @@ __global__ void __launch_bounds__(NT) numeric_kernel(SpArgs g, const int32_t *__
         const int64_t room = c_rp[i + 1] - e0;
         if (nv != room && threadIdx.x == 0) atomicOr(g.err, (uint32_t)DEV_OVERFLOW);
         const int nw = nv < room ? nv : (int)room;
-        for (int q = threadIdx.x; q < nw; q += NT) {
-            uint64_t w = obuf[q];
-            uint32_t slot = (uint32_t)w;
-            int64_t e = e0 + q;
+        for (int q = threadIdx.x; q < nw; q += blockDim.x) {
+            const uint64_t w = obuf[q];
+            const uint32_t slot = (uint32_t)w;
+            const int64_t e = e0 + q;
             c_col[e] = (int32_t)(w >> 32);
             c_cnt[e] = cnt[slot];
             for (int s = 0; s < S; s++) {
-                uint64_t sd = seeds[(int64_t)slot * S + s];
+                const uint64_t sd = seeds[(int64_t)slot * S + s];
                 uint32_t si = 0xFFFFFFFFu, sk = 0xFFFFFFFFu;
                 if (sd != SEED_NONE) {
-                    uint32_t vi = g.a_val[r0 + (int64_t)(sd >> 32)];
-                    uint32_t vk = (uint32_t)sd;
+                    const uint32_t vi = g.a_val[r0 + (int64_t)(sd >> 32)];
+                    const uint32_t vk = (uint32_t)sd;
                     si = vi & 0x7FFFFFFFu;
                     sk = (vk & 0x7FFFFFFFu) | ((vi ^ vk) & 0x80000000u);
                 }
@@ -367,119 +386,91 @@ __global__ void __launch_bounds__(NT) numeric_kernel(SpArgs g, const int32_t *__
 
 static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
 
-static size_t chunk_bytes() { return SP_CH * 4 + SP_CH * 8 + (SP_CH + 2) * 8 + 32 * 8; }
-static size_t symbolic_smem(int log2T) { return chunk_bytes() + (size_t)(2 << log2T) * 4; }
-// the output sort buffer (T/2 u64) overlaps the staging region; the table follows both
-static size_t numeric_tab_off(int log2T) {
-    size_t T = (size_t)1 << log2T;
-    size_t stage = chunk_bytes();
-    if (stage < T / 2 * 8) stage = T / 2 * 8;
-    return (stage + 15) & ~(size_t)15;
-}
-static size_t numeric_smem(int log2T, int S) {
-    return numeric_tab_off(log2T) + ((size_t)1 << log2T) * (8 + 8 * (size_t)S);
+__global__ void pair_kernel(const int32_t *__restrict__ col, const uint32_t *__restrict__ val, int64_t nnz,
+                            uint64_t *__restrict__ pair) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) pair[e] = ((uint64_t)val[e] << 32) | (uint32_t)col[e];
 }
 
-// Bins rows by table size and returns per-class row lists. ub[i] = upper bound of keys of row i.
-struct BinResult {
-    int64_t count[Bins::NB];
-    int64_t base[Bins::NB + 1];
-    int32_t *rows;   // rows of class c at rows[base[c] .. base[c+1])
-    int64_t *goff;   // [n+1] exclusive scan of global table sizes (slots)
-    int64_t gtotal;  // global pool slots
-};
+static int pick_threads(int log2T) { return log2T <= 10 ? 128 : 256; }
 
-static sg_status bin_rows(const int64_t *ub, int64_t n, const Bins &bins, Scratch &sc, cudaStream_t s,
-                          BinResult *out) {
-    const int NT = 256;
-    int32_t *bin = sc.get<int32_t>(n + 1);
-    unsigned long long *counts = sc.get<unsigned long long>(2 * Bins::NB);
-    int64_t *gsize = sc.get<int64_t>(n + 1);
-    out->goff = sc.get<int64_t>(n + 1);
-    int64_t *dbase = sc.get<int64_t>(Bins::NB + 1);
-    out->rows = sc.get<int32_t>(n + 1);
-    if (!bin || !counts || !gsize || !out->goff || !dbase || !out->rows) return SG_ERR_OOM;
-    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, 2 * Bins::NB * sizeof(unsigned long long), s));
-    SG_LAUNCH("bin_rows", bin_kernel, blocks_for(n, NT), NT, 0, s, ub, n, (int64_t)(n > 0 ? n - 1 : 0), bins, bin,
-              counts, gsize);
-    SG_TRY(exclusive_scan<int64_t>(gsize, out->goff, n, s));
-    unsigned long long hc[Bins::NB];
-    SG_CUDA_TRY(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(cudaMemcpyAsync(&out->gtotal, out->goff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(cudaStreamSynchronize(s));
-    out->base[0] = 0;
-    for (int c = 0; c < Bins::NB; c++) {
-        out->count[c] = (int64_t)hc[c];
-        out->base[c + 1] = out->base[c] + out->count[c];
-    }
-    SG_CUDA_TRY(cudaMemcpyAsync(dbase, out->base, sizeof(int64_t) * (Bins::NB + 1), cudaMemcpyHostToDevice, s));
-    SG_LAUNCH("bin_fill", bin_fill_kernel, blocks_for(n, NT), NT, 0, s, bin, n, dbase, counts + Bins::NB,
-              out->rows);
-    return SG_OK;
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-static int grid_for(int64_t rows) {
-    int64_t g = rows < 152 * 16 ? rows : 152 * 16;
-    return (int)(g > 0 ? g : 0);
-}
-
-static sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S,
-                              sg_overlap_csr *C, cudaStream_t s, Scratch &sc) {
+sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S,
+                       sg_overlap_csr *C, cudaStream_t s, Scratch &sc) {
     const int64_t n = A->n_rows;
+    const int NT = 256;
+    constexpr int NCNT = SP_NCLS + 2;  // classes + global class + overflow counter
     uint32_t *err = sc.get<uint32_t>(1);
-    if (!err) return SG_ERR_OOM;
-    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-    SpArgs g{A->row_ptr, A->col, A->val, At->row_ptr, At->col, At->val, n, min_shared, S, err};
     int64_t *work = sc.get<int64_t>(n + 1);
+    int64_t *need = sc.get<int64_t>(n + 1);
     int64_t *nnz_row = sc.get<int64_t>(n + 1);
     int64_t *dist = sc.get<int64_t>(n + 1);
-    if (!work || !nnz_row || !dist) return SG_ERR_OOM;
+    unsigned long long *counts = sc.get<unsigned long long>(2 * NCNT + 1);
+    int32_t *lists = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
+    int32_t *ovf = sc.get<int32_t>(2 * (n + 1));  // overflow list | unused list of the re-run
+    if (!err || !work || !need || !nnz_row || !dist || !counts || !lists || !ovf) return SG_ERR_OOM;
+    unsigned long long *sym_counts = counts, *num_counts = counts + NCNT, *unused = counts + 2 * NCNT;
+    unsigned long long *ovf_count = counts + SP_NCLS + 1;
+    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (2 * NCNT + 1) * sizeof(unsigned long long), s));
     SG_CUDA_TRY(cudaMemsetAsync(nnz_row, 0, (n + 1) * sizeof(int64_t), s));
     SG_CUDA_TRY(cudaMemsetAsync(dist, 0, (n + 1) * sizeof(int64_t), s));
+    int64_t *a_beg = sc.get<int64_t>(A->nnz + 1);
+    uint32_t *a_len = sc.get<uint32_t>(A->nnz + 1);
+    uint64_t *t_pair = sc.get<uint64_t>(At->nnz + 1);
+    if (!a_beg || !a_len || !t_pair) return SG_ERR_OOM;
+    SpArgs g{A->row_ptr, A->col, A->val, At->row_ptr, At->col, At->val, a_beg, a_len, t_pair,
+             n, min_shared, S, err};
     SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr, n,
-              work);
+              work, a_beg, a_len);
+    SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
 
-    // symbolic: smem classes up to 2^14 slots (128 KB of keys + counts)
-    Bins sb{};
-    sb.nsmem = 4;
-    sb.log2T[0] = 8; sb.log2T[1] = 10; sb.log2T[2] = 12; sb.log2T[3] = 14;
-    BinResult br{};
-    SG_TRY(bin_rows(work, n, sb, sc, s, &br));
-    int32_t *gpool_sym = nullptr;
-    const int sg_glob = sb.nsmem;  // index of the global-memory class
-    if (br.count[sg_glob] > 0) {
-        gpool_sym = sc.get<int32_t>(2 * br.gtotal);
-        if (!gpool_sym) return SG_ERR_OOM;
+    // ---- symbolic: guessed shared-memory tables of 2^8 .. 2^14 slots
+    const Classes sym{{8, 10, 12, 14}, 4};
+    SG_LAUNCH("sym_need", sym_need_kernel, blocks_for(n, NT), NT, 0, s, work, n, need);
+    SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, sym, sym_counts, lists);
+    for (int c = 0; c < sym.ncls; c++) {
+        const size_t sm = (size_t)(2 << sym.log2T[c]) * sizeof(int32_t);
+        SG_CUDA_TRY(allow_smem(symbolic_kernel<false>, sm));
+        SG_LAUNCH("spgemm_symbolic", symbolic_kernel<false>, SP_GRID, pick_threads(sym.log2T[c]), sm, s, g,
+                  lists + (int64_t)c * n, sym_counts + c, sym.log2T[c], (const int64_t *)work, (int32_t *)nullptr,
+                  (int64_t)0, ovf, ovf_count, nnz_row, dist);
     }
-    for (int c = 0; c < sb.nsmem; c++) {
-        if (!br.count[c]) continue;
-        size_t sm = symbolic_smem(sb.log2T[c]);
-        SG_CUDA_TRY(cudaFuncSetAttribute(symbolic_kernel<SP_NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm));
-        SG_LAUNCH("spgemm_symbolic", (symbolic_kernel<SP_NT, false>), grid_for(br.count[c]), SP_NT, sm, s, g,
-                  br.rows + br.base[c], br.count[c], sb.log2T[c], (int32_t *)nullptr, (const int64_t *)nullptr,
-                  nnz_row, dist);
-    }
-    if (br.count[sg_glob]) {
-        size_t sm = chunk_bytes();
-        SG_LAUNCH("spgemm_symbolic_gmem", (symbolic_kernel<SP_NT_BIG, true>), grid_for(br.count[sg_glob]),
-                  SP_NT_BIG, sm, s, g, br.rows + br.base[sg_glob], br.count[sg_glob], 0, gpool_sym,
-                  (const int64_t *)br.goff, nnz_row, dist);
+    // rows too large for any shared-memory table, and rows whose guessed table overflowed
+    unsigned long long h_sym[NCNT];
+    SG_CUDA_TRY(read_back(h_sym, sym_counts, sizeof(h_sym), s));
+    const unsigned long long n_big = h_sym[sym.ncls], n_ovf = h_sym[SP_NCLS + 1];
+    if (n_big + n_ovf > 0) {
+        const int64_t slice = 2 * pow2_at_least(2 * (n > 1 ? n - 1 : 1));  // keys + counts of the largest row
+        const unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
+        const int grid = (int)(rows_g < 152 * 2 ? rows_g : 152 * 2);
+        int32_t *pool = sc.get<int32_t>((size_t)slice * grid);
+        if (!pool) return SG_ERR_OOM;
+        if (n_big)
+            SG_LAUNCH("spgemm_symbolic_gmem", symbolic_kernel<true>, grid, 512, 0, s, g,
+                      lists + (int64_t)sym.ncls * n, sym_counts + sym.ncls, 0, (const int64_t *)work, pool, slice,
+                      ovf, ovf_count, nnz_row, dist);
+        if (n_ovf)  // global-slice tables never overflow, so this pass never appends to the list
+            SG_LAUNCH("spgemm_symbolic_gmem", symbolic_kernel<true>, grid, 512, 0, s, g, (const int32_t *)ovf,
+                      ovf_count, 0, (const int64_t *)work, pool, slice, ovf + n + 1, unused, nnz_row, dist);
     }
 
-    // C row pointers
+    // ---- C row pointers; numeric classes from the exact distinct counts
     SG_ALLOC(C->row_ptr, int64_t, n + 1, s);
     SG_TRY(exclusive_scan<int64_t>(nnz_row, C->row_ptr, n, s));
-
-    // numeric bins from the exact distinct-key counts
-    Bins nb{};
-    nb.nsmem = 0;
-    const int lmax = S <= 2 ? 12 : (S <= 4 ? 11 : 10);  // keep the table + staging under ~120 KB
-    for (int l = 8; l <= lmax && nb.nsmem < Bins::NB - 1; l += 2) nb.log2T[nb.nsmem++] = l;
-    if (nb.log2T[nb.nsmem - 1] != lmax) nb.log2T[nb.nsmem - 1] = lmax;
-    BinResult nr{};
-    SG_TRY(bin_rows(dist, n, nb, sc, s, &nr));  // synchronises: C.row_ptr is complete too
+    Classes num{{8, 10, 11, 12}, 4};  // table + sort buffer <= 112 KB for max_seeds <= 2
+    if (S > 2) num = Classes{{8, 9, 10, 11}, 4};
+    if (S > 4) num = Classes{{7, 8, 9, 10}, 4};
+    SG_LAUNCH("num_need", num_need_kernel, blocks_for(n, NT), NT, 0, s, dist, n, need);
+    SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, num, num_counts, lists);
     int64_t nnz = 0;
+    unsigned long long h_num[NCNT];
+    SG_CUDA_TRY(cudaMemcpyAsync(h_num, num_counts, sizeof(h_num), cudaMemcpyDeviceToHost, s));
     SG_CUDA_TRY(read_back(&nnz, C->row_ptr + n, sizeof(int64_t), s));
     C->n = n;
     C->nnz = nnz;
@@ -488,29 +479,24 @@ static sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_
     SG_ALLOC(C->count, uint32_t, nnz, s);
     SG_ALLOC(C->seed_i, uint32_t, (int64_t)S * nnz, s);
     SG_ALLOC(C->seed_k, uint32_t, (int64_t)S * nnz, s);
-    unsigned char *gpool_num = nullptr;
-    const int ng_glob = nb.nsmem;
-    if (nr.count[ng_glob] > 0) {
-        gpool_num = sc.get<unsigned char>((size_t)nr.gtotal * (16 + 8 * (size_t)S));
-        if (!gpool_num) return SG_ERR_OOM;
+    for (int c = 0; c < num.ncls; c++) {
+        if (!h_num[c]) continue;
+        const size_t sm = num_table_bytes((int64_t)1 << num.log2T[c], S);
+        SG_CUDA_TRY(allow_smem(numeric_kernel<false>, sm));
+        SG_LAUNCH("spgemm_numeric", numeric_kernel<false>, SP_GRID, pick_threads(num.log2T[c]), sm, s, g,
+                  lists + (int64_t)c * n, num_counts + c, num.log2T[c], (const int64_t *)need,
+                  (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i,
+                  C->seed_k, nnz);
     }
-    for (int c = 0; c < nb.nsmem; c++) {
-        if (!nr.count[c]) continue;
-        size_t sm = numeric_smem(nb.log2T[c], S);
-        SG_CUDA_TRY(cudaFuncSetAttribute(numeric_kernel<SP_NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm));
-        SG_LAUNCH("spgemm_numeric", (numeric_kernel<SP_NT, false>), grid_for(nr.count[c]), SP_NT, sm, s, g,
-                  nr.rows + nr.base[c], nr.count[c], nb.log2T[c], (int)numeric_tab_off(nb.log2T[c]),
-                  (unsigned char *)nullptr,
-                  (const int64_t *)nullptr, (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i, C->seed_k,
-                  nnz);
-    }
-    if (nr.count[ng_glob]) {
-        size_t sm = chunk_bytes();
-        SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<SP_NT_BIG, true>), grid_for(nr.count[ng_glob]),
-                  SP_NT_BIG, sm, s, g, nr.rows + nr.base[ng_glob], nr.count[ng_glob], 0, 0, gpool_num,
-                  (const int64_t *)nr.goff, (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i, C->seed_k,
-                  nnz);
+    if (h_num[num.ncls]) {
+        const int64_t Tmax = pow2_at_least(2 * (n > 1 ? n - 1 : 1));
+        const int64_t slice_bytes = (int64_t)((num_table_bytes(Tmax, S) + 255) & ~(size_t)255);
+        const int grid = (int)(h_num[num.ncls] < 152 * 2 ? h_num[num.ncls] : 152 * 2);
+        unsigned char *pool = sc.get<unsigned char>((size_t)slice_bytes * grid);
+        if (!pool) return SG_ERR_OOM;
+        SG_LAUNCH("spgemm_numeric_gmem", numeric_kernel<true>, grid, 512, 0, s, g, lists + (int64_t)num.ncls * n,
+                  num_counts + num.ncls, 0, (const int64_t *)need, pool, slice_bytes, (const int64_t *)C->row_ptr,
+                  C->col, C->count, C->seed_i, C->seed_k, nnz);
     }
     uint32_t herr = 0;
     SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));

@@ -17,7 +17,7 @@
 // 2 * out(d_ij) + in(d_jk). N is kept as (sum << 2 | composite) in one 64-bit word so that
 // DIRMATCH (composite must equal d_ik before the min) and LITERAL (lexicographic min of
 // (sum, composite), checked after) share one atomicMin.
-#include "prim.cuh"
+#include "ops.cuh"
 
 namespace sg {
 
@@ -70,7 +70,8 @@ __device__ __forceinline__ int64_t find_col(const int32_t *cols, int64_t deg, in
 // minima live in `gbest` (indexed by entry); otherwise the row is staged in shared memory.
 template <bool GMEM>
 __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const int32_t *__restrict__ rows,
-                                                            int64_t nrows, int mode, uint32_t fuzz,
+                                                            const unsigned long long *__restrict__ nrows_p,
+                                                            const uint32_t *__restrict__ err, int mode, uint32_t fuzz,
                                                             unsigned long long *__restrict__ gbest,
                                                             int64_t *__restrict__ gpre,
                                                             uint8_t *__restrict__ keep, int64_t *__restrict__ kept,
@@ -83,6 +84,8 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
     __shared__ int64_t s_tmp[TR_NT / 32 + 1];
     __shared__ uint32_t s_red[TR_NT / 32];
     __shared__ int64_t s_kept[TR_NT / 32];
+    if (*err) return;  // the graph failed validation: touch nothing
+    const int64_t nrows = (int64_t)*nrows_p;
     for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
         const int32_t i = rows[rb];
         const int64_t r0 = g.rp[i], r1 = g.rp[i + 1], deg = r1 - r0;
@@ -186,14 +189,15 @@ __global__ void tr_bin_kernel(const int64_t *__restrict__ rp, int64_t n, unsigne
     atomicAdd(counts + c, 1ull);
 }
 
+// rows[0 .. n) lists the shared-memory rows, rows[n .. 2n) the global-memory rows
 __global__ void tr_fill_kernel(const int8_t *__restrict__ kind, int64_t n, unsigned long long *__restrict__ cursor,
-                               int64_t base_big, int32_t *__restrict__ rows) {
+                               int32_t *__restrict__ rows) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = kind[i];
     if (c == 0) return;
     unsigned long long p = atomicAdd(cursor + c, 1ull);
-    rows[(c == 1 ? 0 : base_big) + (int64_t)p] = (int32_t)i;
+    rows[(c == 1 ? 0 : n) + (int64_t)p] = (int32_t)i;
 }
 
 // Stable compaction of kept entries: one warp per row.
@@ -220,20 +224,6 @@ __global__ void tr_compact_kernel(TrGraph g, const uint8_t *__restrict__ keep, c
 
 static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
 
-static sg_status validate(const TrGraph &g, int64_t nnz, Scratch &sc, cudaStream_t s) {
-    uint32_t *err = sc.get<uint32_t>(1);
-    if (!err) return SG_ERR_OOM;
-    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-    SG_LAUNCH("validate_graph", validate_graph_kernel, blocks_for((g.n + 1) * 32, 256), 256, 0, s, g, nnz, err);
-    uint32_t h = 0;
-    SG_CUDA_TRY(read_back(&h, err, sizeof(uint32_t), s));
-    if (h) {
-        set_error("graph does not satisfy the CSR contract (sorted unique columns, no diagonal, suffix < 2^30, dir <= 3)");
-        return SG_ERR_INVALID;
-    }
-    return SG_OK;
-}
-
 // Buffers reused by every round (sized for the input graph; later rounds only shrink).
 struct TrWork {
     unsigned long long *counts;  // [6]: rows per kind, then fill cursors
@@ -246,38 +236,33 @@ struct TrWork {
 static sg_status tr_work_alloc(TrWork *w, int64_t n, int64_t nnz, Scratch &sc) {
     w->counts = sc.get<unsigned long long>(6);
     w->kind = sc.get<int8_t>(n + 1);
-    w->rows = sc.get<int32_t>(n + 1);
+    w->rows = sc.get<int32_t>(2 * (n + 1));
     w->gbest = sc.get<unsigned long long>(nnz + 1);
     w->gpre = sc.get<int64_t>(nnz + n + 1);
     return (w->counts && w->kind && w->rows && w->gbest && w->gpre) ? SG_OK : SG_ERR_OOM;
 }
 
-// One round over graph g: keep flags + per-row kept counts (and optionally N / Ndir).
+// One round over graph g: keep flags + per-row kept counts (and optionally N / Ndir). Rows are
+// binned on the device and both kernels run grid-stride over the device-side row counts, so the
+// round needs no host round trip. Nothing runs past a set `err` (failed validation).
 static sg_status minplus_round(const TrGraph &g, int64_t nnz, int mode, uint32_t fuzz, uint8_t *keep,
-                               int64_t *kept, uint32_t *outN, uint8_t *outD, const TrWork &w, cudaStream_t s) {
+                               int64_t *kept, uint32_t *outN, uint8_t *outD, const TrWork &w, const uint32_t *err,
+                               cudaStream_t s) {
+    (void)nnz;
     const int64_t n = g.n;
     unsigned long long *counts = w.counts;
-    int8_t *kind = w.kind;
-    int32_t *rows = w.rows;
     SG_CUDA_TRY(cudaMemsetAsync(counts, 0, 6 * sizeof(unsigned long long), s));
     if (kept) SG_CUDA_TRY(cudaMemsetAsync(kept, 0, (n + 1) * sizeof(int64_t), s));
-    SG_LAUNCH("tr_bin", tr_bin_kernel, blocks_for(n, 256), 256, 0, s, g.rp, n, counts, kind);
-    unsigned long long hc[3];
-    SG_CUDA_TRY(read_back(hc, counts, sizeof(hc), s));
-    SG_LAUNCH("tr_fill", tr_fill_kernel, blocks_for(n, 256), 256, 0, s, kind, n, counts + 3, (int64_t)hc[1], rows);
-    const int grid_cap = 152 * 16;
-    if (hc[1]) {
-        int grid = (int)(hc[1] < (unsigned long long)grid_cap ? hc[1] : grid_cap);
-        SG_LAUNCH("tr_minplus_mark", minplus_mark_kernel<false>, grid, TR_NT, 0, s, g, rows, (int64_t)hc[1], mode,
-                  fuzz, (unsigned long long *)nullptr, (int64_t *)nullptr, keep, kept, outN, outD);
-    }
-    if (hc[2]) {
-        unsigned long long *gbest = w.gbest;
-        int64_t *gpre = w.gpre;
-        int grid = (int)(hc[2] < (unsigned long long)grid_cap ? hc[2] : grid_cap);
-        SG_LAUNCH("tr_minplus_mark_gmem", minplus_mark_kernel<true>, grid, TR_NT, 0, s, g, rows + hc[1],
-                  (int64_t)hc[2], mode, fuzz, gbest, gpre, keep, kept, outN, outD);
-    }
+    if (n == 0) return SG_OK;
+    SG_LAUNCH("tr_bin", tr_bin_kernel, blocks_for(n, 256), 256, 0, s, g.rp, n, counts, w.kind);
+    SG_LAUNCH("tr_fill", tr_fill_kernel, blocks_for(n, 256), 256, 0, s, w.kind, n, counts + 3, w.rows);
+    const int64_t gs = n < 152 * 16 ? n : 152 * 16;
+    SG_LAUNCH("tr_minplus_mark", minplus_mark_kernel<false>, gs, TR_NT, 0, s, g, (const int32_t *)w.rows,
+              counts + 1, err, mode, fuzz, (unsigned long long *)nullptr, (int64_t *)nullptr, keep, kept, outN,
+              outD);
+    const int64_t gg = n < 152 * 2 ? n : 152 * 2;
+    SG_LAUNCH("tr_minplus_mark_gmem", minplus_mark_kernel<true>, gg, TR_NT, 0, s, g, (const int32_t *)(w.rows + n),
+              counts + 2, err, mode, fuzz, w.gbest, w.gpre, keep, kept, outN, outD);
     return SG_OK;
 }
 
@@ -289,68 +274,95 @@ static void free_graph_arrays(sg_graph_csr *x, cudaStream_t s) {
     *x = sg_graph_csr{};
 }
 
-static sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *S, int32_t *iters,
-                         cudaStream_t s) {
-    const int64_t n = R->n;
+// Batches: job_last[b] = max(job_last[b], round) for every job b that lost an entry this round.
+__global__ void job_changes_kernel(const int64_t *__restrict__ rp, const int64_t *__restrict__ kept, int64_t n,
+                                   const int64_t *__restrict__ job_ro, int64_t njobs, int32_t round,
+                                   int32_t *__restrict__ job_last) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (rp[i + 1] - rp[i]) == kept[i]) return;
+    int64_t lo = 0, hi = njobs;  // last job b with job_ro[b] <= i
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (job_ro[mid] <= i) lo = mid; else hi = mid;
+    }
+    atomicMax(job_last + lo, round);
+}
+
+sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *S, int32_t *iters,
+                  cudaStream_t s, const int64_t *job_ro, int64_t njobs, int32_t *job_last) {
+    const int64_t n = R->n, nnz0 = R->nnz;
     Scratch sc(s);
-    TrGraph g{R->row_ptr, R->col, R->suffix, R->dir, n};
-    SG_TRY(validate(g, R->nnz, sc, s));
-    uint8_t *keep = sc.get<uint8_t>(R->nnz);
+    uint32_t *err = sc.get<uint32_t>(1);
+    uint8_t *keep = sc.get<uint8_t>(nnz0 + 1);
     int64_t *kept = sc.get<int64_t>(n + 1);
-    if (!keep || !kept) return SG_ERR_OOM;
+    if (!err || !keep || !kept) return SG_ERR_OOM;
     TrWork wk;
-    SG_TRY(tr_work_alloc(&wk, n, R->nnz, sc));
-    sg_graph_csr cur{};  // library-owned current graph (empty = still the input)
-    int64_t cur_nnz = R->nnz;
+    SG_TRY(tr_work_alloc(&wk, n, nnz0, sc));
+    // two graph buffers of the input's size: round r reads one and compacts into the other
+    int64_t *rp[2];
+    int32_t *col[2];
+    uint32_t *suf[2];
+    uint8_t *dir[2];
+    for (int b = 0; b < 2; b++) {
+        rp[b] = sc.get<int64_t>(n + 1);
+        col[b] = sc.get<int32_t>(nnz0 + 1);
+        suf[b] = sc.get<uint32_t>(nnz0 + 1);
+        dir[b] = sc.get<uint8_t>(nnz0 + 1);
+        if (!rp[b] || !col[b] || !suf[b] || !dir[b]) return SG_ERR_OOM;
+    }
+    TrGraph g{R->row_ptr, R->col, R->suffix, R->dir, n};
+    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    SG_LAUNCH("validate_graph", validate_graph_kernel, blocks_for((n + 1) * 32, 256), 256, 0, s, g, nnz0, err);
+    int64_t cur_nnz = nnz0;
+    int cur = -1;  // -1: the current graph is still the caller's R
     int32_t it = 0;
     for (;;) {
         it++;
-        sg_status rs = minplus_round(g, cur_nnz, mode, fuzz, keep, kept, nullptr, nullptr, wk, s);
-        if (rs != SG_OK) { free_graph_arrays(&cur, s); return rs; }
-        sg_graph_csr nx{};
-        nx.n = n;
-        nx.row_ptr = (int64_t *)dalloc((n + 1) * sizeof(int64_t), s);
-        if (!nx.row_ptr) { free_graph_arrays(&cur, s); return SG_ERR_OOM; }
-        sg_status st = exclusive_scan<int64_t>(kept, nx.row_ptr, n, s);
+        const int nxt = cur == 0 ? 1 : 0;
+        SG_TRY(minplus_round(g, cur_nnz, mode, fuzz, keep, kept, nullptr, nullptr, wk, err, s));
+        if (job_ro)
+            SG_LAUNCH("tr_job_changes", job_changes_kernel, blocks_for(n, 256), 256, 0, s, g.rp,
+                      (const int64_t *)kept, n, job_ro, njobs, it, job_last);
+        SG_TRY(exclusive_scan<int64_t>(kept, rp[nxt], n, s));
         int64_t nnz2 = 0;
-        if (st == SG_OK && read_back(&nnz2, nx.row_ptr + n, sizeof(int64_t), s) != cudaSuccess) {
-            set_error("transitive_reduce: reading nnz back failed");
-            st = SG_ERR_CUDA;
+        uint32_t herr = 0;
+        if (it == 1) SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(read_back(&nnz2, rp[nxt] + n, sizeof(int64_t), s));
+        if (herr) {
+            set_error("graph does not satisfy the CSR contract (sorted unique columns, no diagonal, suffix < 2^30, dir <= 3)");
+            return SG_ERR_INVALID;
         }
-        if (st != SG_OK) { free_graph_arrays(&nx, s); free_graph_arrays(&cur, s); return st; }
-        if (nnz2 == cur_nnz) {  // nothing removed: done
-            dfree(nx.row_ptr, s);
-            break;
-        }
-        nx.nnz = nnz2;
-        nx.col = (int32_t *)dalloc(nnz2 * sizeof(int32_t), s);
-        nx.suffix = (uint32_t *)dalloc(nnz2 * sizeof(uint32_t), s);
-        nx.dir = (uint8_t *)dalloc(nnz2, s);
-        if (!nx.col || !nx.suffix || !nx.dir) { free_graph_arrays(&nx, s); free_graph_arrays(&cur, s); return SG_ERR_OOM; }
-        SG_LAUNCH("tr_compact", tr_compact_kernel, blocks_for(n * 32, 256), 256, 0, s, g, keep, nx.row_ptr, nx.col,
-                  nx.suffix, nx.dir);
-        free_graph_arrays(&cur, s);
-        cur = nx;
+        if (nnz2 == cur_nnz) break;  // nothing removed: R is final
+        SG_LAUNCH("tr_compact", tr_compact_kernel, blocks_for(n * 32, 256), 256, 0, s, g, keep, rp[nxt], col[nxt],
+                  suf[nxt], dir[nxt]);
+        cur = nxt;
         cur_nnz = nnz2;
-        g = TrGraph{cur.row_ptr, cur.col, cur.suffix, cur.dir, n};
+        g = TrGraph{rp[cur], col[cur], suf[cur], dir[cur], n};
     }
-    if (!cur.row_ptr) {  // first round removed nothing: S is a copy of R
-        cur.n = n;
-        cur.nnz = R->nnz;
-        cur.row_ptr = (int64_t *)dalloc((n + 1) * sizeof(int64_t), s);
-        cur.col = (int32_t *)dalloc(R->nnz * sizeof(int32_t), s);
-        cur.suffix = (uint32_t *)dalloc(R->nnz * sizeof(uint32_t), s);
-        cur.dir = (uint8_t *)dalloc(R->nnz, s);
-        if (!cur.row_ptr || !cur.col || !cur.suffix || !cur.dir) { free_graph_arrays(&cur, s); return SG_ERR_OOM; }
-        SG_CUDA_TRY(cudaMemcpyAsync(cur.row_ptr, R->row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-        if (R->nnz) {
-            SG_CUDA_TRY(cudaMemcpyAsync(cur.col, R->col, R->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-            SG_CUDA_TRY(cudaMemcpyAsync(cur.suffix, R->suffix, R->nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-            SG_CUDA_TRY(cudaMemcpyAsync(cur.dir, R->dir, R->nnz, cudaMemcpyDeviceToDevice, s));
-        }
+    // S: exact-size copy of the final graph
+    sg_graph_csr out{};
+    out.n = n;
+    out.nnz = cur_nnz;
+    out.row_ptr = (int64_t *)dalloc((n + 1) * sizeof(int64_t), s);
+    out.col = (int32_t *)dalloc(cur_nnz * sizeof(int32_t), s);
+    out.suffix = (uint32_t *)dalloc(cur_nnz * sizeof(uint32_t), s);
+    out.dir = (uint8_t *)dalloc(cur_nnz, s);
+    if (!out.row_ptr || !out.col || !out.suffix || !out.dir) {
+        free_graph_arrays(&out, s);
+        return SG_ERR_OOM;
     }
-    SG_CUDA_TRY(cudaStreamSynchronize(s));
-    *S = cur;
+    cudaError_t e = cudaMemcpyAsync(out.row_ptr, g.rp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && cur_nnz)
+        e = cudaMemcpyAsync(out.col, g.col, cur_nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && cur_nnz)
+        e = cudaMemcpyAsync(out.suffix, g.suf, cur_nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && cur_nnz) e = cudaMemcpyAsync(out.dir, g.dir, cur_nnz, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        free_graph_arrays(&out, s);
+        set_error("transitive_reduce: copying S failed: %s", cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+    }
+    *S = out;
     *iters = it;
     return SG_OK;
 }
@@ -374,7 +386,7 @@ extern "C" sg_status sg_transitive_reduce(const sg_graph_csr *R, uint32_t fuzz, 
         sg::set_error("transitive_reduce: invalid arguments");
         return SG_ERR_INVALID;
     }
-    return sg::tr_impl(R, fuzz, mode, S, iterations, (cudaStream_t)stream);
+    return sg::tr_impl(R, fuzz, mode, S, iterations, (cudaStream_t)stream, nullptr, 0, nullptr);
 }
 
 extern "C" sg_status sg_minplus_square(const sg_graph_csr *R, int32_t mode, uint32_t *d_N, uint8_t *d_Ndir,
@@ -385,12 +397,20 @@ extern "C" sg_status sg_minplus_square(const sg_graph_csr *R, int32_t mode, uint
     }
     cudaStream_t s = (cudaStream_t)stream;
     sg::Scratch sc(s);
+    uint32_t *err = sc.get<uint32_t>(1);
+    if (!err) return SG_ERR_OOM;
     sg::TrGraph g{R->row_ptr, R->col, R->suffix, R->dir, R->n};
-    SG_TRY(sg::validate(g, R->nnz, sc, s));
     sg::TrWork wk;
     SG_TRY(sg::tr_work_alloc(&wk, R->n, R->nnz, sc));
-    SG_TRY(sg::minplus_round(g, R->nnz, mode, 0, nullptr, nullptr, d_N, d_Ndir, wk, s));
-    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+    SG_LAUNCH("validate_graph", sg::validate_graph_kernel, (R->n + 1 + 7) / 8, 256, 0, s, g, R->nnz, err);
+    SG_TRY(sg::minplus_round(g, R->nnz, mode, 0, nullptr, nullptr, d_N, d_Ndir, wk, err, s));
+    uint32_t herr = 0;
+    SG_CUDA_TRY(sg::read_back(&herr, err, sizeof(uint32_t), s));
+    if (herr) {
+        sg::set_error("minplus_square: graph does not satisfy the CSR contract");
+        return SG_ERR_INVALID;
+    }
     return SG_OK;
 }
 
@@ -488,7 +508,7 @@ extern "C" sg_status sg_minplus_square_noalloc(const sg_graph_csr *R, int32_t mo
         sg::set_error("minplus_square_noalloc: graph does not satisfy the CSR contract");
         return SG_ERR_INVALID;
     }
-    SG_TRY(sg::minplus_round(g, nnz, mode, 0, nullptr, nullptr, d_N, d_Ndir, wk, s));
+    SG_TRY(sg::minplus_round(g, nnz, mode, 0, nullptr, nullptr, d_N, d_Ndir, wk, err, s));
     SG_CUDA_TRY(cudaStreamSynchronize(s));
     return SG_OK;
 }
