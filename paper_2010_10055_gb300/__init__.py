@@ -22,9 +22,9 @@ DIRMATCH, LITERAL = 0, 1
 INF = 0xFFFFFFFF
 
 EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",
-           "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy",
+           "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy", "sg_run_batch", "sg_free_batch",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
-           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_launch_count", "sg_prof_enable", "sg_prof_select",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
 
 
@@ -75,6 +75,23 @@ class PipelineResult(ctypes.Structure):
                 ("s_dir", ctypes.c_void_p)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("d_seq", ctypes.c_void_p), ("d_offsets", ctypes.c_void_p), ("n_reads", ctypes.c_int64),
+                ("total_len", ctypes.c_int64), ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32),
+                ("R", ctypes.POINTER(GraphCsr))]
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("min_shared", ctypes.c_uint32), ("max_seeds", ctypes.c_int32),
+                ("fuzz", ctypes.c_uint32), ("tr_mode", ctypes.c_int32)]
+
+
+class BatchResultC(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int32), ("read_off", ctypes.c_void_p), ("col_off", ctypes.c_void_p),
+                ("iterations", ctypes.c_void_p), ("iterations_all", ctypes.c_int32), ("A", CsrU32), ("At", CsrU32),
+                ("d_kmer_codes", ctypes.c_void_p), ("C", OverlapCsr), ("S", GraphCsr)]
+
+
 _lib = None
 
 
@@ -113,6 +130,16 @@ def lib():
         L.sg_host_arena_create.restype = ctypes.c_int
         L.sg_host_arena_create.argtypes = [ctypes.POINTER(vp)]
         L.sg_host_arena_destroy.argtypes = [vp]
+        L.sg_tune_set.restype = ctypes.c_int
+        L.sg_tune_set.argtypes = [ctypes.c_char_p, i64]
+        L.sg_tune_get.restype = i64
+        L.sg_tune_get.argtypes = [ctypes.c_char_p]
+        L.sg_tune_name.restype = ctypes.c_char_p
+        L.sg_tune_name.argtypes = [ctypes.c_int]
+        L.sg_run_batch.restype = ctypes.c_int
+        L.sg_run_batch.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(BatchParams),
+                                   ctypes.POINTER(BatchResultC), vp]
+        L.sg_free_batch.argtypes = [ctypes.POINTER(BatchResultC), vp]
         L.sg_pipeline_host.restype = ctypes.c_int
         L.sg_pipeline_host.argtypes = [ctypes.POINTER(PipelineJob), vp, ctypes.POINTER(PipelineResult), vp]
         _lib = L
@@ -389,6 +416,22 @@ def prof_collect() -> dict:
     return out
 
 
+def tunables() -> dict:
+    """{name: current value} of the library's launch parameters."""
+    L, out, i = lib(), {}, 0
+    while True:
+        nm = L.sg_tune_name(i)
+        if not nm:
+            return out
+        out[nm.decode()] = int(L.sg_tune_get(nm))
+        i += 1
+
+
+def tune(name: str, value: int):
+    if not lib().sg_tune_set(name.encode(), int(value)):
+        raise ValueError(f"unknown tunable or value out of range: {name}={value}")
+
+
 def debug_fail_alloc_after(n: int):
     lib().sg_debug_fail_alloc_after(int(n))
 
@@ -447,3 +490,90 @@ class HostPipeline:
             out["S"] = dict(n=n, row_ptr=arr(res.s_row_ptr, n + 1, np.int64), col=arr(res.s_col, res.nnz_s, np.int32),
                             suffix=arr(res.s_suffix, res.nnz_s, np.uint32), dir=arr(res.s_dir, res.nnz_s, np.uint8))
         return out
+
+
+# --------------------------------------------------------------------------------- batches
+class BatchResult:
+    """Result of run_batch: the union outputs on the device plus per-set offsets; item(b) gives set
+    b's slice with local indices (numpy), identical to running the three calls on set b alone."""
+
+    def __init__(self, r: BatchResultC, stream, keep):
+        self.r = r
+        self._stream = stream
+        self._keep = keep  # the items' device buffers must outlive the call only; kept for safety
+        n = int(r.n_items)
+        self.n_items = n
+        self.read_off = np.ctypeslib.as_array(ctypes.cast(r.read_off, ctypes.POINTER(ctypes.c_int64)), (n + 1,)).copy()
+        self.col_off = np.ctypeslib.as_array(ctypes.cast(r.col_off, ctypes.POINTER(ctypes.c_int64)), (n + 1,)).copy()
+        self.iterations = np.ctypeslib.as_array(ctypes.cast(r.iterations, ctypes.POINTER(ctypes.c_int32)), (n,)).copy()
+        self.iterations_all = int(r.iterations_all)
+        self._host = None
+
+    def free(self):
+        if self.r is not None and _lib is not None:
+            _lib.sg_free_batch(ctypes.byref(self.r), self._stream)
+        self.r = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def to_numpy(self):
+        """The union outputs on the host (downloaded once)."""
+        if self._host is None:
+            r = self.r
+            A = CsrMatrix.__new__(CsrMatrix); A.s = r.A
+            At = CsrMatrix.__new__(CsrMatrix); At.s = r.At
+            C = Overlap.__new__(Overlap); C.s = r.C
+            out = dict(A=A.to_numpy(), At=At.to_numpy(), C=C.to_numpy(),
+                       codes=_host(_view(r.d_kmer_codes, int(r.A.n_cols), "u8", self), "u8"))
+            if r.S.row_ptr:
+                S = Graph.__new__(Graph); S.s = r.S
+                out["S"] = S.to_numpy()
+            self._host = out
+        return self._host
+
+    def item(self, b: int) -> dict:
+        h = self.to_numpy()
+        r0, r1 = int(self.read_off[b]), int(self.read_off[b + 1])
+        c0, c1 = int(self.col_off[b]), int(self.col_off[b + 1])
+
+        def rows(M, lo, hi):
+            rp = M["row_ptr"][lo:hi + 1]
+            return rp - rp[0], slice(int(rp[0]), int(rp[-1]))
+
+        rp, sl = rows(h["A"], r0, r1)
+        A = dict(n_rows=r1 - r0, n_cols=c1 - c0, row_ptr=rp, col=h["A"]["col"][sl] - c0, val=h["A"]["val"][sl])
+        rp, sl = rows(h["At"], c0, c1)
+        At = dict(n_rows=c1 - c0, n_cols=r1 - r0, row_ptr=rp, col=h["At"]["col"][sl] - r0, val=h["At"]["val"][sl])
+        rp, sl = rows(h["C"], r0, r1)
+        C = dict(n=r1 - r0, row_ptr=rp, col=h["C"]["col"][sl] - r0, count=h["C"]["count"][sl],
+                 seed_i=h["C"]["seed_i"][:, sl], seed_k=h["C"]["seed_k"][:, sl])
+        out = dict(A=A, At=At, codes=h["codes"][c0:c1], C=C, iterations=int(self.iterations[b]))
+        if "S" in h:
+            rp, sl = rows(h["S"], r0, r1)
+            out["S"] = dict(n=r1 - r0, row_ptr=rp, col=h["S"]["col"][sl] - r0, suffix=h["S"]["suffix"][sl],
+                            dir=h["S"]["dir"][sl])
+        return out
+
+
+def run_batch(items: list, k: int = 17, min_shared: int = 2, max_seeds: int = 2, fuzz: int = 0,
+              tr_mode: int = DIRMATCH, stream=None) -> BatchResult:
+    """items: dicts with seq (uint8 CUDA tensor), offsets (int64 CUDA tensor), lo, hi and optionally
+    R (DeviceGraph over the set's reads)."""
+    L = lib()
+    st = _stream(stream)
+    arr = (BatchItem * len(items))()
+    keep = []
+    for b, it in enumerate(items):
+        R = it.get("R")
+        rs = ctypes.pointer(R.s) if R is not None else None
+        keep.append((it, rs))
+        arr[b] = BatchItem(it["seq"].data_ptr() if it["seq"].numel() else None, it["offsets"].data_ptr(),
+                           int(it["offsets"].numel()) - 1, int(it["seq"].numel()), int(it["lo"]), int(it["hi"]), rs)
+    params = BatchParams(int(k), int(min_shared), int(max_seeds), int(fuzz), int(tr_mode))
+    out = BatchResultC()
+    _check(L.sg_run_batch(arr, len(items), ctypes.byref(params), ctypes.byref(out), st), "run_batch")
+    return BatchResult(out, st, keep)

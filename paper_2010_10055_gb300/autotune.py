@@ -1,0 +1,90 @@
+"""Autotuner for the library's launch parameters.
+
+Coordinate descent: each tunable in turn is set to every candidate value while the others stay
+fixed, one timed call of `step` (after a warm-up call) is taken per candidate and repetition, and
+the fastest median wins. The parameters (Bloom slice size, symbolic table guess, grid sizes) only
+change speed, never results. The chosen values can be cached per GPU and workload signature.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+import paper_2010_10055_gb300 as sg
+
+SPACE = {
+    "bloom_slice_mb": [24, 32, 48, 64, 96, 192],
+    "sym_guess_shift": [0, 1, 2, 3],
+    "spgemm_blocks_per_sm": [2, 4, 8, 16],
+    "tr_blocks_per_sm": [4, 8, 16, 32],
+}
+
+
+def _time_ms(step, reps: int) -> float:
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step()  # warm-up with the new setting
+    ts = []
+    for _ in range(reps):
+        e0.record()
+        out = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        del out
+    return statistics.median(ts)
+
+
+def autotune(step, space: dict | None = None, reps: int = 3, rounds: int = 1, log=None) -> dict:
+    """Tunes in place and returns {"params": chosen values, "ms": best step time, "trials": n}."""
+    space = space or SPACE
+    best = _time_ms(step, reps)
+    trials = 1
+    for _ in range(rounds):
+        for name, cands in space.items():
+            cur = sg.tunables()[name]
+            choice, choice_ms = cur, best
+            for v in cands:
+                if v == cur:
+                    continue
+                sg.tune(name, v)
+                ms = _time_ms(step, reps)
+                trials += 1
+                if log:
+                    log(f"{name}={v}: {ms:.3f} ms")
+                if ms < choice_ms:
+                    choice, choice_ms = v, ms
+            sg.tune(name, choice)
+            best = choice_ms
+    return {"params": sg.tunables(), "ms": best, "trials": trials}
+
+
+def cache_key(signature: str) -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|{p.multi_processor_count}|{signature}"
+
+
+def load(path: str, signature: str) -> bool:
+    """Applies cached values for this GPU and workload signature; returns whether any were found."""
+    try:
+        entry = json.load(open(path)).get(cache_key(signature))
+    except (OSError, ValueError):
+        return False
+    if not entry:
+        return False
+    for k, v in entry["params"].items():
+        sg.tune(k, v)
+    return True
+
+
+def store(path: str, signature: str, result: dict) -> None:
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        data = {}
+    data[cache_key(signature)] = result
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1)

@@ -42,6 +42,9 @@ struct Scratch {
     ~Scratch() { for (int i = n - 1; i >= 0; --i) dfree(ptrs[i], s); }
 };
 
+// Current value of a tunable parameter (see sg_tune_set).
+int64_t tune(const char *name);
+
 // Copy one device value to the host and wait for it.
 cudaError_t read_back(void *host, const void *dev, size_t bytes, cudaStream_t s);
 

@@ -30,7 +30,6 @@ namespace sg {
 constexpr int KM_NT = 256;
 constexpr int KM_W = 32;                  // windows per thread
 constexpr int KM_CHUNK = KM_NT * KM_W;    // windows per block
-constexpr uint64_t KM_SLICE_BYTES = 48ull << 20;  // B1 bytes updated per Bloom launch (L2-resident)
 
 // 32-bit mix of a 64-bit k-mer code (multiply-xorshift finaliser).
 __device__ __forceinline__ uint32_t hash32(uint64_t code, uint32_t seed) {
@@ -371,8 +370,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, (size_t)b2.nwords * 4, s));
     }
     if (use_bloom) {
-        // slices of at most KM_SLICE_BYTES of B1, so each launch's atomics stay in L2
-        const uint64_t slice_words = KM_SLICE_BYTES / 4;
+        // slices of at most bloom_slice_mb of B1, so each launch's atomics stay in L2
+        const uint64_t slice_words = ((uint64_t)tune("bloom_slice_mb") << 20) / 4;
         const uint64_t nsl = (b1.nwords + slice_words - 1) / slice_words;
         for (uint64_t q = 0; q < nsl; q++) {
             const uint32_t lo_w = (uint32_t)((uint64_t)b1.nwords * q / nsl);

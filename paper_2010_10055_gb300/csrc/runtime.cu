@@ -143,9 +143,45 @@ LaunchScope::~LaunchScope() {
     }
 }
 
+// ------------------------------------------------------------------------- tunables
+struct Tunable { const char *name; int64_t value; int64_t lo, hi; };
+static Tunable g_tunables[] = {
+    // defaults: the autotuner's choice on a GB300 for the bacterial-scale read set
+    {"bloom_slice_mb", 96, 1, 1 << 20},   // B1 megabytes updated per Bloom launch
+    {"sym_guess_shift", 2, 0, 8},         // symbolic table guess = products >> shift
+    {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch
+    {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch
+};
+static std::mutex g_tune_mu;
+
+int64_t tune(const char *name) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &t : g_tunables)
+        if (strcmp(t.name, name) == 0) return t.value;
+    return 0;
+}
+
 }  // namespace sg
 
 extern "C" {
+
+int sg_tune_set(const char *name, int64_t value) {
+    std::lock_guard<std::mutex> lk(sg::g_tune_mu);
+    for (auto &t : sg::g_tunables)
+        if (name && strcmp(t.name, name) == 0) {
+            if (value < t.lo || value > t.hi) return 0;
+            t.value = value;
+            return 1;
+        }
+    return 0;
+}
+
+int64_t sg_tune_get(const char *name) { return name ? sg::tune(name) : 0; }
+
+const char *sg_tune_name(int idx) {
+    const int n = (int)(sizeof(sg::g_tunables) / sizeof(sg::g_tunables[0]));
+    return (idx >= 0 && idx < n) ? sg::g_tunables[idx].name : nullptr;
+}
 
 const char *sg_last_error(void) { return sg::g_err; }
 

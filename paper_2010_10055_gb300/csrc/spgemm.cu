@@ -29,7 +29,6 @@ namespace sg {
 constexpr int SP_MAX_SEEDS = 8;
 constexpr uint64_t SEED_NONE = ~0ull;
 constexpr int SP_NCLS = 4;        // shared-memory classes per pass
-constexpr int SP_GRID = 152 * 8;  // blocks per class launch (grid-stride over the class's rows)
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t k, int log2T) {
     return ((uint32_t)k * 2654435761u) >> (32 - log2T);
@@ -98,14 +97,14 @@ __global__ void classify_kernel(const int64_t *__restrict__ need, int64_t n, Cla
     lists[(int64_t)c * n + (int64_t)p] = (int32_t)i;
 }
 
-// symbolic table request: nextpow2(max(64, w / 2)), capped at the exact bound 2 * min(w, n - 1)
-__global__ void sym_need_kernel(const int64_t *__restrict__ work, int64_t n, int64_t *__restrict__ need) {
+// symbolic table request: nextpow2(max(64, w >> shift)), capped at the exact bound 2 * min(w, n - 1)
+__global__ void sym_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, int64_t *__restrict__ need) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t w = work[i];
     if (w <= 0) { need[i] = 0; return; }
     int64_t exact = pow2_at_least(2 * (w < n - 1 ? w : n - 1));
-    int64_t guess = pow2_at_least(w / 2 > 64 ? w / 2 : 64);
+    int64_t guess = pow2_at_least((w >> shift) > 64 ? (w >> shift) : 64);
     need[i] = guess < exact ? guess : exact;
 }
 
@@ -432,12 +431,14 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
 
     // ---- symbolic: guessed shared-memory tables of 2^8 .. 2^14 slots
     const Classes sym{{8, 10, 12, 14}, 4};
-    SG_LAUNCH("sym_need", sym_need_kernel, blocks_for(n, NT), NT, 0, s, work, n, need);
+    SG_LAUNCH("sym_need", sym_need_kernel, blocks_for(n, NT), NT, 0, s, work, n, (int)tune("sym_guess_shift"),
+              need);
+    const int grid = (int)(152 * tune("spgemm_blocks_per_sm"));
     SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, sym, sym_counts, lists);
     for (int c = 0; c < sym.ncls; c++) {
         const size_t sm = (size_t)(2 << sym.log2T[c]) * sizeof(int32_t);
         SG_CUDA_TRY(allow_smem(symbolic_kernel<false>, sm));
-        SG_LAUNCH("spgemm_symbolic", symbolic_kernel<false>, SP_GRID, pick_threads(sym.log2T[c]), sm, s, g,
+        SG_LAUNCH("spgemm_symbolic", symbolic_kernel<false>, grid, pick_threads(sym.log2T[c]), sm, s, g,
                   lists + (int64_t)c * n, sym_counts + c, sym.log2T[c], (const int64_t *)work, (int32_t *)nullptr,
                   (int64_t)0, ovf, ovf_count, nnz_row, dist);
     }
@@ -483,7 +484,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         if (!h_num[c]) continue;
         const size_t sm = num_table_bytes((int64_t)1 << num.log2T[c], S);
         SG_CUDA_TRY(allow_smem(numeric_kernel<false>, sm));
-        SG_LAUNCH("spgemm_numeric", numeric_kernel<false>, SP_GRID, pick_threads(num.log2T[c]), sm, s, g,
+        SG_LAUNCH("spgemm_numeric", numeric_kernel<false>, grid, pick_threads(num.log2T[c]), sm, s, g,
                   lists + (int64_t)c * n, num_counts + c, num.log2T[c], (const int64_t *)need,
                   (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i,
                   C->seed_k, nnz);
