@@ -220,6 +220,64 @@ sg_status sg_run_batch(const sg_batch_item *items, int32_t n_items, const sg_bat
 void sg_free_batch(sg_batch_result *r, sg_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Served form: a continuous-batching server. Jobs (host buffers, copied at submit) queue in
+ * arrival order; each of `workers` threads owns a CUDA stream and, whenever idle, admits the
+ * longest prefix of the queue that fits max_batch and the free part of hbm_budget, runs it as one
+ * sg_run_batch and publishes each job's C and S. Jobs arriving while batches run are admitted as
+ * workers and memory free up, and batches of different workers overlap on the device. A job's
+ * result is the same alone and in any mix (the batch is block-diagonal). A job whose own device
+ * estimate (about 64 B per base + 48 B per R entry) exceeds hbm_budget completes with
+ * SG_ERR_BUDGET. All calls are thread-safe.
+ */
+typedef struct sg_server sg_server;
+
+typedef struct {
+    size_t hbm_budget;        /* device bytes the server may commit to admitted jobs */
+    int32_t max_batch;        /* jobs fused into one batch at most */
+    int32_t workers;          /* batches in flight at most (one stream each) */
+    int32_t device;           /* CUDA device ordinal */
+    sg_batch_params params;   /* shared by all jobs */
+} sg_server_config;
+
+typedef struct {              /* host buffers, copied by sg_server_submit */
+    const uint8_t *seq;
+    const int64_t *offsets;   /* [n_reads + 1] */
+    int64_t n_reads, total_len;
+    uint32_t lo, hi;
+    const int64_t *r_row_ptr; /* R over the same reads, or NULL */
+    const int32_t *r_col;
+    const uint32_t *r_suffix;
+    const uint8_t *r_dir;
+    int64_t r_nnz;
+} sg_job;
+
+typedef struct {
+    sg_status status;
+    int64_t n, m, nnz_c, nnz_s;
+    int32_t iterations, max_seeds, batch_size;
+    double t_submit, t_start, t_done;  /* steady-clock seconds: submitted, batch started, results ready */
+    int64_t *c_row_ptr;                /* host (malloc), layouts as sg_overlap_csr / sg_graph_csr */
+    int32_t *c_col;
+    uint32_t *c_count, *c_seed_i, *c_seed_k;
+    int64_t *s_row_ptr;                /* NULL when the job had no R */
+    int32_t *s_col;
+    uint32_t *s_suffix;
+    uint8_t *s_dir;
+} sg_job_result;
+
+sg_status sg_server_create(const sg_server_config *cfg, sg_server **out);
+/* Copies the job and queues it; *ticket identifies it. SG_ERR_INVALID for a malformed job. */
+sg_status sg_server_submit(sg_server *srv, const sg_job *job, uint64_t *ticket);
+/* SG_OK and the result (ownership passes to the caller: sg_job_result_free) if the job is done,
+ * SG_ERR_TIMEOUT if not yet. A result is handed out once. The job's own status is out->status. */
+sg_status sg_server_poll(sg_server *srv, uint64_t ticket, sg_job_result *out);
+/* As poll, waiting up to timeout_s seconds. */
+sg_status sg_server_wait(sg_server *srv, uint64_t ticket, double timeout_s, sg_job_result *out);
+void sg_job_result_free(sg_job_result *r);
+/* Stops the workers after their current batches; queued jobs are dropped. */
+void sg_server_destroy(sg_server *srv);
+
+/* ---------------------------------------------------------------------------------------
  * The whole path on HOST buffers: Algorithm 2 from the reads to S (KmerCounter, GenerateA,
  * Transpose, C = A A^T, TransitiveReduction; the alignment/prune steps that turn C into R are not
  * part of this library, so R is an input). Copies the inputs to the device, runs the three
@@ -287,6 +345,17 @@ void sg_debug_fail_alloc_after(int64_t n);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t sg_launch_count(void);
+
+/* Tunable launch parameters (used by the autotuner; results never depend on them):
+ *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (96)
+ *   sym_guess_shift       symbolic hash table guess = products of the row >> shift (2)
+ *   spgemm_blocks_per_sm  blocks per SM of each SpGEMM class launch (16)
+ *   tr_blocks_per_sm      blocks per SM of the min-plus launch (32)
+ * sg_tune_set returns 1 if the name is known and the value in range, else 0 (no change).
+ * sg_tune_name(i) enumerates the names (NULL past the end). Not thread-safe against running calls. */
+int sg_tune_set(const char *name, int64_t value);
+int64_t sg_tune_get(const char *name);
+const char *sg_tune_name(int idx);
 
 /* Per-kernel CUDA-event timing. While enabled, each kernel launch is bracketed by two events on
  * its stream. sg_prof_collect synchronises on the recorded events and folds them into per-name

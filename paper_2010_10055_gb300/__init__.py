@@ -23,6 +23,8 @@ INF = 0xFFFFFFFF
 
 EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",
            "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy", "sg_run_batch", "sg_free_batch",
+           "sg_server_create", "sg_server_submit", "sg_server_poll", "sg_server_wait", "sg_job_result_free",
+           "sg_server_destroy",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
            "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
@@ -92,6 +94,28 @@ class BatchResultC(ctypes.Structure):
                 ("d_kmer_codes", ctypes.c_void_p), ("C", OverlapCsr), ("S", GraphCsr)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("params", BatchParams)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n_reads", ctypes.c_int64),
+                ("total_len", ctypes.c_int64), ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32),
+                ("r_row_ptr", ctypes.c_void_p), ("r_col", ctypes.c_void_p), ("r_suffix", ctypes.c_void_p),
+                ("r_dir", ctypes.c_void_p), ("r_nnz", ctypes.c_int64)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz_c", ctypes.c_int64),
+                ("nnz_s", ctypes.c_int64), ("iterations", ctypes.c_int32), ("max_seeds", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("c_row_ptr", ctypes.c_void_p), ("c_col", ctypes.c_void_p),
+                ("c_count", ctypes.c_void_p), ("c_seed_i", ctypes.c_void_p), ("c_seed_k", ctypes.c_void_p),
+                ("s_row_ptr", ctypes.c_void_p), ("s_col", ctypes.c_void_p), ("s_suffix", ctypes.c_void_p),
+                ("s_dir", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -136,6 +160,16 @@ def lib():
         L.sg_tune_get.argtypes = [ctypes.c_char_p]
         L.sg_tune_name.restype = ctypes.c_char_p
         L.sg_tune_name.argtypes = [ctypes.c_int]
+        L.sg_server_create.restype = ctypes.c_int
+        L.sg_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+        L.sg_server_submit.restype = ctypes.c_int
+        L.sg_server_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
+        L.sg_server_poll.restype = ctypes.c_int
+        L.sg_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(JobResult)]
+        L.sg_server_wait.restype = ctypes.c_int
+        L.sg_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(JobResult)]
+        L.sg_job_result_free.argtypes = [ctypes.POINTER(JobResult)]
+        L.sg_server_destroy.argtypes = [vp]
         L.sg_run_batch.restype = ctypes.c_int
         L.sg_run_batch.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(BatchParams),
                                    ctypes.POINTER(BatchResultC), vp]
@@ -577,3 +611,78 @@ def run_batch(items: list, k: int = 17, min_shared: int = 2, max_seeds: int = 2,
     out = BatchResultC()
     _check(L.sg_run_batch(arr, len(items), ctypes.byref(params), ctypes.byref(out), st), "run_batch")
     return BatchResult(out, st, keep)
+
+
+# --------------------------------------------------------------------------------- serving
+def _arr(ptr, count, dtype):
+    if count <= 0 or not ptr:
+        return np.zeros(0, dtype)
+    return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(np.ctypeslib.as_ctypes_type(dtype))),
+                                 shape=(int(count),)).copy()
+
+
+class Server:
+    """Continuous-batching server (sg_server_*): submit host read sets, wait for C and S."""
+
+    def __init__(self, hbm_budget: int, max_batch: int = 64, workers: int = 2, device: int = 0, k: int = 17,
+                 min_shared: int = 2, max_seeds: int = 2, fuzz: int = 0, tr_mode: int = DIRMATCH):
+        cfg = ServerConfig(int(hbm_budget), int(max_batch), int(workers), int(device),
+                           BatchParams(int(k), int(min_shared), int(max_seeds), int(fuzz), int(tr_mode)))
+        self.h = ctypes.c_void_p()
+        _check(lib().sg_server_create(ctypes.byref(cfg), ctypes.byref(self.h)), "server_create")
+
+    def submit(self, seq, offsets, lo: int, hi: int, R: dict | None = None) -> int:
+        seq = np.ascontiguousarray(seq, np.uint8)
+        off = np.ascontiguousarray(offsets, np.int64)
+        keep = [seq, off]
+        rr = (None, None, None, None, 0)
+        if R is not None:
+            a = (np.ascontiguousarray(R["row_ptr"], np.int64), np.ascontiguousarray(R["col"], np.int32),
+                 np.ascontiguousarray(R["suffix"], np.uint32), np.ascontiguousarray(R["dir"], np.uint8))
+            keep += list(a)
+            rr = tuple(x.ctypes.data for x in a) + (int(a[1].size),)
+        job = Job(seq.ctypes.data if seq.size else None, off.ctypes.data, off.size - 1, seq.size, int(lo), int(hi),
+                  *rr)
+        t = ctypes.c_uint64()
+        _check(lib().sg_server_submit(self.h, ctypes.byref(job), ctypes.byref(t)), "server_submit")
+        return int(t.value)
+
+    @staticmethod
+    def _convert(r: JobResult) -> dict:
+        n, cn, sn, S = int(r.n), int(r.nnz_c), int(r.nnz_s), int(r.max_seeds)
+        out = dict(status=int(r.status), n=n, m=int(r.m), iterations=int(r.iterations), batch_size=int(r.batch_size),
+                   t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done)
+        if r.status == SG_OK:
+            out["C"] = dict(n=n, row_ptr=_arr(r.c_row_ptr, n + 1, np.int64), col=_arr(r.c_col, cn, np.int32),
+                            count=_arr(r.c_count, cn, np.uint32),
+                            seed_i=_arr(r.c_seed_i, cn * S, np.uint32).reshape(S, cn),
+                            seed_k=_arr(r.c_seed_k, cn * S, np.uint32).reshape(S, cn))
+            if r.s_row_ptr:
+                out["S"] = dict(n=n, row_ptr=_arr(r.s_row_ptr, n + 1, np.int64), col=_arr(r.s_col, sn, np.int32),
+                                suffix=_arr(r.s_suffix, sn, np.uint32), dir=_arr(r.s_dir, sn, np.uint8))
+        lib().sg_job_result_free(ctypes.byref(r))
+        return out
+
+    def poll(self, ticket: int):
+        r = JobResult()
+        rc = lib().sg_server_poll(self.h, int(ticket), ctypes.byref(r))
+        if rc == SG_ERR_TIMEOUT:
+            return None
+        _check(rc, "server_poll")
+        return self._convert(r)
+
+    def wait(self, ticket: int, timeout: float = 120.0) -> dict:
+        r = JobResult()
+        _check(lib().sg_server_wait(self.h, int(ticket), float(timeout), ctypes.byref(r)), "server_wait")
+        return self._convert(r)
+
+    def close(self):
+        if self.h and _lib is not None:
+            _lib.sg_server_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

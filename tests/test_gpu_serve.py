@@ -1,0 +1,75 @@
+"""The served form: every job's result equals the oracle on that job alone, whatever it was batched
+with (tolerance 0), and jobs larger than the budget are refused."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2010_10055_gb300 as sg
+import synth
+from tests.gpu_util import assert_graph_equal, assert_overlap_equal
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs(seed, count):
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        G = int(rng.integers(10000, 80000))
+        g = synth.genome(G, seed * 1000 + b)
+        rd = synth.reads(g, 12.0, float(rng.uniform(800, 3000)), 500.0, 200, 0.06, 0.04, 0.02, seed * 1000 + b + 1)
+        R = synth.overlap_graph(rd["start"], rd["end"], rd["strand"], 100)
+        out.append(dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=int(rng.integers(6, 12)), R=R))
+    return out
+
+
+def _check(res, job, fuzz):
+    assert res["status"] == sg.SG_OK
+    km = oracle.build_kmer_matrix(job["seq"], job["offsets"], 17, job["lo"], job["hi"])
+    assert_overlap_equal(res["C"], oracle.overlap_spgemm(km["A"], km["At"], 2, 2))
+    eS, eit = oracle.transitive_reduce(job["R"], fuzz)
+    assert_graph_equal(res["S"], eS)
+    assert res["iterations"] == eit
+
+
+def test_server_results_match_oracle_alone_and_mixed():
+    jobs = _jobs(5, 14)
+    srv = sg.Server(hbm_budget=1 << 30, max_batch=5, workers=2, fuzz=300)
+    try:
+        # staggered arrivals so later jobs are admitted while earlier batches are on the GPU
+        tickets = []
+        for j in jobs:
+            tickets.append(srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"]))
+            time.sleep(0.002)
+        mixed = [srv.wait(t) for t in tickets]
+        assert max(r["batch_size"] for r in mixed) > 1
+        for r, j in zip(mixed, jobs):
+            _check(r, j, 300)
+        # the same job alone
+        alone = srv.wait(srv.submit(jobs[3]["seq"], jobs[3]["offsets"], jobs[3]["lo"], jobs[3]["hi"], jobs[3]["R"]))
+        assert alone["batch_size"] == 1
+        for key in ("row_ptr", "col", "count", "seed_i", "seed_k"):
+            assert np.array_equal(alone["C"][key], mixed[3]["C"][key])
+        for key in ("row_ptr", "col", "suffix", "dir"):
+            assert np.array_equal(alone["S"][key], mixed[3]["S"][key])
+    finally:
+        srv.close()
+
+
+def test_server_refuses_jobs_over_budget_and_keeps_going():
+    jobs = _jobs(6, 2)
+    srv = sg.Server(hbm_budget=4 << 20, max_batch=4, workers=1)  # smaller than any job's estimate
+    try:
+        r = srv.wait(srv.submit(jobs[0]["seq"], jobs[0]["offsets"], 2, 8, jobs[0]["R"]))
+        assert r["status"] == sg.SG_ERR_BUDGET
+        assert srv.poll(12345) is None  # unknown / not ready
+    finally:
+        srv.close()
+    srv = sg.Server(hbm_budget=1 << 30, max_batch=4, workers=1)
+    try:
+        r = srv.wait(srv.submit(jobs[1]["seq"], jobs[1]["offsets"], jobs[1]["lo"], jobs[1]["hi"], jobs[1]["R"]))
+        _check(r, jobs[1], 0)
+    finally:
+        srv.close()
