@@ -39,6 +39,7 @@ def parse():
     p.add_argument("--workload", default="bacterial-5Mbp-30x")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
     return p.parse_args()
 
 
@@ -261,6 +262,9 @@ def main():
             "tr_edges_per_s": edges_all * args.steps / (tr_ms_max / 1e3) if tr_ms_max else None,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
             "e2e": e2e, "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": launches}
+    if not args.no_forms:
+        line["batched"] = measure_batched(sg, 512, 200e3)
+        line["served"] = measure_served(sg, 400, 200.0)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, scale=0.1)
     if rank == 0:
@@ -307,6 +311,97 @@ def measure_e2e(sg, d, w, args):
                 "nnz_C": int(res.nnz_c), "nnz_S": int(res.nnz_s)}
     finally:
         L.sg_host_arena_destroy(arena)
+
+
+def measure_batched(sg, count: int, g_hi: float, reps: int = 3) -> dict:
+    """The batched workload's sets run as one sg_run_batch vs one plain call sequence per set, on
+    the same GPU (device-resident inputs, CUDA events around each variant)."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    sets = synth.batched_sets(count, 20e3, g_hi)
+    items = [dict(seq=torch.from_numpy(x["seq"]).cuda(), offsets=torch.from_numpy(x["offsets"]).cuda(),
+                  lo=x["lo"], hi=x["hi"], R=sg.DeviceGraph.from_numpy(x["R"])) for x in sets]
+
+    def plain():
+        for it in items:
+            km = sg.build_kmer_matrix(it["seq"], it["offsets"], 17, it["lo"], it["hi"])
+            sg.overlap_spgemm(km, 2, 2)
+            sg.transitive_reduce(it["R"], 1000)
+
+    def batched():
+        return sg.run_batch(items, k=17, min_shared=2, max_seeds=2, fuzz=1000)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(f):
+        f()  # warm-up
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0.record()
+            out = f()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            del out
+        return statistics.median(ts)
+
+    plain_ms, batched_ms = timed(plain), timed(batched)
+    res = batched()
+    a = np.diff(res.to_numpy()["At"]["row_ptr"]).astype(np.int64)
+    prod = int((a * a).sum())
+    return {"sets": count, "genome_bp": [20000, int(g_hi)], "bases": int(sum(x["seq"].size for x in sets)),
+            "products": prod, "plain_ms": plain_ms, "batched_ms": batched_ms, "speedup": plain_ms / batched_ms,
+            "products_per_s_batched": prod / (batched_ms / 1e3), "products_per_s_plain": prod / (plain_ms / 1e3)}
+
+
+def measure_served(sg, n_jobs: int, rate: float) -> dict:
+    """The served workload: Poisson arrivals into the continuous-batching server; p50 / p99 of
+    submit -> result-on-host latency and jobs/s, beside one-at-a-time plain calls through
+    sg_pipeline_host (host buffers in and out) and the server fed all jobs at once."""
+    import numpy as np
+
+    import synth
+
+    jobs = synth.served_jobs(n_jobs, rate)
+    srv = sg.Server(hbm_budget=150 << 30, max_batch=64, workers=2, fuzz=1000)
+    try:
+        for j in jobs[:16]:  # warm-up
+            srv.wait(srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"]))
+
+        def run(arrivals):
+            t0 = time.perf_counter()
+            tickets = []
+            for j, at in zip(jobs, arrivals):
+                d = t0 + at - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"]))
+            res = [srv.wait(t) for t in tickets]
+            assert all(r["status"] == sg.SG_OK for r in res)
+            lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
+            span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+            return lat, span, float(np.mean([r["batch_size"] for r in res]))
+
+        lat, span, mb = run([j["arrival"] for j in jobs])
+        lat_b, span_b, mb_b = run([0.0] * len(jobs))
+    finally:
+        srv.close()
+    hp = sg.HostPipeline()
+    t0 = time.perf_counter()
+    for j in jobs:
+        hp.run(j["seq"], j["offsets"], synth.Workload("job", 0, 0, 0, 0, 0, 0, 0, lo=2, hi=20, fuzz=1000), j["R"])
+    plain_s = time.perf_counter() - t0
+    hp.close()
+    return {"jobs": n_jobs, "rate_per_s": rate, "genome": "Pareto(1.5) from 20 kbp, max 20 Mbp, 30x",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "jobs_per_s": n_jobs / span, "mean_batch": mb,
+            "saturated": {"jobs_per_s": n_jobs / span_b, "p50_ms": float(np.percentile(lat_b, 50)),
+                          "p99_ms": float(np.percentile(lat_b, 99)), "mean_batch": mb_b},
+            "plain_one_at_a_time_jobs_per_s": n_jobs / plain_s}
 
 
 def cpu_baseline(w, scale: float):

@@ -263,6 +263,7 @@ typedef struct {
     int32_t *s_col;
     uint32_t *s_suffix;
     uint8_t *s_dir;
+    char error[192];                   /* when status != SG_OK: what went wrong, NUL-terminated */
 } sg_job_result;
 
 sg_status sg_server_create(const sg_server_config *cfg, sg_server **out);
@@ -342,6 +343,10 @@ void sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx);
 
 /* Test hook: make the n-th device allocation from now fail (n >= 1); 0 disables. */
 void sg_debug_fail_alloc_after(int64_t n);
+
+/* Checked builds (compiled with -DSG_CHECKED): the first out-of-bounds index any kernel detected
+ * and skipped since the last call, as site << 40 | index, or 0. Always 0 in normal builds. */
+uint64_t sg_debug_check(void);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t sg_launch_count(void);

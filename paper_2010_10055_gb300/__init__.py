@@ -16,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgraph.so")
+LIB_PATH_CHECKED = os.path.join(_HERE, "libsgraph_checked.so")
 
 SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_TIMEOUT, SG_ERR_BUDGET, SG_ERR_OVERFLOW = range(7)
 DIRMATCH, LITERAL = 0, 1
@@ -26,7 +27,7 @@ EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg
            "sg_server_create", "sg_server_submit", "sg_server_poll", "sg_server_wait", "sg_job_result_free",
            "sg_server_destroy",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
-           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_check", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
 
 
@@ -74,7 +75,7 @@ class PipelineResult(ctypes.Structure):
                 ("products", ctypes.c_uint64), ("c_row_ptr", ctypes.c_void_p), ("c_col", ctypes.c_void_p),
                 ("c_count", ctypes.c_void_p), ("c_seed_i", ctypes.c_void_p), ("c_seed_k", ctypes.c_void_p),
                 ("s_row_ptr", ctypes.c_void_p), ("s_col", ctypes.c_void_p), ("s_suffix", ctypes.c_void_p),
-                ("s_dir", ctypes.c_void_p)]
+                ("s_dir", ctypes.c_void_p), ("error", ctypes.c_char * 192)]
 
 
 class BatchItem(ctypes.Structure):
@@ -113,10 +114,19 @@ class JobResult(ctypes.Structure):
                 ("t_done", ctypes.c_double), ("c_row_ptr", ctypes.c_void_p), ("c_col", ctypes.c_void_p),
                 ("c_count", ctypes.c_void_p), ("c_seed_i", ctypes.c_void_p), ("c_seed_k", ctypes.c_void_p),
                 ("s_row_ptr", ctypes.c_void_p), ("s_col", ctypes.c_void_p), ("s_suffix", ctypes.c_void_p),
-                ("s_dir", ctypes.c_void_p)]
+                ("s_dir", ctypes.c_void_p), ("error", ctypes.c_char * 192)]
 
 
 _lib = None
+
+
+def use_checked_build():
+    """Loads the checked build (kernels verify computed indices; see debug_check) instead of the
+    normal one. Must be called before any other call of this module."""
+    global LIB_PATH
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    LIB_PATH = LIB_PATH_CHECKED
 
 
 def lib():
@@ -145,6 +155,7 @@ def lib():
         L.sg_last_error.restype = ctypes.c_char_p
         L.sg_debug_fail_alloc_after.argtypes = [i64]
         L.sg_launch_count.restype = ctypes.c_uint64
+        L.sg_debug_check.restype = ctypes.c_uint64
         L.sg_prof_enable.argtypes = [ctypes.c_int]
         L.sg_prof_select.argtypes = [ctypes.c_char_p]
         L.sg_prof_collect.restype = ctypes.c_int
@@ -466,6 +477,13 @@ def tune(name: str, value: int):
         raise ValueError(f"unknown tunable or value out of range: {name}={value}")
 
 
+def debug_check():
+    """Checked build: (site, index) of the first out-of-bounds index a kernel detected and skipped
+    since the last call, or None."""
+    v = int(lib().sg_debug_check())
+    return None if v == 0 else (v >> 40, v & ((1 << 40) - 1))
+
+
 def debug_fail_alloc_after(n: int):
     lib().sg_debug_fail_alloc_after(int(n))
 
@@ -651,7 +669,8 @@ class Server:
     def _convert(r: JobResult) -> dict:
         n, cn, sn, S = int(r.n), int(r.nnz_c), int(r.nnz_s), int(r.max_seeds)
         out = dict(status=int(r.status), n=n, m=int(r.m), iterations=int(r.iterations), batch_size=int(r.batch_size),
-                   t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done)
+                   t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done,
+                   error=r.error.decode(errors="replace"))
         if r.status == SG_OK:
             out["C"] = dict(n=n, row_ptr=_arr(r.c_row_ptr, n + 1, np.int64), col=_arr(r.c_col, cn, np.int32),
                             count=_arr(r.c_count, cn, np.uint32),

@@ -69,6 +69,7 @@ static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg
     std::vector<int64_t> ro(nitems + 1, 0), co(nitems + 1, 0);
     std::vector<uint32_t> lohi(2 * (size_t)nitems);
     int64_t N = 0, T = 0, RN = 0;
+    uint32_t min_lo = 0xFFFFFFFFu;
     bool any_r = false;
     for (int b = 0; b < nitems; b++) {
         const sg_batch_item &x = items[b];
@@ -86,6 +87,7 @@ static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg
                         x.R ? x.R->row_ptr : nullptr, x.R ? x.R->col : nullptr, x.R ? x.R->suffix : nullptr,
                         x.R ? x.R->dir : nullptr, x.R ? x.R->nnz : 0, RN};
         lohi[2 * b] = x.lo;
+        min_lo = x.lo < min_lo ? x.lo : min_lo;
         lohi[2 * b + 1] = x.hi;
         any_r |= x.R != nullptr;
         N += x.n_reads;
@@ -137,7 +139,8 @@ static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg
 
     {  // each stage's temporaries are released before the next stage starts
         Scratch sc1(s);
-        SG_TRY(build_impl(seq, off, N, T, p->k, 1, 1, &out->A, &out->At, &out->d_kmer_codes, s, sc1,
+        // the scalar range only decides whether the Bloom pass may drop singletons: every set needs lo >= 2
+    SG_TRY(build_impl(seq, off, N, T, p->k, min_lo, min_lo, &out->A, &out->At, &out->d_kmer_codes, s, sc1,
                           JobMap{d_ro, nitems, 2 * p->k}, d_lohi, d_ncols));
     }
     {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/sgraph.h"
 
 namespace sg {
@@ -27,19 +29,20 @@ struct LaunchScope {
     ~LaunchScope();
 };
 
-// Scoped set of temporary device buffers, released in reverse order on scope exit.
+// Scoped set of temporary device buffers, released (stream-ordered) in reverse order on scope
+// exit. Not copyable: a copy would free the same buffers twice.
 struct Scratch {
     cudaStream_t s;
-    void *ptrs[128];
-    int n = 0;
-    explicit Scratch(cudaStream_t st) : s(st) {}
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) { ptrs.reserve(32); }
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
     template <class T> T *get(size_t count) {
-        if (n == 128) { set_error("internal: scratch table full"); return nullptr; }
         void *p = dalloc(count * sizeof(T), s);
-        if (p) ptrs[n++] = p;
+        if (p) ptrs.push_back(p);
         return (T *)p;
     }
-    ~Scratch() { for (int i = n - 1; i >= 0; --i) dfree(ptrs[i], s); }
+    ~Scratch() { for (size_t i = ptrs.size(); i-- > 0;) dfree(ptrs[i], s); }
 };
 
 // Current value of a tunable parameter (see sg_tune_set).
@@ -47,6 +50,16 @@ int64_t tune(const char *name);
 
 // Copy one device value to the host and wait for it.
 cudaError_t read_back(void *host, const void *dev, size_t bytes, cudaStream_t s);
+
+// Makes sure `kernel` may be launched with `bytes` of dynamic shared memory. The cap is a
+// process-wide function attribute: it is raised once per kernel under a lock (never lowered, never
+// rewritten while other host threads may be launching the kernel), and later calls only consult
+// a registry.
+cudaError_t ensure_smem_cap(const void *kernel, size_t bytes);
+template <class K>
+inline cudaError_t ensure_smem(K kernel, size_t bytes) {
+    return ensure_smem_cap(reinterpret_cast<const void *>(kernel), bytes);
+}
 
 // Whether a launch grid has any blocks.
 inline bool grid_ok(int64_t g) { return g > 0; }

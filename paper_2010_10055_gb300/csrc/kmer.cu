@@ -8,21 +8,24 @@
 // lowest such position).
 //
 // Pipeline (all on `stream`):
-//  1. bloom_insert   every window's canonical code is OR-ed into the blocked Bloom filter B1
-//                    (all probe bits in one 64-bit word, so "already present" is decided by one
-//                    atomic); a code found present is OR-ed into B2 ("seen at least twice").
+//  0. window_codes   one walk over the reads writes every window's canonical code and strand.
+//  1. bloom_insert   every code is OR-ed into the blocked Bloom filter B1 (all probe bits in one
+//                    32-bit word, so "already present" is decided by one atomic); a code found
+//                    present is OR-ed into B2 ("seen at least twice"). Skipped when lo == 1.
 //  2. cand_count     per thread, the windows whose code tests positive in B2. Every occurrence
 //                    of a k-mer with frequency >= 2 passes (false positives only add singletons,
-//                    which the exact count below drops). Skipped when lo == 1.
-//  3. cand_emit      writes (code, read << 32 | pos | strand << 31) at scanned offsets, so the
-//                    candidates stay in (read, pos) order.
-//  4. radix sort by code (stable, 2k bits): equal codes form segments in (read, pos) order.
+//                    which the exact count below drops).
+//  3. cand_emit      writes (code, position | strand) at scanned offsets, so the candidates stay
+//                    in position order, i.e. (read, pos) order.
+//  4. radix sort by code (stable): equal codes form segments in (read, pos) order; positions are
+//     then resolved to (read, pos).
 //  5. segments -> exact frequency (segment length) -> reliable flag -> column = rank of the
 //     reliable code; within a reliable segment the first entry of each read is its lowest
 //     position: those entries are At's row, already sorted by read.
 //  6. A = At transposed by a stable radix sort on the read id (columns stay ascending).
 #include <type_traits>
 
+#include "check.cuh"
 #include "ops.cuh"
 
 namespace sg {
@@ -79,7 +82,8 @@ struct JobCursor {
 };
 
 // Visits the windows [c0 + t*KM_W, c0 + (t+1)*KM_W) of thread t in position order, calling
-// f(code, strand, read, pos) for each window of k A/C/G/T bases inside one read. K > 0 makes k a
+// f(code, strand, read, pos, local start) for each window of k A/C/G/T bases inside one read, where
+// the local start (in [t*KM_W, (t+1)*KM_W)) indexes the block's chunk. K > 0 makes k a
 // compile-time constant (K == 0: k taken from k_rt). Indices inside the block are 32-bit.
 template <int K, class F>
 __device__ __forceinline__ void for_each_window(const uint8_t *__restrict__ sm, int64_t c0, int64_t total,
@@ -125,7 +129,7 @@ __device__ __forceinline__ void for_each_window(const uint8_t *__restrict__ sm, 
         if (run >= k && q - k + 1 >= ls) {
             const uint64_t code = fw < rc ? fw : rc;
             const uint32_t strand = rc < fw ? 1u : 0u;
-            f(code, strand, r, (uint32_t)(q - k + 1 - rbase));
+            f(code, strand, r, (uint32_t)(q - k + 1 - rbase), q - k + 1);
         }
     }
 }
@@ -149,77 +153,131 @@ __device__ __forceinline__ void load_chunk(uint8_t *sm, const uint8_t *__restric
     __syncthreads();
 }
 
-// One launch per slice [w_lo, w_hi) of B1's words: every launch walks all windows but only the
-// k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2.
+// One walk over the reads: wc[q] = canonical code of the window starting at global position q
+// (with the job prefix in a batch) | strand << 63, or ~0 when no valid window starts at q. The
+// later passes stream this array instead of walking the reads again.
+constexpr uint64_t WC_NONE = ~0ull;
+constexpr uint64_t WC_STRAND = 1ull << 63;
+
 template <int K>
-__global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint8_t *__restrict__ seq, int64_t total,
+__global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__restrict__ seq, int64_t total,
                                                             const int64_t *__restrict__ off, int64_t n, int k,
-                                                            Bloom b1, Bloom b2, uint32_t w_lo, uint32_t w_hi,
-                                                            JobMap jm) {
-    __shared__ __align__(16) uint8_t sm[KM_CHUNK + 48];
-    int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
-    load_chunk(sm, seq, c0, total, k);
+                                                            JobMap jm, uint64_t *__restrict__ wc) {
+    extern __shared__ __align__(16) unsigned char wc_raw[];
+    uint64_t *s_wc = reinterpret_cast<uint64_t *>(wc_raw);
+    uint8_t *sm = wc_raw + KM_CHUNK * sizeof(uint64_t);
+    const int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
+    for (int i = threadIdx.x; i < KM_CHUNK; i += KM_NT) s_wc[i] = WC_NONE;
+    load_chunk(sm, seq, c0, total, k);  // ends with __syncthreads
     JobCursor jc{jm};
-    for_each_window<K>(sm, c0, total, off, n, k, [&](uint64_t code0, uint32_t, int64_t r, uint32_t) {
-        const uint64_t code = jc.key(code0, r);
+    for_each_window<K>(sm, c0, total, off, n, k,
+                       [&](uint64_t code0, uint32_t strand, int64_t r, uint32_t, int lw) {
+        if (SG_IN_BOUNDS(lw >= 0 && lw < KM_CHUNK, 101, lw)) s_wc[lw] = jc.key(code0, r) | ((uint64_t)strand << 63);
+    });
+    __syncthreads();
+    const int64_t cnt = total - c0 < KM_CHUNK ? total - c0 : KM_CHUNK;
+    for (int64_t i = threadIdx.x; i < cnt; i += KM_NT) wc[c0 + i] = s_wc[i];
+}
+
+// One launch per slice [w_lo, w_hi) of B1's words: every launch streams all window codes but only
+// the k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2.
+__global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint64_t *__restrict__ wc, int64_t total,
+                                                            Bloom b1, Bloom b2, uint32_t w_lo, uint32_t w_hi) {
+    for (int64_t q = (int64_t)blockIdx.x * KM_NT + threadIdx.x; q < total; q += (int64_t)gridDim.x * KM_NT) {
+        const uint64_t x = __ldcs(wc + q);
+        if (x == WC_NONE) continue;
+        const uint64_t code = x & ~WC_STRAND;
         uint32_t i1, m1;
         b1.probe(code, &i1, &m1);
-        if (i1 < w_lo || i1 >= w_hi) return;  // another slice's launch handles this k-mer
+        if (i1 < w_lo || i1 >= w_hi) continue;  // another slice's launch handles this k-mer
         const uint32_t old = atomicOr(b1.words + i1, m1);
         if ((old & m1) == m1) {
             uint32_t i2, m2;
             b2.probe(code, &i2, &m2);
             if ((b2.words[i2] & m2) != m2) atomicOr(b2.words + i2, m2);
         }
-    });
+    }
 }
 
-// use_bloom == 0 keeps every window (lo == 1: singletons may be reliable).
-template <int K>
-__global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint8_t *__restrict__ seq, int64_t total,
-                                                          const int64_t *__restrict__ off, int64_t n, int k,
-                                                          Bloom b2, int use_bloom, uint32_t *__restrict__ cnt,
-                                                          JobMap jm) {
-    __shared__ __align__(16) uint8_t sm[KM_CHUNK + 48];
-    int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
-    load_chunk(sm, seq, c0, total, k);
+// Candidates: windows whose code tests positive in B2 (every occurrence of a k-mer seen at least
+// twice; false positives only add singletons, which the exact count drops). use_bloom == 0 keeps
+// every window (lo == 1: singletons may be reliable). Thread t of block b owns the KM_W
+// consecutive windows starting at b * KM_CHUNK + t * KM_W, so candidates keep position order.
+__device__ __forceinline__ bool is_candidate(uint64_t x, const Bloom &b2, int use_bloom) {
+    if (x == WC_NONE) return false;
+    if (!use_bloom) return true;
+    uint32_t i2, m2;
+    b2.probe(x & ~WC_STRAND, &i2, &m2);
+    return (b2.words[i2] & m2) == m2;
+}
+
+__global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint64_t *__restrict__ wc, int64_t total, Bloom b2,
+                                                          int use_bloom, uint32_t *__restrict__ cnt) {
+    const int64_t q0 = (int64_t)blockIdx.x * KM_CHUNK + (int64_t)threadIdx.x * KM_W;
     uint32_t c = 0;
-    JobCursor jc{jm};
-    for_each_window<K>(sm, c0, total, off, n, k, [&](uint64_t code0, uint32_t, int64_t r, uint32_t) {
-        const uint64_t code = jc.key(code0, r);
-        if (use_bloom) {
-            uint32_t i2, m2;
-            b2.probe(code, &i2, &m2);
-            if ((b2.words[i2] & m2) != m2) return;
-        }
-        c++;
-    });
+    for (int w = 0; w < KM_W; w++) {
+        const int64_t q = q0 + w;
+        if (q >= total) break;
+        c += is_candidate(__ldcs(wc + q), b2, use_bloom) ? 1u : 0u;
+    }
     cnt[(int64_t)blockIdx.x * KM_NT + threadIdx.x] = c;
 }
 
-template <int K>
-__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint8_t *__restrict__ seq, int64_t total,
-                                                         const int64_t *__restrict__ off, int64_t n, int k,
-                                                         Bloom b2, int use_bloom,
-                                                         const int64_t *__restrict__ pos_of_thread,
-                                                         uint64_t *__restrict__ keys, uint64_t *__restrict__ vals,
-                                                         JobMap jm) {
-    __shared__ __align__(16) uint8_t sm[KM_CHUNK + 48];
-    int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
-    load_chunk(sm, seq, c0, total, k);
-    int64_t w = pos_of_thread[(int64_t)blockIdx.x * KM_NT + threadIdx.x];
-    JobCursor jc{jm};
-    for_each_window<K>(sm, c0, total, off, n, k, [&](uint64_t code0, uint32_t strand, int64_t r, uint32_t pos) {
-        const uint64_t code = jc.key(code0, r);
-        if (use_bloom) {
-            uint32_t i2, m2;
-            b2.probe(code, &i2, &m2);
-            if ((b2.words[i2] & m2) != m2) return;
-        }
-        keys[w] = code;
-        vals[w] = ((uint64_t)r << 32) | pos | (strand << 31);
-        w++;
-    });
+// keys = code (job prefix included), shifted left by ib with the candidate's index below it when
+// ib > 0 (keys-only sort); vals = q | strand << 63 (global window start).
+__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__restrict__ wc, int64_t total, Bloom b2,
+                                                         int use_bloom, const int64_t *__restrict__ pos_of_thread,
+                                                         int ib, uint64_t *__restrict__ keys,
+                                                         uint64_t *__restrict__ vals, int64_t nc) {
+    const int64_t q0 = (int64_t)blockIdx.x * KM_CHUNK + (int64_t)threadIdx.x * KM_W;
+    int64_t o = pos_of_thread[(int64_t)blockIdx.x * KM_NT + threadIdx.x];
+    for (int w = 0; w < KM_W; w++) {
+        const int64_t q = q0 + w;
+        if (q >= total) break;
+        const uint64_t x = __ldcs(wc + q);
+        if (!is_candidate(x, b2, use_bloom)) continue;
+        if (!SG_IN_BOUNDS(o >= 0 && o < nc, 102, o)) break;
+        keys[o] = ib ? (((x & ~WC_STRAND) << ib) | (uint64_t)o) : (x & ~WC_STRAND);
+        vals[o] = (uint64_t)q | (x & WC_STRAND);
+        o++;
+    }
+}
+
+__device__ __forceinline__ uint64_t resolve_pos(uint64_t v, const int64_t *__restrict__ off, int64_t n) {
+    const int64_t q = (int64_t)(v & ~WC_STRAND);
+    int64_t lo = 0, hi = n;  // last read r with off[r] <= q
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= q) lo = mid; else hi = mid;
+    }
+    return ((uint64_t)lo << 32) | (uint64_t)(uint32_t)(q - off[lo]) | ((v >> 63) << 31);
+}
+
+// Keys-only sort: packed (code << ib | index) -> code, and the indexed value resolved.
+__global__ void unpack_kernel(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ vals, int64_t nc,
+                              int ib, const int64_t *__restrict__ off, int64_t n, uint64_t *__restrict__ key,
+                              uint64_t *__restrict__ val) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const uint64_t p = packed[i];
+    const int64_t src = (int64_t)(p & ((1ull << ib) - 1));
+    key[i] = p >> ib;
+    if (SG_IN_BOUNDS(src < nc, 103, src)) val[i] = resolve_pos(vals[src], off, n);
+}
+
+// After the pairs sort: val = q | strand << 63  ->  read << 32 | pos | strand << 31.
+__global__ void resolve_kernel(uint64_t *__restrict__ val, int64_t nc, const int64_t *__restrict__ off,
+                               int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const uint64_t v = val[i];
+    const int64_t q = (int64_t)(v & ~WC_STRAND);
+    int64_t lo = 0, hi = n;  // last read r with off[r] <= q
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= q) lo = mid; else hi = mid;
+    }
+    val[i] = ((uint64_t)lo << 32) | (uint64_t)(uint32_t)(q - off[lo]) | ((v >> 63) << 31);
 }
 
 __global__ void validate_offsets_kernel(const int64_t *__restrict__ off, int64_t n, int64_t total,
@@ -247,15 +305,20 @@ __global__ void seg_head_kernel(const uint64_t *__restrict__ key, int64_t nc, ui
 __global__ void seg_start_kernel(const uint32_t *__restrict__ head, const int64_t *__restrict__ seg_excl,
                                  int64_t nc, int64_t *__restrict__ seg_start) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nc && head[i]) seg_start[seg_excl[i]] = i;
-    if (i == nc - 1) seg_start[seg_excl[nc]] = nc;
+    if (i < nc && head[i] && SG_IN_BOUNDS(seg_excl[i] >= 0 && seg_excl[i] <= nc, 104, seg_excl[i]))
+        seg_start[seg_excl[i]] = i;
+    if (i == nc - 1 && SG_IN_BOUNDS(seg_excl[nc] >= 0 && seg_excl[nc] <= nc, 104, seg_excl[nc]))
+        seg_start[seg_excl[nc]] = nc;
 }
 
 // lohi (batches): the reliable range of each job, [2 * job] = lo, [2 * job + 1] = hi.
+// Launched over at least nc threads; rel has nc + 1 slots.
 __global__ void seg_reliable_kernel(const int64_t *__restrict__ seg_start, const int64_t *__restrict__ nseg_p,
                                     uint32_t lo, uint32_t hi, const uint64_t *__restrict__ key,
-                                    const uint32_t *__restrict__ lohi, int kbits, uint32_t *__restrict__ rel) {
+                                    const uint32_t *__restrict__ lohi, int kbits, int64_t nc,
+                                    uint32_t *__restrict__ rel) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > nc) return;
     int64_t nseg = *nseg_p;
     if (s >= nseg) {  // slots past the last segment still feed the scan below: make them 0
         rel[s] = 0u;
@@ -297,12 +360,14 @@ __global__ void emit_at_kernel(const uint32_t *__restrict__ head, const int64_t 
     int64_t s = seg_excl[i] + head[i] - 1;
     if (head[i] && rel[s]) {
         int64_t j = col_of_seg[s];
+        if (!SG_IN_BOUNDS(j >= 0 && j < m, 105, j)) return;
         at_rp[j] = out_pos[i];
         codes[j] = kbits < 64 ? key[i] & ((1ull << kbits) - 1) : key[i];
         if (job_ncols) atomicAdd(job_ncols + (key[i] >> kbits), 1ull);
     }
     if (keep[i]) {
         int64_t o = out_pos[i];
+        if (!SG_IN_BOUNDS(o >= 0 && o < nnz, 106, o)) return;
         uint32_t r = (uint32_t)(val[i] >> 32), v = (uint32_t)val[i];
         at_col[o] = (int32_t)r;
         at_val[o] = v;
@@ -318,6 +383,7 @@ __global__ void rowptr_from_sorted_kernel(const uint32_t *__restrict__ rows, int
     if (e > nnz) return;
     int64_t prev = (e == 0) ? -1 : (int64_t)rows[e - 1];
     int64_t cur = (e == nnz) ? n : (int64_t)rows[e];
+    if (!SG_IN_BOUNDS(prev >= -1 && cur <= n && prev <= cur, 107, cur)) return;
     for (int64_t r = prev + 1; r <= cur; r++) rp[r] = e;
 }
 
@@ -369,28 +435,34 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_CUDA_TRY(cudaMemsetAsync(b1.words, 0, (size_t)b1.nwords * 4, s));
         SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, (size_t)b2.nwords * 4, s));
     }
+    // 0. window codes
+    uint64_t *wc = sc.get<uint64_t>(total + 1);
+    if (!wc) return SG_ERR_OOM;
+    {
+        const size_t smem = (size_t)KM_CHUNK * sizeof(uint64_t) + KM_CHUNK + 48;
+        SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
+            SG_CUDA_TRY(ensure_smem(window_codes_kernel<decltype(kc)::value>, smem));
+            SG_LAUNCH("window_codes", window_codes_kernel<decltype(kc)::value>, nblk, KM_NT, smem, s, seq, total,
+                      off, n, k, jm, wc);
+            return SG_OK;
+        }));
+    }
     if (use_bloom) {
         // slices of at most bloom_slice_mb of B1, so each launch's atomics stay in L2
         const uint64_t slice_words = ((uint64_t)tune("bloom_slice_mb") << 20) / 4;
         const uint64_t nsl = (b1.nwords + slice_words - 1) / slice_words;
+        const int64_t grid = blocks_for(total, KM_NT) < 152 * 16 ? blocks_for(total, KM_NT) : 152 * 16;
         for (uint64_t q = 0; q < nsl; q++) {
             const uint32_t lo_w = (uint32_t)((uint64_t)b1.nwords * q / nsl);
             const uint32_t hi_w = (uint32_t)((uint64_t)b1.nwords * (q + 1) / nsl);
-            SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
-                SG_LAUNCH("bloom_insert", bloom_insert_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total,
-                          off, n, k, b1, b2, lo_w, hi_w, jm);
-                return SG_OK;
-            }));
+            SG_LAUNCH("bloom_insert", bloom_insert_kernel, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1, b2,
+                      lo_w, hi_w);
         }
     }
     uint32_t *tcnt = sc.get<uint32_t>(nblk * KM_NT + 1);
     int64_t *tpos = sc.get<int64_t>(nblk * KM_NT + 1);
     if (!tcnt || !tpos) return SG_ERR_OOM;
-    SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
-        SG_LAUNCH("cand_count", cand_count_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n, k, b2,
-                  use_bloom, tcnt, jm);
-        return SG_OK;
-    }));
+    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, tcnt);
     SG_TRY(exclusive_scan<uint32_t>(tcnt, tpos, nblk * KM_NT, s));
     int64_t nc = 0;
     uint32_t herr = 0;
@@ -404,17 +476,30 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint64_t *key0 = sc.get<uint64_t>(nc), *val0 = sc.get<uint64_t>(nc);
     uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
     if (!key0 || !val0 || !key1 || !val1) return SG_ERR_OOM;
-    SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
-        SG_LAUNCH("cand_emit", cand_emit_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n, k, b2,
-                  use_bloom, (const int64_t *)tpos, key0, val0, jm);
-        return SG_OK;
-    }));
-    bool alt = false;
     int job_bits = 0;
     while (jm.ro && ((int64_t)1 << job_bits) < jm.njobs) job_bits++;
-    SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, 2 * k + job_bits, &alt, s)));
-    const uint64_t *key = alt ? key1 : key0;
-    const uint64_t *val = alt ? val1 : val0;
+    const int code_bits = 2 * k + job_bits;
+    int ib = 1;
+    while (((int64_t)1 << ib) < nc) ib++;
+    if (code_bits + ib > 64) ib = 0;  // too wide to pack: sort (key, value) pairs
+    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom,
+              (const int64_t *)tpos, ib, key0, val0, nc);
+    bool alt = false;
+    const uint64_t *key;
+    uint64_t *val;
+    if (ib) {  // 8-byte keys through the radix passes, values gathered once afterwards
+        SG_TRY(radix_sort_keys(key0, key1, nc, ib, ib + code_bits, &alt, s));
+        uint64_t *ks = alt ? key1 : key0, *kfree = alt ? key0 : key1;
+        SG_LAUNCH("unpack", unpack_kernel, blocks_for(nc, NT), NT, 0, s, (const uint64_t *)ks, (const uint64_t *)val0,
+                  nc, ib, off, n, kfree, val1);
+        key = kfree;
+        val = val1;
+    } else {
+        SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, code_bits, &alt, s)));
+        key = alt ? key1 : key0;
+        val = alt ? val1 : val0;
+        SG_LAUNCH("resolve", resolve_kernel, blocks_for(nc, NT), NT, 0, s, val, nc, off, n);
+    }
 
     uint32_t *head = sc.get<uint32_t>(nc + 1);
     int64_t *seg_excl = sc.get<int64_t>(nc + 1);
@@ -429,7 +514,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     SG_LAUNCH("seg_start", seg_start_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, nc, seg_start);
     // number of segments lives on the device at seg_excl[nc]; launch over the upper bound nc
     SG_LAUNCH("seg_reliable", seg_reliable_kernel, blocks_for(nc, NT), NT, 0, s, seg_start, seg_excl + nc, lo,
-              hi, key, lohi, 2 * k, rel);
+              hi, key, lohi, 2 * k, nc, rel);
     SG_TRY(exclusive_scan<uint32_t>(rel, col_of_seg, nc, s));
     SG_LAUNCH("keep", keep_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, rel, val, nc, keep);
     SG_TRY(exclusive_scan<uint32_t>(keep, out_pos, nc, s));

@@ -1,6 +1,7 @@
 // prim.cu -- exclusive scan (reduce, scan partials, downsweep) and stable LSD radix sort
 // (per-tile digit histograms, scan, stable per-warp ranking with __match_any_sync, then a
 // shared-memory staged scatter so that each digit's run is written contiguously).
+#include "check.cuh"
 #include "prim.cuh"
 
 namespace sg {
@@ -112,24 +113,25 @@ __global__ void __launch_bounds__(RS_NT) radix_hist_kernel(const K *__restrict__
     for (int d = threadIdx.x; d < RS_RADIX; d += RS_NT) counts[(int64_t)d * ntiles + blockIdx.x] = hist[d];
 }
 
-template <class K, class V>
+template <class K, class V, bool HAS_V>
 struct RsSmem {
     K keys[RS_TILE];
-    V vals[RS_TILE];
+    V vals[HAS_V ? RS_TILE : 1];
     uint32_t wcnt[RS_WARPS][RS_RADIX];
     uint32_t tstart[RS_RADIX];
     uint32_t tmp[RS_WARPS + 1];
 };
 
-// offsets[d * ntiles + t] = first output position of digit d's keys from tile t.
-template <class K, class V>
+// offsets[d * ntiles + t] = first output position of digit d's keys from tile t. Without values
+// (HAS_V == false) vin / vout are not touched.
+template <class K, class V, bool HAS_V>
 __global__ void __launch_bounds__(RS_NT) radix_scatter_kernel(const K *__restrict__ kin, const V *__restrict__ vin,
                                                              K *__restrict__ kout, V *__restrict__ vout,
                                                              int64_t n, int shift,
                                                              const int64_t *__restrict__ offsets,
                                                              int64_t ntiles) {
     extern __shared__ __align__(16) unsigned char rs_raw[];
-    RsSmem<K, V> &sm = *reinterpret_cast<RsSmem<K, V> *>(rs_raw);
+    RsSmem<K, V, HAS_V> &sm = *reinterpret_cast<RsSmem<K, V, HAS_V> *>(rs_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_NT) (&sm.wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -137,14 +139,14 @@ __global__ void __launch_bounds__(RS_NT) radix_scatter_kernel(const K *__restric
     const int64_t wbase = tbase + (int64_t)w * 32 * RS_ITEMS;
     const uint32_t lt = (1u << lane) - 1u;
     K key[RS_ITEMS];
-    V val[RS_ITEMS];
+    V val[HAS_V ? RS_ITEMS : 1];
     uint32_t local[RS_ITEMS];
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; it++) {
         int64_t idx = wbase + it * 32 + lane;
         bool valid = idx < n;
         key[it] = valid ? kin[idx] : K(0);
-        val[it] = valid ? vin[idx] : V(0);
+        if (HAS_V) val[HAS_V ? it : 0] = valid ? vin[idx] : V(0);
         uint32_t d = (uint32_t)(key[it] >> shift) & (RS_RADIX - 1);
         uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : (RS_RADIX + lane));
         uint32_t base_cnt = valid ? sm.wcnt[w][d] : 0u;
@@ -178,8 +180,9 @@ __global__ void __launch_bounds__(RS_NT) radix_scatter_kernel(const K *__restric
         if (idx < n) {
             uint32_t d = (uint32_t)(key[it] >> shift) & (RS_RADIX - 1);
             uint32_t p = sm.tstart[d] + sm.wcnt[w][d] + local[it];
+            if (!SG_IN_BOUNDS(p < RS_TILE, 201, p)) continue;
             sm.keys[p] = key[it];
-            sm.vals[p] = val[it];
+            if (HAS_V) sm.vals[HAS_V ? p : 0] = val[HAS_V ? it : 0];
         }
     }
     __syncthreads();
@@ -188,37 +191,47 @@ __global__ void __launch_bounds__(RS_NT) radix_scatter_kernel(const K *__restric
         K kk = sm.keys[i];
         uint32_t d = (uint32_t)(kk >> shift) & (RS_RADIX - 1);
         int64_t o = offsets[(int64_t)d * ntiles + blockIdx.x] + (i - (int64_t)sm.tstart[d]);
+        if (!SG_IN_BOUNDS(o >= 0 && o < n, 202, o)) continue;
         kout[o] = kk;
-        vout[o] = sm.vals[i];
+        if (HAS_V) vout[o] = sm.vals[HAS_V ? i : 0];
     }
 }
 
-template <class K, class V>
-sg_status radix_sort_pairs(K *k0, V *v0, K *k1, V *v1, int64_t n, int key_bits, bool *in_alt,
-                           cudaStream_t s) {
+template <class K, class V, bool HAS_V>
+static sg_status radix_sort_impl(K *k0, V *v0, K *k1, V *v1, int64_t n, int lo_bit, int hi_bit, bool *in_alt,
+                                 cudaStream_t s) {
     static_assert(RS_NT == RS_RADIX, "one thread per digit in the scatter's digit scan");
     *in_alt = false;
-    if (n <= 1 || key_bits <= 0) return SG_OK;
+    if (n <= 1 || hi_bit <= lo_bit) return SG_OK;
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     Scratch sc(s);
     uint32_t *counts = sc.get<uint32_t>((size_t)RS_RADIX * ntiles);
     int64_t *offs = sc.get<int64_t>((size_t)RS_RADIX * ntiles + 1);
     if (!counts || !offs) return SG_ERR_OOM;
-    size_t smem = sizeof(RsSmem<K, V>);
-    SG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    size_t smem = sizeof(RsSmem<K, V, HAS_V>);
+    SG_CUDA_TRY(ensure_smem(radix_scatter_kernel<K, V, HAS_V>, smem));
     K *ki = k0, *ko = k1;
     V *vi = v0, *vo = v1;
-    for (int shift = 0; shift < key_bits; shift += RS_BITS) {
+    for (int shift = lo_bit; shift < hi_bit; shift += RS_BITS) {
         SG_LAUNCH("radix_hist", radix_hist_kernel<K>, ntiles, RS_NT, 0, s, ki, n, shift, counts, ntiles);
         SG_TRY(exclusive_scan<uint32_t>(counts, offs, (int64_t)RS_RADIX * ntiles, s));
-        SG_LAUNCH("radix_scatter", (radix_scatter_kernel<K, V>), ntiles, RS_NT, smem, s, ki, vi, ko, vo, n,
+        SG_LAUNCH("radix_scatter", (radix_scatter_kernel<K, V, HAS_V>), ntiles, RS_NT, smem, s, ki, vi, ko, vo, n,
                   shift, (const int64_t *)offs, ntiles);
         K *tk = ki; ki = ko; ko = tk;
         V *tv = vi; vi = vo; vo = tv;
         *in_alt = !*in_alt;
     }
     return SG_OK;
+}
+
+template <class K, class V>
+sg_status radix_sort_pairs(K *k0, V *v0, K *k1, V *v1, int64_t n, int key_bits, bool *in_alt, cudaStream_t s) {
+    return radix_sort_impl<K, V, true>(k0, v0, k1, v1, n, 0, key_bits, in_alt, s);
+}
+
+sg_status radix_sort_keys(uint64_t *k0, uint64_t *k1, int64_t n, int lo_bit, int hi_bit, bool *in_alt,
+                          cudaStream_t s) {
+    return radix_sort_impl<uint64_t, uint64_t, false>(k0, nullptr, k1, nullptr, n, lo_bit, hi_bit, in_alt, s);
 }
 
 template sg_status radix_sort_pairs<uint64_t, uint64_t>(uint64_t *, uint64_t *, uint64_t *, uint64_t *, int64_t,

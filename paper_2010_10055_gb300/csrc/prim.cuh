@@ -17,6 +17,10 @@ template <class K, class V>
 sg_status radix_sort_pairs(K *k0, V *v0, K *k1, V *v1, int64_t n, int key_bits, bool *in_alt,
                            cudaStream_t s);
 
+// Stable LSD radix sort of 64-bit keys by their bits [lo_bit, hi_bit) (other bits ride along).
+sg_status radix_sort_keys(uint64_t *k0, uint64_t *k1, int64_t n, int lo_bit, int hi_bit, bool *in_alt,
+                          cudaStream_t s);
+
 // Block-wide exclusive scan of one value per thread (blockDim.x = NT, a multiple of 32).
 // `tmp` must hold NT/32 + 1 values. Returns the exclusive prefix; *total gets the block total.
 template <int NT, class T>

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "check.cuh"
 
 namespace sg {
 
@@ -31,6 +32,7 @@ static std::atomic<int64_t> g_fail_after{0};
 // memory freed at the end of one call is reused by the next instead of being unmapped at every
 // synchronisation (the default pool's threshold of 0 returns it to the driver each time). The
 // pool belongs to this process and disappears with it.
+int64_t tune(const char *name);
 static std::mutex g_pool_mu;
 static cudaMemPool_t g_pools[256];
 static bool g_pool_tried[256];
@@ -53,6 +55,9 @@ static cudaMemPool_t library_pool() {
         if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
             uint64_t thr = ~0ull;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            int reuse = tune("pool_cross_stream_reuse") ? 1 : 0;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowOpportunistic, &reuse);
+            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &reuse);
             g_pools[dev] = pool;
         } else {
             cudaGetLastError();
@@ -93,6 +98,28 @@ void dfree(void *p, cudaStream_t s) {
         return;
     }
     cudaFreeAsync(p, s);
+}
+
+static std::mutex g_check_mu;
+static std::vector<check_reader_fn> *g_check_readers;
+
+void register_check_reader(check_reader_fn f) {
+    std::lock_guard<std::mutex> lk(g_check_mu);
+    if (!g_check_readers) g_check_readers = new std::vector<check_reader_fn>();
+    g_check_readers->push_back(f);
+}
+
+static std::mutex g_smem_mu;
+static std::map<const void *, size_t> g_smem_caps;
+
+cudaError_t ensure_smem_cap(const void *kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    auto it = g_smem_caps.find(kernel);
+    if (it != g_smem_caps.end() && it->second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g_smem_caps[kernel] = bytes;
+    return e;
 }
 
 cudaError_t read_back(void *host, const void *dev, size_t bytes, cudaStream_t s) {
@@ -151,6 +178,7 @@ static Tunable g_tunables[] = {
     {"sym_guess_shift", 2, 0, 8},         // symbolic table guess = products >> shift
     {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch
     {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch
+    {"pool_cross_stream_reuse", 1, 0, 1}, // pool may hand memory freed on one stream to another
 };
 static std::mutex g_tune_mu;
 
@@ -196,6 +224,17 @@ void sg_debug_fail_alloc_after(int64_t n) { sg::g_fail_after.store(n > 0 ? n : 0
 void sg_free(void *d_ptr, sg_stream_t stream) { sg::dfree(d_ptr, (cudaStream_t)stream); }
 
 uint64_t sg_launch_count(void) { return sg::g_launches.load(); }
+
+uint64_t sg_debug_check(void) {
+    std::lock_guard<std::mutex> lk(sg::g_check_mu);
+    uint64_t first = 0;
+    if (sg::g_check_readers)
+        for (auto f : *sg::g_check_readers) {
+            uint64_t v = f();
+            if (v && !first) first = v;
+        }
+    return first;
+}
 
 void sg_prof_enable(int on) { sg::g_prof_on.store(on ? 1 : 0); }
 

@@ -8,6 +8,7 @@
 // admitted by the next idle worker as soon as memory frees up, and batches on different workers
 // overlap on the device. A job whose estimate alone exceeds the budget completes with
 // SG_ERR_BUDGET.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -65,12 +66,15 @@ struct sg_server {
 
 namespace sg {
 
-static void fill_error(sg_job_result *r, sg_status st, double t_sub) {
+static void fill_error(sg_job_result *r, sg_status st, double t_sub, const char *msg) {
     memset(r, 0, sizeof(*r));
     r->status = st;
     r->t_submit = t_sub;
     r->t_start = r->t_done = now_s();
+    snprintf(r->error, sizeof(r->error), "%s", msg);
 }
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Runs one admitted batch on stream s and fills each job's result.
 static void run_batch_on(sg_server *srv, std::vector<Job *> &jobs, cudaStream_t s, std::vector<Done *> &out) {
@@ -81,31 +85,38 @@ static void run_batch_on(sg_server *srv, std::vector<Job *> &jobs, cudaStream_t 
     sg_status st = SG_OK;
     std::vector<sg_batch_item> items(nb);
     std::vector<sg_graph_csr> Rs(nb);
+    // every job's inputs in one device buffer, each array on a 256-byte boundary
+    size_t bytes = 0;
+    for (Job *jp : jobs) {
+        bytes += up256(jp->seq.size() + 16) + up256(jp->off.size() * 8);
+        if (jp->has_r)
+            bytes += up256(jp->rrp.size() * 8) + up256((jp->rcol.size() + 1) * 4) * 2 + up256(jp->rcol.size() + 1);
+    }
     Scratch sc(s);
+    unsigned char *dbuf = sc.get<unsigned char>(bytes);
+    if (!dbuf) st = SG_ERR_OOM;
+    size_t at = 0;
+    auto put = [&](const void *src, size_t n, size_t room) -> void * {
+        void *dst = dbuf + at;
+        at += up256(room);
+        if (n && st == SG_OK && cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            set_error("server: input upload failed");
+            st = SG_ERR_CUDA;
+        }
+        return dst;
+    };
     for (int b = 0; b < nb && st == SG_OK; b++) {
         Job &j = *jobs[b];
         const int64_t n = (int64_t)j.off.size() - 1;
-        uint8_t *dseq = sc.get<uint8_t>(j.seq.size() + 16);
-        int64_t *doff = sc.get<int64_t>(j.off.size());
-        if (!dseq || !doff) { st = SG_ERR_OOM; break; }
-        if (!j.seq.empty() && cudaMemcpyAsync(dseq, j.seq.data(), j.seq.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-            st = SG_ERR_CUDA;
-        if (cudaMemcpyAsync(doff, j.off.data(), j.off.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
-            st = SG_ERR_CUDA;
+        const uint8_t *dseq = (const uint8_t *)put(j.seq.data(), j.seq.size(), j.seq.size() + 16);
+        const int64_t *doff = (const int64_t *)put(j.off.data(), j.off.size() * 8, j.off.size() * 8);
         items[b] = sg_batch_item{dseq, doff, n, (int64_t)j.seq.size(), j.lo, j.hi, nullptr};
         if (j.has_r) {
             const int64_t nnz = (int64_t)j.rcol.size();
-            int64_t *rp = sc.get<int64_t>(j.rrp.size());
-            int32_t *rc = sc.get<int32_t>(nnz + 1);
-            uint32_t *rs = sc.get<uint32_t>(nnz + 1);
-            uint8_t *rd = sc.get<uint8_t>(nnz + 1);
-            if (!rp || !rc || !rs || !rd) { st = SG_ERR_OOM; break; }
-            cudaMemcpyAsync(rp, j.rrp.data(), j.rrp.size() * 8, cudaMemcpyHostToDevice, s);
-            if (nnz) {
-                cudaMemcpyAsync(rc, j.rcol.data(), nnz * 4, cudaMemcpyHostToDevice, s);
-                cudaMemcpyAsync(rs, j.rsuf.data(), nnz * 4, cudaMemcpyHostToDevice, s);
-                cudaMemcpyAsync(rd, j.rdir.data(), nnz, cudaMemcpyHostToDevice, s);
-            }
+            int64_t *rp = (int64_t *)put(j.rrp.data(), j.rrp.size() * 8, j.rrp.size() * 8);
+            int32_t *rc = (int32_t *)put(j.rcol.data(), nnz * 4, (nnz + 1) * 4);
+            uint32_t *rs = (uint32_t *)put(j.rsuf.data(), nnz * 4, (nnz + 1) * 4);
+            uint8_t *rd = (uint8_t *)put(j.rdir.data(), nnz, nnz + 1);
             Rs[b] = sg_graph_csr{n, nnz, rp, rc, rs, rd};
             items[b].R = &Rs[b];
         }
@@ -132,8 +143,12 @@ static void run_batch_on(sg_server *srv, std::vector<Job *> &jobs, cudaStream_t 
             if (e == cudaSuccess && sn) e = cudaMemcpyAsync(sdir.data(), br.S.dir, sn, cudaMemcpyDeviceToHost, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = SG_ERR_CUDA;
+        if (e != cudaSuccess) {
+            set_error("server: result download failed: %s", cudaGetErrorString(e));
+            st = SG_ERR_CUDA;
+        }
     }
+    const char *msg = st == SG_OK ? "" : sg_last_error();
     const double t_done = now_s();
     for (int b = 0; b < nb; b++) {
         sg_job_result &r = out[b]->r;
@@ -143,7 +158,10 @@ static void run_batch_on(sg_server *srv, std::vector<Job *> &jobs, cudaStream_t 
         r.t_start = t_start;
         r.t_done = t_done;
         r.batch_size = nb;
-        if (st != SG_OK) continue;
+        if (st != SG_OK) {
+            snprintf(r.error, sizeof(r.error), "%s", msg);
+            continue;
+        }
         const int64_t r0 = br.read_off[b], r1 = br.read_off[b + 1], n = r1 - r0, S = br.C.max_seeds;
         const int64_t cb = crp[r0], ce = crp[r1], cn = ce - cb, cN = br.C.nnz;
         r.n = n;
@@ -201,7 +219,10 @@ static void worker_main(sg_server *srv) {
                     Job *j = srv->pending.front();
                     srv->pending.pop_front();
                     Done *d = new Done();
-                    fill_error(&d->r, SG_ERR_BUDGET, j->t_submit);
+                    char msg[128];
+                    snprintf(msg, sizeof(msg), "job needs about %zu bytes of device memory, the budget is %zu",
+                             j->est, budget);
+                    fill_error(&d->r, SG_ERR_BUDGET, j->t_submit, msg);
                     srv->done[j->ticket] = d;
                     delete j;
                     srv->cv_done.notify_all();

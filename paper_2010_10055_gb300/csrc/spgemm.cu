@@ -22,6 +22,9 @@
 // Products of a row are enumerated warp by warp: a warp takes 32 consecutive entries of A's row,
 // scans their At row lengths in registers, and walks the flattened product list 32 at a time,
 // each lane finding its entry with a 5-step shuffle search.
+#include <mutex>
+
+#include "check.cuh"
 #include "ops.cuh"
 
 namespace sg {
@@ -94,7 +97,7 @@ __global__ void classify_kernel(const int64_t *__restrict__ need, int64_t n, Cla
     for (int q = 0; q < cl.ncls; q++)
         if (u <= ((int64_t)1 << cl.log2T[q])) { c = q; break; }
     unsigned long long p = atomicAdd(counts + c, 1ull);
-    lists[(int64_t)c * n + (int64_t)p] = (int32_t)i;
+    if (SG_IN_BOUNDS((int64_t)p < n, 302, p)) lists[(int64_t)c * n + (int64_t)p] = (int32_t)i;
 }
 
 // symbolic table request: nextpow2(max(64, w >> shift)), capped at the exact bound 2 * min(w, n - 1)
@@ -227,7 +230,10 @@ __global__ void __launch_bounds__(512) symbolic_kernel(SpArgs g, const int32_t *
         });
         __syncthreads();
         if (s_ovf) {  // table too small for this row: the global-slice pass redoes it
-            if (threadIdx.x == 0) ovf_list[atomicAdd(ovf_count, 1ull)] = i;
+            if (threadIdx.x == 0) {
+                const unsigned long long q = atomicAdd(ovf_count, 1ull);
+                if (SG_IN_BOUNDS((int64_t)q < g.n, 301, q)) ovf_list[q] = i;
+            }
             __syncthreads();
             continue;
         }
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *_
         for (int x = threadIdx.x; x < T; x += blockDim.x) {
             if (keys[x] != -1 && cnt[x] >= g.min_shared) {
                 const int p = atomicAdd(&s_ctr, 1);
-                obuf[p] = ((uint64_t)(uint32_t)keys[x] << 32) | (uint32_t)x;
+                if (SG_IN_BOUNDS(p < (T >> 1), 303, p)) obuf[p] = ((uint64_t)(uint32_t)keys[x] << 32) | (uint32_t)x;
             }
         }
         __syncthreads();
@@ -393,12 +399,6 @@ __global__ void pair_kernel(const int32_t *__restrict__ col, const uint32_t *__r
 
 static int pick_threads(int log2T) { return log2T <= 10 ? 128 : 256; }
 
-template <class K>
-static cudaError_t allow_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S,
                        sg_overlap_csr *C, cudaStream_t s, Scratch &sc) {
     const int64_t n = A->n_rows;
@@ -437,7 +437,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, sym, sym_counts, lists);
     for (int c = 0; c < sym.ncls; c++) {
         const size_t sm = (size_t)(2 << sym.log2T[c]) * sizeof(int32_t);
-        SG_CUDA_TRY(allow_smem(symbolic_kernel<false>, sm));
+        SG_CUDA_TRY(ensure_smem(symbolic_kernel<false>, sm));
         SG_LAUNCH("spgemm_symbolic", symbolic_kernel<false>, grid, pick_threads(sym.log2T[c]), sm, s, g,
                   lists + (int64_t)c * n, sym_counts + c, sym.log2T[c], (const int64_t *)work, (int32_t *)nullptr,
                   (int64_t)0, ovf, ovf_count, nnz_row, dist);
@@ -483,7 +483,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     for (int c = 0; c < num.ncls; c++) {
         if (!h_num[c]) continue;
         const size_t sm = num_table_bytes((int64_t)1 << num.log2T[c], S);
-        SG_CUDA_TRY(allow_smem(numeric_kernel<false>, sm));
+        SG_CUDA_TRY(ensure_smem(numeric_kernel<false>, sm));
         SG_LAUNCH("spgemm_numeric", numeric_kernel<false>, grid, pick_threads(num.log2T[c]), sm, s, g,
                   lists + (int64_t)c * n, num_counts + c, num.log2T[c], (const int64_t *)need,
                   (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i,

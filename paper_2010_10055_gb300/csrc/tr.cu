@@ -17,6 +17,7 @@
 // 2 * out(d_ij) + in(d_jk). N is kept as (sum << 2 | composite) in one 64-bit word so that
 // DIRMATCH (composite must equal d_ik before the min) and LITERAL (lexicographic min of
 // (sum, composite), checked after) share one atomicMin.
+#include "check.cuh"
 #include "ops.cuh"
 
 namespace sg {
@@ -197,7 +198,7 @@ __global__ void tr_fill_kernel(const int8_t *__restrict__ kind, int64_t n, unsig
     int c = kind[i];
     if (c == 0) return;
     unsigned long long p = atomicAdd(cursor + c, 1ull);
-    rows[(c == 1 ? 0 : n) + (int64_t)p] = (int32_t)i;
+    if (SG_IN_BOUNDS((int64_t)p < n, 403, p)) rows[(c == 1 ? 0 : n) + (int64_t)p] = (int32_t)i;
 }
 
 // Stable compaction of kept entries: one warp per row.

@@ -196,3 +196,42 @@ def make(w: Workload, with_graph: bool = True) -> dict:
     if with_graph:
         out["R"] = overlap_graph(r["start"], r["end"], r["strand"], w.min_overlap, 0, w.seed + 2)
     return out
+
+
+# ------------------------------------------------------------------ batched / served job mixes
+def batched_sets(count: int = 512, g_lo: float = 20e3, g_hi: float = 2e6, seed: int = 2013) -> list:
+    """Independent read sets of the batched workload: genome log-uniform in [g_lo, g_hi], coverage
+    U[10, 40], mean read length U[2, 10] kbp (sd 0.4 x mean), errors U[12, 15] % split 3:2:1
+    (ins:del:sub), k = 17, reliable range [2, max(8, round(0.75 x coverage))], R from true
+    coordinates (overlaps >= 500 bp). Set b is seeded from (seed, b)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        G = int(np.exp(rng.uniform(np.log(g_lo), np.log(g_hi))))
+        cov = float(rng.uniform(10, 40))
+        mean = float(rng.uniform(2000, 10000))
+        err = float(rng.uniform(0.12, 0.15))
+        g = genome(G, seed * 100003 + b)
+        rd = reads(g, cov, mean, 0.4 * mean, 500, err / 2, err / 3, err / 6, seed * 100003 + b + 1)
+        R = overlap_graph(rd["start"], rd["end"], rd["strand"], 500)
+        out.append(dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=max(8, int(round(0.75 * cov))), R=R,
+                        genome=G))
+    return out
+
+
+def served_jobs(count: int = 500, rate: float = 200.0, g_min: float = 20e3, g_max: float = 20e6,
+                alpha: float = 1.5, seed: int = 2014) -> list:
+    """Jobs of the served workload: Poisson arrivals at `rate` per second; genome size Pareto(alpha)
+    from g_min, truncated at g_max; 30x, mean read length 10 kbp (sd 4 kbp), 15 % errors (3:2:1),
+    range [2, 20], R from true coordinates (overlaps >= 500 bp). Each job has an arrival time."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for b in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        G = int(min(g_max, g_min * (1.0 - rng.uniform()) ** (-1.0 / alpha)))
+        g = genome(G, seed * 100003 + b)
+        rd = reads(g, 30.0, 10000.0, 4000.0, 500, 0.075, 0.05, 0.025, seed * 100003 + b + 1)
+        R = overlap_graph(rd["start"], rd["end"], rd["strand"], 500)
+        out.append(dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=20, R=R, genome=G, arrival=t))
+    return out

@@ -38,13 +38,13 @@ def test_server_results_match_oracle_alone_and_mixed():
     jobs = _jobs(5, 14)
     srv = sg.Server(hbm_budget=1 << 30, max_batch=5, workers=2, fuzz=300)
     try:
-        # staggered arrivals so later jobs are admitted while earlier batches are on the GPU
+        # arrivals in a burst and then staggered: jobs are admitted while other batches run
         tickets = []
-        for j in jobs:
+        for b, j in enumerate(jobs):
             tickets.append(srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"]))
-            time.sleep(0.002)
+            if b >= 7:
+                time.sleep(0.002)
         mixed = [srv.wait(t) for t in tickets]
-        assert max(r["batch_size"] for r in mixed) > 1
         for r, j in zip(mixed, jobs):
             _check(r, j, 300)
         # the same job alone
@@ -71,5 +71,26 @@ def test_server_refuses_jobs_over_budget_and_keeps_going():
     try:
         r = srv.wait(srv.submit(jobs[1]["seq"], jobs[1]["offsets"], jobs[1]["lo"], jobs[1]["hi"], jobs[1]["R"]))
         _check(r, jobs[1], 0)
+    finally:
+        srv.close()
+
+
+def test_server_batches_jobs_that_queue_up():
+    """One worker, a burst of submissions: jobs that queue while a batch runs share the next one."""
+    jobs = _jobs(7, 6) * 5
+    srv = sg.Server(hbm_budget=1 << 30, max_batch=64, workers=1)
+    try:
+        tickets = [srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"]) for j in jobs]
+        res = [srv.wait(t) for t in tickets]
+        assert [(r["status"], r["error"]) for r in res if r["status"] != sg.SG_OK] == []
+        assert max(r["batch_size"] for r in res) > 1
+        # identical inputs give identical outputs wherever they were batched
+        for b in range(6, len(jobs)):
+            for key in ("row_ptr", "col", "count", "seed_i", "seed_k"):
+                assert np.array_equal(res[b]["C"][key], res[b % 6]["C"][key])
+            for key in ("row_ptr", "col", "suffix", "dir"):
+                assert np.array_equal(res[b]["S"][key], res[b % 6]["S"][key])
+        for r in res:  # latencies are ordered: submitted <= started <= done
+            assert r["t_submit"] <= r["t_start"] <= r["t_done"]
     finally:
         srv.close()
