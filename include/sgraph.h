@@ -352,10 +352,13 @@ uint64_t sg_debug_check(void);
 uint64_t sg_launch_count(void);
 
 /* Tunable launch parameters (used by the autotuner; results never depend on them):
- *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (96)
+ *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (48)
+ *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4, 8 or 16 (4)
  *   sym_guess_shift       symbolic hash table guess = products of the row >> shift (2)
  *   spgemm_blocks_per_sm  blocks per SM of each SpGEMM class launch (16)
  *   tr_blocks_per_sm      blocks per SM of the min-plus launch (32)
+ *   pool_cross_stream_reuse  1: the library's memory pool may reuse memory freed on one stream for
+ *                         another (read once, when the pool is created) (1)
  * sg_tune_set returns 1 if the name is known and the value in range, else 0 (no change).
  * sg_tune_name(i) enumerates the names (NULL past the end). Not thread-safe against running calls. */
 int sg_tune_set(const char *name, int64_t value);

@@ -12,9 +12,9 @@
 //  1. bloom_insert   every code is OR-ed into the blocked Bloom filter B1 (all probe bits in one
 //                    32-bit word, so "already present" is decided by one atomic); a code found
 //                    present is OR-ed into B2 ("seen at least twice"). Skipped when lo == 1.
-//  2. cand_count     per thread, the windows whose code tests positive in B2. Every occurrence
-//                    of a k-mer with frequency >= 2 passes (false positives only add singletons,
-//                    which the exact count below drops).
+//  2. cand_count     per warp, a ballot mask of the windows whose code tests positive in B2.
+//                    Every occurrence of a k-mer with frequency >= 2 passes (false positives only
+//                    add singletons, which the exact count below drops).
 //  3. cand_emit      writes (code, position | strand) at scanned offsets, so the candidates stay
 //                    in position order, i.e. (read, pos) order.
 //  4. radix sort by code (stable): equal codes form segments in (read, pos) order; positions are
@@ -81,128 +81,196 @@ struct JobCursor {
     }
 };
 
-// Visits the windows [c0 + t*KM_W, c0 + (t+1)*KM_W) of thread t in position order, calling
-// f(code, strand, read, pos, local start) for each window of k A/C/G/T bases inside one read, where
-// the local start (in [t*KM_W, (t+1)*KM_W)) indexes the block's chunk. K > 0 makes k a
-// compile-time constant (K == 0: k taken from k_rt). Indices inside the block are 32-bit.
-template <int K, class F>
-__device__ __forceinline__ void for_each_window(const uint8_t *__restrict__ sm, int64_t c0, int64_t total,
-                                                const int64_t *__restrict__ off, int64_t n, int k_rt,
-                                                F &&f) {
-    const int k = K > 0 ? K : k_rt;
-    const int ls = threadIdx.x * KM_W;
-    const int64_t qs = c0 + ls;
-    if (qs >= total || n <= 0) return;
-    int le = ls + KM_W + k - 1;  // exclusive, local to the block
-    if (c0 + le > total) le = (int)(total - c0);
-    // read containing qs: last r with off[r] <= qs
-    int64_t lo = 0, hi = n;  // invariant: off[lo] <= qs < off[hi] (off[n] = total > qs)
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (off[mid] <= qs) lo = mid; else hi = mid;
-    }
-    int64_t r = lo;
-    int64_t rbase = off[r] - c0;  // start of read r relative to the block
-    int64_t nx = off[r + 1] - c0;
-    int next = nx > (int64_t)0x7fffffff ? 0x7fffffff : (int)nx;
-    const uint64_t mask = (1ull << (2 * k)) - 1;
-    const int rs = 2 * (k - 1);
-    uint64_t fw = 0, rc = 0;
-    int run = 0;
-    for (int q = ls; q < le; q++) {
-        // crossed into the next read (skips empty reads); r + 1 < n keeps every access in
-        // bounds even when the offsets turn out to be invalid (reported after this pass)
-        while (q >= next && r + 1 < n) {
-            r++;
-            rbase = off[r] - c0;
-            nx = off[r + 1] - c0;
-            next = nx > (int64_t)0x7fffffff ? 0x7fffffff : (int)nx;
-            run = 0;
-        }
-        const uint32_t c = sm[q];
-        const bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
-        const uint32_t t = (c >> 1) & 3u;
-        const uint32_t b = t ^ (t >> 1);  // A=0 C=1 G=2 T=3
-        fw = ((fw << 2) | b) & mask;
-        rc = (rc >> 2) | ((uint64_t)(3u - b) << rs);
-        run = ok ? run + 1 : 0;
-        if (run >= k && q - k + 1 >= ls) {
-            const uint64_t code = fw < rc ? fw : rc;
-            const uint32_t strand = rc < fw ? 1u : 0u;
-            f(code, strand, r, (uint32_t)(q - k + 1 - rbase), q - k + 1);
-        }
-    }
-}
+// Staged bases: the block's chunk as 32-bit words (4 bases each), one pad word after every 8, so
+// that thread t's 32-base segment starts at word 9t and a warp reading the j-th word of its
+// segments hits 32 distinct banks. Bytes past the end of the sequence read as 'N'.
+constexpr int KM_SWORDS = KM_CHUNK / 4 + 16;           // covers 32 + k - 1 bases past the last segment
+constexpr int KM_SPAD = KM_SWORDS + KM_SWORDS / 8 + 1;
+__device__ __forceinline__ int spad(int w) { return w + (w >> 3); }
 
-// Stages the block's bases in shared memory. The reads stream through once per pass, so they
-// are loaded evict-first (ld.global.cs) to keep the filters resident in L2; 16-byte loads when
-// the chunk start is 16-byte aligned.
-__device__ __forceinline__ void load_chunk(uint8_t *sm, const uint8_t *__restrict__ seq, int64_t c0,
-                                           int64_t total, int k) {
-    int64_t len = (int64_t)KM_CHUNK + k - 1;
-    if (c0 + len > total) len = total - c0;
-    int64_t done = 0;
-    if ((((uintptr_t)(seq + c0)) & 15) == 0) {
-        const int64_t nv = len >> 4;
-        const uint4 *src = reinterpret_cast<const uint4 *>(seq + c0);
-        uint4 *dst = reinterpret_cast<uint4 *>(sm);
-        for (int64_t i = threadIdx.x; i < nv; i += KM_NT) dst[i] = __ldcs(src + i);
-        done = nv << 4;
+__device__ __forceinline__ void load_chunk(uint32_t *smw, const uint8_t *__restrict__ seq, int64_t c0,
+                                           int64_t total) {
+    const int64_t len = total - c0;  // bytes of the sequence from c0 on
+    const bool al4 = (((uintptr_t)(seq + c0)) & 3) == 0;
+    for (int w = threadIdx.x; w < KM_SWORDS; w += KM_NT) {
+        const int64_t b = 4 * (int64_t)w;
+        uint32_t v;
+        if (al4 && b + 3 < len) {
+            v = __ldcs(reinterpret_cast<const unsigned int *>(seq + c0 + b));
+        } else {
+            v = 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) v |= (uint32_t)(b + u < len ? seq[c0 + b + u] : (uint8_t)'N') << (8 * u);
+        }
+        smw[spad(w)] = v;
     }
-    for (int64_t i = done + threadIdx.x; i < len; i += KM_NT) sm[i] = __ldcs(seq + c0 + i);
     __syncthreads();
 }
 
+// Stores window j's value (thread-local order); every 4th value flushes 4 consecutive windows
+// (one 32-byte sector) with two 16-byte stores.
+struct WcOut {
+    uint64_t buf[4];
+    __device__ __forceinline__ void put(uint64_t *wc, int64_t q0, int64_t total, int j, uint64_t v) {
+        buf[j & 3] = v;
+        if ((j & 3) != 3) return;
+        const int64_t q = q0 + j - 3;  // first of the 4 windows; a multiple of 4
+        if (q + 3 < total) {
+            uint4 *d = reinterpret_cast<uint4 *>(wc + q);
+            d[0] = make_uint4((uint32_t)buf[0], (uint32_t)(buf[0] >> 32), (uint32_t)buf[1], (uint32_t)(buf[1] >> 32));
+            d[1] = make_uint4((uint32_t)buf[2], (uint32_t)(buf[2] >> 32), (uint32_t)buf[3], (uint32_t)(buf[3] >> 32));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (q + u < total) wc[q + u] = buf[u];
+        }
+    }
+};
+
 // One walk over the reads: wc[q] = canonical code of the window starting at global position q
-// (with the job prefix in a batch) | strand << 63, or ~0 when no valid window starts at q. The
-// later passes stream this array instead of walking the reads again.
+// (with the job prefix in a batch) | strand << 63, or ~0 when no valid window starts at q (a
+// non-ACGT base, or the window crosses a read end). The later passes stream this array instead of
+// walking the reads again. Thread t of block b produces windows b * KM_CHUNK + t * KM_W + j,
+// j < KM_W, in order, from bases [t * KM_W, t * KM_W + KM_W + k - 1) of the block's chunk. K > 0
+// makes k a compile-time constant (K == 0: k taken from k_rt).
 constexpr uint64_t WC_NONE = ~0ull;
 constexpr uint64_t WC_STRAND = 1ull << 63;
 
 template <int K>
 __global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__restrict__ seq, int64_t total,
-                                                            const int64_t *__restrict__ off, int64_t n, int k,
+                                                            const int64_t *__restrict__ off, int64_t n, int k_rt,
                                                             JobMap jm, uint64_t *__restrict__ wc) {
-    extern __shared__ __align__(16) unsigned char wc_raw[];
-    uint64_t *s_wc = reinterpret_cast<uint64_t *>(wc_raw);
-    uint8_t *sm = wc_raw + KM_CHUNK * sizeof(uint64_t);
+    static_assert(KM_W % 4 == 0, "windows are flushed four at a time");
+    __shared__ uint32_t smw[KM_SPAD];
+    const int k = K > 0 ? K : k_rt;
     const int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
-    for (int i = threadIdx.x; i < KM_CHUNK; i += KM_NT) s_wc[i] = WC_NONE;
-    load_chunk(sm, seq, c0, total, k);  // ends with __syncthreads
+    load_chunk(smw, seq, c0, total);  // ends with __syncthreads
+    const int ls = threadIdx.x * KM_W;
+    const int64_t qs = c0 + ls;  // first window (and base) of this thread
+    if (qs >= total || n <= 0) return;
+    // read containing qs: last r with off[r] <= qs (off[n] = total > qs)
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= qs) lo = mid; else hi = mid;
+    }
+    int64_t r = lo;
+    int64_t next = off[r + 1] - qs;  // start of read r + 1, relative to qs
     JobCursor jc{jm};
-    for_each_window<K>(sm, c0, total, off, n, k,
-                       [&](uint64_t code0, uint32_t strand, int64_t r, uint32_t, int lw) {
-        if (SG_IN_BOUNDS(lw >= 0 && lw < KM_CHUNK, 101, lw)) s_wc[lw] = jc.key(code0, r) | ((uint64_t)strand << 63);
-    });
-    __syncthreads();
-    const int64_t cnt = total - c0 < KM_CHUNK ? total - c0 : KM_CHUNK;
-    for (int64_t i = threadIdx.x; i < cnt; i += KM_NT) wc[c0 + i] = s_wc[i];
+    uint64_t rkey = jc.key(0, r);   // job prefix of read r (0 outside batches)
+    const uint64_t mask = (1ull << (2 * k)) - 1;
+    const int rs = 2 * (k - 1);
+    uint64_t fw = 0, rc = 0;
+    int run = 0;
+    WcOut out;
+    const int nb = KM_W + k - 1;  // bases this thread reads
+    const int nw = (nb + 3) >> 2;
+    const uint32_t *mine = smw + 9 * threadIdx.x;  // spad(8t + i) = 9t + i + (i >> 3)
+#pragma unroll
+    for (int wi = 0; wi < (K > 0 ? (KM_W + K - 1 + 3) / 4 : 1); wi++) {
+        // K == 0 takes the generic loop below instead
+        if (K == 0) break;
+        const uint32_t word = mine[wi + (wi >> 3)];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int qi = 4 * wi + u;
+            if (qi >= nb) break;
+            // crossed into the next read (skips empty reads); r + 1 < n keeps every access in
+            // bounds even when the offsets turn out to be invalid (reported after this pass)
+            while (qi >= next && r + 1 < n) {
+                r++;
+                next = off[r + 1] - qs;
+                rkey = jc.key(0, r);
+                run = 0;
+            }
+            const uint32_t c = (word >> (8 * u)) & 0xffu;
+            const bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
+            const uint32_t t = (c >> 1) & 3u;
+            const uint32_t b = t ^ (t >> 1);  // A=0 C=1 G=2 T=3
+            fw = ((fw << 2) | b) & mask;
+            rc = (rc >> 2) | ((uint64_t)(3u - b) << rs);
+            run = ok ? run + 1 : 0;
+            const int j = qi - (k - 1);
+            if (j >= 0) {
+                const uint64_t code = fw < rc ? fw : rc;
+                const uint64_t v = run >= k ? (rkey | code | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
+                out.put(wc, qs, total, j, v);
+            }
+        }
+    }
+    if (K == 0) {
+        for (int qi = 0; qi < nb; qi++) {
+            while (qi >= next && r + 1 < n) {
+                r++;
+                next = off[r + 1] - qs;
+                rkey = jc.key(0, r);
+                run = 0;
+            }
+            const int wi = qi >> 2;
+            const uint32_t c = (mine[wi + (wi >> 3)] >> (8 * (qi & 3))) & 0xffu;
+            const bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
+            const uint32_t t = (c >> 1) & 3u;
+            const uint32_t b = t ^ (t >> 1);
+            fw = ((fw << 2) | b) & mask;
+            rc = (rc >> 2) | ((uint64_t)(3u - b) << rs);
+            run = ok ? run + 1 : 0;
+            const int j = qi - (k - 1);
+            if (j >= 0 && qs + j < total) {
+                const uint64_t code = fw < rc ? fw : rc;
+                wc[qs + j] = run >= k ? (rkey | code | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
+            }
+        }
+    }
+    (void)nw;
 }
 
 // One launch per slice [w_lo, w_hi) of B1's words: every launch streams all window codes but only
 // the k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2.
+template <int BI_U>
 __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint64_t *__restrict__ wc, int64_t total,
                                                             Bloom b1, Bloom b2, uint32_t w_lo, uint32_t w_hi) {
-    for (int64_t q = (int64_t)blockIdx.x * KM_NT + threadIdx.x; q < total; q += (int64_t)gridDim.x * KM_NT) {
-        const uint64_t x = __ldcs(wc + q);
-        if (x == WC_NONE) continue;
-        const uint64_t code = x & ~WC_STRAND;
-        uint32_t i1, m1;
-        b1.probe(code, &i1, &m1);
-        if (i1 < w_lo || i1 >= w_hi) continue;  // another slice's launch handles this k-mer
-        const uint32_t old = atomicOr(b1.words + i1, m1);
-        if ((old & m1) == m1) {
-            uint32_t i2, m2;
-            b2.probe(code, &i2, &m2);
-            if ((b2.words[i2] & m2) != m2) atomicOr(b2.words + i2, m2);
+    // BI_U windows per thread per step (each step's loads coalesced across the warp), so that
+    // their atomics are in flight together
+    const int64_t stride = (int64_t)gridDim.x * KM_NT;
+    for (int64_t q0 = (int64_t)blockIdx.x * KM_NT + threadIdx.x; q0 < total; q0 += BI_U * stride) {
+        uint64_t code[BI_U];
+        uint32_t i1[BI_U], m1[BI_U], old[BI_U];
+        bool mine[BI_U];
+#pragma unroll
+        for (int u = 0; u < BI_U; u++) {
+            const int64_t q = q0 + u * stride;
+            const uint64_t x = q < total ? __ldcs(wc + q) : WC_NONE;
+            code[u] = x & ~WC_STRAND;
+            b1.probe(code[u], &i1[u], &m1[u]);
+            // another slice's launch handles k-mers whose word lies outside [w_lo, w_hi)
+            mine[u] = x != WC_NONE && i1[u] >= w_lo && i1[u] < w_hi;
+        }
+#pragma unroll
+        for (int u = 0; u < BI_U; u++) old[u] = mine[u] ? atomicOr(b1.words + i1[u], m1[u]) : 0u;
+#pragma unroll
+        for (int u = 0; u < BI_U; u++) {
+            if (mine[u] && (old[u] & m1[u]) == m1[u]) {
+                uint32_t i2, m2;
+                b2.probe(code[u], &i2, &m2);
+                if ((b2.words[i2] & m2) != m2) atomicOr(b2.words + i2, m2);
+            }
         }
     }
 }
 
 // Candidates: windows whose code tests positive in B2 (every occurrence of a k-mer seen at least
 // twice; false positives only add singletons, which the exact count drops). use_bloom == 0 keeps
-// every window (lo == 1: singletons may be reliable). Thread t of block b owns the KM_W
-// consecutive windows starting at b * KM_CHUNK + t * KM_W, so candidates keep position order.
+// every window (lo == 1: singletons may be reliable).
+//
+// Both passes are warp-cooperative: warp w of block b owns the KM_GW groups of 32 consecutive
+// windows starting at group (b * KM_WARPS + w) * KM_GW, and handles one group (one coalesced
+// 256-byte load) per step. The count pass stores each group's candidate ballot in cmask and the
+// warp's total in wcnt; the emit pass writes each group's candidates contiguously at the scanned
+// offset, so candidates keep position order.
+constexpr int KM_WARPS = KM_NT / 32;
+constexpr int KM_GW = KM_CHUNK / KM_NT;  // groups per warp (32: one mask word per lane)
+static_assert(KM_GW == 32, "one mask word per lane");
+
 __device__ __forceinline__ bool is_candidate(uint64_t x, const Bloom &b2, int use_bloom) {
     if (x == WC_NONE) return false;
     if (!use_bloom) return true;
@@ -212,34 +280,58 @@ __device__ __forceinline__ bool is_candidate(uint64_t x, const Bloom &b2, int us
 }
 
 __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint64_t *__restrict__ wc, int64_t total, Bloom b2,
-                                                          int use_bloom, uint32_t *__restrict__ cnt) {
-    const int64_t q0 = (int64_t)blockIdx.x * KM_CHUNK + (int64_t)threadIdx.x * KM_W;
-    uint32_t c = 0;
-    for (int w = 0; w < KM_W; w++) {
-        const int64_t q = q0 + w;
-        if (q >= total) break;
-        c += is_candidate(__ldcs(wc + q), b2, use_bloom) ? 1u : 0u;
+                                                          int use_bloom, uint32_t *__restrict__ cmask,
+                                                          uint32_t *__restrict__ wcnt) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
+    uint32_t mine = 0, c = 0;
+#pragma unroll 4
+    for (int g = 0; g < KM_GW; g++) {
+        const int64_t q = (g0 + g) * 32 + lane;
+        const uint64_t x = q < total ? __ldcs(wc + q) : WC_NONE;
+        const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(x, b2, use_bloom));
+        if (lane == g) mine = m;
+        c += __popc(m);
     }
-    cnt[(int64_t)blockIdx.x * KM_NT + threadIdx.x] = c;
+    cmask[g0 + lane] = mine;
+    if (lane == 0) wcnt[(int64_t)blockIdx.x * KM_WARPS + w] = c;
 }
 
-// keys = code (job prefix included), shifted left by ib with the candidate's index below it when
-// ib > 0 (keys-only sort); vals = q | strand << 63 (global window start).
-__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__restrict__ wc, int64_t total, Bloom b2,
-                                                         int use_bloom, const int64_t *__restrict__ pos_of_thread,
-                                                         int ib, uint64_t *__restrict__ keys,
-                                                         uint64_t *__restrict__ vals, int64_t nc) {
-    const int64_t q0 = (int64_t)blockIdx.x * KM_CHUNK + (int64_t)threadIdx.x * KM_W;
-    int64_t o = pos_of_thread[(int64_t)blockIdx.x * KM_NT + threadIdx.x];
-    for (int w = 0; w < KM_W; w++) {
-        const int64_t q = q0 + w;
-        if (q >= total) break;
-        const uint64_t x = __ldcs(wc + q);
-        if (!is_candidate(x, b2, use_bloom)) continue;
-        if (!SG_IN_BOUNDS(o >= 0 && o < nc, 102, o)) break;
-        keys[o] = ib ? (((x & ~WC_STRAND) << ib) | (uint64_t)o) : (x & ~WC_STRAND);
-        vals[o] = (uint64_t)q | (x & WC_STRAND);
-        o++;
+// Sort records of the candidates. The code (job prefix included) is the sort key; below it:
+//   PK_POS   key = code << pb | q << 1 | strand  (pb = bits of q + 1): the window itself rides in the
+//            key, nothing else is written and no gather follows the sort;
+//   PK_IDX   key = code << pb | candidate index, vals = q | strand << 63, gathered after the sort;
+//   PK_PAIRS key = code, vals = q | strand << 63, sorted as pairs (nothing fits in 64 bits).
+enum : int { PK_POS = 0, PK_IDX = 1, PK_PAIRS = 2 };
+
+__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__restrict__ wc,
+                                                         const uint32_t *__restrict__ cmask,
+                                                         const int64_t *__restrict__ wpos, int mode, int pb,
+                                                         uint64_t *__restrict__ keys, uint64_t *__restrict__ vals,
+                                                         int64_t nc) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
+    const uint32_t mine = cmask[g0 + lane];
+    const uint32_t below = (1u << lane) - 1u;
+    int64_t o = wpos[(int64_t)blockIdx.x * KM_WARPS + w];
+    for (int g = 0; g < KM_GW; g++) {
+        const uint32_t m = __shfl_sync(0xffffffffu, mine, g);
+        if (m == 0) continue;
+        if ((m >> lane) & 1u) {
+            const int64_t q = (g0 + g) * 32 + lane;
+            const uint64_t x = __ldcs(wc + q);
+            const uint64_t code = x & ~WC_STRAND;
+            const int64_t p = o + __popc(m & below);
+            if (SG_IN_BOUNDS(p >= 0 && p < nc, 102, p)) {
+                if (mode == PK_POS) {
+                    keys[p] = (code << pb) | ((uint64_t)q << 1) | (x >> 63);
+                } else {
+                    keys[p] = mode == PK_IDX ? ((code << pb) | (uint64_t)p) : code;
+                    vals[p] = (uint64_t)q | (x & WC_STRAND);
+                }
+            }
+        }
+        o += __popc(m);
     }
 }
 
@@ -253,16 +345,20 @@ __device__ __forceinline__ uint64_t resolve_pos(uint64_t v, const int64_t *__res
     return ((uint64_t)lo << 32) | (uint64_t)(uint32_t)(q - off[lo]) | ((v >> 63) << 31);
 }
 
-// Keys-only sort: packed (code << ib | index) -> code, and the indexed value resolved.
+// After a keys-only sort (PK_POS, PK_IDX): the code, and the window resolved to its read.
 __global__ void unpack_kernel(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ vals, int64_t nc,
-                              int ib, const int64_t *__restrict__ off, int64_t n, uint64_t *__restrict__ key,
-                              uint64_t *__restrict__ val) {
+                              int mode, int pb, const int64_t *__restrict__ off, int64_t n,
+                              uint64_t *__restrict__ key, uint64_t *__restrict__ val) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const uint64_t p = packed[i];
-    const int64_t src = (int64_t)(p & ((1ull << ib) - 1));
-    key[i] = p >> ib;
-    if (SG_IN_BOUNDS(src < nc, 103, src)) val[i] = resolve_pos(vals[src], off, n);
+    const uint64_t low = p & ((1ull << pb) - 1);
+    key[i] = p >> pb;
+    if (mode == PK_POS) {
+        val[i] = resolve_pos((low >> 1) | (low << 63), off, n);
+    } else if (SG_IN_BOUNDS((int64_t)low < nc, 103, low)) {
+        val[i] = resolve_pos(vals[low], off, n);
+    }
 }
 
 // After the pairs sort: val = q | strand << 63  ->  read << 32 | pos | strand << 31.
@@ -438,15 +534,11 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     // 0. window codes
     uint64_t *wc = sc.get<uint64_t>(total + 1);
     if (!wc) return SG_ERR_OOM;
-    {
-        const size_t smem = (size_t)KM_CHUNK * sizeof(uint64_t) + KM_CHUNK + 48;
-        SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
-            SG_CUDA_TRY(ensure_smem(window_codes_kernel<decltype(kc)::value>, smem));
-            SG_LAUNCH("window_codes", window_codes_kernel<decltype(kc)::value>, nblk, KM_NT, smem, s, seq, total,
-                      off, n, k, jm, wc);
-            return SG_OK;
-        }));
-    }
+    SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
+        SG_LAUNCH("window_codes", window_codes_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n,
+                  k, jm, wc);
+        return SG_OK;
+    }));
     if (use_bloom) {
         // slices of at most bloom_slice_mb of B1, so each launch's atomics stay in L2
         const uint64_t slice_words = ((uint64_t)tune("bloom_slice_mb") << 20) / 4;
@@ -455,43 +547,56 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         for (uint64_t q = 0; q < nsl; q++) {
             const uint32_t lo_w = (uint32_t)((uint64_t)b1.nwords * q / nsl);
             const uint32_t hi_w = (uint32_t)((uint64_t)b1.nwords * (q + 1) / nsl);
-            SG_LAUNCH("bloom_insert", bloom_insert_kernel, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1, b2,
-                      lo_w, hi_w);
+            const int64_t u = tune("bloom_unroll");
+            if (u >= 16)
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<16>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1,
+                          b2, lo_w, hi_w);
+            else if (u >= 8)
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<8>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1,
+                          b2, lo_w, hi_w);
+            else
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<4>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1,
+                          b2, lo_w, hi_w);
         }
     }
-    uint32_t *tcnt = sc.get<uint32_t>(nblk * KM_NT + 1);
-    int64_t *tpos = sc.get<int64_t>(nblk * KM_NT + 1);
-    if (!tcnt || !tpos) return SG_ERR_OOM;
-    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, tcnt);
-    SG_TRY(exclusive_scan<uint32_t>(tcnt, tpos, nblk * KM_NT, s));
+    const int64_t nwarp = nblk * KM_WARPS;
+    uint32_t *cmask = sc.get<uint32_t>(nwarp * KM_GW);
+    uint32_t *wcnt = sc.get<uint32_t>(nwarp + 1);
+    int64_t *wpos = sc.get<int64_t>(nwarp + 1);
+    if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
+    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, cmask,
+              wcnt);
+    SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp, s));
     int64_t nc = 0;
     uint32_t herr = 0;
     SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(read_back(&nc, tpos + nblk * KM_NT, sizeof(int64_t), s));
+    SG_CUDA_TRY(read_back(&nc, wpos + nwarp, sizeof(int64_t), s));
     if (herr) {  // the passes above stayed in bounds; their results are discarded
         set_error("build_kmer_matrix: offsets are not a valid partition of the sequence");
         return SG_ERR_INVALID;
     }
 
-    uint64_t *key0 = sc.get<uint64_t>(nc), *val0 = sc.get<uint64_t>(nc);
-    uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
-    if (!key0 || !val0 || !key1 || !val1) return SG_ERR_OOM;
     int job_bits = 0;
     while (jm.ro && ((int64_t)1 << job_bits) < jm.njobs) job_bits++;
     const int code_bits = 2 * k + job_bits;
-    int ib = 1;
-    while (((int64_t)1 << ib) < nc) ib++;
-    if (code_bits + ib > 64) ib = 0;  // too wide to pack: sort (key, value) pairs
-    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom,
-              (const int64_t *)tpos, ib, key0, val0, nc);
+    int qbits = 1, ibits = 1;
+    while (((int64_t)1 << qbits) < total) qbits++;
+    while (((int64_t)1 << ibits) < nc) ibits++;
+    const int mode = code_bits + qbits + 1 <= 64 ? PK_POS : (code_bits + ibits <= 64 ? PK_IDX : PK_PAIRS);
+    const int pb = mode == PK_POS ? qbits + 1 : (mode == PK_IDX ? ibits : 0);
+    uint64_t *key0 = sc.get<uint64_t>(nc), *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
+    uint64_t *val0 = mode == PK_POS ? nullptr : sc.get<uint64_t>(nc);
+    if (!key0 || !key1 || !val1 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
+    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, (const uint32_t *)cmask,
+              (const int64_t *)wpos, mode, pb, key0, val0, nc);
     bool alt = false;
     const uint64_t *key;
     uint64_t *val;
-    if (ib) {  // 8-byte keys through the radix passes, values gathered once afterwards
-        SG_TRY(radix_sort_keys(key0, key1, nc, ib, ib + code_bits, &alt, s));
+    if (mode != PK_PAIRS) {  // 8-byte keys through the radix passes, then one unpacking pass
+        SG_TRY(radix_sort_keys(key0, key1, nc, pb, pb + code_bits, &alt, s));
         uint64_t *ks = alt ? key1 : key0, *kfree = alt ? key0 : key1;
         SG_LAUNCH("unpack", unpack_kernel, blocks_for(nc, NT), NT, 0, s, (const uint64_t *)ks, (const uint64_t *)val0,
-                  nc, ib, off, n, kfree, val1);
+                  nc, mode, pb, off, n, kfree, val1);
         key = kfree;
         val = val1;
     } else {

@@ -13,8 +13,10 @@ pytestmark = pytest.mark.gpu
 
 
 # ------------------------------------------------------------------------------ A, At
+# k = 17 packs (code, window, strand) into the sort key; k = 23 on this input is too wide for that
+# and packs (code, candidate index); k = 31 is too wide for either and sorts (key, value) pairs.
 @pytest.mark.parametrize("k,lo,hi,seed", [(17, 2, 8, 1), (5, 2, 6, 2), (7, 1, 3, 3), (31, 2, 50, 4),
-                                          (1, 1, 1 << 30, 5), (9, 3, 3, 6)])
+                                          (1, 1, 1 << 30, 5), (9, 3, 3, 6), (23, 2, 9, 7)])
 def test_kmer_matrix_random(k, lo, hi, seed):
     rng = np.random.default_rng(seed)
     g = synth.genome(20000, seed)
@@ -39,6 +41,21 @@ def test_kmer_matrix_edge_cases():
         exp = oracle.build_kmer_matrix(seq, off, k, lo, hi)
         _, got = gpu_kmer(seq, off, k, lo, hi)
         assert_kmer_equal(got, exp)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_kmer_matrix_unaligned_sequence(shift):
+    """A sequence that starts off a 4-byte boundary (a view into a larger buffer) is staged byte
+    by byte; the result is the same."""
+    import torch
+    g = synth.genome(30000, 40 + shift)
+    rd = synth.reads(g, 6.0, 900.0, 300.0, 1, 0.04, 0.03, 0.02, 41 + shift)
+    buf = torch.zeros(rd["seq"].size + 8, dtype=torch.uint8, device="cuda")
+    buf[shift:shift + rd["seq"].size] = dev(rd["seq"], np.uint8)
+    seq = buf[shift:shift + rd["seq"].size]
+    assert seq.data_ptr() % 4 == shift
+    got = sg.build_kmer_matrix(seq, dev(rd["offsets"], np.int64), k=17, lo=2, hi=8).to_numpy()
+    assert_kmer_equal(got, oracle.build_kmer_matrix(rd["seq"], rd["offsets"], 17, 2, 8))
 
 
 def test_kmer_matrix_invalid():
