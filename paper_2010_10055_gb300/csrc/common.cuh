@@ -45,6 +45,10 @@ struct Scratch {
     ~Scratch() { for (size_t i = ptrs.size(); i-- > 0;) dfree(ptrs[i], s); }
 };
 
+// Records that a bounded wait between thread blocks gave up during `what` and returns
+// SG_ERR_TIMEOUT.
+sg_status timeout_error(const char *what);
+
 // Current value of a tunable parameter (see sg_tune_set).
 int64_t tune(const char *name);
 
@@ -66,7 +70,9 @@ inline bool grid_ok(int64_t g) { return g > 0; }
 inline bool grid_ok(dim3 g) { return g.x > 0 && g.y > 0 && g.z > 0; }
 
 // The device-side error word used by validation kernels (one per call, zeroed first).
-enum : uint32_t { DEV_OK = 0, DEV_INVALID = 1, DEV_OVERFLOW = 2 };
+// DEV_TIMEOUT: a bounded wait between thread blocks gave up (never expected; the call fails
+// instead of hanging).
+enum : uint32_t { DEV_OK = 0, DEV_INVALID = 1, DEV_OVERFLOW = 2, DEV_TIMEOUT = 4 };
 
 }  // namespace sg
 

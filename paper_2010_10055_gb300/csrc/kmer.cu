@@ -479,7 +479,8 @@ __global__ void rowptr_from_sorted_kernel(const uint32_t *__restrict__ rows, int
     if (e > nnz) return;
     int64_t prev = (e == 0) ? -1 : (int64_t)rows[e - 1];
     int64_t cur = (e == nnz) ? n : (int64_t)rows[e];
-    if (!SG_IN_BOUNDS(prev >= -1 && cur <= n && prev <= cur, 107, cur)) return;
+    // always in bounds, even for rows that a failed sort left unsorted (the call then fails)
+    if (!SG_IN_BOUNDS(prev >= -1 && cur <= n && prev <= cur, 107, cur) || prev < -1 || cur > n) return;
     for (int64_t r = prev + 1; r <= cur; r++) rp[r] = e;
 }
 
@@ -566,11 +567,12 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
     SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, cmask,
               wcnt);
-    SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp, s));
+    SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp, s, err));
     int64_t nc = 0;
     uint32_t herr = 0;
     SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SG_CUDA_TRY(read_back(&nc, wpos + nwarp, sizeof(int64_t), s));
+    if (herr & DEV_TIMEOUT) return timeout_error("build_kmer_matrix");
     if (herr) {  // the passes above stayed in bounds; their results are discarded
         set_error("build_kmer_matrix: offsets are not a valid partition of the sequence");
         return SG_ERR_INVALID;
@@ -593,14 +595,14 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     const uint64_t *key;
     uint64_t *val;
     if (mode != PK_PAIRS) {  // 8-byte keys through the radix passes, then one unpacking pass
-        SG_TRY(radix_sort_keys(key0, key1, nc, pb, pb + code_bits, &alt, s));
+        SG_TRY(radix_sort_keys(key0, key1, nc, pb, pb + code_bits, &alt, s, err));
         uint64_t *ks = alt ? key1 : key0, *kfree = alt ? key0 : key1;
         SG_LAUNCH("unpack", unpack_kernel, blocks_for(nc, NT), NT, 0, s, (const uint64_t *)ks, (const uint64_t *)val0,
                   nc, mode, pb, off, n, kfree, val1);
         key = kfree;
         val = val1;
     } else {
-        SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, code_bits, &alt, s)));
+        SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, code_bits, &alt, s, err)));
         key = alt ? key1 : key0;
         val = alt ? val1 : val0;
         SG_LAUNCH("resolve", resolve_kernel, blocks_for(nc, NT), NT, 0, s, val, nc, off, n);
@@ -615,19 +617,21 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     int64_t *out_pos = sc.get<int64_t>(nc + 1);
     if (!head || !seg_excl || !seg_start || !rel || !col_of_seg || !keep || !out_pos) return SG_ERR_OOM;
     SG_LAUNCH("seg_head", seg_head_kernel, blocks_for(nc, NT), NT, 0, s, key, nc, head);
-    SG_TRY(exclusive_scan<uint32_t>(head, seg_excl, nc, s));
+    SG_TRY(exclusive_scan<uint32_t>(head, seg_excl, nc, s, err));
     SG_LAUNCH("seg_start", seg_start_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, nc, seg_start);
     // number of segments lives on the device at seg_excl[nc]; launch over the upper bound nc
     SG_LAUNCH("seg_reliable", seg_reliable_kernel, blocks_for(nc, NT), NT, 0, s, seg_start, seg_excl + nc, lo,
               hi, key, lohi, 2 * k, nc, rel);
-    SG_TRY(exclusive_scan<uint32_t>(rel, col_of_seg, nc, s));
+    SG_TRY(exclusive_scan<uint32_t>(rel, col_of_seg, nc, s, err));
     SG_LAUNCH("keep", keep_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, rel, val, nc, keep);
-    SG_TRY(exclusive_scan<uint32_t>(keep, out_pos, nc, s));
+    SG_TRY(exclusive_scan<uint32_t>(keep, out_pos, nc, s, err));
     int64_t sizes[2] = {0, 0};  // m, nnz
     // m = reliable segments = col_of_seg[nc] (rel is 0 past the last segment)
     SG_CUDA_TRY(cudaMemcpyAsync(&sizes[0], col_of_seg + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SG_CUDA_TRY(cudaMemcpyAsync(&sizes[1], out_pos + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr) return timeout_error("build_kmer_matrix");
     const int64_t m = sizes[0], nnz = sizes[1];
     if (m >= ((int64_t)1 << 31)) {
         set_error("build_kmer_matrix: %lld reliable k-mers exceed the int32 column range", (long long)m);
@@ -654,12 +658,14 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     int rbits = 0;
     while (rbits < 32 && ((int64_t)1 << rbits) < n) rbits++;
     bool aalt = false;
-    SG_TRY((radix_sort_pairs<uint32_t, uint64_t>(ak0, av0, ak1, av1, nnz, rbits, &aalt, s)));
+    SG_TRY((radix_sort_pairs<uint32_t, uint64_t>(ak0, av0, ak1, av1, nnz, rbits, &aalt, s, err)));
     const uint32_t *arow = aalt ? ak1 : ak0;
     const uint64_t *apv = aalt ? av1 : av0;
     SG_LAUNCH("rowptr_from_sorted", rowptr_from_sorted_kernel, blocks_for(nnz + 1, NT), NT, 0, s, arow, nnz, n,
               A->row_ptr);
     SG_LAUNCH("split_pairs", split_pairs_kernel, blocks_for(nnz, NT), NT, 0, s, apv, nnz, A->col, A->val);
+    SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));  // the sort of A waits between tiles
+    if (herr) return timeout_error("build_kmer_matrix");
     return SG_OK;
 }
 

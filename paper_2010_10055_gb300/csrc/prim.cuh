@@ -5,21 +5,26 @@
 
 namespace sg {
 
-// out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total. `out` may alias `in` only
-// when T is int64_t. Enqueued on `s`; temporaries come from the stream-ordered allocator.
+// Both primitives coordinate their tiles by bounded waits; if one ever gives up it ORs
+// DEV_TIMEOUT into *err (a device word the caller reads back; may be nullptr) and the results are
+// not valid. Enqueued on `s`; temporaries come from the stream-ordered allocator.
+
+// out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total (< 2^62). `out` may alias `in`
+// only when T is int64_t.
 template <class T>
-sg_status exclusive_scan(const T *in, int64_t *out, int64_t n, cudaStream_t s);
+sg_status exclusive_scan(const T *in, int64_t *out, int64_t n, cudaStream_t s, uint32_t *err);
 
 // Stable LSD radix sort of (keys, vals) by the low `key_bits` bits of the key. Buffers are
 // ping-ponged between (k0, v0) and (k1, v1); on return *in_alt says whether the sorted data is
-// in (k1, v1). Key bits above key_bits must be zero.
+// in (k1, v1). Key bits above the last 8-bit digit that covers key_bits must be zero.
 template <class K, class V>
 sg_status radix_sort_pairs(K *k0, V *v0, K *k1, V *v1, int64_t n, int key_bits, bool *in_alt,
-                           cudaStream_t s);
+                           cudaStream_t s, uint32_t *err);
 
-// Stable LSD radix sort of 64-bit keys by their bits [lo_bit, hi_bit) (other bits ride along).
+// Stable LSD radix sort of 64-bit keys by their bits [lo_bit, hi_bit) (other bits ride along;
+// bits above hi_bit up to the last digit's end must be zero).
 sg_status radix_sort_keys(uint64_t *k0, uint64_t *k1, int64_t n, int lo_bit, int hi_bit, bool *in_alt,
-                          cudaStream_t s);
+                          cudaStream_t s, uint32_t *err);
 
 // Block-wide exclusive scan of one value per thread (blockDim.x = NT, a multiple of 32).
 // `tmp` must hold NT/32 + 1 values. Returns the exclusive prefix; *total gets the block total.

@@ -23,6 +23,11 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 
+sg_status timeout_error(const char *what) {
+    set_error("%s: a bounded wait between thread blocks gave up (internal error); results discarded", what);
+    return SG_ERR_TIMEOUT;
+}
+
 static sg_alloc_fn g_alloc = nullptr;
 static sg_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;

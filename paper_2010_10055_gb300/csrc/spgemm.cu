@@ -31,7 +31,8 @@ namespace sg {
 
 constexpr int SP_MAX_SEEDS = 8;
 constexpr uint64_t SEED_NONE = ~0ull;
-constexpr int SP_NCLS = 4;        // shared-memory classes per pass
+constexpr int SP_NCLS = 9;        // shared-memory classes per pass (one per table size)
+constexpr int SP_MINLOG = 6;      // smallest table: 64 slots
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t k, int log2T) {
     return ((uint32_t)k * 2654435761u) >> (32 - log2T);
@@ -122,6 +123,9 @@ __global__ void num_need_kernel(const int64_t *__restrict__ dist, int64_t n, int
 // ------------------------------------------------------------------- product enumeration
 // Calls f(k, vk, idx) for every product of row i: k = partner read (k != i), vk = the At value
 // (PAIR only), idx = index of the A entry within row i. Stops (per warp) once *stop is nonzero.
+// Each lane takes SP_U products per step, so a warp has SP_U gathers of At in flight at once.
+constexpr int SP_U = 2;
+
 template <bool PAIR, class F>
 __device__ __forceinline__ void for_each_product(const SpArgs &g, int32_t i, int64_t r0, int64_t r1,
                                                  const volatile int *stop, F &&f) {
@@ -143,26 +147,32 @@ __device__ __forceinline__ void for_each_product(const SpArgs &g, int32_t i, int
         }
         const int64_t excl = inc - len;
         const int64_t total = __shfl_sync(0xffffffffu, inc, 31);
-        for (int64_t base = 0; base < total; base += 32) {
-            const int64_t p = base + lane;
-            int owner = 0;  // largest lane whose exclusive prefix is <= p
+        for (int64_t base = 0; base < total; base += 32 * SP_U) {
+            int owner[SP_U];
+            int64_t b[SP_U];
+            uint64_t pr[SP_U];
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                const int64_t v = __shfl_sync(0xffffffffu, excl, (owner + s) & 31);
-                if (owner + s < 32 && v <= p) owner += s;
-            }
-            const int64_t ob = __shfl_sync(0xffffffffu, beg, owner);
-            const int64_t oe = __shfl_sync(0xffffffffu, excl, owner);
-            if (p < total) {
-                const int64_t b = ob + (p - oe);
-                if (PAIR) {
-                    const uint64_t pr = g.t_pair[b];
-                    const int32_t k = (int32_t)(uint32_t)pr;
-                    if (k != i) f(k, (uint32_t)(pr >> 32), a0 - r0 + owner);
-                } else {
-                    const int32_t k = g.t_col[b];
-                    if (k != i) f(k, 0u, a0 - r0 + owner);
+            for (int u = 0; u < SP_U; u++) {
+                const int64_t p = base + u * 32 + lane;
+                int ow = 0;  // largest lane whose exclusive prefix is <= p
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const int64_t v = __shfl_sync(0xffffffffu, excl, (ow + s) & 31);
+                    if (ow + s < 32 && v <= p) ow += s;
                 }
+                const int64_t ob = __shfl_sync(0xffffffffu, beg, ow);
+                const int64_t oe = __shfl_sync(0xffffffffu, excl, ow);
+                owner[u] = ow;
+                b[u] = p < total ? ob + (p - oe) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < SP_U; u++)  // all gathers first, then the table updates
+                if (b[u] >= 0) pr[u] = PAIR ? g.t_pair[b[u]] : (uint64_t)(uint32_t)g.t_col[b[u]];
+#pragma unroll
+            for (int u = 0; u < SP_U; u++) {
+                if (b[u] < 0) continue;
+                const int32_t k = (int32_t)(uint32_t)pr[u];
+                if (k != i) f(k, (uint32_t)(pr[u] >> 32), a0 - r0 + owner[u]);
             }
         }
     }
@@ -397,7 +407,15 @@ __global__ void pair_kernel(const int32_t *__restrict__ col, const uint32_t *__r
     if (e < nnz) pair[e] = ((uint64_t)val[e] << 32) | (uint32_t)col[e];
 }
 
-static int pick_threads(int log2T) { return log2T <= 10 ? 128 : 256; }
+static int pick_threads(int log2T) { return log2T <= 7 ? 64 : (log2T <= 10 ? 128 : 256); }
+
+// Launch names by table size, so that per-kernel timing separates the classes.
+static const char *const SYM_NAMES[] = {"spgemm_symbolic_t64", "spgemm_symbolic_t128", "spgemm_symbolic_t256",
+                                        "spgemm_symbolic_t512", "spgemm_symbolic_t1k", "spgemm_symbolic_t2k",
+                                        "spgemm_symbolic_t4k", "spgemm_symbolic_t8k", "spgemm_symbolic_t16k"};
+static const char *const NUM_NAMES[] = {"spgemm_numeric_t64", "spgemm_numeric_t128", "spgemm_numeric_t256",
+                                        "spgemm_numeric_t512", "spgemm_numeric_t1k", "spgemm_numeric_t2k",
+                                        "spgemm_numeric_t4k", "spgemm_numeric_t8k", "spgemm_numeric_t16k"};
 
 sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S,
                        sg_overlap_csr *C, cudaStream_t s, Scratch &sc) {
@@ -429,8 +447,10 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
               work, a_beg, a_len);
     SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
 
-    // ---- symbolic: guessed shared-memory tables of 2^8 .. 2^14 slots
-    const Classes sym{{8, 10, 12, 14}, 4};
+    // ---- symbolic: guessed shared-memory tables of 2^6 .. 2^14 slots, one class per size
+    Classes sym{};
+    sym.ncls = SP_NCLS;
+    for (int c = 0; c < SP_NCLS; c++) sym.log2T[c] = SP_MINLOG + c;
     SG_LAUNCH("sym_need", sym_need_kernel, blocks_for(n, NT), NT, 0, s, work, n, (int)tune("sym_guess_shift"),
               need);
     const int grid = (int)(152 * tune("spgemm_blocks_per_sm"));
@@ -438,7 +458,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     for (int c = 0; c < sym.ncls; c++) {
         const size_t sm = (size_t)(2 << sym.log2T[c]) * sizeof(int32_t);
         SG_CUDA_TRY(ensure_smem(symbolic_kernel<false>, sm));
-        SG_LAUNCH("spgemm_symbolic", symbolic_kernel<false>, grid, pick_threads(sym.log2T[c]), sm, s, g,
+        SG_LAUNCH(SYM_NAMES[sym.log2T[c] - SP_MINLOG], symbolic_kernel<false>, grid, pick_threads(sym.log2T[c]), sm,
+                  s, g,
                   lists + (int64_t)c * n, sym_counts + c, sym.log2T[c], (const int64_t *)work, (int32_t *)nullptr,
                   (int64_t)0, ovf, ovf_count, nnz_row, dist);
     }
@@ -463,16 +484,23 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
 
     // ---- C row pointers; numeric classes from the exact distinct counts
     SG_ALLOC(C->row_ptr, int64_t, n + 1, s);
-    SG_TRY(exclusive_scan<int64_t>(nnz_row, C->row_ptr, n, s));
-    Classes num{{8, 10, 11, 12}, 4};  // table + sort buffer <= 112 KB for max_seeds <= 2
-    if (S > 2) num = Classes{{8, 9, 10, 11}, 4};
-    if (S > 4) num = Classes{{7, 8, 9, 10}, 4};
+    SG_TRY(exclusive_scan<int64_t>(nnz_row, C->row_ptr, n, s, err));
+    // numeric: one class per table size from 2^6 while the table and its sort buffer fit in 160 KB
+    Classes num{};
+    num.ncls = 0;
+    while (num.ncls < SP_NCLS && num_table_bytes((int64_t)1 << (SP_MINLOG + num.ncls), S) <= (160u << 10)) {
+        num.log2T[num.ncls] = SP_MINLOG + num.ncls;
+        num.ncls++;
+    }
     SG_LAUNCH("num_need", num_need_kernel, blocks_for(n, NT), NT, 0, s, dist, n, need);
     SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, num, num_counts, lists);
     int64_t nnz = 0;
     unsigned long long h_num[NCNT];
+    uint32_t herr = 0;
     SG_CUDA_TRY(cudaMemcpyAsync(h_num, num_counts, sizeof(h_num), cudaMemcpyDeviceToHost, s));
+    SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SG_CUDA_TRY(read_back(&nnz, C->row_ptr + n, sizeof(int64_t), s));
+    if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");  // before anything uses row_ptr
     C->n = n;
     C->nnz = nnz;
     C->max_seeds = S;
@@ -484,7 +512,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         if (!h_num[c]) continue;
         const size_t sm = num_table_bytes((int64_t)1 << num.log2T[c], S);
         SG_CUDA_TRY(ensure_smem(numeric_kernel<false>, sm));
-        SG_LAUNCH("spgemm_numeric", numeric_kernel<false>, grid, pick_threads(num.log2T[c]), sm, s, g,
+        SG_LAUNCH(NUM_NAMES[num.log2T[c] - SP_MINLOG], numeric_kernel<false>, grid, pick_threads(num.log2T[c]), sm,
+                  s, g,
                   lists + (int64_t)c * n, num_counts + c, num.log2T[c], (const int64_t *)need,
                   (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i,
                   C->seed_k, nnz);
@@ -499,8 +528,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                   num_counts + num.ncls, 0, (const int64_t *)need, pool, slice_bytes, (const int64_t *)C->row_ptr,
                   C->col, C->count, C->seed_i, C->seed_k, nnz);
     }
-    uint32_t herr = 0;
     SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));
+    if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
     if (herr) {
         set_error("overlap_spgemm: numeric and symbolic passes disagree on a row size (internal error)");
         return SG_ERR_OVERFLOW;

@@ -325,11 +325,12 @@ sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *
         if (job_ro)
             SG_LAUNCH("tr_job_changes", job_changes_kernel, blocks_for(n, 256), 256, 0, s, g.rp,
                       (const int64_t *)kept, n, job_ro, njobs, it, job_last);
-        SG_TRY(exclusive_scan<int64_t>(kept, rp[nxt], n, s));
+        SG_TRY(exclusive_scan<int64_t>(kept, rp[nxt], n, s, err));
         int64_t nnz2 = 0;
         uint32_t herr = 0;
-        if (it == 1) SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(read_back(&nnz2, rp[nxt] + n, sizeof(int64_t), s));
+        if (herr & DEV_TIMEOUT) return timeout_error("transitive_reduce");
         if (herr) {
             set_error("graph does not satisfy the CSR contract (sorted unique columns, no diagonal, suffix < 2^30, dir <= 3)");
             return SG_ERR_INVALID;
