@@ -352,8 +352,10 @@ uint64_t sg_debug_check(void);
 uint64_t sg_launch_count(void);
 
 /* Tunable launch parameters (used by the autotuner; results never depend on them):
- *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (48)
- *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4, 8 or 16 (4)
+ *   bloom_bits            bits of the first-level Bloom filter per window (8): fewer bits, fewer
+ *                         slices but more false positives (singletons that reach the exact count)
+ *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (64)
+ *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4 or 8 (4)
  *   sym_guess_shift       symbolic hash table guess = products of the row >> shift (2)
  *   spgemm_blocks_per_sm  blocks per SM of each SpGEMM class launch (16)
  *   tr_blocks_per_sm      blocks per SM of the min-plus launch (32)

@@ -14,8 +14,9 @@ import statistics
 import paper_2010_10055_gb300 as sg
 
 SPACE = {
-    "bloom_slice_mb": [24, 32, 48, 64, 96, 192],
-    "bloom_unroll": [4, 8, 16],
+    "bloom_slice_mb": [32, 48, 64, 96, 128],
+    "bloom_unroll": [4, 8],
+    "bloom_bits": [6, 8, 10, 12],
     "sym_guess_shift": [0, 1, 2, 3],
     "spgemm_blocks_per_sm": [2, 4, 8, 16],
     "tr_blocks_per_sm": [4, 8, 16, 32],

@@ -135,6 +135,7 @@ struct WcOut {
 // makes k a compile-time constant (K == 0: k taken from k_rt).
 constexpr uint64_t WC_NONE = ~0ull;
 constexpr uint64_t WC_STRAND = 1ull << 63;
+constexpr uint32_t B1_SEED = 0x9e3779b9u, B2_SEED = 0x7f4a7c15u;
 
 template <int K>
 __global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__restrict__ seq, int64_t total,
@@ -192,8 +193,8 @@ __global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__re
             run = ok ? run + 1 : 0;
             const int j = qi - (k - 1);
             if (j >= 0) {
-                const uint64_t code = fw < rc ? fw : rc;
-                const uint64_t v = run >= k ? (rkey | code | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
+                const uint64_t key = rkey | (fw < rc ? fw : rc);
+                const uint64_t v = run >= k ? (key | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
                 out.put(wc, qs, total, j, v);
             }
         }
@@ -216,8 +217,8 @@ __global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__re
             run = ok ? run + 1 : 0;
             const int j = qi - (k - 1);
             if (j >= 0 && qs + j < total) {
-                const uint64_t code = fw < rc ? fw : rc;
-                wc[qs + j] = run >= k ? (rkey | code | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
+                const uint64_t key = rkey | (fw < rc ? fw : rc);
+                wc[qs + j] = run >= k ? (key | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
             }
         }
     }
@@ -225,25 +226,28 @@ __global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__re
 }
 
 // One launch per slice [w_lo, w_hi) of B1's words: every launch streams all window codes but only
-// the k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2.
+// the k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2. kmask
+// extracts the key (job prefix and code) from a window code.
 template <int BI_U>
 __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint64_t *__restrict__ wc, int64_t total,
-                                                            Bloom b1, Bloom b2, uint32_t w_lo, uint32_t w_hi) {
-    // BI_U windows per thread per step (each step's loads coalesced across the warp), so that
-    // their atomics are in flight together
+                                                            Bloom b1, Bloom b2, uint64_t kmask, uint32_t w_lo,
+                                                            uint32_t w_hi) {
+    // BI_U windows per thread per step (each step's loads coalesced across the warp, all issued
+    // before any is used), so that their atomics are in flight together
     const int64_t stride = (int64_t)gridDim.x * KM_NT;
     for (int64_t q0 = (int64_t)blockIdx.x * KM_NT + threadIdx.x; q0 < total; q0 += BI_U * stride) {
-        uint64_t code[BI_U];
+        uint64_t x[BI_U];
         uint32_t i1[BI_U], m1[BI_U], old[BI_U];
         bool mine[BI_U];
 #pragma unroll
         for (int u = 0; u < BI_U; u++) {
             const int64_t q = q0 + u * stride;
-            const uint64_t x = q < total ? __ldcs(wc + q) : WC_NONE;
-            code[u] = x & ~WC_STRAND;
-            b1.probe(code[u], &i1[u], &m1[u]);
-            // another slice's launch handles k-mers whose word lies outside [w_lo, w_hi)
-            mine[u] = x != WC_NONE && i1[u] >= w_lo && i1[u] < w_hi;
+            x[u] = q < total ? __ldcs(wc + q) : WC_NONE;
+        }
+#pragma unroll
+        for (int u = 0; u < BI_U; u++) {
+            b1.probe(x[u] & kmask, &i1[u], &m1[u]);
+            mine[u] = x[u] != WC_NONE && i1[u] >= w_lo && i1[u] < w_hi;
         }
 #pragma unroll
         for (int u = 0; u < BI_U; u++) old[u] = mine[u] ? atomicOr(b1.words + i1[u], m1[u]) : 0u;
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint64_t *__r
         for (int u = 0; u < BI_U; u++) {
             if (mine[u] && (old[u] & m1[u]) == m1[u]) {
                 uint32_t i2, m2;
-                b2.probe(code[u], &i2, &m2);
+                b2.probe(x[u] & kmask, &i2, &m2);
                 if ((b2.words[i2] & m2) != m2) atomicOr(b2.words + i2, m2);
             }
         }
@@ -271,16 +275,16 @@ constexpr int KM_WARPS = KM_NT / 32;
 constexpr int KM_GW = KM_CHUNK / KM_NT;  // groups per warp (32: one mask word per lane)
 static_assert(KM_GW == 32, "one mask word per lane");
 
-__device__ __forceinline__ bool is_candidate(uint64_t x, const Bloom &b2, int use_bloom) {
+__device__ __forceinline__ bool is_candidate(uint64_t x, const Bloom &b2, int use_bloom, uint64_t kmask) {
     if (x == WC_NONE) return false;
     if (!use_bloom) return true;
     uint32_t i2, m2;
-    b2.probe(x & ~WC_STRAND, &i2, &m2);
+    b2.probe(x & kmask, &i2, &m2);
     return (b2.words[i2] & m2) == m2;
 }
 
 __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint64_t *__restrict__ wc, int64_t total, Bloom b2,
-                                                          int use_bloom, uint32_t *__restrict__ cmask,
+                                                          int use_bloom, uint64_t kmask, uint32_t *__restrict__ cmask,
                                                           uint32_t *__restrict__ wcnt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint64_t *__res
     for (int g = 0; g < KM_GW; g++) {
         const int64_t q = (g0 + g) * 32 + lane;
         const uint64_t x = q < total ? __ldcs(wc + q) : WC_NONE;
-        const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(x, b2, use_bloom));
+        const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(x, b2, use_bloom, kmask));
         if (lane == g) mine = m;
         c += __popc(m);
     }
@@ -307,8 +311,8 @@ enum : int { PK_POS = 0, PK_IDX = 1, PK_PAIRS = 2 };
 __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__restrict__ wc,
                                                          const uint32_t *__restrict__ cmask,
                                                          const int64_t *__restrict__ wpos, int mode, int pb,
-                                                         uint64_t *__restrict__ keys, uint64_t *__restrict__ vals,
-                                                         int64_t nc) {
+                                                         uint64_t kmask, uint64_t *__restrict__ keys,
+                                                         uint64_t *__restrict__ vals, int64_t nc) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
     const uint32_t mine = cmask[g0 + lane];
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__rest
         if ((m >> lane) & 1u) {
             const int64_t q = (g0 + g) * 32 + lane;
             const uint64_t x = __ldcs(wc + q);
-            const uint64_t code = x & ~WC_STRAND;
+            const uint64_t code = x & kmask;
             const int64_t p = o + __popc(m & below);
             if (SG_IN_BOUNDS(p >= 0 && p < nc, 102, p)) {
                 if (mode == PK_POS) {
@@ -520,10 +524,14 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
 
     const int64_t nblk = blocks_for(total, KM_CHUNK);
     const int use_bloom = lo >= 2 ? 1 : 0;
-    Bloom b1{nullptr, 0, 0x9e3779b9u}, b2{nullptr, 0, 0x7f4a7c15u};
+    int job_bits = 0;
+    while (jm.ro && ((int64_t)1 << job_bits) < jm.njobs) job_bits++;
+    const int code_bits = 2 * k + job_bits;
+    const uint64_t kmask = (1ull << code_bits) - 1;  // code_bits <= 62
+    Bloom b1{nullptr, 0, B1_SEED}, b2{nullptr, 0, B2_SEED};
     if (use_bloom && total > 0) {
-        // B1: 8 bits per window; B2 ("seen twice"): 2 bits per window; 32-bit words
-        const int64_t w1 = total / 4 + 1024, w2 = total / 16 + 1024;
+        // B1: bloom_bits (8) bits per window; B2 ("seen twice"): 2 bits per window; 32-bit words
+        const int64_t w1 = total * tune("bloom_bits") / 32 + 1024, w2 = total / 16 + 1024;
         b1.nwords = (uint32_t)(w1 < 0xFFFFFFF0LL ? w1 : 0xFFFFFFF0LL);
         b2.nwords = (uint32_t)(w2 < 0xFFFFFFF0LL ? w2 : 0xFFFFFFF0LL);
         b1.words = sc.get<uint32_t>(b1.nwords);
@@ -545,19 +553,16 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         const uint64_t slice_words = ((uint64_t)tune("bloom_slice_mb") << 20) / 4;
         const uint64_t nsl = (b1.nwords + slice_words - 1) / slice_words;
         const int64_t grid = blocks_for(total, KM_NT) < 152 * 16 ? blocks_for(total, KM_NT) : 152 * 16;
+        const int64_t u = tune("bloom_unroll");
         for (uint64_t q = 0; q < nsl; q++) {
             const uint32_t lo_w = (uint32_t)((uint64_t)b1.nwords * q / nsl);
             const uint32_t hi_w = (uint32_t)((uint64_t)b1.nwords * (q + 1) / nsl);
-            const int64_t u = tune("bloom_unroll");
-            if (u >= 16)
-                SG_LAUNCH("bloom_insert", bloom_insert_kernel<16>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1,
-                          b2, lo_w, hi_w);
-            else if (u >= 8)
-                SG_LAUNCH("bloom_insert", bloom_insert_kernel<8>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1,
-                          b2, lo_w, hi_w);
+            if (u >= 8)
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<8>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1, b2,
+                          kmask, lo_w, hi_w);
             else
-                SG_LAUNCH("bloom_insert", bloom_insert_kernel<4>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1,
-                          b2, lo_w, hi_w);
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<4>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1, b2,
+                          kmask, lo_w, hi_w);
         }
     }
     const int64_t nwarp = nblk * KM_WARPS;
@@ -565,8 +570,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint32_t *wcnt = sc.get<uint32_t>(nwarp + 1);
     int64_t *wpos = sc.get<int64_t>(nwarp + 1);
     if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
-    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, cmask,
-              wcnt);
+    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, kmask,
+              cmask, wcnt);
     SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp, s, err));
     int64_t nc = 0;
     uint32_t herr = 0;
@@ -578,9 +583,6 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         return SG_ERR_INVALID;
     }
 
-    int job_bits = 0;
-    while (jm.ro && ((int64_t)1 << job_bits) < jm.njobs) job_bits++;
-    const int code_bits = 2 * k + job_bits;
     int qbits = 1, ibits = 1;
     while (((int64_t)1 << qbits) < total) qbits++;
     while (((int64_t)1 << ibits) < nc) ibits++;
@@ -590,7 +592,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint64_t *val0 = mode == PK_POS ? nullptr : sc.get<uint64_t>(nc);
     if (!key0 || !key1 || !val1 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
     SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, (const uint32_t *)cmask,
-              (const int64_t *)wpos, mode, pb, key0, val0, nc);
+              (const int64_t *)wpos, mode, pb, kmask, key0, val0, nc);
     bool alt = false;
     const uint64_t *key;
     uint64_t *val;

@@ -179,8 +179,9 @@ LaunchScope::~LaunchScope() {
 struct Tunable { const char *name; int64_t value; int64_t lo, hi; };
 static Tunable g_tunables[] = {
     // defaults: the autotuner's choice on a GB300 for the bacterial-scale read set
-    {"bloom_slice_mb", 48, 1, 1 << 20},   // B1 megabytes updated per Bloom launch
-    {"bloom_unroll", 4, 4, 16},           // windows (atomics in flight) per thread per Bloom step: 4, 8, 16
+    {"bloom_bits", 8, 2, 32},             // bits of the first Bloom filter per window
+    {"bloom_slice_mb", 64, 1, 1 << 20},   // B1 megabytes updated per Bloom launch
+    {"bloom_unroll", 4, 4, 8},            // windows (atomics in flight) per thread per Bloom step: 4 or 8
     {"sym_guess_shift", 2, 0, 8},         // symbolic table guess = products >> shift
     {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch
     {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch
