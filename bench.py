@@ -15,7 +15,9 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -37,6 +39,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--workload", default="bacterial-5Mbp-30x")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="genome length factor: a smaller case of the same workload, for profiling captures")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
@@ -103,20 +107,50 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- roofline
 def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
-    """Bytes the method must move per launch of `kernel` (inputs read once, outputs written once)."""
+    """Bytes the method must move per step in `kernel` (inputs read once, outputs written once),
+    from the per-unit figures: 8-byte window codes, 4-byte filter words (a touch is a read and a
+    write), 8-byte keys, 24-byte C entries."""
+    if kernel == "window_codes":
+        return 1.0 * sz["total"] + 8.0 * sz["total"]           # bases in, one code per position out
     if kernel == "bloom_insert":
-        # every base read once, one 8-byte filter word touched per k-mer window
-        return sz["total"] + 8.0 * sz["windows"]
-    if kernel in ("cand_count", "cand_emit"):
-        extra = 16.0 * (sz["cand"] or 0) if kernel == "cand_emit" else 0.0
-        return sz["total"] + 8.0 * sz["windows"] + extra
+        return 16.0 * sz["windows"]                            # code read + filter word read and write
+    if kernel == "cand_count":
+        return 8.0 * sz["windows"] + 4.0 * sz["windows"]       # code read + second-filter word probe
     if kernel == "spgemm_numeric":
         return 8.0 * sz["nnzA"] + 8.0 * sz["products"] + (8.0 + 8.0 * sz["S"]) * sz["nnzC"] + 8.0 * (sz["n"] + 1)
     if kernel == "spgemm_symbolic":
-        return 8.0 * sz["nnzA"] + 4.0 * sz["products"] + 8.0 * (sz["n"] + 1)
+        return 4.0 * sz["nnzA"] + 4.0 * sz["products"] + 8.0 * (sz["n"] + 1)
     if kernel == "tr_minplus_mark":
-        return 9.0 * sz["nnzR"] + 9.0 * sz["tr_products"] + 1.0 * sz["nnzR"] + 8.0 * sz["n"]
+        return (9.0 * sz["nnzR"] + 9.0 * sz["tr_products"] + 1.0 * sz["nnzR"] + 8.0 * sz["n"]) * sz["rounds"]
     return None
+
+
+def family(name: str) -> str:
+    """Kernel family of a launch name: the SpGEMM passes launch one class per table size
+    (spgemm_numeric_t1k, ...), which are one kernel."""
+    return re.sub(r"_t\d+k?$", "", name)
+
+
+def by_family(prof: dict) -> dict:
+    out = {}
+    for k, (c, ms) in prof.items():
+        f = out.setdefault(family(k), [0, 0.0])
+        f[0] += c
+        f[1] += ms
+    return {k: tuple(v) for k, v in out.items()}
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if that summary was taken
+    on the current source of the kernel (else None: the counters are stale)."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        src = open(os.path.join(ROOT, "paper_2010_10055_gb300", "csrc", t["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != t["source_sha256_16"]:
+            return None
+        return float(t["dram_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def main():
@@ -135,6 +169,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = synth.WORKLOADS[args.workload]
+    if args.scale != 1.0:
+        w = w.scaled(args.scale)
+        w.name = f"{w.name}@{args.scale:g}"
     w = synth.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})  # independent replica per rank
     d = synth.make(w)
     n = int(d["offsets"].size - 1)
@@ -176,7 +213,8 @@ def main():
 
     # ---- timed region: K steps, per-step events, L2 flushed in between; only the dominant
     # kernel of the breakdown is bracketed by events (the roofline's launch time)
-    dom_name = max(breakdown.items(), key=lambda kv: kv[1][1])[0] if breakdown else None
+    fam_breakdown = by_family(breakdown)
+    dom_name = max(fam_breakdown.items(), key=lambda kv: kv[1][1])[0] if fam_breakdown else None
     clocks = ClockSampler(local)
     sg.prof_reset()
     sg.prof_select(dom_name)
@@ -207,7 +245,7 @@ def main():
     step_ms = [a0.elapsed_time(a1) for a0, a1 in ev]
     tr_ms = [a0.elapsed_time(a1) for a0, a1 in tr_ev]
     total_ms = sum(step_ms)
-    prof = sg.prof_collect()
+    prof = by_family(sg.prof_collect())
     if world > 1:
         t = torch.tensor([total_ms, float(products), float(sum(tr_ms)), float(R.nnz)], dtype=torch.float64,
                          device="cuda")
@@ -234,14 +272,15 @@ def main():
     ktot = sum(v[1] for v in breakdown.values()) or 1.0
     roof = None
     if dom_name and dom_name in prof:
-        cnt, ms = prof[dom_name]
-        ab = algorithmic_bytes(dom_name, sz)
-        avg_ms = ms / max(cnt, 1)
-        ach = (ab / (avg_ms / 1e3) / 1e9) if ab else None
+        cnt, ms = prof[dom_name]  # over the K timed steps
+        ab = algorithmic_bytes(dom_name, sz)  # per step
+        ms_step = ms / args.steps
+        ach = (ab / (ms_step / 1e3) / 1e9) if ab else None
         roof = {"kernel": dom_name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": (ach / hbm) if ach else None, "traffic": None, "peak_source": peak_src,
-                "launch_ms": avg_ms, "launches_per_step": cnt / args.steps,
-                "share": breakdown[dom_name][1] / ktot}
+                "frac": (ach / hbm) if ach else None, "traffic": measured_traffic(dom_name),
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": (ab * args.steps / cnt) if ab else None,
+                "launch_ms": ms / max(cnt, 1), "launches_per_step": cnt / args.steps,
+                "share": fam_breakdown[dom_name][1] / ktot}
     # per-kernel shares from the untimed, fully event-bracketed step
     kernels = {k: {"launches": c, "ms": ms, "share": ms / ktot}
                for k, (c, ms) in sorted(breakdown.items(), key=lambda kv: -kv[1][1])}
