@@ -200,7 +200,9 @@ def main():
     km, C, S, it = step()
     torch.cuda.synchronize()
     sg.prof_enable(False)
-    breakdown = sg.prof_collect()
+    collected = sg.prof_collect()
+    stages = {k[len("stage/"):]: {"count": c, "ms": ms} for k, (c, ms) in collected.items() if k.startswith("stage/")}
+    breakdown = {k: v for k, v in collected.items() if not k.startswith("stage/")}
     at_rp = km.At.to_numpy()["row_ptr"]
     a = np.diff(at_rp).astype(np.int64)
     products = int((a * a).sum())
@@ -300,7 +302,8 @@ def main():
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "tr_edges_per_s": edges_all * args.steps / (tr_ms_max / 1e3) if tr_ms_max else None,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
-            "e2e": e2e, "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": launches}
+            "e2e": e2e, "roofline": roof, "kernels": kernels, "stages": stages, "clocks": clk,
+            "gpu_launches": launches}
     if not args.no_forms:
         line["batched"] = measure_batched(sg, 512, 200e3)
         line["served"] = measure_served(sg, 400, 200.0)

@@ -46,7 +46,8 @@ typedef enum {
     SG_ERR_CUDA = 3,     /* a CUDA runtime call failed; sg_last_error() has the CUDA message */
     SG_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
     SG_ERR_BUDGET = 5,   /* a job does not fit the memory budget it was given */
-    SG_ERR_OVERFLOW = 6  /* an intermediate exceeded a documented limit (e.g. nnz >= 2^31 per row) */
+    SG_ERR_OVERFLOW = 6, /* an intermediate exceeded a documented limit (e.g. nnz >= 2^31 per row) */
+    SG_ERR_CANCELLED = 7 /* a served job was cancelled before it ran (sg_server_cancel) */
 } sg_status;
 
 /* Sparse matrix in CSR with a 32-bit payload: A (n x m) and At (m x n).
@@ -176,6 +177,19 @@ sg_status sg_minplus_square_noalloc(const sg_graph_csr *R, int32_t mode, uint32_
 sg_status sg_transitive_reduce(const sg_graph_csr *R, uint32_t fuzz, int32_t mode, sg_graph_csr *S,
                                int32_t *iterations, sg_stream_t stream);
 
+/*
+ * Checkpoint / resume of Algorithm 1. The loop's whole state is the current R, so the reduction
+ * can stop after at most max_rounds (>= 1) rounds and be resumed later by passing the returned
+ * S as R: the final graph is the same as sg_transitive_reduce's, and the rounds of the pieces add
+ * up to its iteration count.
+ *   *rounds     rounds run by this call.
+ *   *converged  1 if the last of them removed nothing (S is final), else 0 (S is an
+ *               intermediate R).
+ * Errors as sg_transitive_reduce; max_rounds < 1 is SG_ERR_INVALID.
+ */
+sg_status sg_transitive_reduce_rounds(const sg_graph_csr *R, uint32_t fuzz, int32_t mode, int32_t max_rounds,
+                                      sg_graph_csr *S, int32_t *rounds, int32_t *converged, sg_stream_t stream);
+
 /* ---------------------------------------------------------------------------------------
  * Batched form: many independent read sets in one pass. The sets are laid end to end as one
  * block-diagonal problem (set b's reads are rows read_off[b] .. read_off[b+1] of A, C and S; its
@@ -275,6 +289,10 @@ sg_status sg_server_poll(sg_server *srv, uint64_t ticket, sg_job_result *out);
 /* As poll, waiting up to timeout_s seconds. */
 sg_status sg_server_wait(sg_server *srv, uint64_t ticket, double timeout_s, sg_job_result *out);
 void sg_job_result_free(sg_job_result *r);
+/* Cancels a job that is still queued: it never runs, its budget share is never taken, and its
+ * result (poll / wait) has status SG_ERR_CANCELLED. SG_ERR_INVALID if the ticket is unknown or the
+ * job has already been admitted to a batch (it then completes normally). */
+sg_status sg_server_cancel(sg_server *srv, uint64_t ticket);
 /* Stops the workers after their current batches; queued jobs are dropped. */
 void sg_server_destroy(sg_server *srv);
 
@@ -343,6 +361,13 @@ void sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx);
 
 /* Test hook: make the n-th device allocation from now fail (n >= 1); 0 disables. */
 void sg_debug_fail_alloc_after(int64_t n);
+
+/* Test hook for the bounded waits between thread blocks. While on, every scan of more than one
+ * tile has its first tile withhold its prefix: the waits of the later tiles give up after their
+ * poll limit (well under a second each), set the call's device error word, and the call returns
+ * SG_ERR_TIMEOUT with its outputs freed. Nothing hangs and the context stays usable. Off by
+ * default; affects all threads. */
+void sg_debug_stall_lookback(int on);
 
 /* Checked builds (compiled with -DSG_CHECKED): the first out-of-bounds index any kernel detected
  * and skipped since the last call, as site << 40 | index, or 0. Always 0 in normal builds. */

@@ -18,16 +18,18 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgraph.so")
 LIB_PATH_CHECKED = os.path.join(_HERE, "libsgraph_checked.so")
 
-SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_TIMEOUT, SG_ERR_BUDGET, SG_ERR_OVERFLOW = range(7)
+(SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_TIMEOUT, SG_ERR_BUDGET, SG_ERR_OVERFLOW,
+ SG_ERR_CANCELLED) = range(8)
 DIRMATCH, LITERAL = 0, 1
 INF = 0xFFFFFFFF
 
 EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",
+           "sg_transitive_reduce_rounds",
            "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy", "sg_run_batch", "sg_free_batch",
            "sg_server_create", "sg_server_submit", "sg_server_poll", "sg_server_wait", "sg_job_result_free",
-           "sg_server_destroy",
+           "sg_server_destroy", "sg_server_cancel",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
-           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_check", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_stall_lookback", "sg_debug_check", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
 
 
@@ -148,12 +150,18 @@ def lib():
         L.sg_transitive_reduce.restype = ctypes.c_int
         L.sg_transitive_reduce.argtypes = [ctypes.POINTER(GraphCsr), u32, i32, ctypes.POINTER(GraphCsr),
                                            ctypes.POINTER(i32), vp]
+        L.sg_transitive_reduce_rounds.restype = ctypes.c_int
+        L.sg_transitive_reduce_rounds.argtypes = [ctypes.POINTER(GraphCsr), u32, i32, i32, ctypes.POINTER(GraphCsr),
+                                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), vp]
+        L.sg_server_cancel.restype = ctypes.c_int
+        L.sg_server_cancel.argtypes = [vp, ctypes.c_uint64]
         L.sg_free_csr_u32.argtypes = [ctypes.POINTER(CsrU32), vp]
         L.sg_free_overlap.argtypes = [ctypes.POINTER(OverlapCsr), vp]
         L.sg_free_graph.argtypes = [ctypes.POINTER(GraphCsr), vp]
         L.sg_free.argtypes = [vp, vp]
         L.sg_last_error.restype = ctypes.c_char_p
         L.sg_debug_fail_alloc_after.argtypes = [i64]
+        L.sg_debug_stall_lookback.argtypes = [ctypes.c_int]
         L.sg_launch_count.restype = ctypes.c_uint64
         L.sg_debug_check.restype = ctypes.c_uint64
         L.sg_prof_enable.argtypes = [ctypes.c_int]
@@ -418,6 +426,18 @@ def transitive_reduce(R, fuzz: int = 0, mode: int = DIRMATCH, stream=None):
     return Graph(S, st), int(it.value)
 
 
+def transitive_reduce_rounds(R, fuzz: int = 0, max_rounds: int = 1, mode: int = DIRMATCH, stream=None):
+    """Algorithm 1 for at most max_rounds rounds: returns (S as Graph, rounds, converged). Pass S
+    back as R to resume."""
+    L = lib()
+    st = _stream(stream)
+    S, it, conv = GraphCsr(), ctypes.c_int32(), ctypes.c_int32()
+    _check(L.sg_transitive_reduce_rounds(ctypes.byref(_graph_struct(R)), int(fuzz), int(mode), int(max_rounds),
+                                         ctypes.byref(S), ctypes.byref(it), ctypes.byref(conv), st),
+           "transitive_reduce_rounds")
+    return Graph(S, st), int(it.value), bool(conv.value)
+
+
 def minplus_square(R, mode: int = DIRMATCH, stream=None):
     """N = R^2 over Algorithm 3's semiring on the pattern of R: (N, Ndir) CUDA tensors; N holds
     uint32 bit patterns in an int32 tensor (0xFFFFFFFF = no qualifying walk)."""
@@ -482,6 +502,12 @@ def debug_check():
     since the last call, or None."""
     v = int(lib().sg_debug_check())
     return None if v == 0 else (v >> 40, v & ((1 << 40) - 1))
+
+
+def debug_stall_lookback(on: bool):
+    """Test hook: multi-tile scans withhold their first tile's prefix, so calls fail with
+    SG_ERR_TIMEOUT after their bounded waits run out (see sg_debug_stall_lookback)."""
+    lib().sg_debug_stall_lookback(1 if on else 0)
 
 
 def debug_fail_alloc_after(n: int):
@@ -694,6 +720,10 @@ class Server:
         r = JobResult()
         _check(lib().sg_server_wait(self.h, int(ticket), float(timeout), ctypes.byref(r)), "server_wait")
         return self._convert(r)
+
+    def cancel(self, ticket: int) -> bool:
+        """Cancels a job still in the queue (True); False if it already started, finished or is unknown."""
+        return lib().sg_server_cancel(self.h, ctypes.c_uint64(int(ticket))) == SG_OK
 
     def close(self):
         if self.h and _lib is not None:

@@ -29,6 +29,18 @@ struct LaunchScope {
     ~LaunchScope();
 };
 
+// A stage of the method (the paper's stage names: CountKmer, CreateSpMat, SpGEMMSymbolic,
+// SpGEMMNumeric, TrReduction, TrRound): an NVTX range on the host, and while profiling is on, a
+// pair of events on `s` reported by sg_prof_collect as "stage/<name>".
+struct StageScope {
+    cudaStream_t stream;
+    int slot;
+    StageScope(const char *name, cudaStream_t s);
+    ~StageScope();
+    StageScope(const StageScope &) = delete;
+    StageScope &operator=(const StageScope &) = delete;
+};
+
 // Scoped set of temporary device buffers, released (stream-ordered) in reverse order on scope
 // exit. Not copyable: a copy would free the same buffers twice.
 struct Scratch {
@@ -48,6 +60,9 @@ struct Scratch {
 // Records that a bounded wait between thread blocks gave up during `what` and returns
 // SG_ERR_TIMEOUT.
 sg_status timeout_error(const char *what);
+
+// Test hook (sg_debug_stall_lookback): nonzero makes multi-tile scans withhold tile 0's prefix.
+int debug_stall_lookback();
 
 // Current value of a tunable parameter (see sg_tune_set).
 int64_t tune(const char *name);

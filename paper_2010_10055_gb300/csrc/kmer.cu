@@ -23,6 +23,7 @@
 //     reliable code; within a reliable segment the first entry of each read is its lowest
 //     position: those entries are At's row, already sorted by read.
 //  6. A = At transposed by a stable radix sort on the read id (columns stay ascending).
+#include <optional>
 #include <type_traits>
 
 #include "check.cuh"
@@ -540,6 +541,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_CUDA_TRY(cudaMemsetAsync(b1.words, 0, (size_t)b1.nwords * 4, s));
         SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, (size_t)b2.nwords * 4, s));
     }
+    std::optional<StageScope> stage;
+    stage.emplace("CountKmer", s);  // a1-a4: codes, Bloom, exact count, columns
     // 0. window codes
     uint64_t *wc = sc.get<uint64_t>(total + 1);
     if (!wc) return SG_ERR_OOM;
@@ -651,6 +654,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     At->n_rows = m; At->n_cols = n; At->nnz = nnz;
     A->n_rows = n; A->n_cols = m; A->nnz = nnz;
 
+    stage.emplace("CreateSpMat", s);  // a5: At, then A by a sort on the read
     uint32_t *ak0 = sc.get<uint32_t>(nnz), *ak1 = sc.get<uint32_t>(nnz);
     uint64_t *av0 = sc.get<uint64_t>(nnz), *av1 = sc.get<uint64_t>(nnz);
     if (!ak0 || !ak1 || !av0 || !av1) return SG_ERR_OOM;

@@ -25,7 +25,10 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
 
 // Transitive reduction (tr.cu). With job_ro (device, njobs + 1 read offsets), job_last (device,
 // njobs, zeroed) receives for each job the last round that removed one of its entries.
+// max_rounds > 0 stops after that many rounds (*converged, if given, says whether the last round
+// removed nothing); 0 runs to the fixpoint.
 sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *S, int32_t *iters,
-                  cudaStream_t s, const int64_t *job_ro, int64_t njobs, int32_t *job_last);
+                  cudaStream_t s, const int64_t *job_ro, int64_t njobs, int32_t *job_last, int32_t max_rounds = 0,
+                  int32_t *converged = nullptr);
 
 }  // namespace sg

@@ -13,7 +13,7 @@ namespace sg {
 // already started and never waits on a later one. Each wait is bounded: after LB_SPIN_LIMIT polls
 // the waiter records DEV_TIMEOUT in *err (read back by the caller) and goes on with a zero.
 constexpr unsigned long long LB_A = 1ull << 62, LB_P = 2ull << 62, LB_VAL = (1ull << 62) - 1;
-constexpr int LB_SPIN_LIMIT = 1 << 22;
+constexpr int LB_SPIN_LIMIT = 1 << 20;  // at least 64 ms of polling; a real wait takes microseconds
 
 __device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long long v) {
     *reinterpret_cast<volatile unsigned long long *>(p) = v;
@@ -39,10 +39,12 @@ constexpr int SCAN_NT = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_ITEMS;
 
+// stall != 0 (test hook, sg_debug_stall_lookback): tile 0 withholds its prefix, so the waits of
+// the tiles after it run out.
 template <class T>
 __global__ void __launch_bounds__(SCAN_NT) scan_kernel(const T *in, int64_t n, int64_t *out,
                                                       unsigned long long *status, unsigned int *tile_ctr,
-                                                      uint32_t *err) {
+                                                      uint32_t *err, int stall) {
     __shared__ int64_t vals[SCAN_TILE + SCAN_TILE / 32];
     __shared__ int64_t tmp[SCAN_NT / 32 + 1];
     __shared__ int64_t s_excl;
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(SCAN_NT) scan_kernel(const T *in, int64_t n, i
             }
         }
         if (lane == 0) {
-            if (status) lb_store(status + tile, LB_P | (unsigned long long)(excl + total));
+            if (status && !(stall && tile == 0)) lb_store(status + tile, LB_P | (unsigned long long)(excl + total));
             s_excl = excl;
         }
     }
@@ -111,14 +113,15 @@ sg_status exclusive_scan(const T *in, int64_t *out, int64_t n, cudaStream_t s, u
     const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nt == 1) {
         SG_LAUNCH("scan", scan_kernel<T>, 1, SCAN_NT, 0, s, in, n, out, (unsigned long long *)nullptr,
-                  (unsigned int *)nullptr, err);
+                  (unsigned int *)nullptr, err, 0);
         return SG_OK;
     }
     Scratch sc(s);
     unsigned long long *status = sc.get<unsigned long long>(nt + 1);  // [nt] status, then the tile counter
     if (!status) return SG_ERR_OOM;
     SG_CUDA_TRY(cudaMemsetAsync(status, 0, (size_t)(nt + 1) * sizeof(unsigned long long), s));
-    SG_LAUNCH("scan", scan_kernel<T>, nt, SCAN_NT, 0, s, in, n, out, status, (unsigned int *)(status + nt), err);
+    SG_LAUNCH("scan", scan_kernel<T>, nt, SCAN_NT, 0, s, in, n, out, status, (unsigned int *)(status + nt), err,
+              debug_stall_lookback());
     return SG_OK;
 }
 

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "check.cuh"
 
@@ -27,6 +29,9 @@ sg_status timeout_error(const char *what) {
     set_error("%s: a bounded wait between thread blocks gave up (internal error); results discarded", what);
     return SG_ERR_TIMEOUT;
 }
+
+static std::atomic<int> g_debug_stall{0};
+int debug_stall_lookback() { return g_debug_stall.load(); }
 
 static sg_alloc_fn g_alloc = nullptr;
 static sg_free_fn g_free = nullptr;
@@ -171,8 +176,29 @@ LaunchScope::LaunchScope(const char *n, cudaStream_t s) : name(n), stream(s), sl
 LaunchScope::~LaunchScope() {
     if (slot >= 0) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
-        cudaEventRecord(g_pending[slot].b, stream);
+        if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].b, stream);  // unless reset meanwhile
     }
+}
+
+StageScope::StageScope(const char *name, cudaStream_t s) : stream(s), slot(-1) {
+    nvtxRangePushA(name);
+    if (g_prof_on.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        const std::string full = std::string("stage/") + name;
+        if (!g_prof_prefix.empty() && full.compare(0, g_prof_prefix.size(), g_prof_prefix) != 0) return;
+        PendingEvent pe{full, take_event(), take_event()};
+        cudaEventRecord(pe.a, s);
+        g_pending.push_back(pe);
+        slot = (int)g_pending.size() - 1;
+    }
+}
+
+StageScope::~StageScope() {
+    if (slot >= 0) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].b, stream);  // unless reset meanwhile
+    }
+    nvtxRangePop();
 }
 
 // ------------------------------------------------------------------------- tunables
@@ -227,6 +253,8 @@ void sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx) {
 }
 
 void sg_debug_fail_alloc_after(int64_t n) { sg::g_fail_after.store(n > 0 ? n : 0); }
+
+void sg_debug_stall_lookback(int on) { sg::g_debug_stall.store(on ? 1 : 0); }
 
 void sg_free(void *d_ptr, sg_stream_t stream) { sg::dfree(d_ptr, (cudaStream_t)stream); }
 

@@ -301,6 +301,35 @@ extern "C" sg_status sg_server_submit(sg_server *srv, const sg_job *job, uint64_
     return SG_OK;
 }
 
+extern "C" sg_status sg_server_cancel(sg_server *srv, uint64_t ticket) {
+    if (!srv) {
+        sg::set_error("server_cancel: NULL server");
+        return SG_ERR_INVALID;
+    }
+    Job *j = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (auto it = srv->pending.begin(); it != srv->pending.end(); ++it)
+            if ((*it)->ticket == ticket) {
+                j = *it;
+                srv->pending.erase(it);
+                break;
+            }
+        if (j) {
+            Done *d = new Done();
+            sg::fill_error(&d->r, SG_ERR_CANCELLED, j->t_submit, "cancelled before it ran");
+            srv->done[ticket] = d;
+        }
+    }
+    if (!j) {
+        sg::set_error("server_cancel: job %llu is not queued (unknown, running or done)", (unsigned long long)ticket);
+        return SG_ERR_INVALID;
+    }
+    delete j;
+    srv->cv_done.notify_all();
+    return SG_OK;
+}
+
 static sg_status take_done(sg_server *srv, uint64_t ticket, sg_job_result *out) {
     auto it = srv->done.find(ticket);
     if (it == srv->done.end()) return SG_ERR_TIMEOUT;

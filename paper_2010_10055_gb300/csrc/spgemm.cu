@@ -23,6 +23,7 @@
 // scans their At row lengths in registers, and walks the flattened product list 32 at a time,
 // each lane finding its entry with a 5-step shuffle search.
 #include <mutex>
+#include <optional>
 
 #include "check.cuh"
 #include "ops.cuh"
@@ -443,6 +444,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     if (!a_beg || !a_len || !t_pair) return SG_ERR_OOM;
     SpArgs g{A->row_ptr, A->col, A->val, At->row_ptr, At->col, At->val, a_beg, a_len, t_pair,
              n, min_shared, S, err};
+    std::optional<StageScope> stage;
+    stage.emplace("SpGEMMSymbolic", s);
     SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr, n,
               work, a_beg, a_len);
     SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
@@ -483,6 +486,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     }
 
     // ---- C row pointers; numeric classes from the exact distinct counts
+    stage.emplace("SpGEMMNumeric", s);
     SG_ALLOC(C->row_ptr, int64_t, n + 1, s);
     SG_TRY(exclusive_scan<int64_t>(nnz_row, C->row_ptr, n, s, err));
     // numeric: one class per table size from 2^6 while the table and its sort buffer fit in 160 KB

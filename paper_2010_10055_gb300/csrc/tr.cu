@@ -291,8 +291,10 @@ __global__ void job_changes_kernel(const int64_t *__restrict__ rp, const int64_t
 }
 
 sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *S, int32_t *iters,
-                  cudaStream_t s, const int64_t *job_ro, int64_t njobs, int32_t *job_last) {
+                  cudaStream_t s, const int64_t *job_ro, int64_t njobs, int32_t *job_last, int32_t max_rounds,
+                  int32_t *converged) {
     const int64_t n = R->n, nnz0 = R->nnz;
+    StageScope stage("TrReduction", s);
     Scratch sc(s);
     uint32_t *err = sc.get<uint32_t>(1);
     uint8_t *keep = sc.get<uint8_t>(nnz0 + 1);
@@ -318,8 +320,11 @@ sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *
     int64_t cur_nnz = nnz0;
     int cur = -1;  // -1: the current graph is still the caller's R
     int32_t it = 0;
+    bool done = false;
     for (;;) {
+        if (max_rounds > 0 && it == max_rounds) break;  // stopped early: S is an intermediate R
         it++;
+        StageScope round("TrRound", s);
         const int nxt = cur == 0 ? 1 : 0;
         SG_TRY(minplus_round(g, cur_nnz, mode, fuzz, keep, kept, nullptr, nullptr, wk, err, s));
         if (job_ro)
@@ -335,7 +340,10 @@ sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *
             set_error("graph does not satisfy the CSR contract (sorted unique columns, no diagonal, suffix < 2^30, dir <= 3)");
             return SG_ERR_INVALID;
         }
-        if (nnz2 == cur_nnz) break;  // nothing removed: R is final
+        if (nnz2 == cur_nnz) {  // nothing removed: R is final
+            done = true;
+            break;
+        }
         SG_LAUNCH("tr_compact", tr_compact_kernel, blocks_for(n * 32, 256), 256, 0, s, g, keep, rp[nxt], col[nxt],
                   suf[nxt], dir[nxt]);
         cur = nxt;
@@ -367,6 +375,7 @@ sg_status tr_impl(const sg_graph_csr *R, uint32_t fuzz, int mode, sg_graph_csr *
     }
     *S = out;
     *iters = it;
+    if (converged) *converged = done ? 1 : 0;
     return SG_OK;
 }
 
@@ -389,7 +398,26 @@ extern "C" sg_status sg_transitive_reduce(const sg_graph_csr *R, uint32_t fuzz, 
         sg::set_error("transitive_reduce: invalid arguments");
         return SG_ERR_INVALID;
     }
-    return sg::tr_impl(R, fuzz, mode, S, iterations, (cudaStream_t)stream, nullptr, 0, nullptr);
+    return sg::tr_impl(R, fuzz, mode, S, iterations, (cudaStream_t)stream, nullptr, 0, nullptr, 0, nullptr);
+}
+
+extern "C" sg_status sg_transitive_reduce_rounds(const sg_graph_csr *R, uint32_t fuzz, int32_t mode,
+                                                 int32_t max_rounds, sg_graph_csr *S, int32_t *rounds,
+                                                 int32_t *converged, sg_stream_t stream) {
+    if (!S || !rounds || !converged) {
+        sg::set_error("transitive_reduce_rounds: NULL output");
+        return SG_ERR_INVALID;
+    }
+    *S = sg_graph_csr{};
+    *rounds = 0;
+    *converged = 0;
+    if (!sg::graph_args_ok(R) || fuzz >= (1u << 30) || (mode != SG_TR_DIRMATCH && mode != SG_TR_LITERAL) ||
+        max_rounds < 1) {
+        sg::set_error("transitive_reduce_rounds: invalid arguments");
+        return SG_ERR_INVALID;
+    }
+    return sg::tr_impl(R, fuzz, mode, S, rounds, (cudaStream_t)stream, nullptr, 0, nullptr, max_rounds,
+                       converged);
 }
 
 extern "C" sg_status sg_minplus_square(const sg_graph_csr *R, int32_t mode, uint32_t *d_N, uint8_t *d_Ndir,

@@ -159,6 +159,26 @@ def test_tr_tiny_workload_and_layouts():
     _tr_check(R, 30, 1)
 
 
+@pytest.mark.parametrize("graph,fuzz,mode", [("tiny", 0, 0), ("random", 500, 1), ("random", 100, 0)])
+def test_tr_checkpoint_resume(graph, fuzz, mode):
+    """Algorithm 1's loop state is R itself: stopping after r rounds and resuming from the
+    intermediate graph gives the oracle's S, and the rounds of the pieces add up."""
+    R = synth.make(synth.TINY)["R"] if graph == "tiny" else synth.random_graph(2000, 12.0, hub_frac=0.05,
+                                                                                   max_suffix=2000, seed=9)
+    eS, eit = oracle.transitive_reduce(R, fuzz, mode)
+    assert eit >= 2
+    for r in range(1, eit + 1):
+        S1, r1, conv = sg.transitive_reduce_rounds(sg.DeviceGraph.from_numpy(R), fuzz, r, mode)
+        assert r1 == min(r, eit)
+        if conv:
+            assert r1 == eit
+            assert_graph_equal(S1.to_numpy(), eS)
+            continue
+        S2, it2 = sg.transitive_reduce(S1, fuzz, mode)
+        assert_graph_equal(S2.to_numpy(), eS)
+        assert r1 + it2 == eit
+
+
 def test_tr_edge_cases():
     empty = dict(n=0, row_ptr=np.zeros(1, np.int64), col=np.zeros(0, np.int32), suffix=np.zeros(0, np.uint32),
                  dir=np.zeros(0, np.uint8))

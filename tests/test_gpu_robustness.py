@@ -1,0 +1,75 @@
+"""Failure detection and order independence on the GPU, without faulting it.
+
+- Bounded waits: the scan's tiles wait on earlier tiles' published prefixes. With the test hook
+  on, the first tile withholds its prefix (a flag nothing sets); the later tiles' waits run out,
+  the call returns SG_ERR_TIMEOUT, and the context stays usable.
+- Launch parameters (tunables) change grids, slice counts, table sizes and which rows take the
+  global-memory path, never the results: every accumulation is commutative (the seeds keep the
+  smallest column indices, counts are sums, the min-plus is a min), so each configuration must
+  reproduce the oracle bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2010_10055_gb300 as sg
+import synth
+from tests.gpu_util import assert_graph_equal, assert_kmer_equal, assert_overlap_equal, dev, gpu_kmer
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_runs_out_and_reports_timeout():
+    R = synth.random_graph(6000, 8.0, hub_frac=0.02, max_suffix=2000, seed=11)  # kept[] scan: 2 tiles
+    D = sg.DeviceGraph.from_numpy(R)
+    sg.debug_stall_lookback(True)
+    try:
+        with pytest.raises(sg.SgError) as e:
+            sg.transitive_reduce(D, fuzz=100)
+        assert e.value.status == sg.SG_ERR_TIMEOUT
+        assert "bounded wait" in str(e.value)
+    finally:
+        sg.debug_stall_lookback(False)
+    # the same call now completes and is exact
+    S, it = sg.transitive_reduce(D, fuzz=100)
+    eS, eit = oracle.transitive_reduce(R, 100)
+    assert_graph_equal(S.to_numpy(), eS)
+    assert it == eit
+
+
+CONFIGS = [
+    {},
+    {"bloom_bits": 4, "bloom_slice_mb": 1},                          # many small Bloom slices
+    {"bloom_bits": 12, "bloom_unroll": 8},
+    {"sym_guess_shift": 8},                                          # tiny guessed tables: overflow path
+    {"sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
+]
+
+
+@pytest.fixture(scope="module")
+def medium():
+    w = synth.BACTERIAL.scaled(0.02)  # 100 kbp genome, two repeat families
+    d = synth.make(w)
+    km = oracle.build_kmer_matrix(d["seq"], d["offsets"], w.k, w.lo, w.hi)
+    C = oracle.overlap_spgemm(km["A"], km["At"], w.min_shared, w.max_seeds)
+    S, it = oracle.transitive_reduce(d["R"], w.fuzz)
+    return w, d, km, C, S, it
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()) or "defaults")
+def test_tunables_never_change_results(medium, cfg):
+    w, d, ekm, eC, eS, eit = medium
+    saved = sg.tunables()
+    try:
+        for k, v in cfg.items():
+            sg.tune(k, v)
+        km, got = gpu_kmer(d["seq"], d["offsets"], w.k, w.lo, w.hi)
+        assert_kmer_equal(got, ekm)
+        C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+        assert_overlap_equal(C.to_numpy(), eC)
+        S, it = sg.transitive_reduce(sg.DeviceGraph.from_numpy(d["R"]), w.fuzz)
+        assert_graph_equal(S.to_numpy(), eS)
+        assert it == eit
+    finally:
+        for k, v in saved.items():
+            sg.tune(k, v)

@@ -94,3 +94,27 @@ def test_server_batches_jobs_that_queue_up():
             assert r["t_submit"] <= r["t_start"] <= r["t_done"]
     finally:
         srv.close()
+
+
+def test_server_cancel_queued_job():
+    """A queued job can be cancelled: it never runs and reports SG_ERR_CANCELLED; the others are
+    unaffected; running, finished and unknown tickets cannot be cancelled."""
+    big = synth.genome(1_500_000, 31)
+    rd = synth.reads(big, 30.0, 10000.0, 4000.0, 500, 0.075, 0.05, 0.025, 32)
+    jobs = _jobs(8, 3)
+    srv = sg.Server(hbm_budget=8 << 30, max_batch=1, workers=1, fuzz=300)
+    try:
+        t0 = srv.submit(rd["seq"], rd["offsets"], 2, 20)  # keeps the single worker busy
+        ts = [srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"]) for j in jobs]
+        assert srv.cancel(ts[1])
+        assert not srv.cancel(ts[1])  # already cancelled
+        assert not srv.cancel(987654321)
+        r0 = srv.wait(t0)
+        assert r0["status"] == sg.SG_OK
+        assert not srv.cancel(t0)  # finished
+        res = [srv.wait(t) for t in ts]
+        assert res[1]["status"] == sg.SG_ERR_CANCELLED and "cancel" in res[1]["error"]
+        _check(res[0], jobs[0], 300)
+        _check(res[2], jobs[2], 300)
+    finally:
+        srv.close()
