@@ -69,7 +69,7 @@ static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg
     std::vector<int64_t> ro(nitems + 1, 0), co(nitems + 1, 0);
     std::vector<uint32_t> lohi(2 * (size_t)nitems);
     int64_t N = 0, T = 0, RN = 0;
-    uint32_t min_lo = 0xFFFFFFFFu;
+    uint32_t min_lo = 0xFFFFFFFFu, max_hi = 0;
     bool any_r = false;
     for (int b = 0; b < nitems; b++) {
         const sg_batch_item &x = items[b];
@@ -88,6 +88,7 @@ static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg
                         x.R ? x.R->dir : nullptr, x.R ? x.R->nnz : 0, RN};
         lohi[2 * b] = x.lo;
         min_lo = x.lo < min_lo ? x.lo : min_lo;
+        max_hi = x.hi > max_hi ? x.hi : max_hi;
         lohi[2 * b + 1] = x.hi;
         any_r |= x.R != nullptr;
         N += x.n_reads;
@@ -141,7 +142,7 @@ static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg
         Scratch sc1(s);
         // the scalar range only decides whether the Bloom pass may drop singletons: every set needs lo >= 2
     SG_TRY(build_impl(seq, off, N, T, p->k, min_lo, min_lo, &out->A, &out->At, &out->d_kmer_codes, s, sc1,
-                          JobMap{d_ro, nitems, 2 * p->k}, d_lohi, d_ncols));
+                          JobMap{d_ro, nitems, 2 * p->k}, d_lohi, d_ncols, max_hi));
     }
     {
         Scratch sc2(s);

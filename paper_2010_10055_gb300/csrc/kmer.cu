@@ -477,6 +477,77 @@ __global__ void emit_at_kernel(const uint32_t *__restrict__ head, const int64_t 
     }
 }
 
+// Fused segment pass (used when every reliable range has hi <= SEG_WALK_MAX): each position walks
+// its run of equal keys at most hmax + 1 steps each way. A run that is still equal after that is
+// longer than any hi, hence unreliable; otherwise the walks give its exact length. Output per
+// position: headrel (it heads a reliable segment) | keep (it lies in a reliable segment and is the
+// first entry of its read there) << 31, so that one scan yields both the column ids and the
+// positions in At.
+constexpr int SEG_WALK_MAX = 64;
+constexpr int PK_SHIFT = 31;
+
+__global__ void seg_flags_kernel(const uint64_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t nc,
+                                 uint32_t lo, uint32_t hi, const uint32_t *__restrict__ lohi, int kbits, int hmax,
+                                 uint64_t *__restrict__ packed) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const uint64_t k = key[i];
+    int64_t h = i, e = i + 1;
+    int back = 0, fwd = 0;
+    while (back <= hmax && h > 0 && key[h - 1] == k) {
+        h--;
+        back++;
+    }
+    while (fwd <= hmax && e < nc && key[e] == k) {
+        e++;
+        fwd++;
+    }
+    if (lohi) {
+        const uint64_t job = k >> kbits;
+        lo = lohi[2 * job];
+        hi = lohi[2 * job + 1];
+    }
+    const int64_t len = e - h;
+    const bool rel = back <= hmax && fwd <= hmax && len >= (int64_t)lo && len <= (int64_t)hi;
+    const bool head = h == i;
+    const bool first = head || (val[i] >> 32) != (val[i - 1] >> 32);
+    packed[i] = (uint64_t)(rel && head) | ((uint64_t)(rel && first) << PK_SHIFT);
+}
+
+// Writes At's entries, its row pointers, the column codes and the (read, col|val) pairs sorted
+// into A, from the fused flags and their exclusive scan (low 31 bits: reliable segments before,
+// high bits: kept entries before).
+__global__ void emit_fused_kernel(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ pre,
+                                  const uint64_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t nc,
+                                  int64_t m, int64_t nnz, int32_t *__restrict__ at_col, uint32_t *__restrict__ at_val,
+                                  int64_t *__restrict__ at_rp, uint64_t *__restrict__ codes,
+                                  uint32_t *__restrict__ a_key, uint64_t *__restrict__ a_val, int kbits,
+                                  unsigned long long *__restrict__ job_ncols) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) at_rp[m] = nnz;
+    if (i >= nc) return;
+    const uint64_t f = packed[i];
+    if (f == 0) return;
+    const uint64_t x = pre[i];
+    const uint64_t lowmask = (1ull << PK_SHIFT) - 1;
+    const int64_t before = (int64_t)(x & lowmask), o = (int64_t)(x >> PK_SHIFT);
+    const int64_t col = before + (int64_t)(f & 1) - 1;  // the segment's column (its head counted)
+    if (!SG_IN_BOUNDS(col >= 0 && col < m, 108, col)) return;
+    if (f & 1) {
+        at_rp[col] = o;
+        codes[col] = kbits < 64 ? key[i] & ((1ull << kbits) - 1) : key[i];
+        if (job_ncols) atomicAdd(job_ncols + (key[i] >> kbits), 1ull);
+    }
+    if (f >> PK_SHIFT) {
+        if (!SG_IN_BOUNDS(o >= 0 && o < nnz, 109, o)) return;
+        const uint32_t r = (uint32_t)(val[i] >> 32), v = (uint32_t)val[i];
+        at_col[o] = (int32_t)r;
+        at_val[o] = v;
+        a_key[o] = r;
+        a_val[o] = ((uint64_t)col << 32) | v;
+    }
+}
+
 // Row pointers of A from the read ids of its entries, sorted ascending.
 __global__ void rowptr_from_sorted_kernel(const uint32_t *__restrict__ rows, int64_t nnz, int64_t n,
                                           int64_t *__restrict__ rp) {
@@ -516,7 +587,7 @@ static sg_status dispatch_k(int k, F &&f) {
 sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t total, int k,
                      uint32_t lo, uint32_t hi, sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **codes_out,
                      cudaStream_t s, Scratch &sc, JobMap jm, const uint32_t *lohi,
-                     unsigned long long *job_ncols) {
+                     unsigned long long *job_ncols, uint32_t hmax) {
     const int NT = 256;
     uint32_t *err = sc.get<uint32_t>(1);
     if (!err) return SG_ERR_OOM;
@@ -613,29 +684,49 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_LAUNCH("resolve", resolve_kernel, blocks_for(nc, NT), NT, 0, s, val, nc, off, n);
     }
 
-    uint32_t *head = sc.get<uint32_t>(nc + 1);
-    int64_t *seg_excl = sc.get<int64_t>(nc + 1);
-    int64_t *seg_start = sc.get<int64_t>(nc + 1);
-    uint32_t *rel = sc.get<uint32_t>(nc + 1);
-    int64_t *col_of_seg = sc.get<int64_t>(nc + 1);
-    uint32_t *keep = sc.get<uint32_t>(nc + 1);
-    int64_t *out_pos = sc.get<int64_t>(nc + 1);
-    if (!head || !seg_excl || !seg_start || !rel || !col_of_seg || !keep || !out_pos) return SG_ERR_OOM;
-    SG_LAUNCH("seg_head", seg_head_kernel, blocks_for(nc, NT), NT, 0, s, key, nc, head);
-    SG_TRY(exclusive_scan<uint32_t>(head, seg_excl, nc, s, err));
-    SG_LAUNCH("seg_start", seg_start_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, nc, seg_start);
-    // number of segments lives on the device at seg_excl[nc]; launch over the upper bound nc
-    SG_LAUNCH("seg_reliable", seg_reliable_kernel, blocks_for(nc, NT), NT, 0, s, seg_start, seg_excl + nc, lo,
-              hi, key, lohi, 2 * k, nc, rel);
-    SG_TRY(exclusive_scan<uint32_t>(rel, col_of_seg, nc, s, err));
-    SG_LAUNCH("keep", keep_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, rel, val, nc, keep);
-    SG_TRY(exclusive_scan<uint32_t>(keep, out_pos, nc, s, err));
+    // segments -> exact frequency -> reliable -> columns; kept entries -> At
+    const bool fused = hmax <= (uint32_t)SEG_WALK_MAX && nc < ((int64_t)1 << PK_SHIFT);
+    uint32_t *head = nullptr, *rel = nullptr, *keep = nullptr;
+    int64_t *seg_excl = nullptr, *seg_start = nullptr, *col_of_seg = nullptr, *out_pos = nullptr;
+    uint64_t *flags = nullptr, *pre = nullptr;
     int64_t sizes[2] = {0, 0};  // m, nnz
-    // m = reliable segments = col_of_seg[nc] (rel is 0 past the last segment)
-    SG_CUDA_TRY(cudaMemcpyAsync(&sizes[0], col_of_seg + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(cudaMemcpyAsync(&sizes[1], out_pos + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (fused) {
+        flags = sc.get<uint64_t>(nc + 1);
+        pre = sc.get<uint64_t>(nc + 1);
+        if (!flags || !pre) return SG_ERR_OOM;
+        SG_LAUNCH("seg_flags", seg_flags_kernel, blocks_for(nc, NT), NT, 0, s, key, (const uint64_t *)val, nc, lo, hi,
+                  lohi, 2 * k, (int)hmax, flags);
+        SG_TRY(exclusive_scan<int64_t>((const int64_t *)flags, (int64_t *)pre, nc, s, err));
+        uint64_t tot = 0;
+        SG_CUDA_TRY(cudaMemcpyAsync(&tot, pre + nc, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaStreamSynchronize(s));
+        sizes[0] = (int64_t)(tot & ((1ull << PK_SHIFT) - 1));
+        sizes[1] = (int64_t)(tot >> PK_SHIFT);
+    } else {
+        head = sc.get<uint32_t>(nc + 1);
+        seg_excl = sc.get<int64_t>(nc + 1);
+        seg_start = sc.get<int64_t>(nc + 1);
+        rel = sc.get<uint32_t>(nc + 1);
+        col_of_seg = sc.get<int64_t>(nc + 1);
+        keep = sc.get<uint32_t>(nc + 1);
+        out_pos = sc.get<int64_t>(nc + 1);
+        if (!head || !seg_excl || !seg_start || !rel || !col_of_seg || !keep || !out_pos) return SG_ERR_OOM;
+        SG_LAUNCH("seg_head", seg_head_kernel, blocks_for(nc, NT), NT, 0, s, key, nc, head);
+        SG_TRY(exclusive_scan<uint32_t>(head, seg_excl, nc, s, err));
+        SG_LAUNCH("seg_start", seg_start_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, nc, seg_start);
+        // number of segments lives on the device at seg_excl[nc]; launch over the upper bound nc
+        SG_LAUNCH("seg_reliable", seg_reliable_kernel, blocks_for(nc, NT), NT, 0, s, seg_start, seg_excl + nc, lo,
+                  hi, key, lohi, 2 * k, nc, rel);
+        SG_TRY(exclusive_scan<uint32_t>(rel, col_of_seg, nc, s, err));
+        SG_LAUNCH("keep", keep_kernel, blocks_for(nc, NT), NT, 0, s, head, seg_excl, rel, val, nc, keep);
+        SG_TRY(exclusive_scan<uint32_t>(keep, out_pos, nc, s, err));
+        // m = reliable segments = col_of_seg[nc] (rel is 0 past the last segment)
+        SG_CUDA_TRY(cudaMemcpyAsync(&sizes[0], col_of_seg + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(&sizes[1], out_pos + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     if (herr) return timeout_error("build_kmer_matrix");
     const int64_t m = sizes[0], nnz = sizes[1];
     if (m >= ((int64_t)1 << 31)) {
@@ -658,9 +749,14 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint32_t *ak0 = sc.get<uint32_t>(nnz), *ak1 = sc.get<uint32_t>(nnz);
     uint64_t *av0 = sc.get<uint64_t>(nnz), *av1 = sc.get<uint64_t>(nnz);
     if (!ak0 || !ak1 || !av0 || !av1) return SG_ERR_OOM;
-    SG_LAUNCH("emit_at", emit_at_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, head, seg_excl, rel, col_of_seg,
-              keep, out_pos, key, val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0, av0, 2 * k,
-              job_ncols);
+    if (fused)
+        SG_LAUNCH("emit_at", emit_fused_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, (const uint64_t *)flags,
+                  (const uint64_t *)pre, key, (const uint64_t *)val, nc, m, nnz, At->col, At->val, At->row_ptr,
+                  *codes_out, ak0, av0, 2 * k, job_ncols);
+    else
+        SG_LAUNCH("emit_at", emit_at_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, head, seg_excl, rel,
+                  col_of_seg, keep, out_pos, key, val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0,
+                  av0, 2 * k, job_ncols);
     int rbits = 0;
     while (rbits < 32 && ((int64_t)1 << rbits) < n) rbits++;
     bool aalt = false;
@@ -699,7 +795,7 @@ extern "C" sg_status sg_build_kmer_matrix(const uint8_t *d_seq, const int64_t *d
     {
         sg::Scratch sc(s);
         st = sg::build_impl(d_seq, d_offsets, n_reads, total_len, k, lo, hi, A, At, d_kmer_codes, s, sc,
-                            sg::JobMap{nullptr, 1, 2 * k}, nullptr, nullptr);
+                            sg::JobMap{nullptr, 1, 2 * k}, nullptr, nullptr, hi);
     }
     if (st != SG_OK) {
         sg_free_csr_u32(A, stream);

@@ -17,7 +17,7 @@ struct JobMap {
 // reliable range and job_ncols (device, zeroed, njobs) receives each job's number of columns.
 sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t total, int k, uint32_t lo,
                      uint32_t hi, sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **codes_out, cudaStream_t s,
-                     Scratch &sc, JobMap jm, const uint32_t *lohi, unsigned long long *job_ncols);
+                     Scratch &sc, JobMap jm, const uint32_t *lohi, unsigned long long *job_ncols, uint32_t hmax);
 
 // C = A At over the overlap semiring (spgemm.cu).
 sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S, sg_overlap_csr *C,
