@@ -381,6 +381,12 @@ uint64_t sg_launch_count(void);
  *                         slices but more false positives (singletons that reach the exact count)
  *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (64)
  *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4 or 8 (4)
+ *   spgemm_fused          1: C in one numeric pass whose tables are sized from a guess (rows that
+ *                         overflow are redone in exact-size global-memory tables) and whose rows
+ *                         go to a temporary region; 0: symbolic pass (exact sizes), then numeric (1)
+ *   num_guess_shift       fused numeric table guess = products of the row >> shift (2)
+ *   spgemm_fused_max_mb   largest temporary region of the fused pass, MB (8192); above it the
+ *                         two-pass form runs
  *   sym_guess_shift       symbolic hash table guess = products of the row >> shift (2)
  *   spgemm_blocks_per_sm  blocks per SM of each SpGEMM class launch (16)
  *   tr_blocks_per_sm      blocks per SM of the min-plus launch (32)

@@ -17,6 +17,8 @@ SPACE = {
     "bloom_slice_mb": [32, 48, 64, 96, 128],
     "bloom_unroll": [4, 8],
     "bloom_bits": [6, 8, 10, 12],
+    "spgemm_fused": [0, 1],
+    "num_guess_shift": [1, 2, 3, 4],
     "sym_guess_shift": [0, 1, 2, 3],
     "spgemm_blocks_per_sm": [2, 4, 8, 16],
     "tr_blocks_per_sm": [4, 8, 16, 32],

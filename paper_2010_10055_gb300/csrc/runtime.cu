@@ -122,9 +122,19 @@ void register_check_reader(check_reader_fn f) {
 static std::mutex g_smem_mu;
 static std::map<const void *, size_t> g_smem_caps;
 
+static std::map<const void *, size_t> g_smem_static;
+
+// The default cap of 48 KB covers a kernel's static and dynamic shared memory together.
 cudaError_t ensure_smem_cap(const void *kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     std::lock_guard<std::mutex> lk(g_smem_mu);
+    auto st = g_smem_static.find(kernel);
+    if (st == g_smem_static.end()) {
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+        if (e != cudaSuccess) return e;
+        st = g_smem_static.emplace(kernel, fa.sharedSizeBytes).first;
+    }
+    if (bytes + st->second <= 48 * 1024) return cudaSuccess;
     auto it = g_smem_caps.find(kernel);
     if (it != g_smem_caps.end() && it->second >= bytes) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -208,6 +218,9 @@ static Tunable g_tunables[] = {
     {"bloom_bits", 8, 2, 32},             // bits of the first Bloom filter per window
     {"bloom_slice_mb", 64, 1, 1 << 20},   // B1 megabytes updated per Bloom launch
     {"bloom_unroll", 4, 4, 8},            // windows (atomics in flight) per thread per Bloom step: 4 or 8
+    {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
+    {"num_guess_shift", 2, 0, 8},         // fused numeric table guess = products >> shift
+    {"spgemm_fused_max_mb", 8192, 0, 1 << 30},  // temporary C region above which the two passes run
     {"sym_guess_shift", 2, 0, 8},         // symbolic table guess = products >> shift
     {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch
     {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch

@@ -31,7 +31,7 @@
 namespace sg {
 
 constexpr int SP_MAX_SEEDS = 8;
-constexpr uint64_t SEED_NONE = ~0ull;
+
 constexpr int SP_NCLS = 9;        // shared-memory classes per pass (one per table size)
 constexpr int SP_MINLOG = 6;      // smallest table: 64 slots
 
@@ -133,7 +133,9 @@ __device__ __forceinline__ void for_each_product(const SpArgs &g, int32_t i, int
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int64_t a0 = r0 + (int64_t)warp * 32; a0 < r1; a0 += (int64_t)nwarps * 32) {
-        if (stop && *stop) return;
+        // one decision for the whole warp: the lanes may not have reconverged after the divergent
+        // table updates, and a lane that left here would strand the others in the shuffles below
+        if (stop && __any_sync(0xffffffffu, *stop != 0)) return;
         const int64_t a = a0 + lane;
         int64_t beg = 0, len = 0;
         if (a < r1) {
@@ -279,80 +281,145 @@ __global__ void __launch_bounds__(512) symbolic_kernel(SpArgs g, const int32_t *
 }
 
 // ----------------------------------------------------------------------------- numeric
-// One table of T slots: seeds [T][S] u64 | keys [T] i32 | counts [T] u32 | sort buffer [T/2] u64,
-// in shared memory (GSLICE == false) or in this block's global slice.
-__host__ __device__ inline size_t num_table_bytes(int64_t T, int S) {
-    return (size_t)T * (8 * (size_t)S + 8) + (size_t)(T / 2) * 8;
+// One table of T slots: sort buffer [T/2] u64 | keys [T] i32 | counts [T] u32 | seeds [T][S] u32,
+// in shared memory (GSLICE == false) or in this block's global slice. A seed is the index of the
+// A entry (i, j) within row i; its order is the order of j, so the S smallest indices are the
+// S shared k-mers with the smallest columns (reading r4). The positions are looked up when the
+// row is written: pos_i from A's entry, pos_k from At's row j (sorted by read).
+constexpr uint32_t SEED_NONE = 0xFFFFFFFFu;
+
+// guessed: a table sized from a guess may hold up to 3/4 T partners, so its sort buffer has T
+// entries; an exact-size table (T >= 2 x distinct) needs T/2.
+__host__ __device__ inline size_t num_table_bytes(int64_t T, int S, bool guessed = false) {
+    return (size_t)(guessed ? T : T / 2) * 8 + (size_t)T * (8 + 4 * (size_t)S);
 }
 
-template <bool GSLICE>
+// At value of partner k in At row [b, b + len) (t_pair = val << 32 | col, ascending col).
+__device__ __forceinline__ uint32_t at_value(const uint64_t *__restrict__ t_pair, int64_t b, int64_t len, int32_t k) {
+    int64_t lo = b, hi = b + len;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int32_t)(uint32_t)t_pair[mid] <= k) lo = mid; else hi = mid;
+    }
+    return (uint32_t)(t_pair[lo] >> 32);
+}
+
+// FUSED == false: the table size comes from the symbolic pass's exact distinct count (need[i]) and
+// row i is written to C at c_rp[i]. FUSED == true (no symbolic pass): shared-memory tables are
+// sized from a guess; a row whose table fills past 3/4 stops and is appended to ovf_list, to be
+// redone in a global-memory table of the exact bound 2 min(w_i, n - 1) (GSLICE, never overflows);
+// a finished row is written to the temporary arrays at c_rp[i] (room for min(w_i / t, n - 1)
+// entries) and its length to nnz_row[i].
+template <bool GSLICE, bool FUSED>
 __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
                                                      const unsigned long long *__restrict__ nrows_p, int log2T,
                                                      const int64_t *__restrict__ need, unsigned char *__restrict__ gpool,
                                                      int64_t slice_bytes, const int64_t *__restrict__ c_rp,
                                                      int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
                                                      uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
-                                                     int64_t c_nnz) {
+                                                     int64_t c_nnz, const int64_t *__restrict__ work,
+                                                     int32_t *__restrict__ ovf_list,
+                                                     unsigned long long *__restrict__ ovf_count,
+                                                     int64_t *__restrict__ nnz_row) {
     extern __shared__ __align__(16) unsigned char num_raw[];
-    __shared__ int s_ctr;
+    __shared__ int s_ctr, s_ins, s_ovf;
     const int S = g.S;
     const int64_t nrows = (int64_t)*nrows_p;
     for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
         const int32_t i = rows[rb];
+        if (!SG_IN_BOUNDS(i >= 0 && i < g.n, 307, i)) continue;
         int lT = log2T;
         unsigned char *tb = num_raw;
         if (GSLICE) {
-            const int64_t T = need[i];
+            int64_t T;
+            if (FUSED) {
+                const int64_t w = work[i];
+                T = pow2_at_least(2 * (w < g.n - 1 ? w : g.n - 1));
+            } else {
+                T = need[i];
+            }
             lT = 0;
-            while (((int64_t)1 << lT) < T) lT++;
+            while (lT < 31 && ((int64_t)1 << lT) < T) lT++;
+            if (!SG_IN_BOUNDS(num_table_bytes((int64_t)1 << lT, S) <= (size_t)slice_bytes, 306, T)) continue;
             tb = gpool + (int64_t)blockIdx.x * slice_bytes;
         }
         const int32_t T = 1 << lT;
-        uint64_t *seeds = (uint64_t *)tb;
-        int32_t *keys = (int32_t *)(seeds + (int64_t)T * S);
+        const bool guessed = FUSED && !GSLICE;
+        const int ob_cap = guessed ? T : (T >> 1);  // sort buffer entries
+        uint64_t *obuf = (uint64_t *)tb;
+        int32_t *keys = (int32_t *)(obuf + ob_cap);
         uint32_t *cnt = (uint32_t *)(keys + T);
-        uint64_t *obuf = (uint64_t *)(cnt + T);
+        uint32_t *seeds = cnt + T;
         for (int x = threadIdx.x; x < T; x += blockDim.x) {
             keys[x] = -1;
             cnt[x] = 0;
         }
         for (int x = threadIdx.x; x < T * S; x += blockDim.x) seeds[x] = SEED_NONE;
-        if (threadIdx.x == 0) s_ctr = 0;
+        if (threadIdx.x == 0) {
+            s_ctr = 0;
+            s_ins = 0;
+            s_ovf = 0;
+        }
         __syncthreads();
         const int64_t r0 = g.a_rp[i], r1 = g.a_rp[i + 1];
         const uint32_t msk = (uint32_t)T - 1u;
-        for_each_product<true>(g, i, r0, r1, nullptr, [&](int32_t k, uint32_t vk, int64_t idx) {
+        const int cap = (T >> 1) + (T >> 2);  // guessed tables: at most 3/4 T partners
+        for_each_product<false>(g, i, r0, r1, guessed ? &s_ovf : nullptr, [&](int32_t k, uint32_t, int64_t idx) {
+            if (guessed && *(volatile int *)&s_ovf) return;  // the row is abandoned
             uint32_t h = hash_slot(k, lT);
-            for (;;) {  // T >= 2 * distinct_i: a free slot or k is always found
+            bool found = false;
+            // exact sizes (T >= 2 * distinct_i) always find a free slot or k; a guessed table may
+            // fill up, which ends the row (s_ovf)
+            for (int probe = 0; probe < T; probe++) {
                 int32_t cur = ((volatile int32_t *)keys)[h];
                 if (cur == -1) {
                     const int32_t old = atomicCAS(keys + h, -1, k);
-                    if (old == -1 || old == k) break;
+                    if (old == -1) {
+                        if (guessed && atomicAdd(&s_ins, 1) >= cap) s_ovf = 1;
+                        found = true;
+                        break;
+                    }
                     cur = old;
                 }
-                if (cur == k) break;
+                if (cur == k) {
+                    found = true;
+                    break;
+                }
                 h = (h + 1) & msk;
+            }
+            if (!found) {
+                s_ovf = 1;
+                return;
             }
             atomicAdd(cnt + h, 1u);
             if (S > 0) {
-                unsigned long long v = ((unsigned long long)idx << 32) | vk;
-                unsigned long long *sl = (unsigned long long *)(seeds + (int64_t)h * S);
+                uint32_t v = (uint32_t)idx;
+                uint32_t *sl = seeds + (int64_t)h * S;
                 for (int q = 0; q < S; q++) {
-                    const unsigned long long old = atomicMin(sl + q, v);
+                    const uint32_t old = atomicMin(sl + q, v);
                     if (old > v) v = old;  // the larger one moves on to the next slot
                     if (v == SEED_NONE) break;
                 }
             }
         });
         __syncthreads();
+        if (guessed && s_ovf) {  // table too small for this row: the global-memory pass redoes it
+            if (threadIdx.x == 0) {
+                const unsigned long long q = atomicAdd(ovf_count, 1ull);
+                if (SG_IN_BOUNDS((int64_t)q < g.n, 304, q)) ovf_list[q] = i;
+            }
+            __syncthreads();
+            continue;
+        }
         for (int x = threadIdx.x; x < T; x += blockDim.x) {
             if (keys[x] != -1 && cnt[x] >= g.min_shared) {
                 const int p = atomicAdd(&s_ctr, 1);
-                if (SG_IN_BOUNDS(p < (T >> 1), 303, p)) obuf[p] = ((uint64_t)(uint32_t)keys[x] << 32) | (uint32_t)x;
+                if (SG_IN_BOUNDS(p < ob_cap, 303, p)) obuf[p] = ((uint64_t)(uint32_t)keys[x] << 32) | (uint32_t)x;
             }
         }
         __syncthreads();
-        const int nv = s_ctr;
+        const int nv = s_ctr < ob_cap ? s_ctr : ob_cap;  // s_ctr <= ob_cap by the table sizes
+        if (!SG_IN_BOUNDS(s_ctr <= ob_cap, 305, s_ctr)) {}
         int P2 = 1;
         while (P2 < nv) P2 <<= 1;
         for (int x = nv + threadIdx.x; x < P2; x += blockDim.x) obuf[x] = ~0ull;
@@ -375,20 +442,23 @@ __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *_
         }
         const int64_t e0 = c_rp[i];
         const int64_t room = c_rp[i + 1] - e0;
-        if (nv != room && threadIdx.x == 0) atomicOr(g.err, (uint32_t)DEV_OVERFLOW);
+        if ((FUSED ? nv > room : nv != room) && threadIdx.x == 0) atomicOr(g.err, (uint32_t)DEV_OVERFLOW);
         const int nw = nv < room ? nv : (int)room;
+        if (FUSED && threadIdx.x == 0) nnz_row[i] = nw;
         for (int q = threadIdx.x; q < nw; q += blockDim.x) {
             const uint64_t w = obuf[q];
             const uint32_t slot = (uint32_t)w;
+            const int32_t k = (int32_t)(w >> 32);
             const int64_t e = e0 + q;
-            c_col[e] = (int32_t)(w >> 32);
+            c_col[e] = k;
             c_cnt[e] = cnt[slot];
             for (int s = 0; s < S; s++) {
-                const uint64_t sd = seeds[(int64_t)slot * S + s];
+                const uint32_t sd = seeds[(int64_t)slot * S + s];
                 uint32_t si = 0xFFFFFFFFu, sk = 0xFFFFFFFFu;
                 if (sd != SEED_NONE) {
-                    const uint32_t vi = g.a_val[r0 + (int64_t)(sd >> 32)];
-                    const uint32_t vk = (uint32_t)sd;
+                    const int64_t a = r0 + sd;
+                    const uint32_t vi = g.a_val[a];
+                    const uint32_t vk = at_value(g.t_pair, g.a_beg[a], g.a_len[a], k);
                     si = vi & 0x7FFFFFFFu;
                     sk = (vk & 0x7FFFFFFFu) | ((vi ^ vk) & 0x80000000u);
                 }
@@ -401,6 +471,45 @@ __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *_
 }
 
 static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
+
+// Fused path: guessed table size (as sym_need) and the row's output room min(w / t, n - 1).
+__global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, uint32_t t,
+                                  int64_t *__restrict__ need, int64_t *__restrict__ room) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t w = work[i];
+    if (w <= 0) {
+        need[i] = 0;
+        room[i] = 0;
+        return;
+    }
+    const int64_t exact = pow2_at_least(2 * (w < n - 1 ? w : n - 1));
+    const int64_t guess = pow2_at_least((w >> shift) > 64 ? (w >> shift) : 64);
+    need[i] = guess < exact ? guess : exact;
+    const int64_t r = w / t;
+    room[i] = r < n - 1 ? r : n - 1;
+}
+
+// Fused path: copies each row's entries from the temporary arrays (row i at tmp_off[i], seeds
+// slot-major with stride tmp_n) to C (row i at c_rp[i], stride nnz). One warp per row.
+__global__ void compact_c_kernel(const int64_t *__restrict__ tmp_off, int64_t tmp_n, const int32_t *__restrict__ t_col,
+                                 const uint32_t *__restrict__ t_cnt, const uint32_t *__restrict__ t_si,
+                                 const uint32_t *__restrict__ t_sk, int S, const int64_t *__restrict__ c_rp, int64_t n,
+                                 int64_t nnz, int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
+                                 uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int64_t src = tmp_off[row], dst = c_rp[row], len = c_rp[row + 1] - dst;
+    for (int64_t e = lane; e < len; e += 32) {
+        c_col[dst + e] = t_col[src + e];
+        c_cnt[dst + e] = t_cnt[src + e];
+        for (int q = 0; q < S; q++) {
+            c_si[(int64_t)q * nnz + dst + e] = t_si[(int64_t)q * tmp_n + src + e];
+            c_sk[(int64_t)q * nnz + dst + e] = t_sk[(int64_t)q * tmp_n + src + e];
+        }
+    }
+}
 
 __global__ void pair_kernel(const int32_t *__restrict__ col, const uint32_t *__restrict__ val, int64_t nnz,
                             uint64_t *__restrict__ pair) {
@@ -428,14 +537,15 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     int64_t *need = sc.get<int64_t>(n + 1);
     int64_t *nnz_row = sc.get<int64_t>(n + 1);
     int64_t *dist = sc.get<int64_t>(n + 1);
-    unsigned long long *counts = sc.get<unsigned long long>(2 * NCNT + 1);
+    unsigned long long *counts = sc.get<unsigned long long>(3 * NCNT + 1);
     int32_t *lists = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
     int32_t *ovf = sc.get<int32_t>(2 * (n + 1));  // overflow list | unused list of the re-run
     if (!err || !work || !need || !nnz_row || !dist || !counts || !lists || !ovf) return SG_ERR_OOM;
     unsigned long long *sym_counts = counts, *num_counts = counts + NCNT, *unused = counts + 2 * NCNT;
     unsigned long long *ovf_count = counts + SP_NCLS + 1;
+    unsigned long long *fz_counts = counts + 2 * NCNT + 1, *fz_ovf = fz_counts + SP_NCLS + 1;
     SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (2 * NCNT + 1) * sizeof(unsigned long long), s));
+    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (3 * NCNT + 1) * sizeof(unsigned long long), s));
     SG_CUDA_TRY(cudaMemsetAsync(nnz_row, 0, (n + 1) * sizeof(int64_t), s));
     SG_CUDA_TRY(cudaMemsetAsync(dist, 0, (n + 1) * sizeof(int64_t), s));
     int64_t *a_beg = sc.get<int64_t>(A->nnz + 1);
@@ -449,6 +559,99 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr, n,
               work, a_beg, a_len);
     SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
+    const int grid = (int)(152 * tune("spgemm_blocks_per_sm"));
+    // numeric: one class per table size from 2^6 while the table and its sort buffer fit in 160 KB
+    Classes num{};
+    num.ncls = 0;
+    while (num.ncls < SP_NCLS && num_table_bytes((int64_t)1 << (SP_MINLOG + num.ncls), S) <= (160u << 10)) {
+        num.log2T[num.ncls] = SP_MINLOG + num.ncls;
+        num.ncls++;
+    }
+    Classes fz{};  // the fused pass's guessed tables (larger sort buffer; up to 220 KB: one block per SM)
+    fz.ncls = 0;
+    while (fz.ncls < SP_NCLS && num_table_bytes((int64_t)1 << (SP_MINLOG + fz.ncls), S, true) <= (220u << 10)) {
+        fz.log2T[fz.ncls] = SP_MINLOG + fz.ncls;
+        fz.ncls++;
+    }
+    // global-memory tables of the exact bound 2 min(w, n - 1) (rows beyond shared memory)
+    const int64_t Tmax = pow2_at_least(2 * (n > 1 ? n - 1 : 1));
+    const int64_t gslice_bytes = (int64_t)((num_table_bytes(Tmax, S) + 255) & ~(size_t)255);
+
+    // ---- fused path (no symbolic pass): guessed tables, rows written to a temporary region
+    if (tune("spgemm_fused")) {
+        stage.emplace("SpGEMMNumeric", s);
+        int64_t *room = sc.get<int64_t>(n + 1), *tmp_off = sc.get<int64_t>(n + 1);
+        if (!room || !tmp_off) return SG_ERR_OOM;
+        SG_LAUNCH("fused_need", fused_need_kernel, blocks_for(n, NT), NT, 0, s, (const int64_t *)work, n,
+                  (int)tune("num_guess_shift"), min_shared, need, room);
+        SG_TRY(exclusive_scan<int64_t>(room, tmp_off, n, s, err));
+        SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, fz, fz_counts, lists);
+        unsigned long long h_fz[NCNT];
+        int64_t tmp_n = 0;
+        uint32_t herr = 0;
+        SG_CUDA_TRY(cudaMemcpyAsync(h_fz, fz_counts, sizeof(h_fz), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(read_back(&tmp_n, tmp_off + n, sizeof(int64_t), s));
+        if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
+        const double tmp_bytes = (double)tmp_n * (8.0 + 8.0 * S);
+        if (tmp_bytes <= (double)tune("spgemm_fused_max_mb") * 1048576.0) {
+            int32_t *t_col = sc.get<int32_t>(tmp_n + 1);
+            uint32_t *t_cnt = sc.get<uint32_t>(tmp_n + 1);
+            uint32_t *t_si = sc.get<uint32_t>((size_t)S * tmp_n + 1), *t_sk = sc.get<uint32_t>((size_t)S * tmp_n + 1);
+            if (!t_col || !t_cnt || !t_si || !t_sk) return SG_ERR_OOM;
+            for (int c = 0; c < fz.ncls; c++) {
+                if (!h_fz[c]) continue;
+                const size_t sm = num_table_bytes((int64_t)1 << fz.log2T[c], S, true);
+                SG_CUDA_TRY(ensure_smem(numeric_kernel<false, true>, sm));
+                SG_LAUNCH(NUM_NAMES[fz.log2T[c] - SP_MINLOG], (numeric_kernel<false, true>), grid,
+                          pick_threads(fz.log2T[c]), sm, s, g, lists + (int64_t)c * n, fz_counts + c, fz.log2T[c],
+                          (const int64_t *)need, (unsigned char *)nullptr, (int64_t)0, (const int64_t *)tmp_off,
+                          t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work, ovf, fz_ovf, nnz_row);
+            }
+            unsigned long long n_ovf = 0;
+            SG_CUDA_TRY(read_back(&n_ovf, fz_ovf, sizeof(n_ovf), s));
+            const unsigned long long n_big = h_fz[fz.ncls];
+            if (n_big + n_ovf > 0) {
+                const unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
+                const int ggrid = (int)(rows_g < 152 * 2 ? rows_g : 152 * 2);
+                unsigned char *pool = sc.get<unsigned char>((size_t)gslice_bytes * ggrid);
+                if (!pool) return SG_ERR_OOM;
+                if (n_big)
+                    SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
+                              lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, 0, (const int64_t *)need, pool,
+                              gslice_bytes, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n,
+                              (const int64_t *)work, ovf + n + 1, unused, nnz_row);
+                if (n_ovf)
+                    SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
+                              (const int32_t *)ovf, fz_ovf, 0, (const int64_t *)need, pool, gslice_bytes,
+                              (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work,
+                              ovf + n + 1, unused, nnz_row);
+            }
+            SG_ALLOC(C->row_ptr, int64_t, n + 1, s);
+            SG_TRY(exclusive_scan<int64_t>(nnz_row, C->row_ptr, n, s, err));
+            int64_t nnz = 0;
+            SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            SG_CUDA_TRY(read_back(&nnz, C->row_ptr + n, sizeof(int64_t), s));
+            if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
+            if (herr) {
+                set_error("overlap_spgemm: a row exceeded its output bound (internal error)");
+                return SG_ERR_OVERFLOW;
+            }
+            C->n = n;
+            C->nnz = nnz;
+            C->max_seeds = S;
+            SG_ALLOC(C->col, int32_t, nnz, s);
+            SG_ALLOC(C->count, uint32_t, nnz, s);
+            SG_ALLOC(C->seed_i, uint32_t, (int64_t)S * nnz, s);
+            SG_ALLOC(C->seed_k, uint32_t, (int64_t)S * nnz, s);
+            SG_LAUNCH("compact_c", compact_c_kernel, blocks_for(n * 32, 256), 256, 0, s, (const int64_t *)tmp_off,
+                      tmp_n, (const int32_t *)t_col, (const uint32_t *)t_cnt, (const uint32_t *)t_si,
+                      (const uint32_t *)t_sk, S, (const int64_t *)C->row_ptr, n, nnz, C->col, C->count, C->seed_i,
+                      C->seed_k);
+            return SG_OK;
+        }
+        // the temporary region would exceed its budget: the two-pass path below
+    }
 
     // ---- symbolic: guessed shared-memory tables of 2^6 .. 2^14 slots, one class per size
     Classes sym{};
@@ -456,7 +659,6 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     for (int c = 0; c < SP_NCLS; c++) sym.log2T[c] = SP_MINLOG + c;
     SG_LAUNCH("sym_need", sym_need_kernel, blocks_for(n, NT), NT, 0, s, work, n, (int)tune("sym_guess_shift"),
               need);
-    const int grid = (int)(152 * tune("spgemm_blocks_per_sm"));
     SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, sym, sym_counts, lists);
     for (int c = 0; c < sym.ncls; c++) {
         const size_t sm = (size_t)(2 << sym.log2T[c]) * sizeof(int32_t);
@@ -489,13 +691,6 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     stage.emplace("SpGEMMNumeric", s);
     SG_ALLOC(C->row_ptr, int64_t, n + 1, s);
     SG_TRY(exclusive_scan<int64_t>(nnz_row, C->row_ptr, n, s, err));
-    // numeric: one class per table size from 2^6 while the table and its sort buffer fit in 160 KB
-    Classes num{};
-    num.ncls = 0;
-    while (num.ncls < SP_NCLS && num_table_bytes((int64_t)1 << (SP_MINLOG + num.ncls), S) <= (160u << 10)) {
-        num.log2T[num.ncls] = SP_MINLOG + num.ncls;
-        num.ncls++;
-    }
     SG_LAUNCH("num_need", num_need_kernel, blocks_for(n, NT), NT, 0, s, dist, n, need);
     SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, num, num_counts, lists);
     int64_t nnz = 0;
@@ -515,22 +710,21 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     for (int c = 0; c < num.ncls; c++) {
         if (!h_num[c]) continue;
         const size_t sm = num_table_bytes((int64_t)1 << num.log2T[c], S);
-        SG_CUDA_TRY(ensure_smem(numeric_kernel<false>, sm));
-        SG_LAUNCH(NUM_NAMES[num.log2T[c] - SP_MINLOG], numeric_kernel<false>, grid, pick_threads(num.log2T[c]), sm,
-                  s, g,
-                  lists + (int64_t)c * n, num_counts + c, num.log2T[c], (const int64_t *)need,
-                  (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i,
-                  C->seed_k, nnz);
+        SG_CUDA_TRY(ensure_smem(numeric_kernel<false, false>, sm));
+        SG_LAUNCH(NUM_NAMES[num.log2T[c] - SP_MINLOG], (numeric_kernel<false, false>), grid,
+                  pick_threads(num.log2T[c]), sm, s, g, lists + (int64_t)c * n, num_counts + c, num.log2T[c],
+                  (const int64_t *)need, (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col,
+                  C->count, C->seed_i, C->seed_k, nnz, (const int64_t *)nullptr, (int32_t *)nullptr,
+                  (unsigned long long *)nullptr, (int64_t *)nullptr);
     }
     if (h_num[num.ncls]) {
-        const int64_t Tmax = pow2_at_least(2 * (n > 1 ? n - 1 : 1));
-        const int64_t slice_bytes = (int64_t)((num_table_bytes(Tmax, S) + 255) & ~(size_t)255);
-        const int grid = (int)(h_num[num.ncls] < 152 * 2 ? h_num[num.ncls] : 152 * 2);
-        unsigned char *pool = sc.get<unsigned char>((size_t)slice_bytes * grid);
+        const int ggrid = (int)(h_num[num.ncls] < 152 * 2 ? h_num[num.ncls] : 152 * 2);
+        unsigned char *pool = sc.get<unsigned char>((size_t)gslice_bytes * ggrid);
         if (!pool) return SG_ERR_OOM;
-        SG_LAUNCH("spgemm_numeric_gmem", numeric_kernel<true>, grid, 512, 0, s, g, lists + (int64_t)num.ncls * n,
-                  num_counts + num.ncls, 0, (const int64_t *)need, pool, slice_bytes, (const int64_t *)C->row_ptr,
-                  C->col, C->count, C->seed_i, C->seed_k, nnz);
+        SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, false>), ggrid, 512, 0, s, g,
+                  lists + (int64_t)num.ncls * n, num_counts + num.ncls, 0, (const int64_t *)need, pool, gslice_bytes,
+                  (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i, C->seed_k, nnz, (const int64_t *)nullptr,
+                  (int32_t *)nullptr, (unsigned long long *)nullptr, (int64_t *)nullptr);
     }
     SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));
     if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");

@@ -41,8 +41,11 @@ CONFIGS = [
     {},
     {"bloom_bits": 4, "bloom_slice_mb": 1},                          # many small Bloom slices
     {"bloom_bits": 12, "bloom_unroll": 8},
-    {"sym_guess_shift": 8},                                          # tiny guessed tables: overflow path
-    {"sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
+    {"spgemm_fused": 0, "sym_guess_shift": 8},                      # two passes, tiny symbolic guesses
+    {"spgemm_fused": 0, "sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
+    {"num_guess_shift": 8},                                          # fused, most rows overflow
+    {"num_guess_shift": 0},                                          # fused, exact-bound guesses
+    {"spgemm_fused_max_mb": 0},                                      # fused path over budget: fallback
 ]
 
 
