@@ -70,6 +70,13 @@ def _load():
         lib.sgo_transitive_reduce.restype = ctypes.c_int
         lib.sgo_transitive_reduce.argtypes = [ctypes.POINTER(_Graph), u32, i32, ctypes.POINTER(_Graph),
                                               ctypes.POINTER(i32)]
+        lib.sgo_kmer_census.restype = ctypes.c_int
+        lib.sgo_kmer_census.argtypes = [vp, vp, i64, i32, vp, i64, vp, i64, vp, vp, vp, vp, ctypes.POINTER(i64)]
+        lib.sgo_read_windows.restype = ctypes.c_int
+        lib.sgo_read_windows.argtypes = [vp, vp, i64, i32, i64, vp, vp, vp, ctypes.POINTER(i64)]
+        lib.sgo_overlap_row.restype = ctypes.c_int
+        lib.sgo_overlap_row.argtypes = [ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), i64, u32, i32, vp, vp, vp, vp,
+                                        ctypes.POINTER(i64)]
         lib.sgo_free.argtypes = [vp]
         _lib = lib
     return _lib
@@ -169,3 +176,59 @@ def transitive_reduce(R: dict, fuzz: int = 0, mode: int = DIRMATCH) -> tuple:
     return (dict(n=int(S.n), row_ptr=_take(lib, S.row_ptr, S.n + 1, np.int64),
                  col=_take(lib, S.col, nnz, np.int32), suffix=_take(lib, S.suffix, nnz, np.uint32),
                  dir=_take(lib, S.dir, nnz, np.uint8)), int(it.value))
+
+
+def kmer_census(seq, offsets, k: int, codes, occ_cap: int = 1 << 22) -> dict:
+    """Frequency of each canonical code in `codes` over all windows of all reads, and up to occ_cap
+    occurrences (q = index into the sorted unique codes, read, pos, strand) in scan order.
+    Returns dict(codes=sorted unique codes, freq, occ_q, occ_read, occ_pos, occ_strand)."""
+    lib = _load()
+    s = np.ascontiguousarray(seq, np.uint8)
+    o = np.ascontiguousarray(offsets, np.int64)
+    q = np.unique(np.asarray(codes, np.uint64))
+    freq = np.zeros(max(q.size, 1), np.uint64)
+    oq = np.zeros(occ_cap, np.int64)
+    orr = np.zeros(occ_cap, np.int32)
+    op = np.zeros(occ_cap, np.uint32)
+    ost = np.zeros(occ_cap, np.uint32)
+    nocc = ctypes.c_int64()
+    _check(lib.sgo_kmer_census(s.ctypes.data, o.ctypes.data, o.size - 1, int(k), q.ctypes.data, q.size,
+                               freq.ctypes.data, occ_cap, oq.ctypes.data, orr.ctypes.data, op.ctypes.data,
+                               ost.ctypes.data, ctypes.byref(nocc)), "kmer_census")
+    c = int(nocc.value)
+    return dict(codes=q, freq=freq[:q.size], occ_q=oq[:c], occ_read=orr[:c], occ_pos=op[:c], occ_strand=ost[:c])
+
+
+def read_windows(seq, offsets, i: int, k: int) -> dict:
+    """Every valid window of read i: dict(code, pos, strand) by position."""
+    lib = _load()
+    s = np.ascontiguousarray(seq, np.uint8)
+    o = np.ascontiguousarray(offsets, np.int64)
+    cap = max(int(o[i + 1] - o[i]), 1)
+    code = np.zeros(cap, np.uint64)
+    pos = np.zeros(cap, np.uint32)
+    st = np.zeros(cap, np.uint32)
+    cnt = ctypes.c_int64()
+    _check(lib.sgo_read_windows(s.ctypes.data, o.ctypes.data, int(i), int(k), cap, code.ctypes.data,
+                                pos.ctypes.data, st.ctypes.data, ctypes.byref(cnt)), "read_windows")
+    c = int(cnt.value)
+    return dict(code=code[:c], pos=pos[:c], strand=st[:c])
+
+
+def overlap_row(A: dict, At: dict, i: int, min_shared: int = 2, max_seeds: int = 2) -> dict:
+    """Row i of C = A At over the overlap semiring: dict(col, count, seed_i [S, e], seed_k [S, e])."""
+    lib = _load()
+    a, keep_a = _csr_in(A)
+    t, keep_t = _csr_in(At)
+    n = int(A["n_rows"])
+    S = int(max_seeds)
+    col = np.zeros(max(n, 1), np.int32)
+    cnt = np.zeros(max(n, 1), np.uint32)
+    si = np.zeros(max(n, 1) * max(S, 1), np.uint32)
+    sk = np.zeros(max(n, 1) * max(S, 1), np.uint32)
+    e = ctypes.c_int64()
+    _check(lib.sgo_overlap_row(ctypes.byref(a), ctypes.byref(t), int(i), int(min_shared), S, col.ctypes.data,
+                               cnt.ctypes.data, si.ctypes.data, sk.ctypes.data, ctypes.byref(e)), "overlap_row")
+    m = int(e.value)
+    return dict(col=col[:m], count=cnt[:m], seed_i=si[:m * S].reshape(m, S).T.copy(),
+                seed_k=sk[:m * S].reshape(m, S).T.copy())

@@ -15,6 +15,9 @@
  *                             Sec. II / IV-E), evaluated on the pattern of R
  *   sgo_transitive_reduce  -- Algorithm 1 (Reduce/Apply/DimApply, M >= N, R o not I, until
  *                             nnz(R) stops changing)
+ *   sgo_kmer_census, sgo_read_windows, sgo_overlap_row -- single outputs of the same definitions
+ *                             (a k-mer's frequency and occurrences, a read's windows, one row of
+ *                             C), for sampled checks at sizes where the whole oracle is too slow
  *
  * Readings of places where the paper is silent (all shared with the CUDA path's spec):
  *  - A_ij keeps the LOWEST position of k-mer j in read i; every occurrence still counts
@@ -403,5 +406,118 @@ int sgo_transitive_reduce(const sgo_graph *R_in, uint32_t fuzz, int32_t mode, sg
     } while (R.nnz != prev);                               /* until nnz == prev */
     free(N); free(Nd); free(v);
     *S = R;
+    return SGO_OK;
+}
+
+/* ============================================ single outputs at full size (sampled checks) */
+
+/*
+ * Census of given k-mers over the whole input (Sec. IV-C: the frequency of a k-mer is its number
+ * of occurrences in the reads). query[0..nq) are canonical codes in ascending order. Every window
+ * of every read is coded as in sgo_build_kmer_matrix; for each window whose code is a query,
+ * freq[q] is incremented and, while fewer than occ_cap have been stored, the occurrence (q, read,
+ * pos, strand) is appended in scan order (reads ascending, positions ascending).
+ */
+int sgo_kmer_census(const uint8_t *seq, const int64_t *offsets, int64_t n, int32_t k,
+                    const uint64_t *query, int64_t nq, uint64_t *freq, int64_t occ_cap,
+                    int64_t *occ_q, int32_t *occ_read, uint32_t *occ_pos, uint32_t *occ_strand,
+                    int64_t *n_occ) {
+    if (k < 1 || k > 31 || (k & 1) == 0 || n < 0) return SGO_INVALID;
+    for (int64_t q = 0; q < nq; q++) freq[q] = 0;
+    int64_t stored = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t len = offsets[i + 1] - offsets[i];
+        for (int64_t p = 0; p + k <= len; p++) {
+            uint64_t code;
+            uint32_t strand;
+            if (!window_code(seq + offsets[i] + p, k, &code, &strand)) continue;
+            int64_t lo = 0, hi = nq;  /* binary search for code among the queries */
+            while (lo < hi) {
+                int64_t mid = (lo + hi) / 2;
+                if (query[mid] < code) lo = mid + 1; else hi = mid;
+            }
+            if (lo == nq || query[lo] != code) continue;
+            freq[lo]++;
+            if (stored < occ_cap) {
+                occ_q[stored] = lo;
+                occ_read[stored] = (int32_t)i;
+                occ_pos[stored] = (uint32_t)p;
+                occ_strand[stored] = strand;
+                stored++;
+            }
+        }
+    }
+    *n_occ = stored;
+    return SGO_OK;
+}
+
+/* Every valid window of read i: canonical code, position and strand, by position. cap entries
+ * at most (len - k + 1 suffice). */
+int sgo_read_windows(const uint8_t *seq, const int64_t *offsets, int64_t i, int32_t k, int64_t cap,
+                     uint64_t *code_out, uint32_t *pos_out, uint32_t *strand_out, int64_t *count) {
+    if (k < 1 || k > 31 || (k & 1) == 0) return SGO_INVALID;
+    int64_t len = offsets[i + 1] - offsets[i], c = 0;
+    for (int64_t p = 0; p + k <= len && c < cap; p++) {
+        uint64_t code;
+        uint32_t strand;
+        if (!window_code(seq + offsets[i] + p, k, &code, &strand)) continue;
+        code_out[c] = code;
+        pos_out[c] = (uint32_t)p;
+        strand_out[c] = strand;
+        c++;
+    }
+    *count = c;
+    return SGO_OK;
+}
+
+/*
+ * Row i of C = A At over the overlap semiring (Sec. IV-D), as in sgo_overlap_spgemm: the columns j
+ * of A_i are visited in ascending order, so the first max_seeds contributions to C_ik are the
+ * shared k-mers with the smallest column index. Writes the row's entries with count >= min_shared
+ * by ascending k into col/count and seeds [e * max_seeds + s] (row-major); returns their number in
+ * *nnz (at most A->n_rows - 1, which the arrays must hold).
+ */
+int sgo_overlap_row(const sgo_csr *A, const sgo_csr *At, int64_t i, uint32_t min_shared, int32_t max_seeds,
+                    int32_t *col, uint32_t *count, uint32_t *seed_i, uint32_t *seed_k, int64_t *nnz) {
+    if (max_seeds < 0 || max_seeds > 8 || min_shared < 1 || i < 0 || i >= A->n_rows) return SGO_INVALID;
+    int64_t n = A->n_rows;
+    int S = max_seeds;
+    uint32_t *cnt = (uint32_t *)calloc((size_t)n, sizeof(uint32_t));
+    uint32_t *si = (uint32_t *)malloc((size_t)n * (S ? S : 1) * sizeof(uint32_t));
+    uint32_t *sk = (uint32_t *)malloc((size_t)n * (S ? S : 1) * sizeof(uint32_t));
+    int64_t *touched = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!cnt || !si || !sk || !touched) { free(cnt); free(si); free(sk); free(touched); return SGO_OOM; }
+    int64_t nt = 0;
+    for (int64_t a = A->row_ptr[i]; a < A->row_ptr[i + 1]; a++) {
+        int64_t j = A->col[a];
+        uint32_t vi = A->val[a];
+        for (int64_t b = At->row_ptr[j]; b < At->row_ptr[j + 1]; b++) {
+            int64_t kk = At->col[b];
+            if (kk == i) continue;
+            uint32_t vk = At->val[b];
+            if (cnt[kk] == 0) touched[nt++] = kk;
+            if (cnt[kk] < (uint32_t)S) {
+                si[kk * S + cnt[kk]] = vi & 0x7FFFFFFFu;
+                sk[kk * S + cnt[kk]] = (vk & 0x7FFFFFFFu) | ((vi ^ vk) & 0x80000000u);
+            }
+            cnt[kk]++;
+        }
+    }
+    qsort(touched, (size_t)nt, sizeof(int64_t), cmp_u64);
+    int64_t e = 0;
+    for (int64_t q = 0; q < nt; q++) {
+        int64_t kk = touched[q];
+        if (cnt[kk] < min_shared) continue;
+        col[e] = (int32_t)kk;
+        count[e] = cnt[kk];
+        for (int s = 0; s < S; s++) {
+            int used = (uint32_t)s < cnt[kk];
+            seed_i[e * S + s] = used ? si[kk * S + s] : SGO_INF;
+            seed_k[e * S + s] = used ? sk[kk * S + s] : SGO_INF;
+        }
+        e++;
+    }
+    *nnz = e;
+    free(cnt); free(si); free(sk); free(touched);
     return SGO_OK;
 }
