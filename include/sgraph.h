@@ -380,6 +380,8 @@ uint64_t sg_launch_count(void);
  *   bloom_bits            bits of the first-level Bloom filter per window (8): fewer bits, fewer
  *                         slices but more false positives (singletons that reach the exact count)
  *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (64)
+ *   bloom_max_slices      at most this many Bloom launches, each streaming all window codes;
+ *                         for larger filters the slices grow instead (8)
  *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4 or 8 (4)
  *   spgemm_fused          1: C in one numeric pass whose tables are sized from a guess (rows that
  *                         overflow are redone in exact-size global-memory tables) and whose rows

@@ -601,13 +601,17 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     const int code_bits = 2 * k + job_bits;
     const uint64_t kmask = (1ull << code_bits) - 1;  // code_bits <= 62
     Bloom b1{nullptr, 0, B1_SEED}, b2{nullptr, 0, B2_SEED};
+    // window codes, filters and candidate masks: released (stream-ordered) once the candidates
+    // are emitted, before the sort allocates its buffers
+    std::optional<Scratch> early;
+    early.emplace(s);
     if (use_bloom && total > 0) {
         // B1: bloom_bits (8) bits per window; B2 ("seen twice"): 2 bits per window; 32-bit words
         const int64_t w1 = total * tune("bloom_bits") / 32 + 1024, w2 = total / 16 + 1024;
         b1.nwords = (uint32_t)(w1 < 0xFFFFFFF0LL ? w1 : 0xFFFFFFF0LL);
         b2.nwords = (uint32_t)(w2 < 0xFFFFFFF0LL ? w2 : 0xFFFFFFF0LL);
-        b1.words = sc.get<uint32_t>(b1.nwords);
-        b2.words = sc.get<uint32_t>(b2.nwords);
+        b1.words = early->get<uint32_t>(b1.nwords);
+        b2.words = early->get<uint32_t>(b2.nwords);
         if (!b1.words || !b2.words) return SG_ERR_OOM;
         SG_CUDA_TRY(cudaMemsetAsync(b1.words, 0, (size_t)b1.nwords * 4, s));
         SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, (size_t)b2.nwords * 4, s));
@@ -615,7 +619,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     std::optional<StageScope> stage;
     stage.emplace("CountKmer", s);  // a1-a4: codes, Bloom, exact count, columns
     // 0. window codes
-    uint64_t *wc = sc.get<uint64_t>(total + 1);
+    uint64_t *wc = early->get<uint64_t>(total + 1);
     if (!wc) return SG_ERR_OOM;
     SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
         SG_LAUNCH("window_codes", window_codes_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n,
@@ -624,8 +628,11 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     }));
     if (use_bloom) {
         // slices of at most bloom_slice_mb of B1, so each launch's atomics stay in L2
-        const uint64_t slice_words = ((uint64_t)tune("bloom_slice_mb") << 20) / 4;
-        const uint64_t nsl = (b1.nwords + slice_words - 1) / slice_words;
+        uint64_t slice_words = ((uint64_t)tune("bloom_slice_mb") << 20) / 4;
+        uint64_t nsl = (b1.nwords + slice_words - 1) / slice_words;
+        // every slice streams all window codes: beyond bloom_max_slices, slices grow instead
+        const uint64_t max_sl = (uint64_t)tune("bloom_max_slices");
+        if (nsl > max_sl) nsl = max_sl;
         const int64_t grid = blocks_for(total, KM_NT) < 152 * 16 ? blocks_for(total, KM_NT) : 152 * 16;
         const int64_t u = tune("bloom_unroll");
         for (uint64_t q = 0; q < nsl; q++) {
@@ -640,9 +647,9 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         }
     }
     const int64_t nwarp = nblk * KM_WARPS;
-    uint32_t *cmask = sc.get<uint32_t>(nwarp * KM_GW);
-    uint32_t *wcnt = sc.get<uint32_t>(nwarp + 1);
-    int64_t *wpos = sc.get<int64_t>(nwarp + 1);
+    uint32_t *cmask = early->get<uint32_t>(nwarp * KM_GW);
+    uint32_t *wcnt = early->get<uint32_t>(nwarp + 1);
+    int64_t *wpos = early->get<int64_t>(nwarp + 1);
     if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
     SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, kmask,
               cmask, wcnt);
@@ -667,6 +674,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     if (!key0 || !key1 || !val1 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
     SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, (const uint32_t *)cmask,
               (const int64_t *)wpos, mode, pb, kmask, key0, val0, nc);
+    early.reset();
     bool alt = false;
     const uint64_t *key;
     uint64_t *val;

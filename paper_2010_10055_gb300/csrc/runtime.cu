@@ -217,6 +217,7 @@ static Tunable g_tunables[] = {
     // defaults: the autotuner's choice on a GB300 for the bacterial-scale read set
     {"bloom_bits", 8, 2, 32},             // bits of the first Bloom filter per window
     {"bloom_slice_mb", 64, 1, 1 << 20},   // B1 megabytes updated per Bloom launch
+    {"bloom_max_slices", 8, 1, 1024},     // at most this many Bloom launches (slices grow beyond)
     {"bloom_unroll", 4, 4, 8},            // windows (atomics in flight) per thread per Bloom step: 4 or 8
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
     {"num_guess_shift", 2, 0, 8},         // fused numeric table guess = products >> shift
