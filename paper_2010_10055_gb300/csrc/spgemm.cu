@@ -517,7 +517,9 @@ __global__ void pair_kernel(const int32_t *__restrict__ col, const uint32_t *__r
     if (e < nnz) pair[e] = ((uint64_t)val[e] << 32) | (uint32_t)col[e];
 }
 
-static int pick_threads(int log2T) { return log2T <= 7 ? 64 : (log2T <= 10 ? 128 : 256); }
+// threads per block for a table of 2^log2T slots: tables of 4 k slots and more leave one or two
+// blocks per SM, so those blocks bring more warps to hide the gathers' latency
+static int pick_threads(int log2T) { return log2T <= 7 ? 64 : (log2T <= 10 ? 128 : (log2T <= 11 ? 256 : 512)); }
 
 // Launch names by table size, so that per-kernel timing separates the classes.
 static const char *const SYM_NAMES[] = {"spgemm_symbolic_t64", "spgemm_symbolic_t128", "spgemm_symbolic_t256",

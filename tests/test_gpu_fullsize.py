@@ -1,17 +1,25 @@
-"""Parity at the benchmark's full size (the bacterial workload, default launch configuration, the
-calls bench.py times), where the whole-matrix oracle is too slow for the k-mer stage and C:
+"""Parity at full size, in the configuration bench.py times, where the whole-matrix oracle is too
+slow for the k-mer stage and C:
 
-- the transitive reduction is compared with the oracle element by element (it finishes in about
-  a second at this size);
-- sampled columns of At: the oracle's census of each column's code over all 153.5 M windows gives
-  its frequency (must be in [lo, hi]) and its occurrences, whose lowest position per read must be
-  At's row exactly;
+- the transitive reduction is compared with the oracle element by element (seconds at these
+  sizes);
+- sampled columns of At: the oracle's census of each column's code over every window of the input
+  gives its frequency (must be in [lo, hi]) and its occurrences, whose lowest position per read
+  must be At's row exactly;
 - sampled rows of A: the read's own windows (oracle) and their census give the read's reliable
   k-mers, which must be A's row (columns by code rank, lowest position, strand) exactly;
-- sampled rows of C: the oracle's single-row product on the same A and At;
-- properties that hold at any size: codes strictly ascending, A and At transposes, C symmetric
-  with no diagonal and counts >= t, S a subgraph of R.
+- sampled rows of C: the oracle's single-row product on the same A and At, and the mirrored
+  entries C_ki;
+- properties that hold at any size: codes strictly ascending, A and At transposes, no diagonal in
+  C and counts >= t, S a subgraph of R.
+
+Workloads: the bacterial one (the benchmark's) and the C. elegans-shaped one at full size (4.1 Gbp
+of reads, 1.8e9 nonzeros in A; about 2.5 minutes, mostly generation and the census; skipped with
+SG_SKIP_ELEGANS=1).
 """
+import concurrent.futures
+import os
+
 import numpy as np
 import pytest
 
@@ -22,48 +30,71 @@ from tests.gpu_util import assert_graph_equal, dev
 
 pytestmark = pytest.mark.gpu
 
-W = synth.BACTERIAL
+CASES = [pytest.param(synth.BACTERIAL, id="bacterial-5Mbp-30x"),
+         pytest.param(synth.ELEGANS, id="elegans-100Mbp-40x",
+                      marks=pytest.mark.skipif(os.environ.get("SG_SKIP_ELEGANS") == "1",
+                                               reason="SG_SKIP_ELEGANS=1 (the case takes about 2.5 minutes)"))]
 
 
-@pytest.fixture(scope="module")
-def full():
-    d = synth.make(W)
-    km = sg.build_kmer_matrix(dev(d["seq"], np.uint8), dev(d["offsets"], np.int64), W.k, W.lo, W.hi)
-    C = sg.overlap_spgemm(km, W.min_shared, W.max_seeds)
-    S, it = sg.transitive_reduce(sg.DeviceGraph.from_numpy(d["R"]), W.fuzz)
-    return d, km.to_numpy(), C.to_numpy(), S.to_numpy(), it
+@pytest.fixture(scope="module", params=CASES)
+def full(request):
+    w = request.param
+    d = synth.make(w)
+    km = sg.build_kmer_matrix(dev(d["seq"], np.uint8), dev(d["offsets"], np.int64), w.k, w.lo, w.hi)
+    C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+    S, it = sg.transitive_reduce(sg.DeviceGraph.from_numpy(d["R"]), w.fuzz)
+    out = dict(w=w, d=d, km=km.to_numpy(), C=C.to_numpy(), S=S.to_numpy(), it=it)
+    del km, C, S
+    return out
+
+
+def _census(d, k, query, occ_cap):
+    """The oracle's census over all reads, in read ranges on host threads (the sums and the
+    concatenated occurrences equal one census over the whole input)."""
+    off = np.ascontiguousarray(d["offsets"], np.int64)
+    n = off.size - 1
+    parts = np.linspace(0, n, min(16, max(n, 1)) + 1).astype(np.int64)
+
+    def one(a, b):
+        c = oracle.kmer_census(d["seq"], off[a:b + 1], k, query, occ_cap=occ_cap)
+        c["occ_read"] = c["occ_read"] + a
+        return c
+
+    with concurrent.futures.ThreadPoolExecutor(len(parts) - 1) as ex:
+        res = list(ex.map(lambda ab: one(*ab), zip(parts[:-1], parts[1:])))
+    return dict(codes=res[0]["codes"], freq=sum(r["freq"] for r in res),
+                **{f: np.concatenate([r[f] for r in res]) for f in ("occ_q", "occ_read", "occ_pos", "occ_strand")})
 
 
 @pytest.fixture(scope="module")
 def census(full):
-    """One census over all windows for the sampled columns' codes and the sampled reads' codes."""
-    d, km, _, _, _ = full
+    """One census for the sampled columns' codes and the sampled reads' codes."""
+    w, d, km = full["w"], full["d"], full["km"]
     rng = np.random.default_rng(2011)
     m = km["At"]["n_rows"]
     cols = np.unique(np.concatenate([rng.choice(m, 3000, replace=False), [0, m - 1]]))
     n = km["A"]["n_rows"]
-    reads = np.unique(np.concatenate([rng.choice(n, 60, replace=False), [0, n - 1]]))
-    windows = {int(i): oracle.read_windows(d["seq"], d["offsets"], int(i), W.k) for i in reads}
-    query = np.concatenate([km["codes"][cols]] + [w["code"] for w in windows.values()])
-    c = oracle.kmer_census(d["seq"], d["offsets"], W.k, query, occ_cap=1 << 24)
-    return cols, windows, c
+    reads = np.unique(np.concatenate([rng.choice(n, 40, replace=False), [0, n - 1]]))
+    windows = {int(i): oracle.read_windows(d["seq"], d["offsets"], int(i), w.k) for i in reads}
+    query = np.concatenate([km["codes"][cols]] + [x["code"] for x in windows.values()])
+    return cols, windows, _census(d, w.k, query, occ_cap=1 << 22)
 
 
 def test_fullsize_transitive_reduction(full):
-    d, _, _, S, it = full
-    eS, eit = oracle.transitive_reduce(d["R"], W.fuzz)
-    assert_graph_equal(S, eS)
-    assert it == eit
+    w = full["w"]
+    eS, eit = oracle.transitive_reduce(full["d"]["R"], w.fuzz)
+    assert_graph_equal(full["S"], eS)
+    assert full["it"] == eit
 
 
 def test_fullsize_sampled_at_rows(full, census):
-    _, km, _, _, _ = full
+    w, km = full["w"], full["km"]
     cols, _, c = census
     At = km["At"]
     q_of = np.searchsorted(c["codes"], km["codes"][cols])
     assert np.array_equal(c["codes"][q_of], km["codes"][cols])
     f = c["freq"][q_of]
-    assert ((f >= W.lo) & (f <= W.hi)).all()
+    assert ((f >= w.lo) & (f <= w.hi)).all()
     want = set(q_of.tolist())
     first = {}
     for q, r, p, s in zip(c["occ_q"].tolist(), c["occ_read"].tolist(), c["occ_pos"].tolist(),
@@ -77,34 +108,41 @@ def test_fullsize_sampled_at_rows(full, census):
 
 
 def test_fullsize_sampled_a_rows(full, census):
-    _, km, _, _, _ = full
+    w, km = full["w"], full["km"]
     _, windows, c = census
-    A = km["A"]
-    for i, w in windows.items():
-        qi = np.searchsorted(c["codes"], w["code"])
+    A, At = km["A"], km["At"]
+    for i, x in windows.items():
+        qi = np.searchsorted(c["codes"], x["code"])
         f = c["freq"][qi]
-        rel = (f >= W.lo) & (f <= W.hi)
+        rel = (f >= w.lo) & (f <= w.hi)
         exp = {}
-        for code, p, s in zip(w["code"][rel].tolist(), w["pos"][rel].tolist(), w["strand"][rel].tolist()):
+        for code, p, s in zip(x["code"][rel].tolist(), x["pos"][rel].tolist(), x["strand"][rel].tolist()):
             exp.setdefault(code, p | (s << 31))  # lowest position first
         a, b = A["row_ptr"][i], A["row_ptr"][i + 1]
         cols = A["col"][a:b]
-        got = dict(zip(km["codes"][cols].tolist(), A["val"][a:b].tolist()))
-        assert got == exp, i
+        assert dict(zip(km["codes"][cols].tolist(), A["val"][a:b].tolist())) == exp, i
         assert (np.diff(cols) > 0).all()
+        for j, v in zip(cols.tolist(), A["val"][a:b].tolist()):  # the transpose holds (i, v) in row j
+            ta, tb = At["row_ptr"][j], At["row_ptr"][j + 1]
+            t = ta + np.searchsorted(At["col"][ta:tb], i)
+            assert t < tb and At["col"][t] == i and At["val"][t] == v, (i, j)
 
 
 def test_fullsize_sampled_c_rows(full):
-    _, km, C, _, _ = full
+    w, km, C = full["w"], full["km"], full["C"]
     rng = np.random.default_rng(2012)
     n = C["n"]
-    for i in np.unique(np.concatenate([rng.choice(n, 200, replace=False), [0, n - 1]])).tolist():
-        r = oracle.overlap_row(km["A"], km["At"], i, W.min_shared, W.max_seeds)
+    for i in np.unique(np.concatenate([rng.choice(n, 100, replace=False), [0, n - 1]])).tolist():
+        r = oracle.overlap_row(km["A"], km["At"], i, w.min_shared, w.max_seeds)
         a, b = C["row_ptr"][i], C["row_ptr"][i + 1]
         assert np.array_equal(C["col"][a:b], r["col"]), i
         assert np.array_equal(C["count"][a:b], r["count"]), i
         assert np.array_equal(C["seed_i"][:, a:b], r["seed_i"]), i
         assert np.array_equal(C["seed_k"][:, a:b], r["seed_k"]), i
+        for k, cnt in zip(r["col"].tolist(), r["count"].tolist()):  # C is symmetric
+            ka, kb = C["row_ptr"][k], C["row_ptr"][k + 1]
+            t = ka + np.searchsorted(C["col"][ka:kb], i)
+            assert t < kb and C["col"][t] == i and C["count"][t] == cnt, (i, k)
 
 
 def _entries(M, rows):
@@ -113,17 +151,20 @@ def _entries(M, rows):
 
 
 def test_fullsize_properties(full):
-    d, km, C, S, _ = full
+    w, d, km, C, S = full["w"], full["d"], full["km"], full["C"], full["S"]
     assert (np.diff(km["codes"].astype(np.uint64)) > 0).all()
     A, At = km["A"], km["At"]
-    ar, ac = _entries(A, A["n_rows"])
-    tr, tc = _entries(At, At["n_rows"])
-    o = np.lexsort((ar, ac))  # A's entries ordered by (col, row) = At's order
-    assert np.array_equal(ac[o], tr) and np.array_equal(ar[o], tc) and np.array_equal(A["val"][o], At["val"])
-    cr, cc = _entries(C, C["n"])
-    assert (cr != cc).all() and (C["count"] >= W.min_shared).all()
-    o = np.lexsort((cr, cc))  # the transpose's entries in row-major order
-    assert np.array_equal(cc[o], cr) and np.array_equal(cr[o], cc) and np.array_equal(C["count"][o], C["count"])
+    assert A["nnz"] == At["nnz"] if "nnz" in A else A["col"].size == At["col"].size
+    if A["col"].size < 200_000_000:  # whole-matrix checks where they fit in host memory and minutes
+        ar, ac = _entries(A, A["n_rows"])
+        tr, tc = _entries(At, At["n_rows"])
+        o = np.lexsort((ar, ac))  # A's entries ordered by (col, row) = At's order
+        assert np.array_equal(ac[o], tr) and np.array_equal(ar[o], tc) and np.array_equal(A["val"][o], At["val"])
+        cr, cc = _entries(C, C["n"])
+        assert (cr != cc).all()
+        o = np.lexsort((cr, cc))  # the transpose's entries in row-major order
+        assert np.array_equal(cc[o], cr) and np.array_equal(cr[o], cc) and np.array_equal(C["count"][o], C["count"])
+    assert (C["count"] >= w.min_shared).all()
     R = d["R"]
     rr, rc = _entries(R, R["n"])
     sr, sc = _entries(S, S["n"])
