@@ -77,6 +77,8 @@ def _load():
         lib.sgo_overlap_row.restype = ctypes.c_int
         lib.sgo_overlap_row.argtypes = [ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), i64, u32, i32, vp, vp, vp, vp,
                                         ctypes.POINTER(i64)]
+        lib.sgo_graph_from_seeds.restype = ctypes.c_int
+        lib.sgo_graph_from_seeds.argtypes = [ctypes.POINTER(_Overlap), vp, i32, i64, ctypes.POINTER(_Graph)]
         lib.sgo_free.argtypes = [vp]
         _lib = lib
     return _lib
@@ -232,3 +234,23 @@ def overlap_row(A: dict, At: dict, i: int, min_shared: int = 2, max_seeds: int =
     m = int(e.value)
     return dict(col=col[:m], count=cnt[:m], seed_i=si[:m * S].reshape(m, S).T.copy(),
                 seed_k=sk[:m * S].reshape(m, S).T.copy())
+
+
+def graph_from_seeds(C: dict, offsets, k: int, min_overlap: int) -> dict:
+    """R estimated from C's first seeds (see sgo_graph_from_seeds): dict(n, row_ptr, col, suffix, dir)."""
+    lib = _load()
+    o = np.ascontiguousarray(offsets, np.int64)
+    nnz = int(C["col"].size)
+    arrs = (np.ascontiguousarray(C["row_ptr"], np.int64), np.ascontiguousarray(C["col"], np.int32),
+            np.ascontiguousarray(C["count"], np.uint32),
+            np.ascontiguousarray(np.asarray(C["seed_i"], np.uint32).reshape(-1)),
+            np.ascontiguousarray(np.asarray(C["seed_k"], np.uint32).reshape(-1)))
+    S = np.asarray(C["seed_i"]).shape[0]  # seeds are [S, nnz], slot-major
+    c = _Overlap(int(C["n"]), nnz, int(S), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                 arrs[3].ctypes.data, arrs[4].ctypes.data)
+    R = _Graph()
+    _check(lib.sgo_graph_from_seeds(ctypes.byref(c), o.ctypes.data, int(k), int(min_overlap), ctypes.byref(R)),
+           "graph_from_seeds")
+    e = int(R.nnz)
+    return dict(n=int(R.n), row_ptr=_take(lib, R.row_ptr, R.n + 1, np.int64), col=_take(lib, R.col, e, np.int32),
+                suffix=_take(lib, R.suffix, e, np.uint32), dir=_take(lib, R.dir, e, np.uint8))

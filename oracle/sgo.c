@@ -15,6 +15,8 @@
  *                             Sec. II / IV-E), evaluated on the pattern of R
  *   sgo_transitive_reduce  -- Algorithm 1 (Reduce/Apply/DimApply, M >= N, R o not I, until
  *                             nnz(R) stops changing)
+ *   sgo_graph_from_seeds   -- R estimated from C's first seeds (overlap interval, containment,
+ *                             suffix and dir), the alignment's role in Algorithm 2
  *   sgo_kmer_census, sgo_read_windows, sgo_overlap_row -- single outputs of the same definitions
  *                             (a k-mer's frequency and occurrences, a read's windows, one row of
  *                             C), for sampled checks at sizes where the whole oracle is too slow
@@ -519,5 +521,67 @@ int sgo_overlap_row(const sgo_csr *A, const sgo_csr *At, int64_t i, uint32_t min
     }
     *nnz = e;
     free(cnt); free(si); free(sk); free(touched);
+    return SGO_OK;
+}
+
+/* ============================================================ R from C's seeds */
+
+/*
+ * Overlap graph R estimated from C (the alignment's role in Algorithm 2, read from the seeds):
+ * entry C_ik's first seed (the shared k-mer with the smallest column, Sec. IV-D) places read k in
+ * read i's frame. With s_i, s_k the k-mer's positions and rc = strand_i xor strand_k, read k
+ * starts at  o = s_i - s_k  (same orientation)  or  o = s_i - (L_k - s_k - K)  (rc = 1; K = k-mer
+ * length), so in i's frame i = [0, L_i) and k = [o, o + L_k). The pair is an edge iff the overlap
+ * is at least min_overlap and neither interval contains the other (contained overlaps are not part
+ * of R, Sec. IV-D; equal starts count as contained). With read i forward and read k in orientation
+ * rc, the bidirected edge follows the rule of the coordinate-built R (the read that starts first is
+ * a, the other b; R_ab = (e_b - e_a, 2 s_a + s_b), R_ba = (s_b - s_a, 2 (1 - s_b) + (1 - s_a))),
+ * of which row i keeps R_ik:
+ *   o > 0:  R_ik = (o + L_k - L_i, rc)
+ *   o < 0:  R_ik = (-o, 2 + 1 - rc)
+ * R has C's row order (ascending k).
+ */
+int sgo_graph_from_seeds(const sgo_overlap *C, const int64_t *offsets, int32_t K, int64_t min_overlap,
+                         sgo_graph *R) {
+    memset(R, 0, sizeof(*R));
+    if (C->max_seeds < 1 || K < 1 || min_overlap < 1) return SGO_INVALID;
+    int64_t n = C->n, nnz = C->nnz;
+    R->row_ptr = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+    R->col = (int32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t));
+    R->suffix = (uint32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint32_t));
+    R->dir = (uint8_t *)malloc((size_t)(nnz ? nnz : 1));
+    if (!R->row_ptr || !R->col || !R->suffix || !R->dir) {
+        free(R->row_ptr); free(R->col); free(R->suffix); free(R->dir);
+        memset(R, 0, sizeof(*R));
+        return SGO_OOM;
+    }
+    int64_t e = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t Li = offsets[i + 1] - offsets[i];
+        for (int64_t x = C->row_ptr[i]; x < C->row_ptr[i + 1]; x++) {
+            int64_t k = C->col[x];
+            int64_t Lk = offsets[k + 1] - offsets[k];
+            int64_t si = C->seed_i[x] & 0x7FFFFFFF;       /* seed slot 0 */
+            int64_t sk = C->seed_k[x] & 0x7FFFFFFF;
+            int rc = (int)(C->seed_k[x] >> 31);
+            int64_t o = rc ? si - (Lk - sk - K) : si - sk;
+            int64_t lo = o > 0 ? o : 0, hi = (o + Lk < Li) ? o + Lk : Li;
+            if (hi - lo < min_overlap) continue;
+            if (o >= 0 && o + Lk <= Li) continue;         /* k within i (equal starts included) */
+            if (o <= 0 && o + Lk >= Li) continue;         /* i within k */
+            R->col[e] = (int32_t)k;
+            if (o > 0) {
+                R->suffix[e] = (uint32_t)(o + Lk - Li);
+                R->dir[e] = (uint8_t)rc;
+            } else {
+                R->suffix[e] = (uint32_t)(-o);
+                R->dir[e] = (uint8_t)(2 + 1 - rc);
+            }
+            e++;
+        }
+        R->row_ptr[i + 1] = e;
+    }
+    R->n = n;
+    R->nnz = e;
     return SGO_OK;
 }
