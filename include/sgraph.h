@@ -165,6 +165,28 @@ sg_status sg_minplus_square_noalloc(const sg_graph_csr *R, int32_t mode, uint32_
                                     sg_stream_t stream);
 
 /*
+ * The overlap graph R estimated from C's seeds: the role the alignment plays between C and R in
+ * Algorithm 2 (Sec. IV-D), read from the positions C keeps. Entry C_ik's first seed (slot 0, the
+ * shared k-mer with the smallest column) places read k in read i's frame: with s_i, s_k the
+ * k-mer's positions and rc = strand_i xor strand_k (bit 31 of seed_k),
+ *     o = s_i - s_k  (rc = 0)      o = s_i - (L_k - s_k - k)  (rc = 1),
+ * so i spans [0, L_i) and k spans [o, o + L_k). The pair is an edge iff the overlap is at least
+ * min_overlap bases and neither interval contains the other (contained overlaps are not part of R;
+ * equal starts count as contained). Row i keeps R_ik = (o + L_k - L_i, rc) if o > 0 and
+ * (-o, 3 - rc) if o < 0: the bidirected rule (suffix = overhang of the walk's second read; dir bit
+ * 1 = orientation of the walk's first read, bit 0 = of its second) with read i forward.
+ *   C          as produced by sg_overlap_spgemm (device arrays), max_seeds >= 1.
+ *   d_offsets  the reads' offsets (device, n + 1 entries; L_i = d_offsets[i + 1] - d_offsets[i]).
+ *   k          the k-mer length C was built with.
+ * Output *R (library-owned device arrays, release with sg_free_graph) has C's row order; it can be
+ * passed to sg_transitive_reduce (suffixes stay below 2^30 for reads shorter than 2^30).
+ * Errors: SG_ERR_INVALID (bad arguments; a column of C outside [0, n)), SG_ERR_OOM, SG_ERR_CUDA.
+ * Synchronises once (R's size).
+ */
+sg_status sg_overlap_graph_from_seeds(const sg_overlap_csr *C, const int64_t *d_offsets, int32_t k,
+                                      uint32_t min_overlap, sg_graph_csr *R, sg_stream_t stream);
+
+/*
  * Algorithm 1: repeat { N = R^2 (Algorithm 3); v = rowmax(R) + fuzz; I = (v_i >= N_ik, with the
  * end-orientation rule); R = R minus I } until nnz(R) stops changing; S = R.
  *   fuzz        < 2^30 (the scalar x of Sec. IV-E).

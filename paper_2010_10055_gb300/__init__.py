@@ -24,7 +24,7 @@ DIRMATCH, LITERAL = 0, 1
 INF = 0xFFFFFFFF
 
 EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",
-           "sg_transitive_reduce_rounds",
+           "sg_transitive_reduce_rounds", "sg_overlap_graph_from_seeds",
            "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy", "sg_run_batch", "sg_free_batch",
            "sg_server_create", "sg_server_submit", "sg_server_poll", "sg_server_wait", "sg_job_result_free",
            "sg_server_destroy", "sg_server_cancel",
@@ -150,6 +150,9 @@ def lib():
         L.sg_transitive_reduce.restype = ctypes.c_int
         L.sg_transitive_reduce.argtypes = [ctypes.POINTER(GraphCsr), u32, i32, ctypes.POINTER(GraphCsr),
                                            ctypes.POINTER(i32), vp]
+        L.sg_overlap_graph_from_seeds.restype = ctypes.c_int
+        L.sg_overlap_graph_from_seeds.argtypes = [ctypes.POINTER(OverlapCsr), vp, i32, u32,
+                                                  ctypes.POINTER(GraphCsr), vp]
         L.sg_transitive_reduce_rounds.restype = ctypes.c_int
         L.sg_transitive_reduce_rounds.argtypes = [ctypes.POINTER(GraphCsr), u32, i32, i32, ctypes.POINTER(GraphCsr),
                                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), vp]
@@ -424,6 +427,17 @@ def transitive_reduce(R, fuzz: int = 0, mode: int = DIRMATCH, stream=None):
     _check(L.sg_transitive_reduce(ctypes.byref(_graph_struct(R)), int(fuzz), int(mode), ctypes.byref(S),
                                   ctypes.byref(it), st), "transitive_reduce")
     return Graph(S, st), int(it.value)
+
+
+def overlap_graph_from_seeds(C: "Overlap", offsets, k: int = 17, min_overlap: int = 1000, stream=None) -> "Graph":
+    """R estimated from C's first seeds (see sg_overlap_graph_from_seeds). offsets: int64 CUDA
+    tensor [n+1] of the reads C was built from."""
+    L = lib()
+    st = _stream(stream)
+    R = GraphCsr()
+    _check(L.sg_overlap_graph_from_seeds(ctypes.byref(C.s), _ptr(offsets), int(k), int(min_overlap), ctypes.byref(R),
+                                         st), "overlap_graph_from_seeds")
+    return Graph(R, st)
 
 
 def transitive_reduce_rounds(R, fuzz: int = 0, max_rounds: int = 1, mode: int = DIRMATCH, stream=None):

@@ -40,11 +40,12 @@ CASES = [pytest.param(synth.BACTERIAL, id="bacterial-5Mbp-30x"),
 def full(request):
     w = request.param
     d = synth.make(w)
-    km = sg.build_kmer_matrix(dev(d["seq"], np.uint8), dev(d["offsets"], np.int64), w.k, w.lo, w.hi)
+    off = dev(d["offsets"], np.int64)
+    km = sg.build_kmer_matrix(dev(d["seq"], np.uint8), off, w.k, w.lo, w.hi)
     C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
     S, it = sg.transitive_reduce(sg.DeviceGraph.from_numpy(d["R"]), w.fuzz)
-    out = dict(w=w, d=d, km=km.to_numpy(), C=C.to_numpy(), S=S.to_numpy(), it=it)
-    del km, C, S
+    out = dict(w=w, d=d, km=km.to_numpy(), C=C.to_numpy(), S=S.to_numpy(), it=it, C_dev=C, off_dev=off)
+    del km, S
     return out
 
 
@@ -143,6 +144,14 @@ def test_fullsize_sampled_c_rows(full):
             ka, kb = C["row_ptr"][k], C["row_ptr"][k + 1]
             t = ka + np.searchsorted(C["col"][ka:kb], i)
             assert t < kb and C["col"][t] == i and C["count"][t] == cnt, (i, k)
+
+
+def test_fullsize_graph_from_seeds(full):
+    """R estimated from C's seeds, element by element against the oracle on the same C."""
+    w, d, C = full["w"], full["d"], full["C"]
+    exp = oracle.graph_from_seeds(C, d["offsets"], w.k, w.min_overlap)
+    got = sg.overlap_graph_from_seeds(full["C_dev"], full["off_dev"], w.k, w.min_overlap).to_numpy()
+    assert_graph_equal(got, exp)
 
 
 def _entries(M, rows):

@@ -233,3 +233,49 @@ def test_host_pipeline_matches_oracle():
     out = hp.run(d["seq"], d["offsets"], w)
     assert_overlap_equal(out["C"], eC) and "S" not in out
     hp.close()
+
+
+# --------------------------------------------------------------------- R from C's seeds
+@pytest.mark.parametrize("workload,scale,min_ov", [("tiny", 1.0, 200), ("bacterial", 0.02, 1000)])
+def test_graph_from_seeds_matches_oracle_and_reduces(workload, scale, min_ov):
+    w = synth.TINY if workload == "tiny" else synth.BACTERIAL.scaled(scale)
+    d = synth.make(w, with_graph=False)
+    ekm = oracle.build_kmer_matrix(d["seq"], d["offsets"], w.k, w.lo, w.hi)
+    eC = oracle.overlap_spgemm(ekm["A"], ekm["At"], w.min_shared, w.max_seeds)
+    eR = oracle.graph_from_seeds(eC, d["offsets"], w.k, min_ov)
+    off = dev(d["offsets"], np.int64)
+    km = sg.build_kmer_matrix(dev(d["seq"], np.uint8), off, w.k, w.lo, w.hi)
+    C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+    R = sg.overlap_graph_from_seeds(C, off, w.k, min_ov)
+    assert_graph_equal(R.to_numpy(), eR)
+    # reads -> A -> C -> R -> S without true coordinates
+    S, it = sg.transitive_reduce(R, fuzz=w.fuzz)
+    eS, eit = oracle.transitive_reduce(eR, w.fuzz)
+    assert_graph_equal(S.to_numpy(), eS)
+    assert it == eit
+
+
+def test_graph_from_seeds_closed_form_error_free():
+    from tests.test_oracle_overlap import _repeat_free_genome
+    g, _ = _repeat_free_genome(20000, 17, 105)
+    rd = synth.reads(g, 10.0, 2000.0, 500.0, 34, 0.0, 0.0, 0.0, 106)
+    off = dev(rd["offsets"], np.int64)
+    km = sg.build_kmer_matrix(dev(rd["seq"], np.uint8), off, 17, 1, 1 << 30)
+    C = sg.overlap_spgemm(km, 2, 1)
+    R = sg.overlap_graph_from_seeds(C, off, 17, 500).to_numpy()
+    T = synth.overlap_graph(rd["start"], rd["end"], rd["strand"], 500)
+    assert R["col"].size > 50
+    assert_graph_equal(R, T)
+
+
+def test_graph_from_seeds_invalid():
+    d = synth.make(synth.TINY, with_graph=False)
+    off = dev(d["offsets"], np.int64)
+    km = sg.build_kmer_matrix(dev(d["seq"], np.uint8), off, 17, 2, 8)
+    C0 = sg.overlap_spgemm(km, 2, 0)  # no seeds kept
+    with pytest.raises(sg.SgError) as e:
+        sg.overlap_graph_from_seeds(C0, off, 17, 100)
+    assert e.value.status == sg.SG_ERR_INVALID
+    C = sg.overlap_spgemm(km, 2, 2)
+    with pytest.raises(sg.SgError):
+        sg.overlap_graph_from_seeds(C, off, 16, 100)  # even k
