@@ -287,6 +287,9 @@ def main():
     kernels = {k: {"launches": c, "ms": ms, "share": ms / ktot}
                for k, (c, ms) in sorted(breakdown.items(), key=lambda kv: -kv[1][1])}
 
+    # ---- the chain without true coordinates: C -> R from C's seeds -> S (one untimed pass)
+    from_seeds = measure_from_seeds(sg, seq, off, w)
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -303,7 +306,7 @@ def main():
             "tr_edges_per_s": edges_all * args.steps / (tr_ms_max / 1e3) if tr_ms_max else None,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
             "e2e": e2e, "roofline": roof, "kernels": kernels, "stages": stages, "clocks": clk,
-            "gpu_launches": launches}
+            "gpu_launches": launches, "from_seeds": from_seeds}
     if not args.no_forms:
         line["batched"] = measure_batched(sg, 512, 200e3)
         line["served"] = measure_served(sg, 400, 200.0)
@@ -445,6 +448,26 @@ def measure_served(sg, n_jobs: int, rate: float) -> dict:
             "saturated": {"jobs_per_s": n_jobs / span_b, "p50_ms": float(np.percentile(lat_b, 50)),
                           "p99_ms": float(np.percentile(lat_b, 99)), "mean_batch": mb_b},
             "plain_one_at_a_time_jobs_per_s": n_jobs / plain_s}
+
+
+def measure_from_seeds(sg, seq, off, w) -> dict:
+    """reads -> A -> C -> R estimated from C's seeds -> S: the overlap graph comes from the seeds
+    instead of true coordinates (min_overlap as the coordinate-built R). CUDA-event times of the
+    graph estimate and of the reduction on it, after one warm-up."""
+    import torch
+
+    km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+    C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for rep in range(2):
+        ev[0].record()
+        R = sg.overlap_graph_from_seeds(C, off, w.k, w.min_overlap)
+        ev[1].record()
+        S, it = sg.transitive_reduce(R, w.fuzz)
+        ev[2].record()
+        torch.cuda.synchronize()
+    return {"min_overlap": w.min_overlap, "nnz_R": R.nnz, "nnz_S": S.nnz, "tr_rounds": it,
+            "graph_ms": ev[0].elapsed_time(ev[1]), "tr_ms": ev[1].elapsed_time(ev[2])}
 
 
 def cpu_baseline(w, scale: float):
