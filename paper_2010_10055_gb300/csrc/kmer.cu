@@ -290,13 +290,20 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint64_t *__res
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
     uint32_t mine = 0, c = 0;
-#pragma unroll 4
-    for (int g = 0; g < KM_GW; g++) {
-        const int64_t q = (g0 + g) * 32 + lane;
-        const uint64_t x = q < total ? __ldcs(wc + q) : WC_NONE;
-        const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(x, b2, use_bloom, kmask));
-        if (lane == g) mine = m;
-        c += __popc(m);
+    constexpr int CC_U = 8;  // groups whose codes (and then filter words) are loaded together
+    for (int g0u = 0; g0u < KM_GW; g0u += CC_U) {
+        uint64_t x[CC_U];
+#pragma unroll
+        for (int u = 0; u < CC_U; u++) {
+            const int64_t q = (g0 + g0u + u) * 32 + lane;
+            x[u] = q < total ? __ldcs(wc + q) : WC_NONE;
+        }
+#pragma unroll
+        for (int u = 0; u < CC_U; u++) {
+            const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(x[u], b2, use_bloom, kmask));
+            if (lane == g0u + u) mine = m;
+            c += __popc(m);
+        }
     }
     cmask[g0 + lane] = mine;
     if (lane == 0) wcnt[(int64_t)blockIdx.x * KM_WARPS + w] = c;
@@ -340,9 +347,29 @@ __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__rest
     }
 }
 
-__device__ __forceinline__ uint64_t resolve_pos(uint64_t v, const int64_t *__restrict__ off, int64_t n) {
-    const int64_t q = (int64_t)(v & ~WC_STRAND);
+// Read lookup: lut[b] = the read containing base b << LUT_SHIFT (the last r with off[r] <= it), so
+// that finding a position's read is a binary search over the few reads of one bucket.
+constexpr int LUT_SHIFT = 12;
+
+__global__ void read_lut_kernel(const int64_t *__restrict__ off, int64_t n, int64_t nb, int32_t *__restrict__ lut) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int64_t q = b << LUT_SHIFT;
     int64_t lo = 0, hi = n;  // last read r with off[r] <= q
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= q) lo = mid; else hi = mid;
+    }
+    lut[b] = (int32_t)lo;
+}
+
+// v = q | strand << 63  ->  read << 32 | pos | strand << 31
+__device__ __forceinline__ uint64_t resolve_pos(uint64_t v, const int64_t *__restrict__ off, int64_t n,
+                                                const int32_t *__restrict__ lut, int64_t nb) {
+    const int64_t q = (int64_t)(v & ~WC_STRAND);
+    const int64_t b = q >> LUT_SHIFT;
+    int64_t lo = lut[b], hi = b + 1 < nb ? (int64_t)lut[b + 1] + 1 : n;  // the read lies in [lo, hi)
+    if (hi > n) hi = n;
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) >> 1;
         if (off[mid] <= q) lo = mid; else hi = mid;
@@ -353,32 +380,26 @@ __device__ __forceinline__ uint64_t resolve_pos(uint64_t v, const int64_t *__res
 // After a keys-only sort (PK_POS, PK_IDX): the code, and the window resolved to its read.
 __global__ void unpack_kernel(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ vals, int64_t nc,
                               int mode, int pb, const int64_t *__restrict__ off, int64_t n,
-                              uint64_t *__restrict__ key, uint64_t *__restrict__ val) {
+                              const int32_t *__restrict__ lut, int64_t nb, uint64_t *__restrict__ key,
+                              uint64_t *__restrict__ val) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const uint64_t p = packed[i];
     const uint64_t low = p & ((1ull << pb) - 1);
     key[i] = p >> pb;
     if (mode == PK_POS) {
-        val[i] = resolve_pos((low >> 1) | (low << 63), off, n);
+        val[i] = resolve_pos((low >> 1) | (low << 63), off, n, lut, nb);
     } else if (SG_IN_BOUNDS((int64_t)low < nc, 103, low)) {
-        val[i] = resolve_pos(vals[low], off, n);
+        val[i] = resolve_pos(vals[low], off, n, lut, nb);
     }
 }
 
 // After the pairs sort: val = q | strand << 63  ->  read << 32 | pos | strand << 31.
-__global__ void resolve_kernel(uint64_t *__restrict__ val, int64_t nc, const int64_t *__restrict__ off,
-                               int64_t n) {
+__global__ void resolve_kernel(uint64_t *__restrict__ val, int64_t nc, const int64_t *__restrict__ off, int64_t n,
+                               const int32_t *__restrict__ lut, int64_t nb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
-    const uint64_t v = val[i];
-    const int64_t q = (int64_t)(v & ~WC_STRAND);
-    int64_t lo = 0, hi = n;  // last read r with off[r] <= q
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (off[mid] <= q) lo = mid; else hi = mid;
-    }
-    val[i] = ((uint64_t)lo << 32) | (uint64_t)(uint32_t)(q - off[lo]) | ((v >> 63) << 31);
+    val[i] = resolve_pos(val[i], off, n, lut, nb);
 }
 
 __global__ void validate_offsets_kernel(const int64_t *__restrict__ off, int64_t n, int64_t total,
@@ -678,18 +699,23 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     bool alt = false;
     const uint64_t *key;
     uint64_t *val;
+    const int64_t nlut = (total >> LUT_SHIFT) + 1;
+    int32_t *lut = sc.get<int32_t>(nlut);
+    if (!lut) return SG_ERR_OOM;
+    SG_LAUNCH("read_lut", read_lut_kernel, blocks_for(nlut, NT), NT, 0, s, off, n, nlut, lut);
     if (mode != PK_PAIRS) {  // 8-byte keys through the radix passes, then one unpacking pass
         SG_TRY(radix_sort_keys(key0, key1, nc, pb, pb + code_bits, &alt, s, err));
         uint64_t *ks = alt ? key1 : key0, *kfree = alt ? key0 : key1;
         SG_LAUNCH("unpack", unpack_kernel, blocks_for(nc, NT), NT, 0, s, (const uint64_t *)ks, (const uint64_t *)val0,
-                  nc, mode, pb, off, n, kfree, val1);
+                  nc, mode, pb, off, n, (const int32_t *)lut, nlut, kfree, val1);
         key = kfree;
         val = val1;
     } else {
         SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, code_bits, &alt, s, err)));
         key = alt ? key1 : key0;
         val = alt ? val1 : val0;
-        SG_LAUNCH("resolve", resolve_kernel, blocks_for(nc, NT), NT, 0, s, val, nc, off, n);
+        SG_LAUNCH("resolve", resolve_kernel, blocks_for(nc, NT), NT, 0, s, val, nc, off, n, (const int32_t *)lut,
+                  nlut);
     }
 
     // segments -> exact frequency -> reliable -> columns; kept entries -> At
