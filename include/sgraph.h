@@ -395,6 +395,17 @@ void sg_debug_stall_lookback(int on);
  * and skipped since the last call, as site << 40 | index, or 0. Always 0 in normal builds. */
 uint64_t sg_debug_check(void);
 
+/* Sizes of the calling thread's last k-mer matrix build (sg_build_kmer_matrix or a batch), for
+ * profiling: windows = sequence positions, candidates = windows that passed the Bloom filters and
+ * were sorted, sort_key_bytes / sort_val_bytes = bytes per candidate through each radix pass
+ * (val 0 when the window rides in the key), sort_passes = 8-bit passes over the candidates,
+ * a_sort_passes = passes of the (read, entry) sort that forms A, m and nnz as in the outputs. */
+typedef struct {
+    int64_t windows, candidates, m, nnz;
+    int32_t sort_key_bytes, sort_val_bytes, sort_passes, a_sort_passes;
+} sg_kmer_stats;
+void sg_last_kmer_stats(sg_kmer_stats *out);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t sg_launch_count(void);
 

@@ -29,7 +29,7 @@ EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg
            "sg_server_create", "sg_server_submit", "sg_server_poll", "sg_server_wait", "sg_job_result_free",
            "sg_server_destroy", "sg_server_cancel",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
-           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_stall_lookback", "sg_debug_check", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_stall_lookback", "sg_debug_check", "sg_last_kmer_stats", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
 
 
@@ -107,6 +107,12 @@ class Job(ctypes.Structure):
                 ("total_len", ctypes.c_int64), ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32),
                 ("r_row_ptr", ctypes.c_void_p), ("r_col", ctypes.c_void_p), ("r_suffix", ctypes.c_void_p),
                 ("r_dir", ctypes.c_void_p), ("r_nnz", ctypes.c_int64)]
+
+
+class KmerStats(ctypes.Structure):
+    _fields_ = [("windows", ctypes.c_int64), ("candidates", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("sort_key_bytes", ctypes.c_int32), ("sort_val_bytes", ctypes.c_int32),
+                ("sort_passes", ctypes.c_int32), ("a_sort_passes", ctypes.c_int32)]
 
 
 class JobResult(ctypes.Structure):
@@ -466,6 +472,13 @@ def minplus_square(R, mode: int = DIRMATCH, stream=None):
 
 
 # ----------------------------------------------------------------------------- tooling
+def last_kmer_stats() -> dict:
+    """Sizes of this thread's last k-mer matrix build (see sg_last_kmer_stats)."""
+    st = KmerStats()
+    lib().sg_last_kmer_stats(ctypes.byref(st))
+    return {f: int(getattr(st, f)) for f, _ in KmerStats._fields_}
+
+
 def launch_count() -> int:
     return int(lib().sg_launch_count())
 

@@ -92,3 +92,52 @@ def store(path: str, signature: str, result: dict) -> None:
     os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
     with open(path, "w") as f:
         json.dump(data, f, indent=1)
+
+
+def _main():
+    """Tunes on a synthetic workload: the full step (k-mer matrix, overlap product, reduction) of a
+    named workload, or with --batched one sg_run_batch over `--sets` read sets of the batched
+    shape. Prints every trial and the choice; --cache stores it for this GPU and workload."""
+    import argparse
+
+    import torch
+
+    import synth
+
+    p = argparse.ArgumentParser(description=_main.__doc__)
+    p.add_argument("--workload", default="bacterial-5Mbp-30x")
+    p.add_argument("--batched", action="store_true")
+    p.add_argument("--sets", type=int, default=128)
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--cache", default=None)
+    a = p.parse_args()
+    if a.batched:
+        sets = synth.batched_sets(a.sets, 20e3, 200e3)
+        items = [dict(seq=torch.from_numpy(x["seq"]).cuda(), offsets=torch.from_numpy(x["offsets"]).cuda(),
+                      lo=x["lo"], hi=x["hi"], R=sg.DeviceGraph.from_numpy(x["R"])) for x in sets]
+        signature = f"batched-{a.sets}"
+
+        def step():
+            sg.run_batch(items, k=17, min_shared=2, max_seeds=2, fuzz=1000)
+    else:
+        w = synth.WORKLOADS[a.workload]
+        d = synth.make(w)
+        seq, off = torch.from_numpy(d["seq"]).cuda(), torch.from_numpy(d["offsets"]).cuda()
+        R = sg.DeviceGraph.from_numpy(d["R"])
+        signature = w.name
+
+        def step():
+            km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+            sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+            sg.transitive_reduce(R, w.fuzz)
+    before = sg.tunables()
+    res = autotune(step, reps=a.reps, log=lambda s: print(s, flush=True))
+    changed = {k: (before[k], v) for k, v in res["params"].items() if before.get(k) != v}
+    print(json.dumps({"signature": signature, "ms": res["ms"], "trials": res["trials"], "changed": changed,
+                      "params": res["params"]}), flush=True)
+    if a.cache:
+        store(a.cache, signature, res)
+
+
+if __name__ == "__main__":
+    _main()

@@ -64,6 +64,9 @@ sg_status timeout_error(const char *what);
 // Test hook (sg_debug_stall_lookback): nonzero makes multi-tile scans withhold tile 0's prefix.
 int debug_stall_lookback();
 
+// The calling thread's last k-mer build sizes (sg_last_kmer_stats).
+sg_kmer_stats &kmer_stats();
+
 // Current value of a tunable parameter (see sg_tune_set).
 int64_t tune(const char *name);
 

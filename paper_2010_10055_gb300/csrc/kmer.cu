@@ -699,6 +699,15 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     bool alt = false;
     const uint64_t *key;
     uint64_t *val;
+    {
+        sg_kmer_stats &ks = kmer_stats();
+        ks = sg_kmer_stats{};
+        ks.windows = total;
+        ks.candidates = nc;
+        ks.sort_key_bytes = 8;
+        ks.sort_val_bytes = mode == PK_PAIRS ? 8 : 0;
+        ks.sort_passes = nc > 1 ? (code_bits + 7) / 8 : 0;
+    }
     const int64_t nlut = (total >> LUT_SHIFT) + 1;
     int32_t *lut = sc.get<int32_t>(nlut);
     if (!lut) return SG_ERR_OOM;
@@ -793,6 +802,9 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
                   av0, 2 * k, job_ncols);
     int rbits = 0;
     while (rbits < 32 && ((int64_t)1 << rbits) < n) rbits++;
+    kmer_stats().m = m;
+    kmer_stats().nnz = nnz;
+    kmer_stats().a_sort_passes = nnz > 1 ? (rbits + 7) / 8 : 0;
     bool aalt = false;
     SG_TRY((radix_sort_pairs<uint32_t, uint64_t>(ak0, av0, ak1, av1, nnz, rbits, &aalt, s, err)));
     const uint32_t *arow = aalt ? ak1 : ak0;

@@ -17,6 +17,8 @@
 namespace sg {
 
 static thread_local char g_err[1024] = "";
+static thread_local sg_kmer_stats g_kstats = {};
+sg_kmer_stats &kmer_stats() { return g_kstats; }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -273,6 +275,10 @@ void sg_debug_stall_lookback(int on) { sg::g_debug_stall.store(on ? 1 : 0); }
 void sg_free(void *d_ptr, sg_stream_t stream) { sg::dfree(d_ptr, (cudaStream_t)stream); }
 
 uint64_t sg_launch_count(void) { return sg::g_launches.load(); }
+
+void sg_last_kmer_stats(sg_kmer_stats *out) {
+    if (out) *out = sg::g_kstats;
+}
 
 uint64_t sg_debug_check(void) {
     std::lock_guard<std::mutex> lk(sg::g_check_mu);
