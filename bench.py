@@ -108,14 +108,14 @@ class ClockSampler:
 # --------------------------------------------------------------------------- roofline
 def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
     """Bytes the method must move per step in `kernel` (inputs read once, outputs written once),
-    from the per-unit figures: 8-byte window codes, 4-byte filter words (a touch is a read and a
-    write), 8-byte keys, 24-byte C entries."""
-    if kernel == "window_codes":
-        return 1.0 * sz["total"] + 8.0 * sz["total"]           # bases in, one code per position out
+    from the per-unit figures: a 4-byte filter hash and 2 bits of packed base per position,
+    4-byte filter words (a touch is a read and a write), 8-byte keys, 24-byte C entries."""
+    if kernel == "pack":
+        return 1.0 * sz["total"] + 4.25 * sz["total"]          # bases in; hash + packed base out
     if kernel == "bloom_insert":
-        return 16.0 * sz["windows"]                            # code read + filter word read and write
+        return 4.0 * sz["total"] + 8.0 * sz["windows"]         # hashes in + filter word read and write
     if kernel == "cand_count":
-        return 8.0 * sz["windows"] + 4.0 * sz["windows"]       # code read + second-filter word probe
+        return 4.0 * sz["total"] + 4.0 * sz["windows"]         # hashes in + second-filter word probe
     if kernel == "radix_onesweep" and sz.get("kstats"):
         k = sz["kstats"]  # every pass reads and writes each record once (the histogram is its own kernel)
         return (2.0 * k["sort_passes"] * k["candidates"] * (k["sort_key_bytes"] + k["sort_val_bytes"])

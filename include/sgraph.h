@@ -375,8 +375,10 @@ void sg_free(void *d_ptr, sg_stream_t stream);
 const char *sg_last_error(void);
 
 /* Optional device allocator (e.g. a framework's caching allocator). alloc returns NULL on
- * failure. Pass NULLs to restore cudaMallocAsync / cudaFreeAsync. Not thread-safe to change
- * while calls are running. */
+ * failure, else a pointer aligned to 256 bytes as cudaMalloc's are (the kernels use 16-byte
+ * vector accesses; a less aligned pointer fails the call with SG_ERR_OOM and a message). Pass
+ * NULLs to restore cudaMallocAsync / cudaFreeAsync. Not thread-safe to change while calls are
+ * running. */
 typedef void *(*sg_alloc_fn)(size_t bytes, sg_stream_t stream, void *ctx);
 typedef void (*sg_free_fn)(void *ptr, sg_stream_t stream, void *ctx);
 void sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx);

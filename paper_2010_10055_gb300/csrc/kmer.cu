@@ -8,7 +8,9 @@
 // lowest such position).
 //
 // Pipeline (all on `stream`):
-//  0. window_codes   one walk over the reads writes every window's canonical code and strand.
+//  0. pack           one walk over the reads packs the bases (2 bits each) and marks where a
+//                    valid window starts (1 bit each); every later pass recomputes a window's
+//                    canonical code and strand from two packed words.
 //  1. bloom_insert   every code is OR-ed into the blocked Bloom filter B1 (all probe bits in one
 //                    32-bit word, so "already present" is decided by one atomic); a code found
 //                    present is OR-ed into B2 ("seen at least twice"). Skipped when lo == 1.
@@ -34,11 +36,10 @@ namespace sg {
 constexpr int KM_NT = 256;
 constexpr int KM_W = 32;                  // windows per thread
 constexpr int KM_CHUNK = KM_NT * KM_W;    // windows per block
+constexpr int KM_WARPS = KM_NT / 32;
 
 // 32-bit mix of a 64-bit k-mer code (multiply-xorshift finaliser).
-__device__ __forceinline__ uint32_t hash32(uint64_t code, uint32_t seed) {
-    uint32_t h = (uint32_t)code * 0x9E3779B1u + seed;
-    h ^= (uint32_t)(code >> 32) * 0x85EBCA77u;
+__device__ __forceinline__ uint32_t fmix(uint32_t h) {
     h ^= h >> 15;
     h *= 0x2C1B3C6Du;
     h ^= h >> 12;
@@ -47,14 +48,20 @@ __device__ __forceinline__ uint32_t hash32(uint64_t code, uint32_t seed) {
     return h;
 }
 
+__device__ __forceinline__ uint32_t hash32(uint64_t code, uint32_t seed) {
+    uint32_t h = (uint32_t)code * 0x9E3779B1u + seed;
+    h ^= (uint32_t)(code >> 32) * 0x85EBCA77u;
+    return fmix(h);
+}
+
 // Blocked Bloom filter: a key sets 4 bits of one 32-bit word, so whether all of them were
-// already set is decided by the single atomicOr that sets them.
+// already set is decided by the single atomicOr that sets them. Word and bits come from the key's
+// 32-bit hash h (B1: h = hash32(key); B2: h = fmix(that hash ^ B2 seed), so both filters work
+// from one stored hash per window).
 struct Bloom {
     uint32_t *words;
     uint32_t nwords;
-    uint32_t seed;
-    __device__ __forceinline__ void probe(uint64_t code, uint32_t *idx, uint32_t *mask) const {
-        const uint32_t h = hash32(code, seed);
+    __device__ __forceinline__ void probe(uint32_t h, uint32_t *idx, uint32_t *mask) const {
         *idx = __umulhi(h, nwords);
         const uint32_t g = h * 0x85EBCA6Bu;  // bit positions from a second mix
         *mask = (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u)) |
@@ -62,25 +69,43 @@ struct Bloom {
     }
 };
 
-// Per-thread cursor over the job map (reads are visited in increasing order).
-struct JobCursor {
-    JobMap m;
+// Batches: the job prefix of a window, from the base offset of each job's first read (jpos[b] =
+// off[ro[b]], jpos[njobs] = total). A window lies in the last job b with jpos[b] <= its position
+// (windows never cross reads, and empty jobs start where the next one does). The cursor keeps the
+// last job's range, so increasing positions search only when they leave it.
+struct JobPos {
+    const int64_t *jpos;  // nullptr: one read set, no prefix
+    int64_t njobs;
+    int kbits;  // 2k
+};
+
+struct JobPosCursor {
+    JobPos m;
     int64_t jb = 0, jlo = 0, jhi = -1;
-    __device__ __forceinline__ uint64_t key(uint64_t code, int64_t r) {
-        if (!m.ro) return code;
-        if (r < jlo || r >= jhi) {  // last job b with ro[b] <= r
+    __device__ __forceinline__ uint64_t prefix(int64_t q) {
+        if (!m.jpos) return 0;
+        if (q < jlo || q >= jhi) {
             int64_t lo = 0, hi = m.njobs;
             while (hi - lo > 1) {
                 const int64_t mid = (lo + hi) >> 1;
-                if (m.ro[mid] <= r) lo = mid; else hi = mid;
+                if (m.jpos[mid] <= q) lo = mid; else hi = mid;
             }
             jb = lo;
-            jlo = m.ro[lo];
-            jhi = m.ro[lo + 1];
+            jlo = m.jpos[lo];
+            jhi = m.jpos[lo + 1];
         }
-        return ((uint64_t)jb << m.kbits) | code;
+        return (uint64_t)jb << m.kbits;
     }
 };
+
+__global__ void job_pos_kernel(const int64_t *__restrict__ ro, int64_t njobs, const int64_t *__restrict__ off,
+                               int64_t n, int64_t *__restrict__ jpos) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > njobs) return;
+    int64_t r = ro[b];
+    r = r < 0 ? 0 : (r > n ? n : r);
+    jpos[b] = off[r];
+}
 
 // Staged bases: the block's chunk as 32-bit words (4 bases each), one pad word after every 8, so
 // that thread t's 32-base segment starts at word 9t and a warp reading the j-th word of its
@@ -108,47 +133,32 @@ __device__ __forceinline__ void load_chunk(uint32_t *smw, const uint8_t *__restr
     __syncthreads();
 }
 
-// Stores window j's value (thread-local order); every 4th value flushes 4 consecutive windows
-// (one 32-byte sector) with two 16-byte stores.
-struct WcOut {
-    uint64_t buf[4];
-    __device__ __forceinline__ void put(uint64_t *wc, int64_t q0, int64_t total, int j, uint64_t v) {
-        buf[j & 3] = v;
-        if ((j & 3) != 3) return;
-        const int64_t q = q0 + j - 3;  // first of the 4 windows; a multiple of 4
-        if (q + 3 < total) {
-            uint4 *d = reinterpret_cast<uint4 *>(wc + q);
-            d[0] = make_uint4((uint32_t)buf[0], (uint32_t)(buf[0] >> 32), (uint32_t)buf[1], (uint32_t)(buf[1] >> 32));
-            d[1] = make_uint4((uint32_t)buf[2], (uint32_t)(buf[2] >> 32), (uint32_t)buf[3], (uint32_t)(buf[3] >> 32));
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (q + u < total) wc[q + u] = buf[u];
-        }
-    }
-};
-
-// One walk over the reads: wc[q] = canonical code of the window starting at global position q
-// (with the job prefix in a batch) | strand << 63, or ~0 when no valid window starts at q (a
-// non-ACGT base, or the window crosses a read end). The later passes stream this array instead of
-// walking the reads again. Thread t of block b produces windows b * KM_CHUNK + t * KM_W + j,
-// j < KM_W, in order, from bases [t * KM_W, t * KM_W + KM_W + k - 1) of the block's chunk. K > 0
-// makes k a compile-time constant (K == 0: k taken from k_rt).
+// One walk over the reads. Every window q gets H[q] = the 32-bit hash of its canonical key (code,
+// with the job prefix in a batch), or H_NONE when no valid window starts at q (a non-ACGT base, or
+// the window crosses a read end); the Bloom passes and the candidate test work from H alone. P[g]
+// holds bases 32g .. 32g + 31 as 2-bit codes (A=0 C=1 G=2 T=3), base 32g + j at bits 2j, from which
+// the emit pass recomputes the code and strand of the few windows that are candidates
+// (window_key). Thread t of block b covers windows and bases b * KM_CHUNK + t * KM_W + j, j < KM_W,
+// reading bases [t * KM_W, t * KM_W + KM_W + k - 1) of the block's chunk. K > 0 makes k a
+// compile-time constant (K == 0: k taken from k_rt).
 constexpr uint64_t WC_NONE = ~0ull;
 constexpr uint64_t WC_STRAND = 1ull << 63;
+constexpr uint32_t H_NONE = 0xFFFFFFFFu;
 constexpr uint32_t B1_SEED = 0x9e3779b9u, B2_SEED = 0x7f4a7c15u;
+static_assert(KM_W == 32, "one packed word per thread");
+
+__device__ __forceinline__ uint32_t b2_hash(uint32_t h1) { return fmix(h1 ^ B2_SEED); }
 
 template <int K>
-__global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__restrict__ seq, int64_t total,
-                                                            const int64_t *__restrict__ off, int64_t n, int k_rt,
-                                                            JobMap jm, uint64_t *__restrict__ wc) {
-    static_assert(KM_W % 4 == 0, "windows are flushed four at a time");
+__global__ void __launch_bounds__(KM_NT) pack_kernel(const uint8_t *__restrict__ seq, int64_t total,
+                                                    const int64_t *__restrict__ off, int64_t n, int k_rt, JobPos jp,
+                                                    uint64_t *__restrict__ P, uint32_t *__restrict__ H) {
     __shared__ uint32_t smw[KM_SPAD];
     const int k = K > 0 ? K : k_rt;
     const int64_t c0 = (int64_t)blockIdx.x * KM_CHUNK;
     load_chunk(smw, seq, c0, total);  // ends with __syncthreads
     const int ls = threadIdx.x * KM_W;
-    const int64_t qs = c0 + ls;  // first window (and base) of this thread
+    const int64_t qs = c0 + ls;  // first window (and base) of this thread; a multiple of 32
     if (qs >= total || n <= 0) return;
     // read containing qs: last r with off[r] <= qs (off[n] = total > qs)
     int64_t lo = 0, hi = n;
@@ -158,20 +168,16 @@ __global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__re
     }
     int64_t r = lo;
     int64_t next = off[r + 1] - qs;  // start of read r + 1, relative to qs
-    JobCursor jc{jm};
-    uint64_t rkey = jc.key(0, r);   // job prefix of read r (0 outside batches)
+    JobPosCursor jc{jp};
     const uint64_t mask = (1ull << (2 * k)) - 1;
     const int rs = 2 * (k - 1);
-    uint64_t fw = 0, rc = 0;
-    int run = 0;
-    WcOut out;
-    const int nb = KM_W + k - 1;  // bases this thread reads
-    const int nw = (nb + 3) >> 2;
+    uint64_t fw = 0, rc = 0, pw = 0;
+    int run = 0;  // ACGT bases ending here inside the current read
+    uint32_t hb[4];
     const uint32_t *mine = smw + 9 * threadIdx.x;  // spad(8t + i) = 9t + i + (i >> 3)
+    const int nb = KM_W + k - 1;                   // bases this thread reads
 #pragma unroll
-    for (int wi = 0; wi < (K > 0 ? (KM_W + K - 1 + 3) / 4 : 1); wi++) {
-        // K == 0 takes the generic loop below instead
-        if (K == 0) break;
+    for (int wi = 0; wi < (K > 0 ? (KM_W + K - 1 + 3) / 4 : (KM_W + 31 - 1 + 3) / 4); wi++) {
         const uint32_t word = mine[wi + (wi >> 3)];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -182,73 +188,77 @@ __global__ void __launch_bounds__(KM_NT) window_codes_kernel(const uint8_t *__re
             while (qi >= next && r + 1 < n) {
                 r++;
                 next = off[r + 1] - qs;
-                rkey = jc.key(0, r);
                 run = 0;
             }
             const uint32_t c = (word >> (8 * u)) & 0xffu;
             const bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
             const uint32_t t = (c >> 1) & 3u;
             const uint32_t b = t ^ (t >> 1);  // A=0 C=1 G=2 T=3
+            if (qi < KM_W) pw |= (uint64_t)b << (2 * qi);
             fw = ((fw << 2) | b) & mask;
             rc = (rc >> 2) | ((uint64_t)(3u - b) << rs);
-            run = ok ? run + 1 : 0;
+            run = ok ? run + 1 : 0;  // bases past the end read as 'N'
             const int j = qi - (k - 1);
             if (j >= 0) {
-                const uint64_t key = rkey | (fw < rc ? fw : rc);
-                const uint64_t v = run >= k ? (key | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
-                out.put(wc, qs, total, j, v);
+                uint32_t h = H_NONE;
+                if (run >= k) {
+                    h = hash32(jc.prefix(qs + j) | (fw < rc ? fw : rc), B1_SEED);
+                    h = h == H_NONE ? H_NONE - 1 : h;
+                }
+                if (K > 0) {  // j is a compile-time index: buffer 4 windows, one 16-byte store
+                    hb[j & 3] = h;
+                    if ((j & 3) == 3) *reinterpret_cast<uint4 *>(H + qs + j - 3) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
+                } else {
+                    H[qs + j] = h;
+                }
             }
         }
     }
-    if (K == 0) {
-        for (int qi = 0; qi < nb; qi++) {
-            while (qi >= next && r + 1 < n) {
-                r++;
-                next = off[r + 1] - qs;
-                rkey = jc.key(0, r);
-                run = 0;
-            }
-            const int wi = qi >> 2;
-            const uint32_t c = (mine[wi + (wi >> 3)] >> (8 * (qi & 3))) & 0xffu;
-            const bool ok = (c == 'A') | (c == 'C') | (c == 'G') | (c == 'T');
-            const uint32_t t = (c >> 1) & 3u;
-            const uint32_t b = t ^ (t >> 1);
-            fw = ((fw << 2) | b) & mask;
-            rc = (rc >> 2) | ((uint64_t)(3u - b) << rs);
-            run = ok ? run + 1 : 0;
-            const int j = qi - (k - 1);
-            if (j >= 0 && qs + j < total) {
-                const uint64_t key = rkey | (fw < rc ? fw : rc);
-                wc[qs + j] = run >= k ? (key | (rc < fw ? WC_STRAND : 0ull)) : WC_NONE;
-            }
-        }
-    }
-    (void)nw;
+    P[qs >> 5] = pw;
 }
 
-// One launch per slice [w_lo, w_hi) of B1's words: every launch streams all window codes but only
-// the k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2. kmask
-// extracts the key (job prefix and code) from a window code.
+// Key of window q = 32g + lane from P[g] = w0 and P[g + 1] = w1 (a valid window): the canonical
+// code (with the job prefix) | strand << 63. The 2k bits from
+// bit 2 * lane of w1:w0 hold the window's bases, first base lowest; complementing them gives the
+// reverse complement's code (last base's complement highest), and reversing the order of the
+// 2-bit groups gives the forward code (first base highest).
+__device__ __forceinline__ uint64_t window_key(uint64_t w0, uint64_t w1, int lane, int k, JobPosCursor &jc,
+                                               int64_t q) {
+    const int sh = 2 * lane;
+    const uint64_t x = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
+    const uint64_t rc = ~x & ((1ull << (2 * k)) - 1);  // k <= 31
+    uint64_t y = __brevll(x);
+    y = ((y >> 1) & 0x5555555555555555ull) | ((y & 0x5555555555555555ull) << 1);
+    const uint64_t fw = y >> (64 - 2 * k);
+    return jc.prefix(q) | (fw < rc ? fw : rc) | (rc < fw ? WC_STRAND : 0ull);
+}
+
+// One launch per slice [w_lo, w_hi) of B1's words: every launch streams all window hashes but
+// only the k-mers whose B1 word lies in its slice touch the filter, so the slice stays in L2.
 template <int BI_U>
-__global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint64_t *__restrict__ wc, int64_t total,
-                                                            Bloom b1, Bloom b2, uint64_t kmask, uint32_t w_lo,
-                                                            uint32_t w_hi) {
-    // BI_U windows per thread per step (each step's loads coalesced across the warp, all issued
-    // before any is used), so that their atomics are in flight together
+__global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint32_t *__restrict__ H, int64_t nvec, Bloom b1,
+                                                            Bloom b2, uint32_t w_lo, uint32_t w_hi) {
+    // BI_U / 4 16-byte loads (4 windows each) per thread per step, coalesced across the warp and
+    // all issued before any is used, so that BI_U atomics per thread are in flight together
+    constexpr int NV = BI_U / 4;
     const int64_t stride = (int64_t)gridDim.x * KM_NT;
-    for (int64_t q0 = (int64_t)blockIdx.x * KM_NT + threadIdx.x; q0 < total; q0 += BI_U * stride) {
-        uint64_t x[BI_U];
-        uint32_t i1[BI_U], m1[BI_U], old[BI_U];
+    const uint4 *H4 = reinterpret_cast<const uint4 *>(H);
+    for (int64_t v0 = (int64_t)blockIdx.x * KM_NT + threadIdx.x; v0 < nvec; v0 += NV * stride) {
+        uint32_t h[BI_U], i1[BI_U], m1[BI_U], old[BI_U];
         bool mine[BI_U];
 #pragma unroll
-        for (int u = 0; u < BI_U; u++) {
-            const int64_t q = q0 + u * stride;
-            x[u] = q < total ? __ldcs(wc + q) : WC_NONE;
+        for (int u = 0; u < NV; u++) {
+            const int64_t v = v0 + u * stride;
+            const uint4 x = v < nvec ? __ldcs(H4 + v) : make_uint4(H_NONE, H_NONE, H_NONE, H_NONE);
+            h[4 * u] = x.x;
+            h[4 * u + 1] = x.y;
+            h[4 * u + 2] = x.z;
+            h[4 * u + 3] = x.w;
         }
 #pragma unroll
         for (int u = 0; u < BI_U; u++) {
-            b1.probe(x[u] & kmask, &i1[u], &m1[u]);
-            mine[u] = x[u] != WC_NONE && i1[u] >= w_lo && i1[u] < w_hi;
+            b1.probe(h[u], &i1[u], &m1[u]);
+            mine[u] = h[u] != H_NONE && i1[u] >= w_lo && i1[u] < w_hi;
         }
 #pragma unroll
         for (int u = 0; u < BI_U; u++) old[u] = mine[u] ? atomicOr(b1.words + i1[u], m1[u]) : 0u;
@@ -256,7 +266,7 @@ __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint64_t *__r
         for (int u = 0; u < BI_U; u++) {
             if (mine[u] && (old[u] & m1[u]) == m1[u]) {
                 uint32_t i2, m2;
-                b2.probe(x[u] & kmask, &i2, &m2);
+                b2.probe(b2_hash(h[u]), &i2, &m2);
                 if ((b2.words[i2] & m2) != m2) atomicOr(b2.words + i2, m2);
             }
         }
@@ -268,39 +278,38 @@ __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint64_t *__r
 // every window (lo == 1: singletons may be reliable).
 //
 // Both passes are warp-cooperative: warp w of block b owns the KM_GW groups of 32 consecutive
-// windows starting at group (b * KM_WARPS + w) * KM_GW, and handles one group (one coalesced
-// 256-byte load) per step. The count pass stores each group's candidate ballot in cmask and the
-// warp's total in wcnt; the emit pass writes each group's candidates contiguously at the scanned
-// offset, so candidates keep position order.
-constexpr int KM_WARPS = KM_NT / 32;
+// windows starting at group (b * KM_WARPS + w) * KM_GW, and handles one group (lane l: window
+// 32g + l, from the group's two packed words) per step. The count pass stores each group's
+// candidate ballot in cmask and the warp's total in wcnt; the emit pass writes each group's
+// candidates contiguously at the scanned offset, so candidates keep position order.
 constexpr int KM_GW = KM_CHUNK / KM_NT;  // groups per warp (32: one mask word per lane)
 static_assert(KM_GW == 32, "one mask word per lane");
 
-__device__ __forceinline__ bool is_candidate(uint64_t x, const Bloom &b2, int use_bloom, uint64_t kmask) {
-    if (x == WC_NONE) return false;
+__device__ __forceinline__ bool is_candidate(uint32_t h, const Bloom &b2, int use_bloom) {
+    if (h == H_NONE) return false;
     if (!use_bloom) return true;
     uint32_t i2, m2;
-    b2.probe(x & kmask, &i2, &m2);
+    b2.probe(b2_hash(h), &i2, &m2);
     return (b2.words[i2] & m2) == m2;
 }
 
-__global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint64_t *__restrict__ wc, int64_t total, Bloom b2,
-                                                          int use_bloom, uint64_t kmask, uint32_t *__restrict__ cmask,
+__global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__restrict__ H, int64_t nwin, Bloom b2,
+                                                          int use_bloom, uint32_t *__restrict__ cmask,
                                                           uint32_t *__restrict__ wcnt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
     uint32_t mine = 0, c = 0;
-    constexpr int CC_U = 8;  // groups whose codes (and then filter words) are loaded together
+    constexpr int CC_U = 8;  // groups whose hashes (and then filter words) are loaded together
     for (int g0u = 0; g0u < KM_GW; g0u += CC_U) {
-        uint64_t x[CC_U];
+        uint32_t h[CC_U];
 #pragma unroll
         for (int u = 0; u < CC_U; u++) {
             const int64_t q = (g0 + g0u + u) * 32 + lane;
-            x[u] = q < total ? __ldcs(wc + q) : WC_NONE;
+            h[u] = q < nwin ? __ldcs(H + q) : H_NONE;
         }
 #pragma unroll
         for (int u = 0; u < CC_U; u++) {
-            const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(x[u], b2, use_bloom, kmask));
+            const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(h[u], b2, use_bloom));
             if (lane == g0u + u) mine = m;
             c += __popc(m);
         }
@@ -316,22 +325,23 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint64_t *__res
 //   PK_PAIRS key = code, vals = q | strand << 63, sorted as pairs (nothing fits in 64 bits).
 enum : int { PK_POS = 0, PK_IDX = 1, PK_PAIRS = 2 };
 
-__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__restrict__ wc,
+__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__restrict__ P, int k, JobPos jp,
                                                          const uint32_t *__restrict__ cmask,
                                                          const int64_t *__restrict__ wpos, int mode, int pb,
                                                          uint64_t kmask, uint64_t *__restrict__ keys,
                                                          uint64_t *__restrict__ vals, int64_t nc) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
+    JobPosCursor jc{jp};
     const uint32_t mine = cmask[g0 + lane];
     const uint32_t below = (1u << lane) - 1u;
     int64_t o = wpos[(int64_t)blockIdx.x * KM_WARPS + w];
     for (int g = 0; g < KM_GW; g++) {
         const uint32_t m = __shfl_sync(0xffffffffu, mine, g);
-        if (m == 0) continue;
+        if (m == 0) continue;  // no candidate: also every group past the sequence
         if ((m >> lane) & 1u) {
             const int64_t q = (g0 + g) * 32 + lane;
-            const uint64_t x = __ldcs(wc + q);
+            const uint64_t x = window_key(P[g0 + g], P[g0 + g + 1], lane, k, jc, q);
             const uint64_t code = x & kmask;
             const int64_t p = o + __popc(m & below);
             if (SG_IN_BOUNDS(p >= 0 && p < nc, 102, p)) {
@@ -621,8 +631,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     while (jm.ro && ((int64_t)1 << job_bits) < jm.njobs) job_bits++;
     const int code_bits = 2 * k + job_bits;
     const uint64_t kmask = (1ull << code_bits) - 1;  // code_bits <= 62
-    Bloom b1{nullptr, 0, B1_SEED}, b2{nullptr, 0, B2_SEED};
-    // window codes, filters and candidate masks: released (stream-ordered) once the candidates
+    Bloom b1{nullptr, 0}, b2{nullptr, 0};
+    // packed bases, filters and candidate masks: released (stream-ordered) once the candidates
     // are emitted, before the sort allocates its buffers
     std::optional<Scratch> early;
     early.emplace(s);
@@ -639,12 +649,21 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     }
     std::optional<StageScope> stage;
     stage.emplace("CountKmer", s);  // a1-a4: codes, Bloom, exact count, columns
-    // 0. window codes
-    uint64_t *wc = early->get<uint64_t>(total + 1);
-    if (!wc) return SG_ERR_OOM;
+    // 0. packed bases and window hashes (job prefixes by base position in a batch)
+    const int64_t ngroups = (total + 31) / 32;
+    JobPos jp{nullptr, 0, 2 * k};
+    if (jm.ro) {
+        int64_t *jpos = early->get<int64_t>(jm.njobs + 1);
+        if (!jpos) return SG_ERR_OOM;
+        SG_LAUNCH("job_pos", job_pos_kernel, blocks_for(jm.njobs + 1, NT), NT, 0, s, jm.ro, jm.njobs, off, n, jpos);
+        jp = JobPos{jpos, jm.njobs, jm.kbits};
+    }
+    uint64_t *P = early->get<uint64_t>(ngroups + 1);
+    uint32_t *H = early->get<uint32_t>(ngroups * 32);
+    if (!P || !H) return SG_ERR_OOM;
+    SG_CUDA_TRY(cudaMemsetAsync(P + ngroups, 0, sizeof(uint64_t), s));
     SG_TRY(dispatch_k(k, [&](auto kc) -> sg_status {
-        SG_LAUNCH("window_codes", window_codes_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n,
-                  k, jm, wc);
+        SG_LAUNCH("pack", pack_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n, k, jp, P, H);
         return SG_OK;
     }));
     if (use_bloom) {
@@ -654,17 +673,18 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         // every slice streams all window codes: beyond bloom_max_slices, slices grow instead
         const uint64_t max_sl = (uint64_t)tune("bloom_max_slices");
         if (nsl > max_sl) nsl = max_sl;
-        const int64_t grid = blocks_for(total, KM_NT) < 152 * 16 ? blocks_for(total, KM_NT) : 152 * 16;
+        const int64_t nvec = ngroups * 8;  // 16-byte vectors of 4 hashes
+        const int64_t grid = blocks_for(nvec, KM_NT) < 152 * 16 ? blocks_for(nvec, KM_NT) : 152 * 16;
         const int64_t u = tune("bloom_unroll");
         for (uint64_t q = 0; q < nsl; q++) {
             const uint32_t lo_w = (uint32_t)((uint64_t)b1.nwords * q / nsl);
             const uint32_t hi_w = (uint32_t)((uint64_t)b1.nwords * (q + 1) / nsl);
             if (u >= 8)
-                SG_LAUNCH("bloom_insert", bloom_insert_kernel<8>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1, b2,
-                          kmask, lo_w, hi_w);
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<8>, grid, KM_NT, 0, s, (const uint32_t *)H, nvec, b1, b2, lo_w,
+                          hi_w);
             else
-                SG_LAUNCH("bloom_insert", bloom_insert_kernel<4>, grid, KM_NT, 0, s, (const uint64_t *)wc, total, b1, b2,
-                          kmask, lo_w, hi_w);
+                SG_LAUNCH("bloom_insert", bloom_insert_kernel<4>, grid, KM_NT, 0, s, (const uint32_t *)H, nvec, b1, b2, lo_w,
+                          hi_w);
         }
     }
     const int64_t nwarp = nblk * KM_WARPS;
@@ -672,7 +692,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint32_t *wcnt = early->get<uint32_t>(nwarp + 1);
     int64_t *wpos = early->get<int64_t>(nwarp + 1);
     if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
-    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, total, b2, use_bloom, kmask,
+    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint32_t *)H, ngroups * 32, b2, use_bloom,
               cmask, wcnt);
     SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp, s, err));
     int64_t nc = 0;
@@ -693,7 +713,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint64_t *key0 = sc.get<uint64_t>(nc), *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
     uint64_t *val0 = mode == PK_POS ? nullptr : sc.get<uint64_t>(nc);
     if (!key0 || !key1 || !val1 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
-    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)wc, (const uint32_t *)cmask,
+    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)P, k, jp, (const uint32_t *)cmask,
               (const int64_t *)wpos, mode, pb, kmask, key0, val0, nc);
     early.reset();
     bool alt = false;

@@ -91,6 +91,11 @@ void *dalloc(size_t bytes, cudaStream_t s) {
     if (g_alloc) {
         p = g_alloc(bytes, (sg_stream_t)s, g_alloc_ctx);
         if (!p) set_error("device allocation of %zu bytes failed (user allocator)", bytes);
+        if (p && ((uintptr_t)p & 255)) {
+            set_error("user allocator returned %p, which is not 256-byte aligned", p);
+            if (g_free) g_free(p, (sg_stream_t)s, g_alloc_ctx);
+            return nullptr;
+        }
         return p;
     }
     cudaMemPool_t pool = library_pool();
