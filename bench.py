@@ -131,8 +131,8 @@ def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
 
 def family(name: str) -> str:
     """Kernel family of a launch name: the SpGEMM passes launch one class per table size
-    (spgemm_numeric_t1k, ...), which are one kernel."""
-    return re.sub(r"_t\d+k?$", "", name)
+    (spgemm_numeric_t1k, ..., and _f1k, ... for filtered rows), which are one kernel."""
+    return re.sub(r"_[tf]\d+k?$", "", name)
 
 
 def by_family(prof: dict) -> dict:
@@ -297,7 +297,12 @@ def main():
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(sg, d, w, args)
+        try:
+            e2e = measure_e2e(sg, d, w, args)
+        except sg.SgError as ex:  # reported in the line, with the device's memory state
+            free_b, total_b = torch.cuda.mem_get_info()
+            e2e = {"value": None, "unit": UNIT, "error": str(ex)[:300], "device_free_gb": free_b / 1e9,
+                   "device_total_gb": total_b / 1e9, "torch_reserved_gb": torch.cuda.memory_reserved() / 1e9}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
@@ -306,6 +311,8 @@ def main():
                        "min_shared": w.min_shared, "max_seeds": w.max_seeds, "fuzz": w.fuzz,
                        "m": sz["m"], "nnz_A": sz["nnzA"], "products": products, "nnz_C": sz["nnzC"],
                        "nnz_R": sz["nnzR"], "nnz_S": sz["nnzS"], "tr_rounds": sz["rounds"],
+                       "candidates": sz["kstats"]["candidates"],
+                       "candidate_sort_bytes": sz["kstats"]["sort_key_bytes"] + sz["kstats"]["sort_val_bytes"],
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "tr_edges_per_s": edges_all * args.steps / (tr_ms_max / 1e3) if tr_ms_max else None,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),

@@ -415,15 +415,29 @@ uint64_t sg_launch_count(void);
  *   bloom_bits            bits of the first-level Bloom filter per window (8): fewer bits, fewer
  *                         slices but more false positives (singletons that reach the exact count)
  *   bloom_slice_mb        megabytes of the first-level Bloom filter updated per launch (64)
- *   bloom_max_slices      at most this many Bloom launches, each streaming all window codes;
+ *   bloom_max_slices      at most this many Bloom launches, each streaming all window hashes;
  *                         for larger filters the slices grow instead (8)
  *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4 or 8 (4)
  *   spgemm_fused          1: C in one numeric pass whose tables are sized from a guess (rows that
  *                         overflow are redone in exact-size global-memory tables) and whose rows
  *                         go to a temporary region; 0: symbolic pass (exact sizes), then numeric (1)
- *   num_guess_shift       fused numeric table guess = products of the row >> shift (2)
- *   spgemm_fused_max_mb   largest temporary region of the fused pass, MB (8192); above it the
- *                         two-pass form runs
+ *   spgemm_sample_rows    rows sampled before the fused pass when nnz(A) >= spgemm_sample_min_nnz
+ *                         (2^26) (256): their partners per product
+ *                         (distinct, and seen at least twice) scale every row's table guess, and
+ *                         the seen-twice filter is used only where it keeps under half the
+ *                         partners; 0: no sample, guesses by the shifts below
+ *   spgemm_guess_pct      sampled guess = pct / 100 x partners per product x products (300)
+ *   num_guess_shift       fused numeric table guess without a sample = products >> shift (2)
+ *   spgemm_fused_max_mb   largest temporary region of the fused pass, MB (65536); above it, or
+ *                         above half the device memory free at the call, the two-pass form runs
+ *   spgemm_filter_mode    seen-twice filter for fused rows of spgemm_filter_work products or
+ *                         more: they first mark, in two bit filters, the partners seen once and
+ *                         seen twice, and tabulate only the latter (count-1 partners cannot reach C
+ *                         when min_shared >= 2). 0 never, 1 when the row sample finds that fewer
+ *                         than half the partners recur (1), 2 always
+ *   spgemm_filter_work    rows with at least this many products may be filtered; 0: none (2048)
+ *   spgemm_filter_shift   table guess of those rows without a sample = products >> shift (2)
+ *   spgemm_filter_log2    bits per filter: one per read up to 2^this, hashed beyond (17)
  *   sym_guess_shift       symbolic hash table guess = products of the row >> shift (2)
  *   spgemm_blocks_per_sm  blocks per SM of each SpGEMM class launch (16)
  *   tr_blocks_per_sm      blocks per SM of the min-plus launch (32)

@@ -19,6 +19,9 @@ SPACE = {
     "bloom_bits": [6, 8, 10, 12],
     "spgemm_fused": [0, 1],
     "num_guess_shift": [1, 2, 3, 4],
+    "spgemm_filter_mode": [0, 1, 2],
+    "spgemm_filter_work": [1024, 2048, 4096, 8192],
+    "spgemm_guess_pct": [150, 200, 300, 400],
     "sym_guess_shift": [0, 1, 2, 3],
     "spgemm_blocks_per_sm": [2, 4, 8, 16],
     "tr_blocks_per_sm": [4, 8, 16, 32],

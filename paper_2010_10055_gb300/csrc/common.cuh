@@ -64,6 +64,9 @@ sg_status timeout_error(const char *what);
 // Test hook (sg_debug_stall_lookback): nonzero makes multi-tile scans withhold tile 0's prefix.
 int debug_stall_lookback();
 
+// Device memory a call can still obtain (driver free + unused memory held by the library's pool).
+size_t device_bytes_available();
+
 // The calling thread's last k-mer build sizes (sg_last_kmer_stats).
 sg_kmer_stats &kmer_stats();
 

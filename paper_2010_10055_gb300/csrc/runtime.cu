@@ -78,6 +78,25 @@ static cudaMemPool_t library_pool() {
     return g_pools[dev];
 }
 
+// Device memory a call can still obtain: free in the driver plus what the library's pool holds
+// unused (the pool keeps freed memory reserved).
+size_t device_bytes_available() {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaMemPool_t pool = g_alloc ? nullptr : library_pool();
+    if (pool) {
+        uint64_t reserved = 0, used = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            free_b += (size_t)(reserved - used);
+        cudaGetLastError();
+    }
+    return free_b;
+}
+
 void *dalloc(size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
     int64_t f = g_fail_after.load();
@@ -100,9 +119,24 @@ void *dalloc(size_t bytes, cudaStream_t s) {
     }
     cudaMemPool_t pool = library_pool();
     cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess && pool) {
+        // the pool keeps freed memory reserved; blocks freed by earlier calls may not fit this
+        // request. Once this stream's frees have completed, give the unused part back and retry.
+        cudaGetLastError();
+        if (cudaStreamSynchronize(s) == cudaSuccess && cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
+            e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        size_t free_b = 0, total_b = 0;
+        uint64_t reserved = 0, used = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+        if (pool && (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+                     cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess))
+            cudaGetLastError();
+        set_error("cudaMallocAsync(%zu bytes) failed: %s (device: %.1f of %.1f GB free; library pool: %.1f GB "
+                  "reserved, %.1f GB in use)",
+                  bytes, cudaGetErrorString(e), free_b / 1e9, total_b / 1e9, reserved / 1e9, used / 1e9);
         return nullptr;
     }
     return p;
@@ -227,8 +261,18 @@ static Tunable g_tunables[] = {
     {"bloom_max_slices", 8, 1, 1024},     // at most this many Bloom launches (slices grow beyond)
     {"bloom_unroll", 4, 4, 8},            // windows (atomics in flight) per thread per Bloom step: 4 or 8
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
-    {"num_guess_shift", 2, 0, 8},         // fused numeric table guess = products >> shift
-    {"spgemm_fused_max_mb", 8192, 0, 1 << 30},  // temporary C region above which the two passes run
+    {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)
+    {"spgemm_sample_min_nnz", (int64_t)1 << 26, 0, (int64_t)1 << 50},  // ... when nnz(A) is at least this
+    {"spgemm_guess_pct", 300, 25, 10000}, // guess = pct / 100 x sampled partners per product x products
+    {"num_guess_shift", 2, 0, 8},         // fused numeric table guess = products >> shift (no sample)
+    {"spgemm_fused_max_mb", 65536, 0, 1 << 30},  // temporary C region above which the two passes run
+                                                  // (also when it exceeds half the free memory)
+    {"spgemm_filter_mode", 1, 0, 2},      // seen-twice filter: 0 never, 1 where the sample finds it
+                                          // pays, 2 always (rows of spgemm_filter_work products or more)
+    {"spgemm_filter_work", 2048, 0, (int64_t)1 << 40},  // fused rows with this many products or more
+                                          // may first mark partners seen twice (0: never)
+    {"spgemm_filter_shift", 2, 0, 8},     // their table guess = products >> shift (no sample)
+    {"spgemm_filter_log2", 17, 10, 19},   // at most 2^this bits per seen-once / seen-twice filter
     {"sym_guess_shift", 2, 0, 8},         // symbolic table guess = products >> shift
     {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch
     {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch

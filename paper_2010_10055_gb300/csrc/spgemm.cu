@@ -19,6 +19,14 @@
 //                of j; inserting into the S-slot list is a chain of atomicMin's that pushes the
 //                loser down. Entries with count >= min_shared are compacted, bitonic-sorted by
 //                k and written to C; seed positions are resolved from A's row.
+// Fused path (default): no symbolic pass; tables sized from a guess, overflowing rows redone in
+// global memory. A row with many products first walks them once to mark, in two bit filters in
+// shared memory, the partners seen once and seen twice; the table then takes only partners whose
+// seen-twice bit is set -- every partner with count >= 2, all its products, plus the few count-1
+// partners that share a filter bit with another -- so it is sized for the kept partners rather
+// than every partner (reads sharing one chance k-mer outnumber true overlaps many times over in
+// large genomes). Entries below min_shared are dropped when the row is written, as before, so C is
+// unchanged.
 // Products of a row are enumerated warp by warp: a warp takes 32 consecutive entries of A's row,
 // scans their At row lengths in registers, and walks the flattened product list 32 at a time,
 // each lane finding its entry with a 5-step shuffle search.
@@ -310,9 +318,13 @@ __device__ __forceinline__ uint32_t at_value(const uint64_t *__restrict__ t_pair
 // redone in a global-memory table of the exact bound 2 min(w_i, n - 1) (GSLICE, never overflows);
 // a finished row is written to the temporary arrays at c_rp[i] (room for min(w_i / t, n - 1)
 // entries) and its length to nnz_row[i].
-template <bool GSLICE, bool FUSED>
+// FILT (fused shared-memory tables only, min_shared >= 2): the seen-once / seen-twice filters of
+// 2^log2F bits each sit before the table; partner k maps to bit k when n <= 2^log2F, else to a
+// multiplicative hash of k.
+template <bool GSLICE, bool FUSED, bool FILT = false>
 __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
                                                      const unsigned long long *__restrict__ nrows_p, int log2T,
+                                                     int log2F,
                                                      const int64_t *__restrict__ need, unsigned char *__restrict__ gpool,
                                                      int64_t slice_bytes, const int64_t *__restrict__ c_rp,
                                                      int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
@@ -329,7 +341,8 @@ __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *_
         const int32_t i = rows[rb];
         if (!SG_IN_BOUNDS(i >= 0 && i < g.n, 307, i)) continue;
         int lT = log2T;
-        unsigned char *tb = num_raw;
+        unsigned char *tb = FILT ? num_raw + ((size_t)2 << log2F) / 8 : num_raw;
+        uint32_t *F1 = (uint32_t *)num_raw, *F2 = F1 + ((1 << log2F) >> 5);
         if (GSLICE) {
             int64_t T;
             if (FUSED) {
@@ -355,6 +368,8 @@ __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *_
             cnt[x] = 0;
         }
         for (int x = threadIdx.x; x < T * S; x += blockDim.x) seeds[x] = SEED_NONE;
+        if (FILT)
+            for (int x = threadIdx.x; x < (2 << log2F) >> 5; x += blockDim.x) F1[x] = 0u;  // F1 and F2
         if (threadIdx.x == 0) {
             s_ctr = 0;
             s_ins = 0;
@@ -363,9 +378,25 @@ __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *_
         __syncthreads();
         const int64_t r0 = g.a_rp[i], r1 = g.a_rp[i + 1];
         const uint32_t msk = (uint32_t)T - 1u;
+        const bool fid = g.n <= ((int64_t)1 << log2F);
+        auto fbit = [&](int32_t k) -> uint32_t {
+            return fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
+        };
+        if (FILT) {  // seen once -> F1, seen again -> F2 (bits are only ever set)
+            for_each_product<false>(g, i, r0, r1, nullptr, [&](int32_t k, uint32_t, int64_t) {
+                const uint32_t b = fbit(k), m = 1u << (b & 31u);
+                if (((volatile uint32_t *)F2)[b >> 5] & m) return;
+                if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
+            });
+            __syncthreads();
+        }
         const int cap = (T >> 1) + (T >> 2);  // guessed tables: at most 3/4 T partners
         for_each_product<false>(g, i, r0, r1, guessed ? &s_ovf : nullptr, [&](int32_t k, uint32_t, int64_t idx) {
             if (guessed && *(volatile int *)&s_ovf) return;  // the row is abandoned
+            if (FILT) {  // seen once only: count 1 < min_shared
+                const uint32_t b = fbit(k);
+                if (!((F2[b >> 5] >> (b & 31u)) & 1u)) return;
+            }
             uint32_t h = hash_slot(k, lT);
             bool found = false;
             // exact sizes (T >= 2 * distinct_i) always find a free slot or k; a guessed table may
@@ -472,20 +503,66 @@ __global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *_
 
 static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
 
-// Fused path: guessed table size (as sym_need) and the row's output room min(w / t, n - 1).
-__global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, uint32_t t,
-                                  int64_t *__restrict__ need, int64_t *__restrict__ room) {
+// Sampled rows (every stride-th row, one block each): the products w, and the bits set in the
+// seen-once and seen-twice filters after the row's products -- about its distinct partners and
+// its partners seen at least twice. sums = {sum w, sum F1 bits, sum F2 bits}.
+__global__ void __launch_bounds__(512) sample_kernel(SpArgs g, const int64_t *__restrict__ work, int64_t stride,
+                                                    int log2F, unsigned long long *__restrict__ sums) {
+    extern __shared__ __align__(16) uint32_t smp_f[];
+    __shared__ unsigned long long s_c[2];
+    const int64_t i = (int64_t)blockIdx.x * stride;
+    if (i >= g.n) return;
+    const int nw = (1 << log2F) >> 5;
+    uint32_t *F1 = smp_f, *F2 = smp_f + nw;
+    for (int x = threadIdx.x; x < 2 * nw; x += blockDim.x) smp_f[x] = 0u;
+    if (threadIdx.x < 2) s_c[threadIdx.x] = 0ull;
+    __syncthreads();
+    const bool fid = g.n <= ((int64_t)1 << log2F);
+    for_each_product<false>(g, (int32_t)i, g.a_rp[i], g.a_rp[i + 1], nullptr, [&](int32_t k, uint32_t, int64_t) {
+        const uint32_t b = fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
+        const uint32_t m = 1u << (b & 31u);
+        if (((volatile uint32_t *)F2)[b >> 5] & m) return;
+        if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
+    });
+    __syncthreads();
+    unsigned long long c1 = 0, c2 = 0;
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) {
+        c1 += __popc(F1[x]);
+        c2 += __popc(F2[x]);
+    }
+    atomicAdd(&s_c[0], c1);
+    atomicAdd(&s_c[1], c2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(sums, (unsigned long long)(work[i] > 0 ? work[i] : 0));
+        atomicAdd(sums + 1, s_c[0]);
+        atomicAdd(sums + 2, s_c[1]);
+    }
+}
+
+// Fused path: guessed table size and the row's output room min(w / t, n - 1). The guess is
+// (w * fu) >> 16 for a sampled partner ratio fu (fixed point), or w >> shift without a sample.
+// Rows with w >= fwork (fwork > 0) take the filtered pass: their guess ((w * ff) >> 16, or
+// w >> fshift) goes to need_f and need is 0, else need_f is 0.
+__global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, uint64_t fu, uint32_t t,
+                                  int64_t fwork, int fshift, uint64_t ff, int64_t *__restrict__ need,
+                                  int64_t *__restrict__ need_f, int64_t *__restrict__ room) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t w = work[i];
+    need_f[i] = 0;
     if (w <= 0) {
         need[i] = 0;
         room[i] = 0;
         return;
     }
+    const bool filt = fwork > 0 && w >= fwork;
+    const uint64_t mul = filt ? ff : fu;
+    const int64_t g0 = mul ? (int64_t)(((unsigned __int128)w * mul) >> 16) : (w >> (filt ? fshift : shift));
     const int64_t exact = pow2_at_least(2 * (w < n - 1 ? w : n - 1));
-    const int64_t guess = pow2_at_least((w >> shift) > 64 ? (w >> shift) : 64);
-    need[i] = guess < exact ? guess : exact;
+    const int64_t guess = pow2_at_least(g0 > 64 ? g0 : 64);
+    (filt ? need_f : need)[i] = guess < exact ? guess : exact;
+    if (filt) need[i] = 0;
     const int64_t r = w / t;
     room[i] = r < n - 1 ? r : n - 1;
 }
@@ -528,6 +605,9 @@ static const char *const SYM_NAMES[] = {"spgemm_symbolic_t64", "spgemm_symbolic_
 static const char *const NUM_NAMES[] = {"spgemm_numeric_t64", "spgemm_numeric_t128", "spgemm_numeric_t256",
                                         "spgemm_numeric_t512", "spgemm_numeric_t1k", "spgemm_numeric_t2k",
                                         "spgemm_numeric_t4k", "spgemm_numeric_t8k", "spgemm_numeric_t16k"};
+static const char *const FIL_NAMES[] = {"spgemm_numeric_f64", "spgemm_numeric_f128", "spgemm_numeric_f256",
+                                        "spgemm_numeric_f512", "spgemm_numeric_f1k", "spgemm_numeric_f2k",
+                                        "spgemm_numeric_f4k", "spgemm_numeric_f8k", "spgemm_numeric_f16k"};
 
 sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S,
                        sg_overlap_csr *C, cudaStream_t s, Scratch &sc) {
@@ -539,15 +619,16 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     int64_t *need = sc.get<int64_t>(n + 1);
     int64_t *nnz_row = sc.get<int64_t>(n + 1);
     int64_t *dist = sc.get<int64_t>(n + 1);
-    unsigned long long *counts = sc.get<unsigned long long>(3 * NCNT + 1);
+    unsigned long long *counts = sc.get<unsigned long long>(4 * NCNT + 4);
     int32_t *lists = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
     int32_t *ovf = sc.get<int32_t>(2 * (n + 1));  // overflow list | unused list of the re-run
     if (!err || !work || !need || !nnz_row || !dist || !counts || !lists || !ovf) return SG_ERR_OOM;
     unsigned long long *sym_counts = counts, *num_counts = counts + NCNT, *unused = counts + 2 * NCNT;
     unsigned long long *ovf_count = counts + SP_NCLS + 1;
     unsigned long long *fz_counts = counts + 2 * NCNT + 1, *fz_ovf = fz_counts + SP_NCLS + 1;
+    unsigned long long *ff_counts = counts + 3 * NCNT + 1;  // filtered rows' classes + global class
     SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (3 * NCNT + 1) * sizeof(unsigned long long), s));
+    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (4 * NCNT + 4) * sizeof(unsigned long long), s));
     SG_CUDA_TRY(cudaMemsetAsync(nnz_row, 0, (n + 1) * sizeof(int64_t), s));
     SG_CUDA_TRY(cudaMemsetAsync(dist, 0, (n + 1) * sizeof(int64_t), s));
     int64_t *a_beg = sc.get<int64_t>(A->nnz + 1);
@@ -575,6 +656,17 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         fz.log2T[fz.ncls] = SP_MINLOG + fz.ncls;
         fz.ncls++;
     }
+    // filtered rows (fused path): two filters of 2^log2F bits, one bit per read while n fits
+    int log2F = 10;
+    while (log2F < (int)tune("spgemm_filter_log2") && ((int64_t)1 << log2F) < n) log2F++;
+    const size_t fbytes = ((size_t)2 << log2F) / 8;
+    Classes ff{};
+    ff.ncls = 0;
+    while (ff.ncls < SP_NCLS &&
+           num_table_bytes((int64_t)1 << (SP_MINLOG + ff.ncls), S, true) + fbytes <= (220u << 10)) {
+        ff.log2T[ff.ncls] = SP_MINLOG + ff.ncls;
+        ff.ncls++;
+    }
     // global-memory tables of the exact bound 2 min(w, n - 1) (rows beyond shared memory)
     const int64_t Tmax = pow2_at_least(2 * (n > 1 ? n - 1 : 1));
     const int64_t gslice_bytes = (int64_t)((num_table_bytes(Tmax, S) + 255) & ~(size_t)255);
@@ -582,21 +674,54 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     // ---- fused path (no symbolic pass): guessed tables, rows written to a temporary region
     if (tune("spgemm_fused")) {
         stage.emplace("SpGEMMNumeric", s);
-        int64_t *room = sc.get<int64_t>(n + 1), *tmp_off = sc.get<int64_t>(n + 1);
-        if (!room || !tmp_off) return SG_ERR_OOM;
+        int64_t *room = sc.get<int64_t>(n + 1), *tmp_off = sc.get<int64_t>(n + 1), *need_f = sc.get<int64_t>(n + 1);
+        int32_t *lists_f = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
+        if (!room || !tmp_off || !need_f || !lists_f) return SG_ERR_OOM;
+        // filtered rows: mode 2 always, mode 1 when the sample finds under half the partners recur
+        const int64_t fmode = tune("spgemm_filter_mode");
+        int64_t fwork = min_shared >= 2 && ff.ncls > 0 && fmode > 0 ? tune("spgemm_filter_work") : 0;
+        // table guesses from a sample of rows (large inputs only): partners per product, r1 distinct
+        // and r2 seen at least twice
+        uint64_t fu = 0, ffq = 0;
+        const int64_t nsamp = A->nnz >= tune("spgemm_sample_min_nnz") ? tune("spgemm_sample_rows") : 0;
+        bool recur = true;  // without a sample, mode 1 does not filter
+        if (nsamp > 0 && n > 0) {
+            const int64_t stride = n > nsamp ? n / nsamp : 1;
+            const int64_t nb = (n + stride - 1) / stride;
+            unsigned long long *sums = counts + 4 * NCNT + 1;  // zeroed with the counters
+            SG_CUDA_TRY(ensure_smem(sample_kernel, fbytes));
+            SG_LAUNCH("spgemm_sample", sample_kernel, nb, 256, fbytes, s, g, (const int64_t *)work, stride, log2F,
+                      sums);
+            unsigned long long h[3] = {0, 0, 0};
+            SG_CUDA_TRY(read_back(h, sums, sizeof(h), s));
+            if (h[0] > 0) {
+                const double pct = (double)tune("spgemm_guess_pct") / 100.0;
+                const double r1 = (double)h[1] / (double)h[0], r2 = (double)h[2] / (double)h[0];
+                fu = (uint64_t)(pct * r1 * 65536.0) + 1;
+                ffq = (uint64_t)(pct * r2 * 65536.0) + 1;
+                recur = r1 < 2.0 * r2;  // most partners recur: the filter would keep nearly all
+            }
+        }
+        if (fmode == 1 && recur) fwork = 0;
         SG_LAUNCH("fused_need", fused_need_kernel, blocks_for(n, NT), NT, 0, s, (const int64_t *)work, n,
-                  (int)tune("num_guess_shift"), min_shared, need, room);
+                  (int)tune("num_guess_shift"), fu, min_shared, fwork, (int)tune("spgemm_filter_shift"), ffq, need,
+                  need_f, room);
         SG_TRY(exclusive_scan<int64_t>(room, tmp_off, n, s, err));
         SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, fz, fz_counts, lists);
-        unsigned long long h_fz[NCNT];
+        if (fwork)
+            SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need_f, n, ff, ff_counts, lists_f);
+        unsigned long long h_fz[NCNT], h_ff[NCNT];
         int64_t tmp_n = 0;
         uint32_t herr = 0;
+        SG_CUDA_TRY(cudaMemcpyAsync(h_ff, ff_counts, sizeof(h_ff), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(cudaMemcpyAsync(h_fz, fz_counts, sizeof(h_fz), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(read_back(&tmp_n, tmp_off + n, sizeof(int64_t), s));
         if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
         const double tmp_bytes = (double)tmp_n * (8.0 + 8.0 * S);
-        if (tmp_bytes <= (double)tune("spgemm_fused_max_mb") * 1048576.0) {
+        // the region is reserved, mostly untouched: at most half of what the device can still give
+        const double avail = (double)device_bytes_available();
+        if (tmp_bytes <= (double)tune("spgemm_fused_max_mb") * 1048576.0 && tmp_bytes <= 0.5 * avail) {
             int32_t *t_col = sc.get<int32_t>(tmp_n + 1);
             uint32_t *t_cnt = sc.get<uint32_t>(tmp_n + 1);
             uint32_t *t_si = sc.get<uint32_t>((size_t)S * tmp_n + 1), *t_sk = sc.get<uint32_t>((size_t)S * tmp_n + 1);
@@ -606,26 +731,42 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 const size_t sm = num_table_bytes((int64_t)1 << fz.log2T[c], S, true);
                 SG_CUDA_TRY(ensure_smem(numeric_kernel<false, true>, sm));
                 SG_LAUNCH(NUM_NAMES[fz.log2T[c] - SP_MINLOG], (numeric_kernel<false, true>), grid,
-                          pick_threads(fz.log2T[c]), sm, s, g, lists + (int64_t)c * n, fz_counts + c, fz.log2T[c],
+                          pick_threads(fz.log2T[c]), sm, s, g, lists + (int64_t)c * n, fz_counts + c, fz.log2T[c], 0,
                           (const int64_t *)need, (unsigned char *)nullptr, (int64_t)0, (const int64_t *)tmp_off,
                           t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work, ovf, fz_ovf, nnz_row);
             }
+            for (int c = 0; fwork && c < ff.ncls; c++) {  // rows with many products: filtered first
+                if (!h_ff[c]) continue;
+                const size_t sm = num_table_bytes((int64_t)1 << ff.log2T[c], S, true) + fbytes;
+                SG_CUDA_TRY(ensure_smem(numeric_kernel<false, true, true>, sm));
+                SG_LAUNCH(FIL_NAMES[ff.log2T[c] - SP_MINLOG], (numeric_kernel<false, true, true>), grid,
+                          ff.log2T[c] <= 11 ? 256 : 512, sm, s, g, lists_f + (int64_t)c * n, ff_counts + c,
+                          ff.log2T[c], log2F, (const int64_t *)need_f, (unsigned char *)nullptr, (int64_t)0,
+                          (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work, ovf,
+                          fz_ovf, nnz_row);
+            }
             unsigned long long n_ovf = 0;
             SG_CUDA_TRY(read_back(&n_ovf, fz_ovf, sizeof(n_ovf), s));
-            const unsigned long long n_big = h_fz[fz.ncls];
-            if (n_big + n_ovf > 0) {
-                const unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
+            const unsigned long long n_big = h_fz[fz.ncls], n_big_f = fwork ? h_ff[ff.ncls] : 0;
+            if (n_big + n_big_f + n_ovf > 0) {
+                unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
+                rows_g = rows_g > n_big_f ? rows_g : n_big_f;
                 const int ggrid = (int)(rows_g < 152 * 2 ? rows_g : 152 * 2);
                 unsigned char *pool = sc.get<unsigned char>((size_t)gslice_bytes * ggrid);
                 if (!pool) return SG_ERR_OOM;
                 if (n_big)
                     SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
-                              lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, 0, (const int64_t *)need, pool,
+                              lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, 0, 0, (const int64_t *)need, pool,
                               gslice_bytes, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n,
+                              (const int64_t *)work, ovf + n + 1, unused, nnz_row);
+                if (n_big_f)
+                    SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
+                              lists_f + (int64_t)ff.ncls * n, ff_counts + ff.ncls, 0, 0, (const int64_t *)need_f,
+                              pool, gslice_bytes, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n,
                               (const int64_t *)work, ovf + n + 1, unused, nnz_row);
                 if (n_ovf)
                     SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
-                              (const int32_t *)ovf, fz_ovf, 0, (const int64_t *)need, pool, gslice_bytes,
+                              (const int32_t *)ovf, fz_ovf, 0, 0, (const int64_t *)need, pool, gslice_bytes,
                               (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work,
                               ovf + n + 1, unused, nnz_row);
             }
@@ -714,7 +855,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         const size_t sm = num_table_bytes((int64_t)1 << num.log2T[c], S);
         SG_CUDA_TRY(ensure_smem(numeric_kernel<false, false>, sm));
         SG_LAUNCH(NUM_NAMES[num.log2T[c] - SP_MINLOG], (numeric_kernel<false, false>), grid,
-                  pick_threads(num.log2T[c]), sm, s, g, lists + (int64_t)c * n, num_counts + c, num.log2T[c],
+                  pick_threads(num.log2T[c]), sm, s, g, lists + (int64_t)c * n, num_counts + c, num.log2T[c], 0,
                   (const int64_t *)need, (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col,
                   C->count, C->seed_i, C->seed_k, nnz, (const int64_t *)nullptr, (int32_t *)nullptr,
                   (unsigned long long *)nullptr, (int64_t *)nullptr);
@@ -724,7 +865,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         unsigned char *pool = sc.get<unsigned char>((size_t)gslice_bytes * ggrid);
         if (!pool) return SG_ERR_OOM;
         SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, false>), ggrid, 512, 0, s, g,
-                  lists + (int64_t)num.ncls * n, num_counts + num.ncls, 0, (const int64_t *)need, pool, gslice_bytes,
+                  lists + (int64_t)num.ncls * n, num_counts + num.ncls, 0, 0, (const int64_t *)need, pool,
+                  gslice_bytes,
                   (const int64_t *)C->row_ptr, C->col, C->count, C->seed_i, C->seed_k, nnz, (const int64_t *)nullptr,
                   (int32_t *)nullptr, (unsigned long long *)nullptr, (int64_t *)nullptr);
     }

@@ -46,6 +46,13 @@ CONFIGS = [
     {"num_guess_shift": 8},                                          # fused, most rows overflow
     {"num_guess_shift": 0},                                          # fused, exact-bound guesses
     {"spgemm_fused_max_mb": 0},                                      # fused path over budget: fallback
+    {"spgemm_filter_work": 0},                                       # no seen-twice filter
+    {"spgemm_filter_mode": 2, "spgemm_filter_work": 1},              # every row filtered first
+    {"spgemm_filter_mode": 2, "spgemm_filter_work": 1, "spgemm_filter_shift": 8},  # filtered rows overflow
+    {"spgemm_sample_min_nnz": 0},                                    # sampled guesses
+    {"spgemm_sample_min_nnz": 0, "spgemm_sample_rows": 1, "spgemm_guess_pct": 25},  # tables too small
+    {"spgemm_sample_min_nnz": 0, "spgemm_guess_pct": 10000},         # tables at the exact bound
+    {"spgemm_sample_min_nnz": 0, "spgemm_filter_mode": 2, "spgemm_filter_work": 1},  # sampled, filtered
 ]
 
 
@@ -73,6 +80,30 @@ def test_tunables_never_change_results(medium, cfg):
         S, it = sg.transitive_reduce(sg.DeviceGraph.from_numpy(d["R"]), w.fuzz)
         assert_graph_equal(S.to_numpy(), eS)
         assert it == eit
+    finally:
+        for k, v in saved.items():
+            sg.tune(k, v)
+
+
+@pytest.mark.parametrize("cfg", [{"spgemm_filter_mode": 2, "spgemm_filter_work": 1, "spgemm_filter_log2": 10},
+                                 {"spgemm_filter_mode": 2, "spgemm_filter_work": 1, "spgemm_filter_log2": 10,
+                                  "spgemm_filter_shift": 6}],
+                         ids=["hashed-filter", "hashed-filter-small-tables"])
+def test_hashed_seen_twice_filter(cfg):
+    """More reads (about 1500) than filter bits (2^10): partners share filter bits, count-1
+    partners reach the table, and C must still be exact."""
+    w = synth.BACTERIAL.scaled(0.1)
+    d = synth.make(w)
+    km = oracle.build_kmer_matrix(d["seq"], d["offsets"], w.k, w.lo, w.hi)
+    assert km["A"]["n_rows"] > 1024
+    eC = oracle.overlap_spgemm(km["A"], km["At"], w.min_shared, w.max_seeds)
+    saved = sg.tunables()
+    try:
+        for k, v in cfg.items():
+            sg.tune(k, v)
+        gkm, got = gpu_kmer(d["seq"], d["offsets"], w.k, w.lo, w.hi)
+        assert_kmer_equal(got, km)
+        assert_overlap_equal(sg.overlap_spgemm(gkm, w.min_shared, w.max_seeds).to_numpy(), eC)
     finally:
         for k, v in saved.items():
             sg.tune(k, v)
