@@ -229,6 +229,7 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     launches0 = sg.launch_count()
+    sg.memory_reset_peak()
     sg.prof_enable(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     tr_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -245,6 +246,7 @@ def main():
     torch.cuda.synchronize()
     sg.prof_enable(False)
     launches = sg.launch_count() - launches0
+    mem_peak = sg.memory_stats()[2]
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -317,7 +319,7 @@ def main():
             "tr_edges_per_s": edges_all * args.steps / (tr_ms_max / 1e3) if tr_ms_max else None,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
             "e2e": e2e, "roofline": roof, "kernels": kernels, "stages": stages, "clocks": clk,
-            "gpu_launches": launches, "from_seeds": from_seeds}
+            "gpu_launches": launches, "device_memory_peak_gb": mem_peak / 1e9, "from_seeds": from_seeds}
     if not args.no_forms:
         line["batched"] = measure_batched(sg, 512, 200e3)
         line["served"] = measure_served(sg, 400, 200.0)

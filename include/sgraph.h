@@ -411,6 +411,15 @@ void sg_last_kmer_stats(sg_kmer_stats *out);
 /* Number of kernels this library has launched in this process. */
 uint64_t sg_launch_count(void);
 
+/* Device memory of the library's pool on the current device, in bytes: reserved = held by the
+ * pool (freed memory stays reserved for reuse), in_use = allocated and not yet freed (library
+ * outputs the caller still holds, and work memory of calls in flight), in_use_peak = the largest
+ * in_use since the pool was created or sg_memory_reset_peak. All 0 while an allocator installed by
+ * sg_set_allocator is in use. NULL pointers are skipped. Returns SG_OK, or SG_ERR_CUDA if the pool
+ * cannot be queried. */
+sg_status sg_memory_stats(uint64_t *reserved, uint64_t *in_use, uint64_t *in_use_peak);
+void sg_memory_reset_peak(void);
+
 /* Tunable launch parameters (used by the autotuner; results never depend on them):
  *   bloom_bits            bits of the first-level Bloom filter per window (8): fewer bits, fewer
  *                         slices but more false positives (singletons that reach the exact count)

@@ -29,7 +29,7 @@ EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg
            "sg_server_create", "sg_server_submit", "sg_server_poll", "sg_server_wait", "sg_job_result_free",
            "sg_server_destroy", "sg_server_cancel",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
-           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_stall_lookback", "sg_debug_check", "sg_last_kmer_stats", "sg_launch_count", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_stall_lookback", "sg_debug_check", "sg_last_kmer_stats", "sg_launch_count", "sg_memory_stats", "sg_memory_reset_peak", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
 
 
@@ -172,6 +172,7 @@ def lib():
         L.sg_debug_fail_alloc_after.argtypes = [i64]
         L.sg_debug_stall_lookback.argtypes = [ctypes.c_int]
         L.sg_launch_count.restype = ctypes.c_uint64
+        L.sg_memory_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64)] * 3
         L.sg_debug_check.restype = ctypes.c_uint64
         L.sg_prof_enable.argtypes = [ctypes.c_int]
         L.sg_prof_select.argtypes = [ctypes.c_char_p]
@@ -477,6 +478,18 @@ def last_kmer_stats() -> dict:
     st = KmerStats()
     lib().sg_last_kmer_stats(ctypes.byref(st))
     return {f: int(getattr(st, f)) for f, _ in KmerStats._fields_}
+
+
+def memory_stats() -> tuple:
+    """(reserved, in_use, in_use_peak) bytes of the library's device memory pool (see
+    sg_memory_stats)."""
+    r, u, h = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().sg_memory_stats(ctypes.byref(r), ctypes.byref(u), ctypes.byref(h)), "memory_stats")
+    return int(r.value), int(u.value), int(h.value)
+
+
+def memory_reset_peak():
+    lib().sg_memory_reset_peak()
 
 
 def launch_count() -> int:

@@ -54,6 +54,15 @@ struct Scratch {
         if (p) ptrs.push_back(p);
         return (T *)p;
     }
+    // releases one buffer before scope exit (stream-ordered: later work may reuse its memory)
+    void release(const void *p) {
+        for (size_t i = ptrs.size(); i-- > 0;)
+            if (ptrs[i] == p) {
+                dfree(ptrs[i], s);
+                ptrs.erase(ptrs.begin() + (std::ptrdiff_t)i);
+                return;
+            }
+    }
     ~Scratch() { for (size_t i = ptrs.size(); i-- > 0;) dfree(ptrs[i], s); }
 };
 

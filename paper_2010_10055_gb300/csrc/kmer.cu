@@ -517,9 +517,11 @@ __global__ void emit_at_kernel(const uint32_t *__restrict__ head, const int64_t 
 constexpr int SEG_WALK_MAX = 64;
 constexpr int PK_SHIFT = 31;
 
+// nkeep receives the number of kept entries (nnz), which must stay below 2^31 for the packed
+// scan.
 __global__ void seg_flags_kernel(const uint64_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t nc,
                                  uint32_t lo, uint32_t hi, const uint32_t *__restrict__ lohi, int kbits, int hmax,
-                                 uint64_t *__restrict__ packed) {
+                                 uint64_t *__restrict__ packed, unsigned long long *__restrict__ nkeep) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const uint64_t k = key[i];
@@ -543,12 +545,15 @@ __global__ void seg_flags_kernel(const uint64_t *__restrict__ key, const uint64_
     const bool head = h == i;
     const bool first = head || (val[i] >> 32) != (val[i - 1] >> 32);
     packed[i] = (uint64_t)(rel && head) | ((uint64_t)(rel && first) << PK_SHIFT);
+    const unsigned act = __activemask();  // the lanes here now; each lane is counted once
+    const unsigned kept = __ballot_sync(act, rel && first);
+    if ((int)(threadIdx.x & 31) == __ffs(act) - 1 && kept) atomicAdd(nkeep, (unsigned long long)__popc(kept));
 }
 
 // Writes At's entries, its row pointers, the column codes and the (read, col|val) pairs sorted
-// into A, from the fused flags and their exclusive scan (low 31 bits: reliable segments before,
-// high bits: kept entries before).
-__global__ void emit_fused_kernel(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ pre,
+// into A, from the exclusive scan of the fused flags (low 31 bits: reliable segments before, high
+// bits: kept entries before; pre[nc] = the totals). Entry i's own flags are pre[i + 1] - pre[i].
+__global__ void emit_fused_kernel(const uint64_t *__restrict__ pre,
                                   const uint64_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t nc,
                                   int64_t m, int64_t nnz, int32_t *__restrict__ at_col, uint32_t *__restrict__ at_val,
                                   int64_t *__restrict__ at_rp, uint64_t *__restrict__ codes,
@@ -557,9 +562,9 @@ __global__ void emit_fused_kernel(const uint64_t *__restrict__ packed, const uin
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) at_rp[m] = nnz;
     if (i >= nc) return;
-    const uint64_t f = packed[i];
-    if (f == 0) return;
     const uint64_t x = pre[i];
+    const uint64_t f = pre[i + 1] - x;
+    if (f == 0) return;
     const uint64_t lowmask = (1ull << PK_SHIFT) - 1;
     const int64_t before = (int64_t)(x & lowmask), o = (int64_t)(x >> PK_SHIFT);
     const int64_t col = before + (int64_t)(f & 1) - 1;  // the segment's column (its head counted)
@@ -710,12 +715,17 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     while (((int64_t)1 << ibits) < nc) ibits++;
     const int mode = code_bits + qbits + 1 <= 64 ? PK_POS : (code_bits + ibits <= 64 ? PK_IDX : PK_PAIRS);
     const int pb = mode == PK_POS ? qbits + 1 : (mode == PK_IDX ? ibits : 0);
-    uint64_t *key0 = sc.get<uint64_t>(nc), *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
+    // buffers live only as long as they are needed, so that the pool can hand their memory to the
+    // next phase: the emitted records, then (once the window hashes and filters are gone) the
+    // sort's second buffers
+    uint64_t *key0 = sc.get<uint64_t>(nc);
     uint64_t *val0 = mode == PK_POS ? nullptr : sc.get<uint64_t>(nc);
-    if (!key0 || !key1 || !val1 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
+    if (!key0 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
     SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)P, k, jp, (const uint32_t *)cmask,
               (const int64_t *)wpos, mode, pb, kmask, key0, val0, nc);
     early.reset();
+    uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
+    if (!key1 || !val1) return SG_ERR_OOM;
     bool alt = false;
     const uint64_t *key;
     uint64_t *val;
@@ -739,27 +749,46 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
                   nc, mode, pb, off, n, (const int32_t *)lut, nlut, kfree, val1);
         key = kfree;
         val = val1;
+        sc.release(ks);
+        if (val0) sc.release(val0);
     } else {
         SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, code_bits, &alt, s, err)));
         key = alt ? key1 : key0;
         val = alt ? val1 : val0;
+        sc.release(alt ? key0 : key1);
+        sc.release(alt ? val0 : val1);
         SG_LAUNCH("resolve", resolve_kernel, blocks_for(nc, NT), NT, 0, s, val, nc, off, n, (const int32_t *)lut,
                   nlut);
     }
 
     // segments -> exact frequency -> reliable -> columns; kept entries -> At
-    const bool fused = hmax <= (uint32_t)SEG_WALK_MAX && nc < ((int64_t)1 << PK_SHIFT);
+    // The fused form packs (reliable segments, kept entries) into one scanned 64-bit word whose
+    // look-back keeps 62 bits: segments < 2^31 (at most nc / 2 with the Bloom filter, each reliable
+    // segment holding >= lo >= 2 entries) and kept entries < 2^31 (counted first).
+    bool fused = hmax <= (uint32_t)SEG_WALK_MAX && nc < ((int64_t)1 << 32) &&
+                 (use_bloom || nc < ((int64_t)1 << PK_SHIFT));
     uint32_t *head = nullptr, *rel = nullptr, *keep = nullptr;
     int64_t *seg_excl = nullptr, *seg_start = nullptr, *col_of_seg = nullptr, *out_pos = nullptr;
-    uint64_t *flags = nullptr, *pre = nullptr;
+    uint64_t *pre = nullptr;
     int64_t sizes[2] = {0, 0};  // m, nnz
     if (fused) {
-        flags = sc.get<uint64_t>(nc + 1);
         pre = sc.get<uint64_t>(nc + 1);
-        if (!flags || !pre) return SG_ERR_OOM;
+        unsigned long long *nkeep = sc.get<unsigned long long>(1);
+        if (!pre || !nkeep) return SG_ERR_OOM;
+        SG_CUDA_TRY(cudaMemsetAsync(nkeep, 0, sizeof(unsigned long long), s));
         SG_LAUNCH("seg_flags", seg_flags_kernel, blocks_for(nc, NT), NT, 0, s, key, (const uint64_t *)val, nc, lo, hi,
-                  lohi, 2 * k, (int)hmax, flags);
-        SG_TRY(exclusive_scan<int64_t>((const int64_t *)flags, (int64_t *)pre, nc, s, err));
+                  lohi, 2 * k, (int)hmax, pre, nkeep);
+        unsigned long long hk = 0;
+        SG_CUDA_TRY(read_back(&hk, nkeep, sizeof(hk), s));
+        if (hk >= (1ull << PK_SHIFT)) {  // too many kept entries for the packed scan
+            sc.release(pre);
+            pre = nullptr;
+            fused = false;
+        }
+    }
+    if (fused) {
+        // flags scanned in place: each tile reads its items before it writes them
+        SG_TRY(exclusive_scan<int64_t>((const int64_t *)pre, (int64_t *)pre, nc, s, err));
         uint64_t tot = 0;
         SG_CUDA_TRY(cudaMemcpyAsync(&tot, pre + nc, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -797,29 +826,36 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         return SG_ERR_OVERFLOW;
     }
 
-    // outputs
+    // outputs: At and the column codes now, A once the candidate records are gone
     SG_ALLOC(At->row_ptr, int64_t, m + 1, s);
     SG_ALLOC(At->col, int32_t, nnz, s);
     SG_ALLOC(At->val, uint32_t, nnz, s);
-    SG_ALLOC(A->row_ptr, int64_t, n + 1, s);
-    SG_ALLOC(A->col, int32_t, nnz, s);
-    SG_ALLOC(A->val, uint32_t, nnz, s);
     SG_ALLOC(*codes_out, uint64_t, m, s);
     At->n_rows = m; At->n_cols = n; At->nnz = nnz;
-    A->n_rows = n; A->n_cols = m; A->nnz = nnz;
 
     stage.emplace("CreateSpMat", s);  // a5: At, then A by a sort on the read
-    uint32_t *ak0 = sc.get<uint32_t>(nnz), *ak1 = sc.get<uint32_t>(nnz);
-    uint64_t *av0 = sc.get<uint64_t>(nnz), *av1 = sc.get<uint64_t>(nnz);
-    if (!ak0 || !ak1 || !av0 || !av1) return SG_ERR_OOM;
+    uint32_t *ak0 = sc.get<uint32_t>(nnz);
+    uint64_t *av0 = sc.get<uint64_t>(nnz);
+    if (!ak0 || !av0) return SG_ERR_OOM;
     if (fused)
-        SG_LAUNCH("emit_at", emit_fused_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, (const uint64_t *)flags,
-                  (const uint64_t *)pre, key, (const uint64_t *)val, nc, m, nnz, At->col, At->val, At->row_ptr,
-                  *codes_out, ak0, av0, 2 * k, job_ncols);
+        SG_LAUNCH("emit_at", emit_fused_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, (const uint64_t *)pre, key,
+                  (const uint64_t *)val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0, av0, 2 * k,
+                  job_ncols);
     else
         SG_LAUNCH("emit_at", emit_at_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, head, seg_excl, rel,
                   col_of_seg, keep, out_pos, key, val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0,
                   av0, 2 * k, job_ncols);
+    for (const void *p : {(const void *)key, (const void *)val, (const void *)pre,
+                          (const void *)head, (const void *)seg_excl, (const void *)seg_start, (const void *)rel,
+                          (const void *)col_of_seg, (const void *)keep, (const void *)out_pos})
+        if (p) sc.release(p);
+    SG_ALLOC(A->row_ptr, int64_t, n + 1, s);
+    SG_ALLOC(A->col, int32_t, nnz, s);
+    SG_ALLOC(A->val, uint32_t, nnz, s);
+    A->n_rows = n; A->n_cols = m; A->nnz = nnz;
+    uint32_t *ak1 = sc.get<uint32_t>(nnz);
+    uint64_t *av1 = sc.get<uint64_t>(nnz);
+    if (!ak1 || !av1) return SG_ERR_OOM;
     int rbits = 0;
     while (rbits < 32 && ((int64_t)1 << rbits) < n) rbits++;
     kmer_stats().m = m;

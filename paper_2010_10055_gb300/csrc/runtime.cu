@@ -325,6 +325,28 @@ void sg_free(void *d_ptr, sg_stream_t stream) { sg::dfree(d_ptr, (cudaStream_t)s
 
 uint64_t sg_launch_count(void) { return sg::g_launches.load(); }
 
+sg_status sg_memory_stats(uint64_t *reserved, uint64_t *in_use, uint64_t *in_use_peak) {
+    uint64_t r = 0, u = 0, h = 0;
+    cudaMemPool_t pool = sg::g_alloc ? nullptr : sg::library_pool();
+    if (pool && (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess ||
+                 cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess ||
+                 cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &h) != cudaSuccess)) {
+        cudaGetLastError();
+        sg::set_error("memory_stats: the pool cannot be queried");
+        return SG_ERR_CUDA;
+    }
+    if (reserved) *reserved = r;
+    if (in_use) *in_use = u;
+    if (in_use_peak) *in_use_peak = h;
+    return SG_OK;
+}
+
+void sg_memory_reset_peak(void) {
+    cudaMemPool_t pool = sg::g_alloc ? nullptr : sg::library_pool();
+    uint64_t zero = 0;
+    if (pool && cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess) cudaGetLastError();
+}
+
 void sg_last_kmer_stats(sg_kmer_stats *out) {
     if (out) *out = sg::g_kstats;
 }

@@ -543,9 +543,10 @@ __global__ void __launch_bounds__(512) sample_kernel(SpArgs g, const int64_t *__
 // Fused path: guessed table size and the row's output room min(w / t, n - 1). The guess is
 // (w * fu) >> 16 for a sampled partner ratio fu (fixed point), or w >> shift without a sample.
 // Rows with w >= fwork (fwork > 0) take the filtered pass: their guess ((w * ff) >> 16, or
-// w >> fshift) goes to need_f and need is 0, else need_f is 0.
+// w >> fshift, at most fcap = the largest filtered shared-memory table) goes to need_f and need is
+// 0, else need_f is 0.
 __global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, uint64_t fu, uint32_t t,
-                                  int64_t fwork, int fshift, uint64_t ff, int64_t *__restrict__ need,
+                                  int64_t fwork, int fshift, uint64_t ff, int64_t fcap, int64_t *__restrict__ need,
                                   int64_t *__restrict__ need_f, int64_t *__restrict__ room) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -560,7 +561,8 @@ __global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, i
     const uint64_t mul = filt ? ff : fu;
     const int64_t g0 = mul ? (int64_t)(((unsigned __int128)w * mul) >> 16) : (w >> (filt ? fshift : shift));
     const int64_t exact = pow2_at_least(2 * (w < n - 1 ? w : n - 1));
-    const int64_t guess = pow2_at_least(g0 > 64 ? g0 : 64);
+    int64_t guess = pow2_at_least(g0 > 64 ? g0 : 64);
+    if (filt && guess > fcap) guess = fcap;  // kept partners are few: try the largest table first
     (filt ? need_f : need)[i] = guess < exact ? guess : exact;
     if (filt) need[i] = 0;
     const int64_t r = w / t;
@@ -704,8 +706,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         }
         if (fmode == 1 && recur) fwork = 0;
         SG_LAUNCH("fused_need", fused_need_kernel, blocks_for(n, NT), NT, 0, s, (const int64_t *)work, n,
-                  (int)tune("num_guess_shift"), fu, min_shared, fwork, (int)tune("spgemm_filter_shift"), ffq, need,
-                  need_f, room);
+                  (int)tune("num_guess_shift"), fu, min_shared, fwork, (int)tune("spgemm_filter_shift"), ffq,
+                  ff.ncls > 0 ? (int64_t)1 << ff.log2T[ff.ncls - 1] : (int64_t)64, need, need_f, room);
         SG_TRY(exclusive_scan<int64_t>(room, tmp_off, n, s, err));
         SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, fz, fz_counts, lists);
         if (fwork)

@@ -107,3 +107,67 @@ def test_hashed_seen_twice_filter(cfg):
     finally:
         for k, v in saved.items():
             sg.tune(k, v)
+
+
+def _every_entry_point(w, d):
+    """One pass through every device entry point on the workload, all outputs released."""
+    seq, off = dev(d["seq"], np.uint8), dev(d["offsets"], np.int64)
+    km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+    C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+    G = sg.overlap_graph_from_seeds(C, off, w.k, w.min_overlap)
+    R = sg.DeviceGraph.from_numpy(d["R"])
+    S, _ = sg.transitive_reduce(R, w.fuzz)
+    S1, _, _ = sg.transitive_reduce_rounds(R, w.fuzz, max_rounds=1)
+    N = sg.minplus_square(R)  # torch outputs; its work memory is the library's
+    hp = sg.HostPipeline()
+    hp.run(d["seq"], d["offsets"], w, d["R"])
+    hp.close()
+    b = sg.run_batch([dict(seq=seq, offsets=off, lo=w.lo, hi=w.hi, R=R)] * 2, k=w.k, fuzz=w.fuzz)
+    b.free()
+    for x in (km, C, G, S, S1):
+        x.free()
+    del N
+
+
+def test_every_call_returns_its_memory(medium):
+    """After the outputs are freed, the library pool's in-use bytes return to where they were, for
+    every entry point and for calls that fail part way (allocation failures injected at each
+    successive allocation of the k-mer, SpGEMM and reduction calls)."""
+    import gc
+
+    import torch
+    w, d = medium[0], medium[1]
+    _every_entry_point(w, d)
+    torch.cuda.synchronize()
+    gc.collect()
+    base = sg.memory_stats()[1]
+    _every_entry_point(w, d)
+    torch.cuda.synchronize()
+    gc.collect()
+    assert sg.memory_stats()[1] == base
+    seq, off = dev(d["seq"], np.uint8), dev(d["offsets"], np.int64)
+    km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+    R = sg.DeviceGraph.from_numpy(d["R"])
+    torch.cuda.synchronize()
+    held = sg.memory_stats()[1]
+    calls = [lambda: sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi),
+             lambda: sg.overlap_spgemm(km, w.min_shared, w.max_seeds),
+             lambda: sg.transitive_reduce(R, w.fuzz)[0]]
+    for call in calls:
+        for nth in range(1, 80):
+            sg.debug_fail_alloc_after(nth)
+            try:
+                out = call()
+            except sg.SgError as e:
+                assert e.status == sg.SG_ERR_OOM
+                out = None
+            finally:
+                sg.debug_fail_alloc_after(0)
+            if out is None:
+                torch.cuda.synchronize()
+                gc.collect()
+                assert sg.memory_stats()[1] == held, nth
+            else:  # fewer allocations than nth: the call completed
+                out.free()
+                break
+    km.free()
