@@ -112,6 +112,11 @@ def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
     4-byte filter words (a touch is a read and a write), 8-byte keys, 24-byte C entries."""
     if kernel == "pack":
         return 1.0 * sz["total"] + 4.25 * sz["total"]          # bases in; hash + packed base out
+    k = sz.get("kstats") or {}
+    if kernel == "bloom_insert" and k.get("bloom_bins"):      # shared-memory bins: binned hashes in, B2 out
+        return 4.0 * sz["windows"] + k["bloom_b2_bytes"]
+    if kernel == "bloom_bin_scatter":                         # hashes in, binned hashes out
+        return 4.0 * sz["total"] + 4.0 * sz["windows"]
     if kernel == "bloom_insert":
         return 4.0 * sz["total"] + 8.0 * sz["windows"]         # hashes in + filter word read and write
     if kernel == "cand_count":

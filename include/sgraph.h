@@ -401,10 +401,13 @@ uint64_t sg_debug_check(void);
  * profiling: windows = sequence positions, candidates = windows that passed the Bloom filters and
  * were sorted, sort_key_bytes / sort_val_bytes = bytes per candidate through each radix pass
  * (val 0 when the window rides in the key), sort_passes = 8-bit passes over the candidates,
- * a_sort_passes = passes of the (read, entry) sort that forms A, m and nnz as in the outputs. */
+ * a_sort_passes = passes of the (read, entry) sort that forms A, m and nnz as in the outputs,
+ * bloom_bins = shared-memory filter bins (0: the filters were sliced global-memory arrays),
+ * bloom_b2_bytes = size of the seen-twice filter. */
 typedef struct {
     int64_t windows, candidates, m, nnz;
     int32_t sort_key_bytes, sort_val_bytes, sort_passes, a_sort_passes;
+    int64_t bloom_bins, bloom_b2_bytes;
 } sg_kmer_stats;
 void sg_last_kmer_stats(sg_kmer_stats *out);
 
@@ -427,6 +430,11 @@ void sg_memory_reset_peak(void);
  *   bloom_max_slices      at most this many Bloom launches, each streaming all window hashes;
  *                         for larger filters the slices grow instead (8)
  *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4 or 8 (4)
+ *   bloom_binned          1: when the filters cut into at most 4096 bins, the window hashes are
+ *                         grouped by bin and each bin's filters are built in shared memory (1)
+ *   bloom_bin_kb          first-filter kilobytes per bin (160; the second filter gets a quarter)
+ *   bloom_bin_room_pct    hash buffer per bin, % of the mean bin (112, plus 16 K); a bin that
+ *                         overflows sends the whole build to the sliced filters
  *   spgemm_fused          1: C in one numeric pass whose tables are sized from a guess (rows that
  *                         overflow are redone in exact-size global-memory tables) and whose rows
  *                         go to a temporary region; 0: symbolic pass (exact sizes), then numeric (1)

@@ -112,7 +112,8 @@ class Job(ctypes.Structure):
 class KmerStats(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int64), ("candidates", ctypes.c_int64), ("m", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("sort_key_bytes", ctypes.c_int32), ("sort_val_bytes", ctypes.c_int32),
-                ("sort_passes", ctypes.c_int32), ("a_sort_passes", ctypes.c_int32)]
+                ("sort_passes", ctypes.c_int32), ("a_sort_passes", ctypes.c_int32), ("bloom_bins", ctypes.c_int64),
+                ("bloom_b2_bytes", ctypes.c_int64)]
 
 
 class JobResult(ctypes.Structure):

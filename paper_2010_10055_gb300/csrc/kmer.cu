@@ -273,6 +273,121 @@ __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint32_t *__r
     }
 }
 
+// Binned Bloom insertion (when the filters split into at most BB_MAXBINS bins): B1 and B2 are cut
+// into bins of w1b and w2b words; a key's bin is that of its B1 word (idx1 / w1b), and its B2 word
+// lies in the same bin (bin * w2b + a word from its B2 hash). bin_scatter groups the window hashes
+// by bin (order within a bin is arbitrary: insertion into a filter is order-free); bin_insert runs
+// one block per bin with the bin's two slices in shared memory, so every filter update is a
+// shared-memory atomic, and writes the B2 slice out. B1 itself is never stored.
+struct BinnedBloom {
+    uint32_t nbins = 0;  // 0: the sliced global-memory filters
+    uint32_t w1b = 0, w2b = 0;
+    uint32_t nwords1 = 0;  // nbins * w1b
+    uint32_t cap = 0;      // hashes a bin can hold in the scatter buffer
+};
+
+constexpr int BS_NT = 512, BS_ITEMS = 16, BS_TILE = BS_NT * BS_ITEMS;
+constexpr int BB_MAXBINS = 4096;
+constexpr int BB_CSTRIDE = 32;  // bin cursors 128 bytes apart
+constexpr int BI_NT = 1024;
+
+__device__ __forceinline__ uint32_t bloom_mask(uint32_t h) {
+    const uint32_t g = h * 0x85EBCA6Bu;
+    return (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u)) | (1u << ((g >> 12) & 31u));
+}
+
+// B2 word and bits of a key (B1 hash h1) in the binned layout
+__device__ __forceinline__ void b2_binned(uint32_t h1, const BinnedBloom &bb, uint32_t *idx, uint32_t *mask) {
+    const uint32_t h2 = b2_hash(h1);
+    *idx = (__umulhi(h1, bb.nwords1) / bb.w1b) * bb.w2b + __umulhi(h2, bb.w2b);
+    *mask = bloom_mask(h2);
+}
+
+// One tile of BS_TILE hashes per block: count per bin, reserve each bin's run in its global buffer
+// (one atomic per bin and tile, on a cursor of its own 128-byte line), order the tile by bin in
+// shared memory, then write it out so that consecutive threads fill consecutive slots of a run.
+__global__ void __launch_bounds__(BS_NT, 2) bloom_bin_scatter_kernel(const uint32_t *__restrict__ H, int64_t nwin,
+                                                                 BinnedBloom bb, uint32_t *__restrict__ cursor,
+                                                                 uint32_t *__restrict__ Hb, uint32_t *__restrict__ ovf) {
+    extern __shared__ uint32_t bs_sm[];
+    uint32_t *cnt = bs_sm;                // [nbins] tile count per bin
+    uint32_t *lofs = cnt + bb.nbins;      // [nbins] the bin's first slot in the ordered tile
+    uint32_t *gbase = lofs + bb.nbins;    // [nbins] the bin's run in its global buffer
+    uint32_t *tile = gbase + bb.nbins;    // [BS_TILE] the tile ordered by bin
+    __shared__ uint32_t s_tmp[BS_NT / 32 + 1];
+    for (uint32_t b = threadIdx.x; b < bb.nbins; b += BS_NT) cnt[b] = 0u;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * BS_TILE;
+    uint32_t h[BS_ITEMS], bin[BS_ITEMS], rk[BS_ITEMS];
+#pragma unroll
+    for (int u = 0; u < BS_ITEMS; u++) {
+        const int64_t q = t0 + u * BS_NT + threadIdx.x;
+        h[u] = q < nwin ? __ldcs(H + q) : H_NONE;
+        bin[u] = __umulhi(h[u], bb.nwords1) / bb.w1b;  // < nbins
+        rk[u] = h[u] != H_NONE ? atomicAdd(cnt + bin[u], 1u) : 0u;
+    }
+    __syncthreads();
+    // thread t owns bins [t * per, t * per + per): their prefix, and their global runs
+    const uint32_t per = (bb.nbins + BS_NT - 1) / BS_NT;
+    const uint32_t b0 = threadIdx.x * per;
+    uint32_t mine = 0;
+    for (uint32_t b = b0; b < b0 + per && b < bb.nbins; b++) mine += cnt[b];
+    uint32_t ntot;
+    uint32_t run = block_exclusive_scan<BS_NT>(mine, s_tmp, &ntot);
+    for (uint32_t b = b0; b < b0 + per && b < bb.nbins; b++) {
+        const uint32_t c = cnt[b];
+        lofs[b] = run;
+        run += c;
+        gbase[b] = c ? atomicAdd(cursor + (size_t)b * BB_CSTRIDE, c) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < BS_ITEMS; u++)
+        if (h[u] != H_NONE) tile[lofs[bin[u]] + rk[u]] = h[u];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < ntot; i += BS_NT) {
+        const uint32_t hv = tile[i];
+        const uint32_t b = __umulhi(hv, bb.nwords1) / bb.w1b;
+        const uint32_t pos = gbase[b] + (i - lofs[b]);
+        if (pos < bb.cap) Hb[(int64_t)b * bb.cap + pos] = hv;
+        else *ovf = 1u;  // the bin is fuller than its room: the caller redoes the filters sliced
+    }
+}
+
+__global__ void __launch_bounds__(BI_NT) bloom_bin_insert_kernel(const uint32_t *__restrict__ Hb,
+                                                                const uint32_t *__restrict__ cursor, BinnedBloom bb,
+                                                                uint32_t *__restrict__ b2words) {
+    extern __shared__ uint32_t bi_sm[];
+    uint32_t *s1 = bi_sm, *s2 = bi_sm + bb.w1b;
+    const uint32_t bin = blockIdx.x;
+    for (uint32_t x = threadIdx.x; x < bb.w1b + bb.w2b; x += BI_NT) bi_sm[x] = 0u;
+    __syncthreads();
+    const uint32_t fill = cursor[(size_t)bin * BB_CSTRIDE];
+    const uint32_t c = fill < bb.cap ? fill : bb.cap;
+    const uint32_t *hb = Hb + (int64_t)bin * bb.cap;
+    const uint32_t lo1 = bin * bb.w1b;
+    constexpr int U = 4;  // loads in flight per thread
+    for (uint32_t i0 = threadIdx.x; i0 < c; i0 += U * BI_NT) {
+        uint32_t h[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) h[u] = i0 + u * BI_NT < c ? __ldcs(hb + i0 + u * BI_NT) : H_NONE;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (h[u] == H_NONE) continue;
+            const uint32_t w1 = __umulhi(h[u], bb.nwords1) - lo1;  // < w1b: the bin is that of the word
+            const uint32_t m1 = bloom_mask(h[u]);
+            if ((atomicOr(s1 + w1, m1) & m1) == m1) {
+                const uint32_t h2 = b2_hash(h[u]);
+                const uint32_t w2 = __umulhi(h2, bb.w2b), m2 = bloom_mask(h2);
+                if ((s2[w2] & m2) != m2) atomicOr(s2 + w2, m2);
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t *out = b2words + (int64_t)bin * bb.w2b;
+    for (uint32_t x = threadIdx.x; x < bb.w2b; x += BI_NT) out[x] = s2[x];
+}
+
 // Candidates: windows whose code tests positive in B2 (every occurrence of a k-mer seen at least
 // twice; false positives only add singletons, which the exact count drops). use_bloom == 0 keeps
 // every window (lo == 1: singletons may be reliable).
@@ -285,16 +400,19 @@ __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint32_t *__r
 constexpr int KM_GW = KM_CHUNK / KM_NT;  // groups per warp (32: one mask word per lane)
 static_assert(KM_GW == 32, "one mask word per lane");
 
-__device__ __forceinline__ bool is_candidate(uint32_t h, const Bloom &b2, int use_bloom) {
+__device__ __forceinline__ bool is_candidate(uint32_t h, const Bloom &b2, int use_bloom, const BinnedBloom &bb) {
     if (h == H_NONE) return false;
     if (!use_bloom) return true;
     uint32_t i2, m2;
-    b2.probe(b2_hash(h), &i2, &m2);
+    if (bb.nbins)
+        b2_binned(h, bb, &i2, &m2);
+    else
+        b2.probe(b2_hash(h), &i2, &m2);
     return (b2.words[i2] & m2) == m2;
 }
 
 __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__restrict__ H, int64_t nwin, Bloom b2,
-                                                          int use_bloom, uint32_t *__restrict__ cmask,
+                                                          int use_bloom, BinnedBloom bb, uint32_t *__restrict__ cmask,
                                                           uint32_t *__restrict__ wcnt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
@@ -309,7 +427,7 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__res
         }
 #pragma unroll
         for (int u = 0; u < CC_U; u++) {
-            const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(h[u], b2, use_bloom));
+            const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(h[u], b2, use_bloom, bb));
             if (lane == g0u + u) mine = m;
             c += __popc(m);
         }
@@ -522,32 +640,40 @@ constexpr int PK_SHIFT = 31;
 __global__ void seg_flags_kernel(const uint64_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t nc,
                                  uint32_t lo, uint32_t hi, const uint32_t *__restrict__ lohi, int kbits, int hmax,
                                  uint64_t *__restrict__ packed, unsigned long long *__restrict__ nkeep) {
+    __shared__ unsigned int s_kept;
+    if (threadIdx.x == 0) s_kept = 0u;
+    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nc) return;
-    const uint64_t k = key[i];
-    int64_t h = i, e = i + 1;
-    int back = 0, fwd = 0;
-    while (back <= hmax && h > 0 && key[h - 1] == k) {
-        h--;
-        back++;
+    bool kept = false;
+    if (i < nc) {
+        const uint64_t k = key[i];
+        int64_t h = i, e = i + 1;
+        int back = 0, fwd = 0;
+        while (back <= hmax && h > 0 && key[h - 1] == k) {
+            h--;
+            back++;
+        }
+        while (fwd <= hmax && e < nc && key[e] == k) {
+            e++;
+            fwd++;
+        }
+        uint32_t lo_i = lo, hi_i = hi;
+        if (lohi) {
+            const uint64_t job = k >> kbits;
+            lo_i = lohi[2 * job];
+            hi_i = lohi[2 * job + 1];
+        }
+        const int64_t len = e - h;
+        const bool rel = back <= hmax && fwd <= hmax && len >= (int64_t)lo_i && len <= (int64_t)hi_i;
+        const bool head = h == i;
+        const bool first = head || (val[i] >> 32) != (val[i - 1] >> 32);
+        packed[i] = (uint64_t)(rel && head) | ((uint64_t)(rel && first) << PK_SHIFT);
+        kept = rel && first;
     }
-    while (fwd <= hmax && e < nc && key[e] == k) {
-        e++;
-        fwd++;
-    }
-    if (lohi) {
-        const uint64_t job = k >> kbits;
-        lo = lohi[2 * job];
-        hi = lohi[2 * job + 1];
-    }
-    const int64_t len = e - h;
-    const bool rel = back <= hmax && fwd <= hmax && len >= (int64_t)lo && len <= (int64_t)hi;
-    const bool head = h == i;
-    const bool first = head || (val[i] >> 32) != (val[i - 1] >> 32);
-    packed[i] = (uint64_t)(rel && head) | ((uint64_t)(rel && first) << PK_SHIFT);
-    const unsigned act = __activemask();  // the lanes here now; each lane is counted once
-    const unsigned kept = __ballot_sync(act, rel && first);
-    if ((int)(threadIdx.x & 31) == __ffs(act) - 1 && kept) atomicAdd(nkeep, (unsigned long long)__popc(kept));
+    const unsigned m = __ballot_sync(0xffffffffu, kept);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&s_kept, (unsigned)__popc(m));
+    __syncthreads();
+    if (threadIdx.x == 0 && s_kept) atomicAdd(nkeep, (unsigned long long)s_kept);
 }
 
 // Writes At's entries, its row pointers, the column codes and the (read, col|val) pairs sorted
@@ -641,9 +767,12 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     // are emitted, before the sort allocates its buffers
     std::optional<Scratch> early;
     early.emplace(s);
-    if (use_bloom && total > 0) {
-        // B1: bloom_bits (8) bits per window; B2 ("seen twice"): 2 bits per window; 32-bit words
-        const int64_t w1 = total * tune("bloom_bits") / 32 + 1024, w2 = total / 16 + 1024;
+    BinnedBloom bb{};
+    // B1: bloom_bits (8) bits per window; B2 ("seen twice"): a quarter of B1; 32-bit words. Binned
+    // (shared-memory) filters when they cut into at most BB_MAXBINS bins of bloom_bin_kb KB of B1,
+    // else sliced global-memory filters.
+    auto sliced_filters = [&]() -> sg_status {
+        const int64_t w1 = total * tune("bloom_bits") / 32 + 1024, w2 = w1 / 4 + 256;
         b1.nwords = (uint32_t)(w1 < 0xFFFFFFF0LL ? w1 : 0xFFFFFFF0LL);
         b2.nwords = (uint32_t)(w2 < 0xFFFFFFF0LL ? w2 : 0xFFFFFFF0LL);
         b1.words = early->get<uint32_t>(b1.nwords);
@@ -651,6 +780,28 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         if (!b1.words || !b2.words) return SG_ERR_OOM;
         SG_CUDA_TRY(cudaMemsetAsync(b1.words, 0, (size_t)b1.nwords * 4, s));
         SG_CUDA_TRY(cudaMemsetAsync(b2.words, 0, (size_t)b2.nwords * 4, s));
+        return SG_OK;
+    };
+    if (use_bloom && total > 0) {
+        const int64_t w1 = total * tune("bloom_bits") / 32 + 1024;
+        const int64_t w1b = tune("bloom_bin_kb") * 256;
+        const int64_t nbins = (w1 + w1b - 1) / w1b;
+        if (tune("bloom_binned") && nbins <= BB_MAXBINS) {
+            bb.nbins = (uint32_t)nbins;
+            bb.w1b = (uint32_t)w1b;
+            bb.w2b = (uint32_t)(w1b / 4);
+            bb.nwords1 = (uint32_t)(nbins * w1b);
+            // a bin's expected hashes and room for repeats (bloom_bin_room_pct % of the mean, and
+            // 16 K more when that is at least 100 %)
+            const int64_t mean = total / nbins + 1, pct = tune("bloom_bin_room_pct");
+            bb.cap = (uint32_t)(mean * pct / 100 + (pct >= 100 ? 16384 : 0) + 1);
+            b1.nwords = bb.nwords1;  // never allocated in this form
+            b2.nwords = bb.nbins * bb.w2b;
+            b2.words = early->get<uint32_t>(b2.nwords);  // every word written by the bin pass
+            if (!b2.words) return SG_ERR_OOM;
+        } else {
+            SG_TRY(sliced_filters());
+        }
     }
     std::optional<StageScope> stage;
     stage.emplace("CountKmer", s);  // a1-a4: codes, Bloom, exact count, columns
@@ -671,7 +822,31 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_LAUNCH("pack", pack_kernel<decltype(kc)::value>, nblk, KM_NT, 0, s, seq, total, off, n, k, jp, P, H);
         return SG_OK;
     }));
-    if (use_bloom) {
+    if (use_bloom && bb.nbins) {
+        std::optional<Scratch> bins;
+        bins.emplace(s);
+        const size_t ncur = (size_t)bb.nbins * BB_CSTRIDE;
+        uint32_t *cursor = bins->get<uint32_t>(ncur + 1);  // [nbins, padded] fill | overflow flag
+        uint32_t *Hb = bins->get<uint32_t>((size_t)bb.nbins * bb.cap);
+        if (!cursor || !Hb) return SG_ERR_OOM;
+        SG_CUDA_TRY(cudaMemsetAsync(cursor, 0, (ncur + 1) * sizeof(uint32_t), s));
+        const int64_t nwin = ngroups * 32;
+        const size_t ssm = ((size_t)3 * bb.nbins + BS_TILE) * sizeof(uint32_t);
+        SG_CUDA_TRY(ensure_smem(bloom_bin_scatter_kernel, ssm));
+        SG_LAUNCH("bloom_bin_scatter", bloom_bin_scatter_kernel, blocks_for(nwin, BS_TILE), BS_NT, ssm, s,
+                  (const uint32_t *)H, nwin, bb, cursor, Hb, cursor + ncur);
+        const size_t ism = (size_t)(bb.w1b + bb.w2b) * sizeof(uint32_t);
+        SG_CUDA_TRY(ensure_smem(bloom_bin_insert_kernel, ism));
+        SG_LAUNCH("bloom_insert", bloom_bin_insert_kernel, bb.nbins, BI_NT, ism, s, (const uint32_t *)Hb,
+                  (const uint32_t *)cursor, bb, b2.words);
+        uint32_t ovf = 0;
+        SG_CUDA_TRY(read_back(&ovf, cursor + ncur, sizeof(uint32_t), s));
+        if (ovf) {  // a bin outgrew its room (a hash value shared by very many windows): sliced filters
+            bb = BinnedBloom{};
+            SG_TRY(sliced_filters());
+        }
+    }
+    if (use_bloom && !bb.nbins) {
         // slices of at most bloom_slice_mb of B1, so each launch's atomics stay in L2
         uint64_t slice_words = ((uint64_t)tune("bloom_slice_mb") << 20) / 4;
         uint64_t nsl = (b1.nwords + slice_words - 1) / slice_words;
@@ -698,7 +873,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     int64_t *wpos = early->get<int64_t>(nwarp + 1);
     if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
     SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint32_t *)H, ngroups * 32, b2, use_bloom,
-              cmask, wcnt);
+              bb, cmask, wcnt);
     SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp, s, err));
     int64_t nc = 0;
     uint32_t herr = 0;
@@ -737,6 +912,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         ks.sort_key_bytes = 8;
         ks.sort_val_bytes = mode == PK_PAIRS ? 8 : 0;
         ks.sort_passes = nc > 1 ? (code_bits + 7) / 8 : 0;
+        ks.bloom_bins = bb.nbins;
+        ks.bloom_b2_bytes = use_bloom ? (int64_t)b2.nwords * 4 : 0;
     }
     const int64_t nlut = (total >> LUT_SHIFT) + 1;
     int32_t *lut = sc.get<int32_t>(nlut);

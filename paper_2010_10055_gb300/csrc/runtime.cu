@@ -260,6 +260,9 @@ static Tunable g_tunables[] = {
     {"bloom_slice_mb", 64, 1, 1 << 20},   // B1 megabytes updated per Bloom launch
     {"bloom_max_slices", 8, 1, 1024},     // at most this many Bloom launches (slices grow beyond)
     {"bloom_unroll", 4, 4, 8},            // windows (atomics in flight) per thread per Bloom step: 4 or 8
+    {"bloom_binned", 1, 0, 1},            // 1: shared-memory filter bins where they fit (else sliced)
+    {"bloom_bin_kb", 160, 16, 176},       // B1 kilobytes per bin (B2: a quarter of it)
+    {"bloom_bin_room_pct", 112, 1, 1000}, // a bin's hash buffer, % of the mean (overflow: sliced)
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
     {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)
     {"spgemm_sample_min_nnz", (int64_t)1 << 26, 0, (int64_t)1 << 50},  // ... when nnz(A) is at least this

@@ -39,8 +39,10 @@ def test_bounded_wait_runs_out_and_reports_timeout():
 
 CONFIGS = [
     {},
-    {"bloom_bits": 4, "bloom_slice_mb": 1},                          # many small Bloom slices
-    {"bloom_bits": 12, "bloom_unroll": 8},
+    {"bloom_binned": 0, "bloom_bits": 4, "bloom_slice_mb": 1},       # many small Bloom slices
+    {"bloom_binned": 0, "bloom_bits": 12, "bloom_unroll": 8},
+    {"bloom_bin_kb": 16, "bloom_bits": 32},                          # many shared-memory bins
+    {"bloom_bin_room_pct": 50},                                      # bins overflow: sliced redo
     {"spgemm_fused": 0, "sym_guess_shift": 8},                      # two passes, tiny symbolic guesses
     {"spgemm_fused": 0, "sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
     {"num_guess_shift": 8},                                          # fused, most rows overflow
