@@ -432,7 +432,13 @@ void sg_memory_reset_peak(void);
  *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4 or 8 (4)
  *   bloom_binned          1: when the filters cut into at most 4096 bins, the window hashes are
  *                         grouped by bin and each bin's filters are built in shared memory (1)
- *   bloom_bin_kb          first-filter kilobytes per bin (160; the second filter gets a quarter)
+ *   bloom_bin_kb          first-filter kilobytes per bin, rounded down to a power of two (128;
+ *                         the second filter gets a quarter)
+ *   bloom_scatter_cfg     tile of the pass that groups hashes by bin: 0 512 x 16, 1 256 x 16,
+ *                         2 256 x 32 threads x hashes (0)
+ *   kmer_sort_buckets     at most this many top code bits may split the candidates into buckets
+ *                         sorted apart, where that lets the rest of the code fit beside the
+ *                         position in an 8-byte key (3); 0: 16-byte pairs instead
  *   bloom_bin_room_pct    hash buffer per bin, % of the mean bin (112, plus 16 K); a bin that
  *                         overflows sends the whole build to the sliced filters
  *   spgemm_fused          1: C in one numeric pass whose tables are sized from a guess (rows that

@@ -15,7 +15,9 @@ import paper_2010_10055_gb300 as sg
 
 SPACE = {
     "bloom_binned": [0, 1],
-    "bloom_bin_kb": [64, 96, 128, 160, 176],
+    "bloom_bin_kb": [64, 128],
+    "bloom_scatter_cfg": [0, 1, 2],
+    "kmer_sort_buckets": [0, 2, 3],
     "bloom_slice_mb": [32, 48, 64, 96, 128],
     "bloom_unroll": [4, 8],
     "bloom_bits": [6, 8, 10, 12],

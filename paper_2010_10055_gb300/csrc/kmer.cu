@@ -281,12 +281,12 @@ __global__ void __launch_bounds__(KM_NT) bloom_insert_kernel(const uint32_t *__r
 // shared-memory atomic, and writes the B2 slice out. B1 itself is never stored.
 struct BinnedBloom {
     uint32_t nbins = 0;  // 0: the sliced global-memory filters
-    uint32_t w1b = 0, w2b = 0;
-    uint32_t nwords1 = 0;  // nbins * w1b
+    uint32_t w1b = 0, w2b = 0;  // powers of two
+    uint32_t lw1b = 0;          // log2(w1b)
+    uint32_t nwords1 = 0;       // nbins * w1b
     uint32_t cap = 0;      // hashes a bin can hold in the scatter buffer
 };
 
-constexpr int BS_NT = 512, BS_ITEMS = 16, BS_TILE = BS_NT * BS_ITEMS;
 constexpr int BB_MAXBINS = 4096;
 constexpr int BB_CSTRIDE = 32;  // bin cursors 128 bytes apart
 constexpr int BI_NT = 1024;
@@ -299,41 +299,44 @@ __device__ __forceinline__ uint32_t bloom_mask(uint32_t h) {
 // B2 word and bits of a key (B1 hash h1) in the binned layout
 __device__ __forceinline__ void b2_binned(uint32_t h1, const BinnedBloom &bb, uint32_t *idx, uint32_t *mask) {
     const uint32_t h2 = b2_hash(h1);
-    *idx = (__umulhi(h1, bb.nwords1) / bb.w1b) * bb.w2b + __umulhi(h2, bb.w2b);
+    *idx = (__umulhi(h1, bb.nwords1) >> bb.lw1b) * bb.w2b + __umulhi(h2, bb.w2b);
     *mask = bloom_mask(h2);
 }
 
-// One tile of BS_TILE hashes per block: count per bin, reserve each bin's run in its global buffer
-// (one atomic per bin and tile, on a cursor of its own 128-byte line), order the tile by bin in
-// shared memory, then write it out so that consecutive threads fill consecutive slots of a run.
-__global__ void __launch_bounds__(BS_NT, 2) bloom_bin_scatter_kernel(const uint32_t *__restrict__ H, int64_t nwin,
-                                                                 BinnedBloom bb, uint32_t *__restrict__ cursor,
-                                                                 uint32_t *__restrict__ Hb, uint32_t *__restrict__ ovf) {
+// One tile of NT * ITEMS hashes per block: count per bin, reserve each bin's run in its global
+// buffer (one atomic per bin and tile, on a cursor of its own 128-byte line), order the tile by bin
+// in shared memory, then write it out so that consecutive threads fill consecutive slots of a run.
+template <int NT, int ITEMS>
+__global__ void __launch_bounds__(NT, 1024 / NT) bloom_bin_scatter_kernel(const uint32_t *__restrict__ H,
+                                                                         int64_t nwin, BinnedBloom bb,
+                                                                         uint32_t *__restrict__ cursor,
+                                                                         uint32_t *__restrict__ Hb,
+                                                                         uint32_t *__restrict__ ovf) {
+    constexpr int TILE = NT * ITEMS;
     extern __shared__ uint32_t bs_sm[];
     uint32_t *cnt = bs_sm;                // [nbins] tile count per bin
     uint32_t *lofs = cnt + bb.nbins;      // [nbins] the bin's first slot in the ordered tile
     uint32_t *gbase = lofs + bb.nbins;    // [nbins] the bin's run in its global buffer
-    uint32_t *tile = gbase + bb.nbins;    // [BS_TILE] the tile ordered by bin
-    __shared__ uint32_t s_tmp[BS_NT / 32 + 1];
-    for (uint32_t b = threadIdx.x; b < bb.nbins; b += BS_NT) cnt[b] = 0u;
+    uint32_t *tile = gbase + bb.nbins;    // [TILE] the tile ordered by bin
+    __shared__ uint32_t s_tmp[NT / 32 + 1];
+    for (uint32_t b = threadIdx.x; b < bb.nbins; b += NT) cnt[b] = 0u;
     __syncthreads();
-    const int64_t t0 = (int64_t)blockIdx.x * BS_TILE;
-    uint32_t h[BS_ITEMS], bin[BS_ITEMS], rk[BS_ITEMS];
+    const int64_t t0 = (int64_t)blockIdx.x * TILE;
+    uint32_t h[ITEMS], rk[ITEMS];
 #pragma unroll
-    for (int u = 0; u < BS_ITEMS; u++) {
-        const int64_t q = t0 + u * BS_NT + threadIdx.x;
+    for (int u = 0; u < ITEMS; u++) {
+        const int64_t q = t0 + u * NT + threadIdx.x;
         h[u] = q < nwin ? __ldcs(H + q) : H_NONE;
-        bin[u] = __umulhi(h[u], bb.nwords1) / bb.w1b;  // < nbins
-        rk[u] = h[u] != H_NONE ? atomicAdd(cnt + bin[u], 1u) : 0u;
+        rk[u] = h[u] != H_NONE ? atomicAdd(cnt + (__umulhi(h[u], bb.nwords1) >> bb.lw1b), 1u) : 0u;
     }
     __syncthreads();
     // thread t owns bins [t * per, t * per + per): their prefix, and their global runs
-    const uint32_t per = (bb.nbins + BS_NT - 1) / BS_NT;
+    const uint32_t per = (bb.nbins + NT - 1) / NT;
     const uint32_t b0 = threadIdx.x * per;
     uint32_t mine = 0;
     for (uint32_t b = b0; b < b0 + per && b < bb.nbins; b++) mine += cnt[b];
     uint32_t ntot;
-    uint32_t run = block_exclusive_scan<BS_NT>(mine, s_tmp, &ntot);
+    uint32_t run = block_exclusive_scan<NT>(mine, s_tmp, &ntot);
     for (uint32_t b = b0; b < b0 + per && b < bb.nbins; b++) {
         const uint32_t c = cnt[b];
         lofs[b] = run;
@@ -342,12 +345,12 @@ __global__ void __launch_bounds__(BS_NT, 2) bloom_bin_scatter_kernel(const uint3
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < BS_ITEMS; u++)
-        if (h[u] != H_NONE) tile[lofs[bin[u]] + rk[u]] = h[u];
+    for (int u = 0; u < ITEMS; u++)
+        if (h[u] != H_NONE) tile[lofs[__umulhi(h[u], bb.nwords1) >> bb.lw1b] + rk[u]] = h[u];
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < ntot; i += BS_NT) {
+    for (uint32_t i = threadIdx.x; i < ntot; i += NT) {
         const uint32_t hv = tile[i];
-        const uint32_t b = __umulhi(hv, bb.nwords1) / bb.w1b;
+        const uint32_t b = __umulhi(hv, bb.nwords1) >> bb.lw1b;
         const uint32_t pos = gbase[b] + (i - lofs[b]);
         if (pos < bb.cap) Hb[(int64_t)b * bb.cap + pos] = hv;
         else *ovf = 1u;  // the bin is fuller than its room: the caller redoes the filters sliced
@@ -411,12 +414,32 @@ __device__ __forceinline__ bool is_candidate(uint32_t h, const Bloom &b2, int us
     return (b2.words[i2] & m2) == m2;
 }
 
+// Candidate buckets by the top bits of the code (PK_POS with nb > 1): the candidates of bucket b
+// go to one contiguous range, in position order, so that each range is sorted on the code's low
+// `shift` bits only -- fewer radix passes, and on large inputs an 8-byte key where the whole code
+// and position would need 16 bytes. wcnt / wpos are bucket-major: [b * nwarp + warp].
+struct Buckets {
+    const uint64_t *P;
+    int k;
+    JobPos jp;
+    int nb;     // 1: no buckets
+    int shift;  // code bits below the bucket bits
+    uint64_t kmask;
+    int64_t nwarp;
+};
+
+__device__ __forceinline__ uint32_t bucket_of(const Buckets &bk, uint64_t x) {
+    return (uint32_t)((x & bk.kmask) >> bk.shift);
+}
+
 __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__restrict__ H, int64_t nwin, Bloom b2,
-                                                          int use_bloom, BinnedBloom bb, uint32_t *__restrict__ cmask,
-                                                          uint32_t *__restrict__ wcnt) {
+                                                          int use_bloom, BinnedBloom bb, Buckets bk,
+                                                          uint32_t *__restrict__ cmask, uint32_t *__restrict__ wcnt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
-    uint32_t mine = 0, c = 0;
+    const int64_t warp = (int64_t)blockIdx.x * KM_WARPS + w;
+    const int64_t g0 = warp * KM_GW;
+    JobPosCursor jc{bk.jp};
+    uint32_t mine = 0, c = 0, cb = 0;  // cb: lane b's count of bucket b
     constexpr int CC_U = 8;  // groups whose hashes (and then filter words) are loaded together
     for (int g0u = 0; g0u < KM_GW; g0u += CC_U) {
         uint32_t h[CC_U];
@@ -430,10 +453,24 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__res
             const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(h[u], b2, use_bloom, bb));
             if (lane == g0u + u) mine = m;
             c += __popc(m);
+            if (bk.nb > 1 && m) {
+                const int64_t g = g0 + g0u + u;
+                const bool cand = (m >> lane) & 1u;
+                const uint32_t b = cand ? bucket_of(bk, window_key(bk.P[g], bk.P[g + 1], lane, bk.k, jc, g * 32 + lane))
+                                        : 0u;
+                for (int j = 0; j < bk.nb; j++) {
+                    const uint32_t mb = __ballot_sync(0xffffffffu, cand && b == (uint32_t)j);
+                    if (lane == j) cb += __popc(mb);
+                }
+            }
         }
     }
     cmask[g0 + lane] = mine;
-    if (lane == 0) wcnt[(int64_t)blockIdx.x * KM_WARPS + w] = c;
+    if (bk.nb > 1) {
+        if (lane < bk.nb) wcnt[(int64_t)lane * bk.nwarp + warp] = cb;
+    } else if (lane == 0) {
+        wcnt[warp] = c;
+    }
 }
 
 // Sort records of the candidates. The code (job prefix included) is the sort key; below it:
@@ -443,35 +480,48 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__res
 //   PK_PAIRS key = code, vals = q | strand << 63, sorted as pairs (nothing fits in 64 bits).
 enum : int { PK_POS = 0, PK_IDX = 1, PK_PAIRS = 2 };
 
-__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(const uint64_t *__restrict__ P, int k, JobPos jp,
-                                                         const uint32_t *__restrict__ cmask,
+__global__ void __launch_bounds__(KM_NT) cand_emit_kernel(Buckets bk, const uint32_t *__restrict__ cmask,
                                                          const int64_t *__restrict__ wpos, int mode, int pb,
-                                                         uint64_t kmask, uint64_t *__restrict__ keys,
-                                                         uint64_t *__restrict__ vals, int64_t nc) {
+                                                         uint64_t *__restrict__ keys, uint64_t *__restrict__ vals,
+                                                         int64_t nc) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t g0 = ((int64_t)blockIdx.x * KM_WARPS + w) * KM_GW;
-    JobPosCursor jc{jp};
+    const int64_t warp = (int64_t)blockIdx.x * KM_WARPS + w;
+    const int64_t g0 = warp * KM_GW;
+    JobPosCursor jc{bk.jp};
     const uint32_t mine = cmask[g0 + lane];
     const uint32_t below = (1u << lane) - 1u;
-    int64_t o = wpos[(int64_t)blockIdx.x * KM_WARPS + w];
+    const uint64_t lowmask = bk.shift < 64 ? (1ull << bk.shift) - 1 : ~0ull;
+    // next free slot: of the warp (one bucket), or of bucket `lane` (lane < nb)
+    int64_t o = bk.nb > 1 ? (lane < bk.nb ? wpos[(int64_t)lane * bk.nwarp + warp] : 0) : wpos[warp];
     for (int g = 0; g < KM_GW; g++) {
         const uint32_t m = __shfl_sync(0xffffffffu, mine, g);
         if (m == 0) continue;  // no candidate: also every group past the sequence
-        if ((m >> lane) & 1u) {
-            const int64_t q = (g0 + g) * 32 + lane;
-            const uint64_t x = window_key(P[g0 + g], P[g0 + g + 1], lane, k, jc, q);
-            const uint64_t code = x & kmask;
-            const int64_t p = o + __popc(m & below);
-            if (SG_IN_BOUNDS(p >= 0 && p < nc, 102, p)) {
-                if (mode == PK_POS) {
-                    keys[p] = (code << pb) | ((uint64_t)q << 1) | (x >> 63);
-                } else {
-                    keys[p] = mode == PK_IDX ? ((code << pb) | (uint64_t)p) : code;
-                    vals[p] = (uint64_t)q | (x & WC_STRAND);
-                }
+        const bool cand = (m >> lane) & 1u;
+        const int64_t q = (g0 + g) * 32 + lane;
+        const uint64_t x = cand ? window_key(bk.P[g0 + g], bk.P[g0 + g + 1], lane, bk.k, jc, q) : 0ull;
+        int64_t p;
+        if (bk.nb > 1) {
+            const uint32_t b = cand ? bucket_of(bk, x) : 0u;
+            p = 0;
+            for (int j = 0; j < bk.nb; j++) {
+                const uint32_t mb = __ballot_sync(0xffffffffu, cand && b == (uint32_t)j);
+                const int64_t base = __shfl_sync(0xffffffffu, o, j);
+                if (cand && b == (uint32_t)j) p = base + __popc(mb & below);
+                if (lane == j) o += __popc(mb);
+            }
+        } else {
+            p = o + __popc(m & below);
+            o += __popc(m);
+        }
+        if (cand && SG_IN_BOUNDS(p >= 0 && p < nc, 102, p)) {
+            const uint64_t code = x & bk.kmask;
+            if (mode == PK_POS) {
+                keys[p] = ((code & lowmask) << pb) | ((uint64_t)q << 1) | (x >> 63);
+            } else {
+                keys[p] = mode == PK_IDX ? ((code << pb) | (uint64_t)p) : code;
+                vals[p] = (uint64_t)q | (x & WC_STRAND);
             }
         }
-        o += __popc(m);
     }
 }
 
@@ -505,16 +555,25 @@ __device__ __forceinline__ uint64_t resolve_pos(uint64_t v, const int64_t *__res
     return ((uint64_t)lo << 32) | (uint64_t)(uint32_t)(q - off[lo]) | ((v >> 63) << 31);
 }
 
+// Bucket ranges of the candidate keys: bucket b holds [start[b], start[b + 1]).
+struct BucketStarts {
+    int64_t start[9];
+    int nb;
+    int shift;
+};
+
 // After a keys-only sort (PK_POS, PK_IDX): the code, and the window resolved to its read.
 __global__ void unpack_kernel(const uint64_t *__restrict__ packed, const uint64_t *__restrict__ vals, int64_t nc,
-                              int mode, int pb, const int64_t *__restrict__ off, int64_t n,
+                              int mode, int pb, BucketStarts bs, const int64_t *__restrict__ off, int64_t n,
                               const int32_t *__restrict__ lut, int64_t nb, uint64_t *__restrict__ key,
                               uint64_t *__restrict__ val) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const uint64_t p = packed[i];
     const uint64_t low = p & ((1ull << pb) - 1);
-    key[i] = p >> pb;
+    uint64_t b = 0;  // the bucket's bits above the sorted code bits
+    for (int j = 1; j < bs.nb; j++) b += (uint64_t)(i >= bs.start[j]);
+    key[i] = (b << bs.shift) | (p >> pb);
     if (mode == PK_POS) {
         val[i] = resolve_pos((low >> 1) | (low << 63), off, n, lut, nb);
     } else if (SG_IN_BOUNDS((int64_t)low < nc, 103, low)) {
@@ -784,11 +843,14 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     };
     if (use_bloom && total > 0) {
         const int64_t w1 = total * tune("bloom_bits") / 32 + 1024;
-        const int64_t w1b = tune("bloom_bin_kb") * 256;
+        int lw1b = 0;  // bins of a power of two of words: a word's bin is a shift
+        while (((int64_t)2 << lw1b) <= tune("bloom_bin_kb") * 256) lw1b++;
+        const int64_t w1b = (int64_t)1 << lw1b;
         const int64_t nbins = (w1 + w1b - 1) / w1b;
         if (tune("bloom_binned") && nbins <= BB_MAXBINS) {
             bb.nbins = (uint32_t)nbins;
             bb.w1b = (uint32_t)w1b;
+            bb.lw1b = (uint32_t)lw1b;
             bb.w2b = (uint32_t)(w1b / 4);
             bb.nwords1 = (uint32_t)(nbins * w1b);
             // a bin's expected hashes and room for repeats (bloom_bin_room_pct % of the mean, and
@@ -831,10 +893,18 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         if (!cursor || !Hb) return SG_ERR_OOM;
         SG_CUDA_TRY(cudaMemsetAsync(cursor, 0, (ncur + 1) * sizeof(uint32_t), s));
         const int64_t nwin = ngroups * 32;
-        const size_t ssm = ((size_t)3 * bb.nbins + BS_TILE) * sizeof(uint32_t);
-        SG_CUDA_TRY(ensure_smem(bloom_bin_scatter_kernel, ssm));
-        SG_LAUNCH("bloom_bin_scatter", bloom_bin_scatter_kernel, blocks_for(nwin, BS_TILE), BS_NT, ssm, s,
-                  (const uint32_t *)H, nwin, bb, cursor, Hb, cursor + ncur);
+        auto scatter = [&](auto kern, int nt, int tile) -> sg_status {
+            const size_t ssm = ((size_t)3 * bb.nbins + tile) * sizeof(uint32_t);
+            SG_CUDA_TRY(ensure_smem(kern, ssm));
+            SG_LAUNCH("bloom_bin_scatter", kern, blocks_for(nwin, tile), nt, ssm, s, (const uint32_t *)H, nwin, bb,
+                      cursor, Hb, cursor + ncur);
+            return SG_OK;
+        };
+        switch (tune("bloom_scatter_cfg")) {  // threads x hashes per thread
+            case 0: SG_TRY(scatter(bloom_bin_scatter_kernel<512, 16>, 512, 8192)); break;
+            case 1: SG_TRY(scatter(bloom_bin_scatter_kernel<256, 16>, 256, 4096)); break;
+            default: SG_TRY(scatter(bloom_bin_scatter_kernel<256, 32>, 256, 8192)); break;
+        }
         const size_t ism = (size_t)(bb.w1b + bb.w2b) * sizeof(uint32_t);
         SG_CUDA_TRY(ensure_smem(bloom_bin_insert_kernel, ism));
         SG_LAUNCH("bloom_insert", bloom_bin_insert_kernel, bb.nbins, BI_NT, ism, s, (const uint32_t *)Hb,
@@ -867,28 +937,42 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
                           hi_w);
         }
     }
+    // Candidate records: PK_POS (code, position and strand in one 8-byte key) where the code's low
+    // bits fit beside the position once its top 0..3 bits become buckets (the fewest that fit:
+    // buckets cost a code per candidate in the count pass and per-bucket sort launches, so they
+    // are used only to make the key fit), else PK_IDX or PK_PAIRS, chosen once nc is known.
+    int qbits = 1;
+    while (((int64_t)1 << qbits) < total) qbits++;
+    int bbits = -1;
+    for (int b = 0; b <= (int)tune("kmer_sort_buckets") && b < code_bits && bbits < 0; b++)
+        if ((code_bits - b) + qbits + 1 <= 64) bbits = b;
     const int64_t nwarp = nblk * KM_WARPS;
+    Buckets bk{P, k, jp, bbits > 0 ? 1 << bbits : 1, code_bits - (bbits > 0 ? bbits : 0), kmask, nwarp};
     uint32_t *cmask = early->get<uint32_t>(nwarp * KM_GW);
-    uint32_t *wcnt = early->get<uint32_t>(nwarp + 1);
-    int64_t *wpos = early->get<int64_t>(nwarp + 1);
+    uint32_t *wcnt = early->get<uint32_t>(nwarp * bk.nb + 1);
+    int64_t *wpos = early->get<int64_t>(nwarp * bk.nb + 1);
     if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
     SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint32_t *)H, ngroups * 32, b2, use_bloom,
-              bb, cmask, wcnt);
-    SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp, s, err));
-    int64_t nc = 0;
+              bb, bk, cmask, wcnt);
+    SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp * bk.nb, s, err));
+    BucketStarts bs{};
+    bs.nb = bk.nb;
+    bs.shift = bk.shift;
+    for (int b = 0; b <= bk.nb; b++)
+        SG_CUDA_TRY(cudaMemcpyAsync(&bs.start[b], wpos + (int64_t)b * nwarp, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     uint32_t herr = 0;
     SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    SG_CUDA_TRY(read_back(&nc, wpos + nwarp, sizeof(int64_t), s));
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nc = bs.start[bk.nb];
     if (herr & DEV_TIMEOUT) return timeout_error("build_kmer_matrix");
     if (herr) {  // the passes above stayed in bounds; their results are discarded
         set_error("build_kmer_matrix: offsets are not a valid partition of the sequence");
         return SG_ERR_INVALID;
     }
 
-    int qbits = 1, ibits = 1;
-    while (((int64_t)1 << qbits) < total) qbits++;
+    int ibits = 1;
     while (((int64_t)1 << ibits) < nc) ibits++;
-    const int mode = code_bits + qbits + 1 <= 64 ? PK_POS : (code_bits + ibits <= 64 ? PK_IDX : PK_PAIRS);
+    const int mode = bbits >= 0 ? PK_POS : (code_bits + ibits <= 64 ? PK_IDX : PK_PAIRS);
     const int pb = mode == PK_POS ? qbits + 1 : (mode == PK_IDX ? ibits : 0);
     // buffers live only as long as they are needed, so that the pool can hand their memory to the
     // next phase: the emitted records, then (once the window hashes and filters are gone) the
@@ -896,8 +980,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint64_t *key0 = sc.get<uint64_t>(nc);
     uint64_t *val0 = mode == PK_POS ? nullptr : sc.get<uint64_t>(nc);
     if (!key0 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
-    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, (const uint64_t *)P, k, jp, (const uint32_t *)cmask,
-              (const int64_t *)wpos, mode, pb, kmask, key0, val0, nc);
+    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, bk, (const uint32_t *)cmask, (const int64_t *)wpos,
+              mode, pb, key0, val0, nc);
     early.reset();
     uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
     if (!key1 || !val1) return SG_ERR_OOM;
@@ -911,7 +995,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         ks.candidates = nc;
         ks.sort_key_bytes = 8;
         ks.sort_val_bytes = mode == PK_PAIRS ? 8 : 0;
-        ks.sort_passes = nc > 1 ? (code_bits + 7) / 8 : 0;
+        ks.sort_passes = nc > 1 ? (bk.shift + 7) / 8 : 0;
         ks.bloom_bins = bb.nbins;
         ks.bloom_b2_bytes = use_bloom ? (int64_t)b2.nwords * 4 : 0;
     }
@@ -920,10 +1004,24 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     if (!lut) return SG_ERR_OOM;
     SG_LAUNCH("read_lut", read_lut_kernel, blocks_for(nlut, NT), NT, 0, s, off, n, nlut, lut);
     if (mode != PK_PAIRS) {  // 8-byte keys through the radix passes, then one unpacking pass
-        SG_TRY(radix_sort_keys(key0, key1, nc, pb, pb + code_bits, &alt, s, err));
+        // each bucket sorted on its `shift` code bits; buckets of 0 or 1 keys need no pass, but
+        // must end in the same buffer as the others
+        const int npass = (bk.shift + 7) / 8;
+        bool any = false;
+        for (int b = 0; b < bk.nb; b++) any |= bs.start[b + 1] - bs.start[b] > 1;
+        alt = any && (npass & 1);
+        for (int b = 0; b < bk.nb; b++) {
+            const int64_t s0 = bs.start[b], nbk = bs.start[b + 1] - s0;
+            if (nbk > 1) {
+                bool a = false;
+                SG_TRY(radix_sort_keys(key0 + s0, key1 + s0, nbk, pb, pb + bk.shift, &a, s, err));
+            } else if (nbk == 1 && alt) {
+                SG_CUDA_TRY(cudaMemcpyAsync(key1 + s0, key0 + s0, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+            }
+        }
         uint64_t *ks = alt ? key1 : key0, *kfree = alt ? key0 : key1;
         SG_LAUNCH("unpack", unpack_kernel, blocks_for(nc, NT), NT, 0, s, (const uint64_t *)ks, (const uint64_t *)val0,
-                  nc, mode, pb, off, n, (const int32_t *)lut, nlut, kfree, val1);
+                  nc, mode, pb, bs, off, n, (const int32_t *)lut, nlut, kfree, val1);
         key = kfree;
         val = val1;
         sc.release(ks);

@@ -261,7 +261,10 @@ static Tunable g_tunables[] = {
     {"bloom_max_slices", 8, 1, 1024},     // at most this many Bloom launches (slices grow beyond)
     {"bloom_unroll", 4, 4, 8},            // windows (atomics in flight) per thread per Bloom step: 4 or 8
     {"bloom_binned", 1, 0, 1},            // 1: shared-memory filter bins where they fit (else sliced)
-    {"bloom_bin_kb", 160, 16, 176},       // B1 kilobytes per bin (B2: a quarter of it)
+    {"bloom_bin_kb", 128, 16, 176},       // B1 kilobytes per bin, rounded down to a power of two
+                                          // (B2: a quarter of it)
+    {"bloom_scatter_cfg", 0, 0, 2},       // bin scatter tile: 0 512x16, 1 256x16, 2 256x32 hashes
+    {"kmer_sort_buckets", 3, 0, 3},       // at most this many top code bits become candidate buckets
     {"bloom_bin_room_pct", 112, 1, 1000}, // a bin's hash buffer, % of the mean (overflow: sliced)
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
     {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)

@@ -13,8 +13,9 @@ pytestmark = pytest.mark.gpu
 
 
 # ------------------------------------------------------------------------------ A, At
-# k = 17 packs (code, window, strand) into the sort key; k = 23 on this input is too wide for that
-# and packs (code, candidate index); k = 31 is too wide for either and sorts (key, value) pairs.
+# k = 17 packs (code, window, strand) into the sort key (the top two code bits as buckets); k = 23
+# on this input fits that only with a bucket bit; k = 31 is too wide for any packing and sorts
+# (key, value) pairs. test_kmer_matrix_sort_forms covers the candidate-index packing.
 @pytest.mark.parametrize("k,lo,hi,seed", [(17, 2, 8, 1), (5, 2, 6, 2), (7, 1, 3, 3), (31, 2, 50, 4),
                                           (1, 1, 1 << 30, 5), (9, 3, 3, 6), (23, 2, 9, 7)])
 def test_kmer_matrix_random(k, lo, hi, seed):
@@ -26,6 +27,27 @@ def test_kmer_matrix_random(k, lo, hi, seed):
         seq[p] = rng.choice(np.frombuffer(b"NnX-", np.uint8))
     exp = oracle.build_kmer_matrix(seq, rd["offsets"], k, lo, hi)
     _, got = gpu_kmer(seq, rd["offsets"], k, lo, hi)
+    assert_kmer_equal(got, exp)
+
+
+# (k, bucket bits allowed, genome): 10x reads of G bases hold 2^18 (20 kbp), 2^19 (40 kbp) or
+# 2^20 (60 kbp) positions, so k = 23 needs 1, 2 or 3 bucket bits for (code, position, strand) to
+# fit 64 bits; with none allowed it packs (code, candidate index); k = 31 sorts pairs.
+@pytest.mark.parametrize("k,buckets,G", [(23, 3, 20000), (23, 3, 40000), (23, 3, 60000), (23, 0, 40000),
+                                         (17, 3, 40000), (31, 3, 40000)])
+def test_kmer_matrix_sort_forms(k, buckets, G):
+    """Each packing of the candidate records, on a read set with ragged reads and N's."""
+    g = synth.genome(G, 11)
+    rd = synth.reads(g, 10.0, 900.0, 400.0, 1, 0.05, 0.04, 0.03, 12)
+    seq = rd["seq"].copy()
+    seq[::997] = ord("N")
+    exp = oracle.build_kmer_matrix(seq, rd["offsets"], k, 2, 12)
+    saved = sg.tunables()["kmer_sort_buckets"]
+    try:
+        sg.tune("kmer_sort_buckets", buckets)
+        _, got = gpu_kmer(seq, rd["offsets"], k, 2, 12)
+    finally:
+        sg.tune("kmer_sort_buckets", saved)
     assert_kmer_equal(got, exp)
 
 
