@@ -430,8 +430,10 @@ void sg_memory_reset_peak(void);
  *   bloom_max_slices      at most this many Bloom launches, each streaming all window hashes;
  *                         for larger filters the slices grow instead (8)
  *   bloom_unroll          windows (independent atomics) per thread per Bloom step: 4 or 8 (4)
- *   bloom_binned          1: when the filters cut into at most 4096 bins, the window hashes are
- *                         grouped by bin and each bin's filters are built in shared memory (1)
+ *   bloom_binned          1: the window hashes are grouped by filter bin and each bin's filters
+ *                         are built in shared memory (1); 0: sliced global-memory filters
+ *   bloom_scatter_levels  passes that group the hashes: 1 straight into bins, 2 into superbins
+ *                         first (0, and always beyond 4096 bins: two only where needed)
  *   bloom_bin_kb          first-filter kilobytes per bin, rounded down to a power of two (128;
  *                         the second filter gets a quarter)
  *   bloom_scatter_cfg     tile of the pass that groups hashes by bin: 0 512 x 16, 1 256 x 16,

@@ -287,7 +287,7 @@ struct BinnedBloom {
     uint32_t cap = 0;      // hashes a bin can hold in the scatter buffer
 };
 
-constexpr int BB_MAXBINS = 4096;
+constexpr int BB_MAXBINS = 1 << 20;  // one pass up to 4096 bins, two beyond
 constexpr int BB_CSTRIDE = 32;  // bin cursors 128 bytes apart
 constexpr int BI_NT = 1024;
 
@@ -303,56 +303,81 @@ __device__ __forceinline__ void b2_binned(uint32_t h1, const BinnedBloom &bb, ui
     *mask = bloom_mask(h2);
 }
 
+// One pass of grouping hashes by bin. The source is flat (n hashes), or grouped by an earlier pass
+// (group g: src + g * cap_src, min(fill[g], cap_src) hashes). A hash's bin within its group is
+// (umulhi(h, nwords1) >> shift) - g * nb; it goes to output bin g * nb + that, whose room is
+// cap_out. One pass (shift = log2 w1b) groups straight into filter bins; two passes first into
+// superbins of nb filter bins, then each superbin into its bins, so that every pass has few
+// enough bins per tile to write long runs.
+struct ScatterLevel {
+    const uint32_t *src;
+    int64_t n;
+    const uint32_t *fill;  // nullptr: flat source
+    uint32_t cap_src;
+    uint32_t tiles_per_group;
+    uint32_t shift;
+    uint32_t nb;
+    uint32_t cap_out;
+};
+
 // One tile of NT * ITEMS hashes per block: count per bin, reserve each bin's run in its global
 // buffer (one atomic per bin and tile, on a cursor of its own 128-byte line), order the tile by bin
 // in shared memory, then write it out so that consecutive threads fill consecutive slots of a run.
 template <int NT, int ITEMS>
-__global__ void __launch_bounds__(NT, 1024 / NT) bloom_bin_scatter_kernel(const uint32_t *__restrict__ H,
-                                                                         int64_t nwin, BinnedBloom bb,
+__global__ void __launch_bounds__(NT, 1024 / NT) bloom_bin_scatter_kernel(ScatterLevel L, uint32_t nwords1,
                                                                          uint32_t *__restrict__ cursor,
-                                                                         uint32_t *__restrict__ Hb,
+                                                                         uint32_t *__restrict__ out,
                                                                          uint32_t *__restrict__ ovf) {
     constexpr int TILE = NT * ITEMS;
     extern __shared__ uint32_t bs_sm[];
-    uint32_t *cnt = bs_sm;                // [nbins] tile count per bin
-    uint32_t *lofs = cnt + bb.nbins;      // [nbins] the bin's first slot in the ordered tile
-    uint32_t *gbase = lofs + bb.nbins;    // [nbins] the bin's run in its global buffer
-    uint32_t *tile = gbase + bb.nbins;    // [TILE] the tile ordered by bin
+    uint32_t *cnt = bs_sm;             // [nb] tile count per bin
+    uint32_t *lofs = cnt + L.nb;       // [nb] the bin's first slot in the ordered tile
+    uint32_t *gbase = lofs + L.nb;     // [nb] the bin's run in its global buffer
+    uint32_t *tile = gbase + L.nb;     // [TILE] the tile ordered by bin
     __shared__ uint32_t s_tmp[NT / 32 + 1];
-    for (uint32_t b = threadIdx.x; b < bb.nbins; b += NT) cnt[b] = 0u;
+    const uint32_t g = L.fill ? blockIdx.x / L.tiles_per_group : 0u;
+    const int64_t t0 = (int64_t)(L.fill ? blockIdx.x % L.tiles_per_group : blockIdx.x) * TILE;
+    const uint32_t *src = L.fill ? L.src + (int64_t)g * L.cap_src : L.src;
+    int64_t n = L.n;
+    if (L.fill) {
+        const uint32_t f = L.fill[(size_t)g * BB_CSTRIDE];
+        n = f < L.cap_src ? f : L.cap_src;
+    }
+    if (t0 >= n) return;  // the whole block: past its group's hashes
+    const uint32_t gb0 = g * L.nb;
+    for (uint32_t b = threadIdx.x; b < L.nb; b += NT) cnt[b] = 0u;
     __syncthreads();
-    const int64_t t0 = (int64_t)blockIdx.x * TILE;
     uint32_t h[ITEMS], rk[ITEMS];
 #pragma unroll
     for (int u = 0; u < ITEMS; u++) {
         const int64_t q = t0 + u * NT + threadIdx.x;
-        h[u] = q < nwin ? __ldcs(H + q) : H_NONE;
-        rk[u] = h[u] != H_NONE ? atomicAdd(cnt + (__umulhi(h[u], bb.nwords1) >> bb.lw1b), 1u) : 0u;
+        h[u] = q < n ? __ldcs(src + q) : H_NONE;
+        rk[u] = h[u] != H_NONE ? atomicAdd(cnt + ((__umulhi(h[u], nwords1) >> L.shift) - gb0), 1u) : 0u;
     }
     __syncthreads();
     // thread t owns bins [t * per, t * per + per): their prefix, and their global runs
-    const uint32_t per = (bb.nbins + NT - 1) / NT;
+    const uint32_t per = (L.nb + NT - 1) / NT;
     const uint32_t b0 = threadIdx.x * per;
     uint32_t mine = 0;
-    for (uint32_t b = b0; b < b0 + per && b < bb.nbins; b++) mine += cnt[b];
+    for (uint32_t b = b0; b < b0 + per && b < L.nb; b++) mine += cnt[b];
     uint32_t ntot;
     uint32_t run = block_exclusive_scan<NT>(mine, s_tmp, &ntot);
-    for (uint32_t b = b0; b < b0 + per && b < bb.nbins; b++) {
+    for (uint32_t b = b0; b < b0 + per && b < L.nb; b++) {
         const uint32_t c = cnt[b];
         lofs[b] = run;
         run += c;
-        gbase[b] = c ? atomicAdd(cursor + (size_t)b * BB_CSTRIDE, c) : 0u;
+        gbase[b] = c ? atomicAdd(cursor + (size_t)(gb0 + b) * BB_CSTRIDE, c) : 0u;
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < ITEMS; u++)
-        if (h[u] != H_NONE) tile[lofs[__umulhi(h[u], bb.nwords1) >> bb.lw1b] + rk[u]] = h[u];
+        if (h[u] != H_NONE) tile[lofs[(__umulhi(h[u], nwords1) >> L.shift) - gb0] + rk[u]] = h[u];
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < ntot; i += NT) {
         const uint32_t hv = tile[i];
-        const uint32_t b = __umulhi(hv, bb.nwords1) >> bb.lw1b;
+        const uint32_t b = (__umulhi(hv, nwords1) >> L.shift) - gb0;
         const uint32_t pos = gbase[b] + (i - lofs[b]);
-        if (pos < bb.cap) Hb[(int64_t)b * bb.cap + pos] = hv;
+        if (pos < L.cap_out) out[(int64_t)(gb0 + b) * L.cap_out + pos] = hv;
         else *ovf = 1u;  // the bin is fuller than its room: the caller redoes the filters sliced
     }
 }
@@ -847,7 +872,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         while (((int64_t)2 << lw1b) <= tune("bloom_bin_kb") * 256) lw1b++;
         const int64_t w1b = (int64_t)1 << lw1b;
         const int64_t nbins = (w1 + w1b - 1) / w1b;
-        if (tune("bloom_binned") && nbins <= BB_MAXBINS) {
+        if (tune("bloom_binned") && nbins <= BB_MAXBINS && nbins * w1b < ((int64_t)1 << 32)) {
             bb.nbins = (uint32_t)nbins;
             bb.w1b = (uint32_t)w1b;
             bb.lw1b = (uint32_t)lw1b;
@@ -887,30 +912,60 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     if (use_bloom && bb.nbins) {
         std::optional<Scratch> bins;
         bins.emplace(s);
-        const size_t ncur = (size_t)bb.nbins * BB_CSTRIDE;
-        uint32_t *cursor = bins->get<uint32_t>(ncur + 1);  // [nbins, padded] fill | overflow flag
-        uint32_t *Hb = bins->get<uint32_t>((size_t)bb.nbins * bb.cap);
-        if (!cursor || !Hb) return SG_ERR_OOM;
-        SG_CUDA_TRY(cudaMemsetAsync(cursor, 0, (ncur + 1) * sizeof(uint32_t), s));
         const int64_t nwin = ngroups * 32;
-        auto scatter = [&](auto kern, int nt, int tile) -> sg_status {
-            const size_t ssm = ((size_t)3 * bb.nbins + tile) * sizeof(uint32_t);
-            SG_CUDA_TRY(ensure_smem(kern, ssm));
-            SG_LAUNCH("bloom_bin_scatter", kern, blocks_for(nwin, tile), nt, ssm, s, (const uint32_t *)H, nwin, bb,
-                      cursor, Hb, cursor + ncur);
-            return SG_OK;
+        // one grouping pass, or two (superbins of 2^lsup filter bins first): two where the filter
+        // has more bins than one pass can count in shared memory (4096), or when asked
+        const int64_t lv = tune("bloom_scatter_levels");
+        const int levels = bb.nbins > 4096 ? 2 : (lv ? (int)lv : 1);
+        int lsup = 0;
+        if (levels == 2)
+            while (((int64_t)1 << (2 * lsup)) < (int64_t)bb.nbins) lsup++;  // 2^lsup >= sqrt(nbins)
+        const uint32_t nsup = levels == 2 ? (uint32_t)((bb.nbins + (1u << lsup) - 1) >> lsup) : 0u;
+        const int64_t pct = tune("bloom_bin_room_pct");
+        auto room = [&](int64_t groups) {  // hashes a group can hold: pct % of the mean, plus slack
+            const int64_t mean = total / groups + 1;
+            return (uint32_t)(mean * pct / 100 + (pct >= 100 ? 16384 : 0) + 1);
         };
-        switch (tune("bloom_scatter_cfg")) {  // threads x hashes per thread
-            case 0: SG_TRY(scatter(bloom_bin_scatter_kernel<512, 16>, 512, 8192)); break;
-            case 1: SG_TRY(scatter(bloom_bin_scatter_kernel<256, 16>, 256, 4096)); break;
-            default: SG_TRY(scatter(bloom_bin_scatter_kernel<256, 32>, 256, 8192)); break;
+        const uint32_t cap1 = levels == 2 ? room(nsup) : 0u;
+        const size_t ncur = (size_t)bb.nbins * BB_CSTRIDE, ncur1 = (size_t)nsup * BB_CSTRIDE;
+        uint32_t *cursor = bins->get<uint32_t>(ncur + ncur1 + 1);  // bins | superbins | overflow flag
+        uint32_t *Hs = levels == 2 ? bins->get<uint32_t>((size_t)nsup * cap1) : nullptr;
+        uint32_t *Hb = bins->get<uint32_t>((size_t)bb.nbins * bb.cap);
+        if (!cursor || !Hb || (levels == 2 && !Hs)) return SG_ERR_OOM;
+        SG_CUDA_TRY(cudaMemsetAsync(cursor, 0, (ncur + ncur1 + 1) * sizeof(uint32_t), s));
+        uint32_t *ovf_flag = cursor + ncur + ncur1;
+        const int64_t cfg = tune("bloom_scatter_cfg");
+        const int nt = cfg == 0 ? 512 : 256, tile = cfg == 1 ? 4096 : 8192;
+        auto scatter = [&](ScatterLevel L, uint32_t *cur, uint32_t *dst, int64_t grid) -> sg_status {
+            const size_t ssm = ((size_t)3 * L.nb + tile) * sizeof(uint32_t);
+            auto run = [&](auto kern) -> sg_status {
+                SG_CUDA_TRY(ensure_smem(kern, ssm));
+                SG_LAUNCH("bloom_bin_scatter", kern, grid, nt, ssm, s, L, bb.nwords1, cur, dst, ovf_flag);
+                return SG_OK;
+            };
+            switch (cfg) {  // threads x hashes per thread
+                case 0: return run(bloom_bin_scatter_kernel<512, 16>);
+                case 1: return run(bloom_bin_scatter_kernel<256, 16>);
+                default: return run(bloom_bin_scatter_kernel<256, 32>);
+            }
+        };
+        if (levels == 2) {
+            const ScatterLevel l1{(const uint32_t *)H, nwin, nullptr, 0u, 0u, bb.lw1b + lsup, nsup, cap1};
+            SG_TRY(scatter(l1, cursor + ncur, Hs, blocks_for(nwin, tile)));
+            const uint32_t tpg = (uint32_t)blocks_for(cap1, tile);
+            const ScatterLevel l2{(const uint32_t *)Hs, 0, (const uint32_t *)(cursor + ncur), cap1, tpg, bb.lw1b,
+                                  1u << lsup, bb.cap};
+            SG_TRY(scatter(l2, cursor, Hb, (int64_t)nsup * tpg));
+        } else {
+            const ScatterLevel l1{(const uint32_t *)H, nwin, nullptr, 0u, 0u, bb.lw1b, bb.nbins, bb.cap};
+            SG_TRY(scatter(l1, cursor, Hb, blocks_for(nwin, tile)));
         }
         const size_t ism = (size_t)(bb.w1b + bb.w2b) * sizeof(uint32_t);
         SG_CUDA_TRY(ensure_smem(bloom_bin_insert_kernel, ism));
         SG_LAUNCH("bloom_insert", bloom_bin_insert_kernel, bb.nbins, BI_NT, ism, s, (const uint32_t *)Hb,
                   (const uint32_t *)cursor, bb, b2.words);
         uint32_t ovf = 0;
-        SG_CUDA_TRY(read_back(&ovf, cursor + ncur, sizeof(uint32_t), s));
+        SG_CUDA_TRY(read_back(&ovf, ovf_flag, sizeof(uint32_t), s));
         if (ovf) {  // a bin outgrew its room (a hash value shared by very many windows): sliced filters
             bb = BinnedBloom{};
             SG_TRY(sliced_filters());

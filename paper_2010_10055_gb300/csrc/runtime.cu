@@ -264,6 +264,7 @@ static Tunable g_tunables[] = {
     {"bloom_bin_kb", 128, 16, 176},       // B1 kilobytes per bin, rounded down to a power of two
                                           // (B2: a quarter of it)
     {"bloom_scatter_cfg", 0, 0, 2},       // bin scatter tile: 0 512x16, 1 256x16, 2 256x32 hashes
+    {"bloom_scatter_levels", 0, 0, 2},    // passes grouping hashes by bin (0: two beyond 4096 bins)
     {"kmer_sort_buckets", 3, 0, 3},       // at most this many top code bits become candidate buckets
     {"bloom_bin_room_pct", 112, 1, 1000}, // a bin's hash buffer, % of the mean (overflow: sliced)
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass

@@ -44,6 +44,8 @@ CONFIGS = [
     {"bloom_bin_kb": 16, "bloom_bits": 32},                          # many shared-memory bins
     {"bloom_bin_room_pct": 50},                                      # bins overflow: sliced redo
     {"bloom_bin_kb": 64, "bloom_scatter_cfg": 1},                    # smaller bins, 256 x 16 tiles
+    {"bloom_scatter_levels": 2, "bloom_bin_kb": 16},                 # two grouping passes
+    {"bloom_scatter_levels": 2, "bloom_bin_room_pct": 50},           # superbins overflow: sliced redo
     {"bloom_scatter_cfg": 2, "kmer_sort_buckets": 0},                # 256 x 32 tiles, one bucket
     {"spgemm_fused": 0, "sym_guess_shift": 8},                      # two passes, tiny symbolic guesses
     {"spgemm_fused": 0, "sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
