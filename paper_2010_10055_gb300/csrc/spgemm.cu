@@ -322,7 +322,7 @@ __device__ __forceinline__ uint32_t at_value(const uint64_t *__restrict__ t_pair
 // 2^log2F bits each sit before the table; partner k maps to bit k when n <= 2^log2F, else to a
 // multiplicative hash of k.
 template <bool GSLICE, bool FUSED, bool FILT = false>
-__global__ void __launch_bounds__(512) numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
+__global__ void __launch_bounds__(1024) numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
                                                      const unsigned long long *__restrict__ nrows_p, int log2T,
                                                      int log2F,
                                                      const int64_t *__restrict__ need, unsigned char *__restrict__ gpool,
@@ -600,6 +600,13 @@ __global__ void pair_kernel(const int32_t *__restrict__ col, const uint32_t *__r
 // blocks per SM, so those blocks bring more warps to hide the gathers' latency
 static int pick_threads(int log2T) { return log2T <= 7 ? 64 : (log2T <= 10 ? 128 : (log2T <= 11 ? 256 : 512)); }
 
+// numeric launches of 4 K slots and more run one block per SM: spgemm_big_threads (512 or 1024)
+static int pick_numeric_threads(int log2T, bool filtered) {
+    const int big = (int)tune("spgemm_big_threads");
+    if (log2T >= 12) return big;
+    return filtered ? (log2T <= 11 ? 256 : 512) : pick_threads(log2T);
+}
+
 // Launch names by table size, so that per-kernel timing separates the classes.
 static const char *const SYM_NAMES[] = {"spgemm_symbolic_t64", "spgemm_symbolic_t128", "spgemm_symbolic_t256",
                                         "spgemm_symbolic_t512", "spgemm_symbolic_t1k", "spgemm_symbolic_t2k",
@@ -733,7 +740,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 const size_t sm = num_table_bytes((int64_t)1 << fz.log2T[c], S, true);
                 SG_CUDA_TRY(ensure_smem(numeric_kernel<false, true>, sm));
                 SG_LAUNCH(NUM_NAMES[fz.log2T[c] - SP_MINLOG], (numeric_kernel<false, true>), grid,
-                          pick_threads(fz.log2T[c]), sm, s, g, lists + (int64_t)c * n, fz_counts + c, fz.log2T[c], 0,
+                          pick_numeric_threads(fz.log2T[c], false), sm, s, g, lists + (int64_t)c * n, fz_counts + c,
+                          fz.log2T[c], 0,
                           (const int64_t *)need, (unsigned char *)nullptr, (int64_t)0, (const int64_t *)tmp_off,
                           t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work, ovf, fz_ovf, nnz_row);
             }
@@ -742,7 +750,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 const size_t sm = num_table_bytes((int64_t)1 << ff.log2T[c], S, true) + fbytes;
                 SG_CUDA_TRY(ensure_smem(numeric_kernel<false, true, true>, sm));
                 SG_LAUNCH(FIL_NAMES[ff.log2T[c] - SP_MINLOG], (numeric_kernel<false, true, true>), grid,
-                          ff.log2T[c] <= 11 ? 256 : 512, sm, s, g, lists_f + (int64_t)c * n, ff_counts + c,
+                          pick_numeric_threads(ff.log2T[c], true), sm, s, g, lists_f + (int64_t)c * n, ff_counts + c,
                           ff.log2T[c], log2F, (const int64_t *)need_f, (unsigned char *)nullptr, (int64_t)0,
                           (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work, ovf,
                           fz_ovf, nnz_row);
@@ -857,7 +865,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         const size_t sm = num_table_bytes((int64_t)1 << num.log2T[c], S);
         SG_CUDA_TRY(ensure_smem(numeric_kernel<false, false>, sm));
         SG_LAUNCH(NUM_NAMES[num.log2T[c] - SP_MINLOG], (numeric_kernel<false, false>), grid,
-                  pick_threads(num.log2T[c]), sm, s, g, lists + (int64_t)c * n, num_counts + c, num.log2T[c], 0,
+                  pick_numeric_threads(num.log2T[c], false), sm, s, g, lists + (int64_t)c * n, num_counts + c,
+                  num.log2T[c], 0,
                   (const int64_t *)need, (unsigned char *)nullptr, (int64_t)0, (const int64_t *)C->row_ptr, C->col,
                   C->count, C->seed_i, C->seed_k, nnz, (const int64_t *)nullptr, (int32_t *)nullptr,
                   (unsigned long long *)nullptr, (int64_t *)nullptr);
