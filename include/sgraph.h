@@ -466,7 +466,7 @@ void sg_memory_reset_peak(void);
  *   sym_guess_shift       symbolic hash table guess = products of the row >> shift (2)
  *   spgemm_blocks_per_sm  blocks per SM of each SpGEMM class launch (16)
  *   spgemm_big_threads    threads per numeric block for tables of 4 K slots or more: 512 or 1024
- *                         (512)
+ *                         (1024)
  *   tr_blocks_per_sm      blocks per SM of the min-plus launch (32)
  *   pool_cross_stream_reuse  1: the library's memory pool may reuse memory freed on one stream for
  *                         another (read once, when the pool is created) (1)

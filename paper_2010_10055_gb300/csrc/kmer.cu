@@ -457,6 +457,7 @@ __device__ __forceinline__ uint32_t bucket_of(const Buckets &bk, uint64_t x) {
     return (uint32_t)((x & bk.kmask) >> bk.shift);
 }
 
+template <bool BKT>
 __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__restrict__ H, int64_t nwin, Bloom b2,
                                                           int use_bloom, BinnedBloom bb, Buckets bk,
                                                           uint32_t *__restrict__ cmask, uint32_t *__restrict__ wcnt) {
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__res
             const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(h[u], b2, use_bloom, bb));
             if (lane == g0u + u) mine = m;
             c += __popc(m);
-            if (bk.nb > 1 && m) {
+            if (BKT && m) {
                 const int64_t g = g0 + g0u + u;
                 const bool cand = (m >> lane) & 1u;
                 const uint32_t b = cand ? bucket_of(bk, window_key(bk.P[g], bk.P[g + 1], lane, bk.k, jc, g * 32 + lane))
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__res
         }
     }
     cmask[g0 + lane] = mine;
-    if (bk.nb > 1) {
+    if (BKT) {
         if (lane < bk.nb) wcnt[(int64_t)lane * bk.nwarp + warp] = cb;
     } else if (lane == 0) {
         wcnt[warp] = c;
@@ -505,6 +506,7 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__res
 //   PK_PAIRS key = code, vals = q | strand << 63, sorted as pairs (nothing fits in 64 bits).
 enum : int { PK_POS = 0, PK_IDX = 1, PK_PAIRS = 2 };
 
+template <bool BKT>
 __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(Buckets bk, const uint32_t *__restrict__ cmask,
                                                          const int64_t *__restrict__ wpos, int mode, int pb,
                                                          uint64_t *__restrict__ keys, uint64_t *__restrict__ vals,
@@ -517,15 +519,33 @@ __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(Buckets bk, const uint
     const uint32_t below = (1u << lane) - 1u;
     const uint64_t lowmask = bk.shift < 64 ? (1ull << bk.shift) - 1 : ~0ull;
     // next free slot: of the warp (one bucket), or of bucket `lane` (lane < nb)
-    int64_t o = bk.nb > 1 ? (lane < bk.nb ? wpos[(int64_t)lane * bk.nwarp + warp] : 0) : wpos[warp];
+    int64_t o = BKT ? (lane < bk.nb ? wpos[(int64_t)lane * bk.nwarp + warp] : 0) : wpos[warp];
     for (int g = 0; g < KM_GW; g++) {
         const uint32_t m = __shfl_sync(0xffffffffu, mine, g);
         if (m == 0) continue;  // no candidate: also every group past the sequence
         const bool cand = (m >> lane) & 1u;
+        if (!BKT) {  // one bucket: the candidates of a group go out in lane order
+            if (cand) {
+                const int64_t q = (g0 + g) * 32 + lane;
+                const uint64_t x = window_key(bk.P[g0 + g], bk.P[g0 + g + 1], lane, bk.k, jc, q);
+                const int64_t p = o + __popc(m & below);
+                if (SG_IN_BOUNDS(p >= 0 && p < nc, 102, p)) {
+                    const uint64_t code = x & bk.kmask;
+                    if (mode == PK_POS) {
+                        keys[p] = ((code & lowmask) << pb) | ((uint64_t)q << 1) | (x >> 63);
+                    } else {
+                        keys[p] = mode == PK_IDX ? ((code << pb) | (uint64_t)p) : code;
+                        vals[p] = (uint64_t)q | (x & WC_STRAND);
+                    }
+                }
+            }
+            o += __popc(m);
+            continue;
+        }
         const int64_t q = (g0 + g) * 32 + lane;
         const uint64_t x = cand ? window_key(bk.P[g0 + g], bk.P[g0 + g + 1], lane, bk.k, jc, q) : 0ull;
         int64_t p;
-        if (bk.nb > 1) {
+        {
             const uint32_t b = cand ? bucket_of(bk, x) : 0u;
             p = 0;
             for (int j = 0; j < bk.nb; j++) {
@@ -534,19 +554,9 @@ __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(Buckets bk, const uint
                 if (cand && b == (uint32_t)j) p = base + __popc(mb & below);
                 if (lane == j) o += __popc(mb);
             }
-        } else {
-            p = o + __popc(m & below);
-            o += __popc(m);
         }
-        if (cand && SG_IN_BOUNDS(p >= 0 && p < nc, 102, p)) {
-            const uint64_t code = x & bk.kmask;
-            if (mode == PK_POS) {
-                keys[p] = ((code & lowmask) << pb) | ((uint64_t)q << 1) | (x >> 63);
-            } else {
-                keys[p] = mode == PK_IDX ? ((code << pb) | (uint64_t)p) : code;
-                vals[p] = (uint64_t)q | (x & WC_STRAND);
-            }
-        }
+        if (cand && SG_IN_BOUNDS(p >= 0 && p < nc, 102, p))  // buckets: always PK_POS
+            keys[p] = (((x & bk.kmask) & lowmask) << pb) | ((uint64_t)q << 1) | (x >> 63);
     }
 }
 
@@ -597,7 +607,9 @@ __global__ void unpack_kernel(const uint64_t *__restrict__ packed, const uint64_
     const uint64_t p = packed[i];
     const uint64_t low = p & ((1ull << pb) - 1);
     uint64_t b = 0;  // the bucket's bits above the sorted code bits
-    for (int j = 1; j < bs.nb; j++) b += (uint64_t)(i >= bs.start[j]);
+#pragma unroll
+    for (int j = 1; j < 8; j++)  // constant indices: the ranges stay in parameter space
+        if (j < bs.nb) b += (uint64_t)(i >= bs.start[j]);
     key[i] = (b << bs.shift) | (p >> pb);
     if (mode == PK_POS) {
         val[i] = resolve_pos((low >> 1) | (low << 63), off, n, lut, nb);
@@ -1007,8 +1019,12 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint32_t *wcnt = early->get<uint32_t>(nwarp * bk.nb + 1);
     int64_t *wpos = early->get<int64_t>(nwarp * bk.nb + 1);
     if (!cmask || !wcnt || !wpos) return SG_ERR_OOM;
-    SG_LAUNCH("cand_count", cand_count_kernel, nblk, KM_NT, 0, s, (const uint32_t *)H, ngroups * 32, b2, use_bloom,
-              bb, bk, cmask, wcnt);
+    if (bk.nb > 1)
+        SG_LAUNCH("cand_count", cand_count_kernel<true>, nblk, KM_NT, 0, s, (const uint32_t *)H, ngroups * 32, b2,
+                  use_bloom, bb, bk, cmask, wcnt);
+    else
+        SG_LAUNCH("cand_count", cand_count_kernel<false>, nblk, KM_NT, 0, s, (const uint32_t *)H, ngroups * 32, b2,
+                  use_bloom, bb, bk, cmask, wcnt);
     SG_TRY(exclusive_scan<uint32_t>(wcnt, wpos, nwarp * bk.nb, s, err));
     BucketStarts bs{};
     bs.nb = bk.nb;
@@ -1035,8 +1051,12 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint64_t *key0 = sc.get<uint64_t>(nc);
     uint64_t *val0 = mode == PK_POS ? nullptr : sc.get<uint64_t>(nc);
     if (!key0 || (mode != PK_POS && !val0)) return SG_ERR_OOM;
-    SG_LAUNCH("cand_emit", cand_emit_kernel, nblk, KM_NT, 0, s, bk, (const uint32_t *)cmask, (const int64_t *)wpos,
-              mode, pb, key0, val0, nc);
+    if (bk.nb > 1)
+        SG_LAUNCH("cand_emit", cand_emit_kernel<true>, nblk, KM_NT, 0, s, bk, (const uint32_t *)cmask,
+                  (const int64_t *)wpos, mode, pb, key0, val0, nc);
+    else
+        SG_LAUNCH("cand_emit", cand_emit_kernel<false>, nblk, KM_NT, 0, s, bk, (const uint32_t *)cmask,
+                  (const int64_t *)wpos, mode, pb, key0, val0, nc);
     early.reset();
     uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
     if (!key1 || !val1) return SG_ERR_OOM;

@@ -282,7 +282,7 @@ static Tunable g_tunables[] = {
     {"spgemm_filter_log2", 17, 10, 19},   // at most 2^this bits per seen-once / seen-twice filter
     {"sym_guess_shift", 2, 0, 8},         // symbolic table guess = products >> shift
     {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch
-    {"spgemm_big_threads", 512, 512, 1024},  // threads of numeric blocks with 4 K table slots or more
+    {"spgemm_big_threads", 1024, 512, 1024},  // threads of numeric blocks with 4 K table slots or more
     {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch
     {"pool_cross_stream_reuse", 1, 0, 1}, // pool may hand memory freed on one stream to another
 };

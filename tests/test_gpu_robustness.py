@@ -51,7 +51,7 @@ CONFIGS = [
     {"spgemm_fused": 0, "sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
     {"num_guess_shift": 8},                                          # fused, most rows overflow
     {"num_guess_shift": 0},                                          # fused, exact-bound guesses
-    {"num_guess_shift": 0, "spgemm_big_threads": 1024},              # 4 K+ tables, 1024 threads
+    {"num_guess_shift": 0, "spgemm_big_threads": 512},               # 4 K+ tables, 512 threads
     {"spgemm_fused_max_mb": 0},                                      # fused path over budget: fallback
     {"spgemm_filter_work": 0},                                       # no seen-twice filter
     {"spgemm_filter_mode": 2, "spgemm_filter_work": 1},              # every row filtered first
