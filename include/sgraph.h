@@ -91,8 +91,12 @@ typedef struct {
  * not say which orientation that min carries when walks with different end orientations tie). */
 enum {
     SG_TR_DIRMATCH = 0, /* N_ik = min over valid walks i->j->k whose end orientations match d_ik */
-    SG_TR_LITERAL = 1   /* N_ik = lexicographic min of (sum, composite dir) over valid walks; the
+    SG_TR_LITERAL = 1,  /* N_ik = lexicographic min of (sum, composite dir) over valid walks; the
                            end-orientation check is applied to that one min afterwards */
+    SG_TR_PER_END = 2   /* flag, or-ed with either: the row max of Algorithm 1's Reduce is taken
+                           per read end (over the entries i -> k that leave read i through the
+                           same end, out(d_ik)), and each entry is bounded by its own end's max,
+                           instead of the whole row's (the transitive reduction) */
 };
 
 /*
@@ -190,7 +194,7 @@ sg_status sg_overlap_graph_from_seeds(const sg_overlap_csr *C, const int64_t *d_
  * Algorithm 1: repeat { N = R^2 (Algorithm 3); v = rowmax(R) + fuzz; I = (v_i >= N_ik, with the
  * end-orientation rule); R = R minus I } until nnz(R) stops changing; S = R.
  *   fuzz        < 2^30 (the scalar x of Sec. IV-E).
- *   mode        SG_TR_DIRMATCH or SG_TR_LITERAL.
+ *   mode        SG_TR_DIRMATCH or SG_TR_LITERAL, optionally | SG_TR_PER_END.
  *   *iterations rounds run, including the last round that removed nothing.
  * Output *S keeps the surviving entries of R with their values, in R's order.
  * Errors: SG_ERR_INVALID (R breaks the sg_graph_csr contract, fuzz or mode out of range),

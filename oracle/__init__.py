@@ -21,6 +21,7 @@ _lib = None
 OK, INVALID, OOM = 0, 1, 2
 INF = 0xFFFFFFFF
 DIRMATCH, LITERAL = 0, 1
+PER_END = 2  # mode flag: per-read-end row maxima in the reduction (or-ed with the semiring)
 
 
 class OracleError(RuntimeError):

@@ -355,11 +355,19 @@ int sgo_minplus(const sgo_graph *R, int32_t mode, uint32_t *N, uint8_t *Ndir) {
     return SGO_OK;
 }
 
+/*
+ * mode bit 0: the semiring reading (0 DIRMATCH, 1 LITERAL). mode bit 1 (PER_END): the row max of
+ * Algorithm 1's Reduce is taken per read end instead of over the whole row -- v_i,e = max of R_ik
+ * over the entries that leave read i through end e = out(d_ik), the orientation of read i in the
+ * overlap -- and an entry is compared with the max of its own end (the per-end bound of the
+ * string-graph reduction the paper builds on, as opposed to its literal whole-row Reduce).
+ */
 int sgo_transitive_reduce(const sgo_graph *R_in, uint32_t fuzz, int32_t mode, sgo_graph *S,
                           int32_t *iterations) {
     memset(S, 0, sizeof(*S));
     *iterations = 0;
-    if (fuzz >= (1u << 30) || (mode != 0 && mode != 1)) return SGO_INVALID;
+    if (fuzz >= (1u << 30) || mode < 0 || mode > 3) return SGO_INVALID;
+    const int32_t semiring = mode & 1, per_end = (mode >> 1) & 1;
     if (sgo_validate_graph(R_in) != SGO_OK) return SGO_INVALID;
     int64_t n = R_in->n, nnz = R_in->nnz;
     sgo_graph R;
@@ -370,7 +378,7 @@ int sgo_transitive_reduce(const sgo_graph *R_in, uint32_t fuzz, int32_t mode, sg
     R.dir = (uint8_t *)malloc((size_t)(nnz ? nnz : 1));
     uint32_t *N = (uint32_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(uint32_t));
     uint8_t *Nd = (uint8_t *)malloc((size_t)(nnz ? nnz : 1));
-    uint64_t *v = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    uint64_t *v = (uint64_t *)malloc((size_t)(n ? 2 * n : 2) * sizeof(uint64_t));  /* [i][end] */
     if (!R.row_ptr || !R.col || !R.suffix || !R.dir || !N || !Nd || !v) {
         free(R.row_ptr); free(R.col); free(R.suffix); free(R.dir); free(N); free(Nd); free(v);
         return SGO_OOM;
@@ -382,12 +390,15 @@ int sgo_transitive_reduce(const sgo_graph *R_in, uint32_t fuzz, int32_t mode, sg
     int64_t prev;
     do {
         prev = R.nnz;                                      /* prev <- R.nnz() */
-        sgo_minplus(&R, mode, N, Nd);                      /* N <- R^2 */
+        sgo_minplus(&R, semiring, N, Nd);                  /* N <- R^2 */
         for (int64_t i = 0; i < n; i++) {                  /* v <- R.Reduce(Row, 0, max) */
-            uint64_t mx = 0;
-            for (int64_t e = R.row_ptr[i]; e < R.row_ptr[i + 1]; e++)
-                if (R.suffix[e] > mx) mx = R.suffix[e];
-            v[i] = mx + fuzz;                              /* v <- v.Apply(x, add) */
+            uint64_t mx[2] = {0, 0};
+            for (int64_t e = R.row_ptr[i]; e < R.row_ptr[i + 1]; e++) {
+                const int end = per_end ? dir_out(R.dir[e]) : 0;
+                if (R.suffix[e] > mx[end]) mx[end] = R.suffix[e];
+            }
+            v[2 * i] = mx[0] + fuzz;                       /* v <- v.Apply(x, add) */
+            v[2 * i + 1] = mx[1] + fuzz;
         }
         /* M <- DimApply(Row, v); I <- M >= N (with the endpoint rule); R <- R o not I */
         int64_t w = 0;
@@ -395,7 +406,8 @@ int sgo_transitive_reduce(const sgo_graph *R_in, uint32_t fuzz, int32_t mode, sg
             int64_t b = R.row_ptr[i], e_end = R.row_ptr[i + 1];
             R.row_ptr[i] = w;
             for (int64_t e = b; e < e_end; e++) {
-                int transitive = N[e] != SGO_INF && Nd[e] == R.dir[e] && v[i] >= (uint64_t)N[e];
+                const uint64_t vi = v[2 * i + (per_end ? dir_out(R.dir[e]) : 0)];
+                int transitive = N[e] != SGO_INF && Nd[e] == R.dir[e] && vi >= (uint64_t)N[e];
                 if (!transitive) {
                     R.col[w] = R.col[e]; R.suffix[w] = R.suffix[e]; R.dir[w] = R.dir[e];
                     w++;

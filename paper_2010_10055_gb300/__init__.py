@@ -21,6 +21,7 @@ LIB_PATH_CHECKED = os.path.join(_HERE, "libsgraph_checked.so")
 (SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_TIMEOUT, SG_ERR_BUDGET, SG_ERR_OVERFLOW,
  SG_ERR_CANCELLED) = range(8)
 DIRMATCH, LITERAL = 0, 1
+PER_END = 2  # mode flag: per-read-end row maxima in the reduction (or-ed with the semiring)
 INF = 0xFFFFFFFF
 
 EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",

@@ -188,7 +188,7 @@ extern "C" sg_status sg_run_batch(const sg_batch_item *items, int32_t n_items, c
     memset(out, 0, sizeof(*out));
     if (!params || n_items < 1 || !items || params->k < 1 || params->k > 31 || (params->k & 1) == 0 ||
         params->min_shared < 1 || params->max_seeds < 0 || params->max_seeds > 8 || params->fuzz >= (1u << 30) ||
-        (params->tr_mode != SG_TR_DIRMATCH && params->tr_mode != SG_TR_LITERAL)) {
+        params->tr_mode < 0 || params->tr_mode > (SG_TR_LITERAL | SG_TR_PER_END)) {
         sg::set_error("run_batch: invalid parameters");
         return SG_ERR_INVALID;
     }

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
     __shared__ unsigned long long s_best[GMEM ? 1 : TR_SMEM_ROW];
     __shared__ int64_t s_pre[GMEM ? 1 : TR_SMEM_ROW + 1];
     __shared__ int64_t s_tmp[TR_NT / 32 + 1];
-    __shared__ uint32_t s_red[TR_NT / 32];
+    __shared__ uint32_t s_red[2 * (TR_NT / 32)];
     __shared__ int64_t s_kept[TR_NT / 32];
     if (*err) return;  // the graph failed validation: touch nothing
     const int64_t nrows = (int64_t)*nrows_p;
@@ -95,8 +95,9 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
         const uint8_t *dir = GMEM ? g.dir + r0 : s_dir;
         unsigned long long *best = GMEM ? gbest + r0 : s_best;
         int64_t *pre = GMEM ? gpre + r0 + i : s_pre;  // deg + 1 slots per row
-        // stage row i and the exclusive prefix of its neighbours' degrees
-        uint32_t vmax = 0;
+        // stage row i and the exclusive prefix of its neighbours' degrees; the row max per read
+        // end of i (out(d)), folded into one for the whole-row form
+        uint32_t vmax0 = 0, vmax1 = 0;
         int64_t run = 0;
         for (int64_t base = 0; base < deg; base += TR_NT) {
             int64_t a = base + threadIdx.x;
@@ -104,13 +105,15 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
             if (a < deg) {
                 int32_t j = g.col[r0 + a];
                 uint32_t sv = g.suf[r0 + a];
+                const uint8_t da = g.dir[r0 + a];
                 if (!GMEM) {
                     s_col[a] = j;
                     s_suf[a] = sv;
-                    s_dir[a] = g.dir[r0 + a];
+                    s_dir[a] = da;
                 }
                 best[a] = TR_NONE;
-                vmax = sv > vmax ? sv : vmax;
+                if (da >> 1) vmax1 = sv > vmax1 ? sv : vmax1;
+                else vmax0 = sv > vmax0 ? sv : vmax0;
                 dj = g.rp[j + 1] - g.rp[j];
             }
             int64_t tot;
@@ -121,10 +124,15 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
         if (threadIdx.x == 0) pre[deg] = run;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            uint32_t y = __shfl_xor_sync(0xffffffffu, vmax, o);
-            vmax = y > vmax ? y : vmax;
+            uint32_t y = __shfl_xor_sync(0xffffffffu, vmax0, o);
+            vmax0 = y > vmax0 ? y : vmax0;
+            y = __shfl_xor_sync(0xffffffffu, vmax1, o);
+            vmax1 = y > vmax1 ? y : vmax1;
         }
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = vmax;
+        if ((threadIdx.x & 31) == 0) {
+            s_red[2 * (threadIdx.x >> 5)] = vmax0;
+            s_red[2 * (threadIdx.x >> 5) + 1] = vmax1;
+        }
         __syncthreads();
         const int64_t P = pre[deg];
         // N = R^2 on the pattern of row i
@@ -144,21 +152,25 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
             const uint32_t dij = dir[a], djk = g.dir[b];
             if ((dij & 1u) != (djk >> 1)) continue;  // heads at j must point opposite ways
             const uint32_t comp = (dij & 2u) | (djk & 1u);
-            if (mode == SG_TR_DIRMATCH && comp != dir[t]) continue;
+            if ((mode & 1) == SG_TR_DIRMATCH && comp != dir[t]) continue;
             const unsigned long long key = ((unsigned long long)(suf[a] + g.suf[b]) << 2) | comp;
             atomicMin(best + t, key);
         }
         __syncthreads();
-        uint32_t vm = 0;
-        for (int w = 0; w < TR_NT / 32; w++) vm = s_red[w] > vm ? s_red[w] : vm;
-        const uint64_t v = (uint64_t)vm + fuzz;  // M_ik for every k of row i
+        uint32_t vm[2] = {0u, 0u};
+        for (int w = 0; w < TR_NT / 32; w++)
+            for (int e = 0; e < 2; e++) vm[e] = s_red[2 * w + e] > vm[e] ? s_red[2 * w + e] : vm[e];
+        const bool per_end = (mode & SG_TR_PER_END) != 0;
+        const uint32_t vrow = vm[0] > vm[1] ? vm[0] : vm[1];
+        const uint64_t v0 = (uint64_t)(per_end ? vm[0] : vrow) + fuzz;  // M_ik: the bound of end 0
+        const uint64_t v1 = (uint64_t)(per_end ? vm[1] : vrow) + fuzz;  // ... and of end 1
         int64_t mykept = 0;
         for (int64_t t = threadIdx.x; t < deg; t += TR_NT) {
             const unsigned long long bt = best[t];
             const uint32_t d = dir[t];
             const bool has = bt != TR_NONE;
             const uint64_t N = bt >> 2;
-            const bool transitive = has && (uint32_t)(bt & 3u) == d && v >= N;
+            const bool transitive = has && (uint32_t)(bt & 3u) == d && ((d >> 1) ? v1 : v0) >= N;
             if (keep) keep[r0 + t] = transitive ? 0 : 1;
             mykept += transitive ? 0 : 1;
             if (outN) outN[r0 + t] = has ? (uint32_t)N : 0xFFFFFFFFu;
@@ -394,7 +406,7 @@ extern "C" sg_status sg_transitive_reduce(const sg_graph_csr *R, uint32_t fuzz, 
     }
     *S = sg_graph_csr{};
     *iterations = 0;
-    if (!sg::graph_args_ok(R) || fuzz >= (1u << 30) || (mode != SG_TR_DIRMATCH && mode != SG_TR_LITERAL)) {
+    if (!sg::graph_args_ok(R) || fuzz >= (1u << 30) || mode < 0 || mode > (SG_TR_LITERAL | SG_TR_PER_END)) {
         sg::set_error("transitive_reduce: invalid arguments");
         return SG_ERR_INVALID;
     }
@@ -411,7 +423,7 @@ extern "C" sg_status sg_transitive_reduce_rounds(const sg_graph_csr *R, uint32_t
     *S = sg_graph_csr{};
     *rounds = 0;
     *converged = 0;
-    if (!sg::graph_args_ok(R) || fuzz >= (1u << 30) || (mode != SG_TR_DIRMATCH && mode != SG_TR_LITERAL) ||
+    if (!sg::graph_args_ok(R) || fuzz >= (1u << 30) || mode < 0 || mode > (SG_TR_LITERAL | SG_TR_PER_END) ||
         max_rounds < 1) {
         sg::set_error("transitive_reduce_rounds: invalid arguments");
         return SG_ERR_INVALID;

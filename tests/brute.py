@@ -73,9 +73,11 @@ def overlap_pairs(per_read: list, min_shared: int, max_seeds: int) -> dict:
     return out
 
 
-def dense_tr(n: int, entries: dict, fuzz: int):
+def dense_tr(n: int, entries: dict, fuzz: int, per_end: bool = False):
     """Algorithm 1 on dense n x n arrays, every intermediate j tried for every pair (i, k).
-    entries: {(i, k): (suffix, dir)}. Returns (surviving entries, rounds, N of round 1)."""
+    entries: {(i, k): (suffix, dir)}. per_end: an entry is bounded by the max over the entries of
+    its row that use the same end of read i (dir >> 1) instead of the whole row's max. Returns
+    (surviving entries, rounds, N of round 1)."""
     W = np.full((n, n), -1, np.int64)
     D = np.zeros((n, n), np.int64)
     for (i, k), (s, d) in entries.items():
@@ -106,8 +108,16 @@ def dense_tr(n: int, entries: dict, fuzz: int):
                 N[i, k] = best
         if first_N is None:
             first_N = N.copy()
-        rowmax = np.where(W >= 0, W, 0).max(axis=1) if n else np.zeros(0, np.int64)
-        drop = (W >= 0) & (N != INF) & ((rowmax[:, None] + fuzz) >= N)
+        if per_end:
+            ends = D >> 1
+            bound = np.zeros((n, n), np.int64)
+            for e in (0, 1):
+                m = np.where((W >= 0) & (ends == e), W, 0).max(axis=1) if n else np.zeros(0, np.int64)
+                bound = np.where(ends == e, m[:, None], bound)
+        else:
+            rowmax = np.where(W >= 0, W, 0).max(axis=1) if n else np.zeros(0, np.int64)
+            bound = rowmax[:, None]
+        drop = (W >= 0) & (N != INF) & ((bound + fuzz) >= N)
         W[drop] = -1
         if int((W >= 0).sum()) == prev:
             break

@@ -185,3 +185,64 @@ def test_edge_cases_and_validation():
         oracle.transitive_reduce(big)
     with pytest.raises(ValueError):
         oracle.transitive_reduce(brute.dict_to_graph(3, {(0, 1): (5, 0)}), fuzz=1 << 30)
+
+
+# ---------------------------------------------------------------- per-end row maxima (mode bit 1)
+@pytest.mark.parametrize("seed,n,deg,fuzz", [(1, 12, 3.0, 0), (2, 20, 4.0, 50), (3, 30, 2.5, 200),
+                                             (4, 25, 6.0, 10), (5, 16, 8.0, 1000)])
+def test_per_end_dense_brute_force(seed, n, deg, fuzz):
+    R = synth.random_graph(n, deg, hub_frac=0.1, max_suffix=300, seed=seed)
+    surv, rounds, _ = brute.dense_tr(n, brute.graph_to_dict(R), fuzz, per_end=True)
+    S, it = oracle.transitive_reduce(R, fuzz=fuzz, mode=oracle.DIRMATCH | oracle.PER_END)
+    assert brute.graph_to_dict(S) == surv
+    assert it == rounds
+
+
+def test_per_end_jittered_layout_brute_force():
+    w = synth.genome(3000, 5)
+    rd = synth.reads(w, 6.0, 400.0, 150.0, 50, 0, 0, 0, 6)
+    R = synth.overlap_graph(rd["start"], rd["end"], rd["strand"], 1, jitter=30, seed=7)
+    surv, rounds, _ = brute.dense_tr(R["n"], brute.graph_to_dict(R), 20, per_end=True)
+    S, it = oracle.transitive_reduce(R, fuzz=20, mode=oracle.PER_END)
+    assert brute.graph_to_dict(S) == surv and it == rounds
+
+
+@pytest.mark.parametrize("strands", list(itertools.product([0, 1], repeat=3)))
+def test_per_end_three_read_layout_all_orientations(strands):
+    """A transitive edge uses the same end of its read as the walk's first edge, so the per-end
+    bound still removes a <-> c in every orientation."""
+    R = _layout([0, 40, 80], [100, 100, 100], strands)
+    S, it = oracle.transitive_reduce(R, fuzz=0, mode=oracle.PER_END)
+    assert set(brute.graph_to_dict(S)) == {(0, 1), (1, 0), (1, 2), (2, 1)}
+    assert it == 2
+
+
+def test_per_end_bound_is_the_end_max():
+    """Read 0 has a long edge on one end (0 -> 3, suffix 5000) and a transitive triple on its
+    other end (0 -> 1 -> 2 with suffixes 30 + 40 against 0 -> 2 with 50): the whole-row bound
+    (5000) removes 0 -> 2; the per-end bound (max 50 on that end, fuzz 10 -> 60 < 70) keeps it."""
+    ent = {(0, 1): (30, 0), (1, 2): (40, 0), (0, 2): (50, 0), (0, 3): (5000, 3)}
+    R = brute.dict_to_graph(4, ent)
+    whole, _ = oracle.transitive_reduce(R, fuzz=10)
+    per, _ = oracle.transitive_reduce(R, fuzz=10, mode=oracle.PER_END)
+    assert (0, 2) not in brute.graph_to_dict(whole)
+    assert (0, 2) in brute.graph_to_dict(per)
+    per20, _ = oracle.transitive_reduce(R, fuzz=20, mode=oracle.PER_END)  # 50 + 20 >= 70
+    assert (0, 2) not in brute.graph_to_dict(per20)
+
+
+def test_per_end_first_round_removes_subset_of_whole_row():
+    """Each end's max is at most the row's max, so in the first round the per-end form removes a
+    subset of what the whole-row form removes (graphs with no second round: every transitive
+    entry goes in round one)."""
+    for strands in itertools.product([0, 1], repeat=4):
+        R = _layout([0, 30, 60, 90], [100, 100, 100, 100], strands)
+        whole, itw = oracle.transitive_reduce(R, fuzz=0)
+        per, itp = oracle.transitive_reduce(R, fuzz=0, mode=oracle.PER_END)
+        assert set(brute.graph_to_dict(whole)) <= set(brute.graph_to_dict(per))
+        assert itw == 2 and itp == 2
+    R = synth.random_graph(300, 8.0, hub_frac=0.05, max_suffix=2000, seed=21)
+    ent = set(brute.graph_to_dict(R))
+    for sem in (oracle.DIRMATCH, oracle.LITERAL):
+        per, _ = oracle.transitive_reduce(R, fuzz=100, mode=sem | oracle.PER_END)
+        assert set(brute.graph_to_dict(per)) <= ent
