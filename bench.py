@@ -297,6 +297,15 @@ def main():
     # per-kernel shares from the untimed, fully event-bracketed step
     kernels = {k: {"launches": c, "ms": ms, "share": ms / ktot}
                for k, (c, ms) in sorted(breakdown.items(), key=lambda kv: -kv[1][1])}
+    # the same roofline for every kernel family with a byte model, from the breakdown step's
+    # event times (the dominant kernel's line above is timed inside the timed region instead)
+    rooflines = []
+    for f, (c, ms) in sorted(fam_breakdown.items(), key=lambda kv: -kv[1][1]):
+        ab = algorithmic_bytes(f, sz)
+        if ab and ms > 0:
+            ach = ab / (ms / 1e3) / 1e9
+            rooflines.append({"kernel": f, "achieved": ach, "frac": ach / hbm, "unit": "GB/s", "ms": ms,
+                              "share": ms / ktot})
 
     # ---- the chain without true coordinates: C -> R from C's seeds -> S (one untimed pass)
     from_seeds = measure_from_seeds(sg, seq, off, w)
@@ -323,7 +332,8 @@ def main():
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "tr_edges_per_s": edges_all * args.steps / (tr_ms_max / 1e3) if tr_ms_max else None,
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
-            "e2e": e2e, "roofline": roof, "kernels": kernels, "stages": stages, "clocks": clk,
+            "e2e": e2e, "roofline": roof, "rooflines": rooflines, "kernels": kernels, "stages": stages,
+            "clocks": clk,
             "gpu_launches": launches, "device_memory_peak_gb": mem_peak / 1e9, "from_seeds": from_seeds}
     if not args.no_forms:
         line["batched"] = measure_batched(sg, 512, 200e3)
