@@ -22,7 +22,7 @@
  *    memory stays allocated.
  *  - All work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream). Each
  *    compute call validates its device inputs on the device and synchronises the stream to read
- *    that verdict and its output sizes back, so outputs are complete when it returns.
+ *    that outcome and its output sizes back, so outputs are complete when it returns.
  *  - Errors: a non-SG_OK status; sg_last_error() describes it (per host thread). There is no
  *    CPU fallback: if the GPU cannot run the call, it fails.
  *  - Sizes are int64. Row pointers are int64, column indices int32 (so n and m < 2^31).

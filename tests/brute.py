@@ -77,7 +77,7 @@ def dense_tr(n: int, entries: dict, fuzz: int, per_end: bool = False):
     """Algorithm 1 on dense n x n arrays, every intermediate j tried for every pair (i, k).
     entries: {(i, k): (suffix, dir)}. per_end: an entry is bounded by the max over the entries of
     its row that use the same end of read i (dir >> 1) instead of the whole row's max. Returns
-    (surviving entries, rounds, N of round 1)."""
+    (surviving entries, rounds, N of the first reduction round)."""
     W = np.full((n, n), -1, np.int64)
     D = np.zeros((n, n), np.int64)
     for (i, k), (s, d) in entries.items():
