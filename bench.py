@@ -47,6 +47,20 @@ def parse():
     return p.parse_args()
 
 
+def combine_ranks(total_ms: float, products: int, tr_ms: float, edges: int, world: int, device: str = "cuda"):
+    """Whole-job figures of a replica run: the slowest rank's step and TR times (MAX over ranks)
+    and the work of all ranks (SUM), as (total_ms, products, tr_ms, edges)."""
+    if world <= 1:
+        return float(total_ms), float(products), float(tr_ms), float(edges)
+    import torch
+    import torch.distributed as dist
+    times = torch.tensor([float(total_ms), float(tr_ms)], dtype=torch.float64, device=device)
+    work = torch.tensor([float(products), float(edges)], dtype=torch.float64, device=device)
+    dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    dist.all_reduce(work, op=dist.ReduceOp.SUM)
+    return float(times[0]), float(work[0]), float(times[1]), float(work[1])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -259,19 +273,7 @@ def main():
     tr_ms = [a0.elapsed_time(a1) for a0, a1 in tr_ev]
     total_ms = sum(step_ms)
     prof = by_family(sg.prof_collect())
-    if world > 1:
-        t = torch.tensor([total_ms, float(products), float(sum(tr_ms)), float(R.nnz)], dtype=torch.float64,
-                         device="cuda")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        total_ms_all = float(mx[0])
-        products_all = float(sm[1])
-        tr_ms_max = float(sm[2]) / world
-        edges_all = float(sm[3])
-    else:
-        total_ms_all, products_all, tr_ms_max, edges_all = total_ms, float(products), sum(tr_ms), float(R.nnz)
+    total_ms_all, products_all, tr_ms_max, edges_all = combine_ranks(total_ms, products, sum(tr_ms), R.nnz, world)
     value = products_all * args.steps / (total_ms_all / 1e3)
 
     # ---- roofline of the dominant kernel
