@@ -37,6 +37,8 @@
  *    d_ik. mode 1 (LITERAL): N_ik is the lexicographic min of (R_ij + R_jk, composite) over all
  *    valid walks, and the endpoint check is applied to that single minimum afterwards.
  *  - The row maximum is over the whole row (0 for an empty row); M_ik >= N_ik removes on ties.
+ *    With mode bit 1 (PER_END) it is taken per read end of the row's read instead, each entry
+ *    bounded by the maximum of the entries that leave the read through the same end.
  */
 #include <stdint.h>
 #include <stdlib.h>
