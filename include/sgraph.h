@@ -237,7 +237,7 @@ typedef struct {
     uint32_t min_shared;
     int32_t max_seeds;
     uint32_t fuzz;
-    int32_t tr_mode;
+    int32_t tr_mode;           /* as sg_transitive_reduce's mode */
 } sg_batch_params;
 
 typedef struct {
@@ -342,7 +342,7 @@ typedef struct {
     const uint8_t *r_dir;
     int64_t r_nnz;
     uint32_t fuzz;            /* as sg_transitive_reduce */
-    int32_t tr_mode;
+    int32_t tr_mode;          /* as sg_transitive_reduce's mode */
 } sg_pipeline_job;
 
 /* Host results. The arrays point into the arena passed to sg_pipeline_host and stay valid until
