@@ -141,7 +141,6 @@ __device__ __forceinline__ void load_chunk(uint32_t *smw, const uint8_t *__restr
 // (window_key). Thread t of block b covers windows and bases b * KM_CHUNK + t * KM_W + j, j < KM_W,
 // reading bases [t * KM_W, t * KM_W + KM_W + k - 1) of the block's chunk. K > 0 makes k a
 // compile-time constant (K == 0: k taken from k_rt).
-constexpr uint64_t WC_NONE = ~0ull;
 constexpr uint64_t WC_STRAND = 1ull << 63;
 constexpr uint32_t H_NONE = 0xFFFFFFFFu;
 constexpr uint32_t B1_SEED = 0x9e3779b9u, B2_SEED = 0x7f4a7c15u;
