@@ -73,6 +73,9 @@ sg_status timeout_error(const char *what);
 // Test hook (sg_debug_stall_lookback): nonzero makes multi-tile scans withhold tile 0's prefix.
 int debug_stall_lookback();
 
+// Multiprocessors of the current device, for grid sizes.
+int sm_count();
+
 // Device memory a call can still obtain (driver free + unused memory held by the library's pool).
 size_t device_bytes_available();
 

@@ -990,7 +990,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         const uint64_t max_sl = (uint64_t)tune("bloom_max_slices");
         if (nsl > max_sl) nsl = max_sl;
         const int64_t nvec = ngroups * 8;  // 16-byte vectors of 4 hashes
-        const int64_t grid = blocks_for(nvec, KM_NT) < 152 * 16 ? blocks_for(nvec, KM_NT) : 152 * 16;
+        const int64_t gmax = (int64_t)sm_count() * 16;
+        const int64_t grid = blocks_for(nvec, KM_NT) < gmax ? blocks_for(nvec, KM_NT) : gmax;
         const int64_t u = tune("bloom_unroll");
         for (uint64_t q = 0; q < nsl; q++) {
             const uint32_t lo_w = (uint32_t)((uint64_t)b1.nwords * q / nsl);

@@ -101,7 +101,7 @@ static sg_status pipeline_impl(const sg_pipeline_job *j, sg_host_arena *ar, sg_p
         {
             LaunchScope ls("products", s);
             int grid = (int)((At.n_rows + 255) / 256);
-            if (grid > 152 * 8) grid = 152 * 8;
+            if (grid > sm_count() * 8) grid = sm_count() * 8;
             if (grid > 0) products_kernel<<<grid, 256, 0, s>>>(At.row_ptr, At.n_rows, prod);
         }
         st = sg_overlap_spgemm(&A, &At, j->min_shared, j->max_seeds, &C, (sg_stream_t)s);

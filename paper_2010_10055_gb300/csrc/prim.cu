@@ -291,7 +291,8 @@ static sg_status radix_sort_impl(K *k0, V *v0, K *k1, V *v1, int64_t n, int lo_b
     unsigned long long *ghist = ws, *status = ws + (size_t)npass * RS_RADIX;
     unsigned int *ctr = (unsigned int *)(status + (size_t)npass * ntiles * RS_RADIX);
     SG_CUDA_TRY(cudaMemsetAsync(ws, 0, words * sizeof(unsigned long long), s));
-    const int64_t hgrid = ntiles < 152 * 8 ? ntiles : 152 * 8;
+    const int64_t hmax = (int64_t)sm_count() * 8;
+    const int64_t hgrid = ntiles < hmax ? ntiles : hmax;
     SG_LAUNCH("radix_upfront", radix_upfront_kernel<K>, hgrid, RS_NT, 0, s, (const K *)k0, n, lo_bit, npass, ghist);
     const size_t smem = sizeof(RsSmem<K, V, HAS_V>);
     SG_CUDA_TRY(ensure_smem(radix_onesweep_kernel<K, V, HAS_V>, smem));

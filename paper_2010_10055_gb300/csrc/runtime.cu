@@ -78,6 +78,24 @@ static cudaMemPool_t library_pool() {
     return g_pools[dev];
 }
 
+// Multiprocessors of the current device (152 on a GB300), for grid sizes; read once per device.
+int sm_count() {
+    static std::atomic<int> cache[256];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        cudaGetLastError();
+        return 152;
+    }
+    int v = cache[dev].load();
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        v = 152;
+    }
+    cache[dev].store(v);
+    return v;
+}
+
 // Device memory a call can still obtain: free in the driver plus what the library's pool holds
 // unused (the pool keeps freed memory reserved).
 size_t device_bytes_available() {

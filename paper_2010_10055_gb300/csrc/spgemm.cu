@@ -651,7 +651,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr, n,
               work, a_beg, a_len);
     SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
-    const int grid = (int)(152 * tune("spgemm_blocks_per_sm"));
+    const int nsm = sm_count();
+    const int grid = (int)(nsm * tune("spgemm_blocks_per_sm"));
     // numeric: one class per table size from 2^6 while the table and its sort buffer fit in 160 KB
     Classes num{};
     num.ncls = 0;
@@ -761,7 +762,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
             if (n_big + n_big_f + n_ovf > 0) {
                 unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
                 rows_g = rows_g > n_big_f ? rows_g : n_big_f;
-                const int ggrid = (int)(rows_g < 152 * 2 ? rows_g : 152 * 2);
+                const int ggrid = (int)(rows_g < (unsigned long long)nsm * 2 ? rows_g : (unsigned long long)nsm * 2);
                 unsigned char *pool = sc.get<unsigned char>((size_t)gslice_bytes * ggrid);
                 if (!pool) return SG_ERR_OOM;
                 if (n_big)
@@ -828,7 +829,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     if (n_big + n_ovf > 0) {
         const int64_t slice = 2 * pow2_at_least(2 * (n > 1 ? n - 1 : 1));  // keys + counts of the largest row
         const unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
-        const int grid = (int)(rows_g < 152 * 2 ? rows_g : 152 * 2);
+        const int grid = (int)(rows_g < (unsigned long long)nsm * 2 ? rows_g : (unsigned long long)nsm * 2);
         int32_t *pool = sc.get<int32_t>((size_t)slice * grid);
         if (!pool) return SG_ERR_OOM;
         if (n_big)
@@ -872,7 +873,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                   (unsigned long long *)nullptr, (int64_t *)nullptr);
     }
     if (h_num[num.ncls]) {
-        const int ggrid = (int)(h_num[num.ncls] < 152 * 2 ? h_num[num.ncls] : 152 * 2);
+        const int ggrid =
+            (int)(h_num[num.ncls] < (unsigned long long)nsm * 2 ? h_num[num.ncls] : (unsigned long long)nsm * 2);
         unsigned char *pool = sc.get<unsigned char>((size_t)gslice_bytes * ggrid);
         if (!pool) return SG_ERR_OOM;
         SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, false>), ggrid, 512, 0, s, g,

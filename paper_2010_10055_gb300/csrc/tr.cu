@@ -269,12 +269,12 @@ static sg_status minplus_round(const TrGraph &g, int64_t nnz, int mode, uint32_t
     if (n == 0) return SG_OK;
     SG_LAUNCH("tr_bin", tr_bin_kernel, blocks_for(n, 256), 256, 0, s, g.rp, n, counts, w.kind);
     SG_LAUNCH("tr_fill", tr_fill_kernel, blocks_for(n, 256), 256, 0, s, w.kind, n, counts + 3, w.rows);
-    const int64_t gcap = 152 * tune("tr_blocks_per_sm");
+    const int64_t gcap = (int64_t)sm_count() * tune("tr_blocks_per_sm");
     const int64_t gs = n < gcap ? n : gcap;
     SG_LAUNCH("tr_minplus_mark", minplus_mark_kernel<false>, gs, TR_NT, 0, s, g, (const int32_t *)w.rows,
               counts + 1, err, mode, fuzz, (unsigned long long *)nullptr, (int64_t *)nullptr, keep, kept, outN,
               outD);
-    const int64_t gg = n < 152 * 2 ? n : 152 * 2;
+    const int64_t gg = n < (int64_t)sm_count() * 2 ? n : (int64_t)sm_count() * 2;
     SG_LAUNCH("tr_minplus_mark_gmem", minplus_mark_kernel<true>, gg, TR_NT, 0, s, g, (const int32_t *)(w.rows + n),
               counts + 2, err, mode, fuzz, w.gbest, w.gpre, keep, kept, outN, outD);
     return SG_OK;
