@@ -73,27 +73,31 @@ def overlap_pairs(per_read: list, min_shared: int, max_seeds: int) -> dict:
     return out
 
 
-def dense_tr(n: int, entries: dict, fuzz: int, per_end: bool = False):
+def dense_tr(n: int, entries: dict, fuzz: int, per_end: bool = False, literal: bool = False):
     """Algorithm 1 on dense n x n arrays, every intermediate j tried for every pair (i, k).
     entries: {(i, k): (suffix, dir)}. per_end: an entry is bounded by the max over the entries of
-    its row that use the same end of read i (dir >> 1) instead of the whole row's max. Returns
-    (surviving entries, rounds, N of the first reduction round)."""
+    its row that use the same end of read i (dir >> 1) instead of the whole row's max.
+    literal: the MinPlus entry is the smallest (sum, composite dir) pair over every valid walk,
+    compared as a Python tuple, and the endpoint rule is applied to that one walk afterwards;
+    otherwise only walks whose ends already agree with d_ik compete. Returns (surviving entries,
+    rounds, N of the first reduction round, composite dir of that N's walk or d_ik)."""
     W = np.full((n, n), -1, np.int64)
     D = np.zeros((n, n), np.int64)
     for (i, k), (s, d) in entries.items():
         W[i, k] = s
         D[i, k] = d
     rounds = 0
-    first_N = None
+    first_N = first_D = None
     while True:
         rounds += 1
         prev = int((W >= 0).sum())
         N = np.full((n, n), INF, np.int64)
+        ND = D.copy()
         for i in range(n):
             for k in range(n):
                 if W[i, k] < 0:
                     continue
-                best = INF
+                best = None
                 for j in range(n):
                     if W[i, j] < 0 or W[j, k] < 0:
                         continue
@@ -101,13 +105,18 @@ def dense_tr(n: int, entries: dict, fuzz: int, per_end: bool = False):
                     # equals orientation of j seen from (j, k)
                     if (D[i, j] & 1) != (D[j, k] >> 1):
                         continue
-                    # heads at i agree and heads at k agree
-                    if (D[i, j] >> 1) != (D[i, k] >> 1) or (D[j, k] & 1) != (D[i, k] & 1):
+                    # the walk's end orientations: read i as in (i, j), read k as in (j, k)
+                    ends = (int(D[i, j] >> 1), int(D[j, k] & 1))
+                    if not literal and ends != (int(D[i, k] >> 1), int(D[i, k] & 1)):
                         continue
-                    best = min(best, int(W[i, j] + W[j, k]))
-                N[i, k] = best
+                    cand = (int(W[i, j] + W[j, k]), 2 * ends[0] + ends[1])
+                    if best is None or cand < best:
+                        best = cand
+                if best is not None:
+                    N[i, k] = best[0]
+                    ND[i, k] = best[1]
         if first_N is None:
-            first_N = N.copy()
+            first_N, first_D = N.copy(), ND.copy()
         if per_end:
             ends = D >> 1
             bound = np.zeros((n, n), np.int64)
@@ -117,12 +126,12 @@ def dense_tr(n: int, entries: dict, fuzz: int, per_end: bool = False):
         else:
             rowmax = np.where(W >= 0, W, 0).max(axis=1) if n else np.zeros(0, np.int64)
             bound = rowmax[:, None]
-        drop = (W >= 0) & (N != INF) & ((bound + fuzz) >= N)
+        drop = (W >= 0) & (N != INF) & (ND == D) & ((bound + fuzz) >= N)
         W[drop] = -1
         if int((W >= 0).sum()) == prev:
             break
     surv = {(int(i), int(k)): (int(W[i, k]), int(D[i, k])) for i, k in zip(*np.nonzero(W >= 0))}
-    return surv, rounds, first_N
+    return surv, rounds, first_N, first_D
 
 
 def graph_to_dict(R: dict) -> dict:

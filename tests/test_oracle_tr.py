@@ -108,7 +108,7 @@ def test_corrupted_orientation_keeps_edge(edge, bit):
 def test_dense_brute_force(seed, n, deg, fuzz):
     R = synth.random_graph(n, deg, hub_frac=0.1, max_suffix=300, seed=seed)
     ent = brute.graph_to_dict(R)
-    surv, rounds, N1 = brute.dense_tr(n, ent, fuzz)
+    surv, rounds, N1, _ = brute.dense_tr(n, ent, fuzz)
     N, _ = oracle.minplus(R)
     for e, (i, k) in enumerate(sorted(ent)):
         assert N[e] == N1[i, k]
@@ -122,7 +122,7 @@ def test_jittered_layout_brute_force():
     rd = synth.reads(w, 6.0, 400.0, 150.0, 50, 0, 0, 0, 6)
     R = synth.overlap_graph(rd["start"], rd["end"], rd["strand"], 1, jitter=30, seed=7)
     ent = brute.graph_to_dict(R)
-    surv, rounds, _ = brute.dense_tr(R["n"], ent, 20)
+    surv, rounds, _, _ = brute.dense_tr(R["n"], ent, 20)
     S, it = oracle.transitive_reduce(R, fuzz=20)
     assert brute.graph_to_dict(S) == surv and it == rounds
 
@@ -192,7 +192,7 @@ def test_edge_cases_and_validation():
                                              (4, 25, 6.0, 10), (5, 16, 8.0, 1000)])
 def test_per_end_dense_brute_force(seed, n, deg, fuzz):
     R = synth.random_graph(n, deg, hub_frac=0.1, max_suffix=300, seed=seed)
-    surv, rounds, _ = brute.dense_tr(n, brute.graph_to_dict(R), fuzz, per_end=True)
+    surv, rounds, _, _ = brute.dense_tr(n, brute.graph_to_dict(R), fuzz, per_end=True)
     S, it = oracle.transitive_reduce(R, fuzz=fuzz, mode=oracle.DIRMATCH | oracle.PER_END)
     assert brute.graph_to_dict(S) == surv
     assert it == rounds
@@ -202,7 +202,7 @@ def test_per_end_jittered_layout_brute_force():
     w = synth.genome(3000, 5)
     rd = synth.reads(w, 6.0, 400.0, 150.0, 50, 0, 0, 0, 6)
     R = synth.overlap_graph(rd["start"], rd["end"], rd["strand"], 1, jitter=30, seed=7)
-    surv, rounds, _ = brute.dense_tr(R["n"], brute.graph_to_dict(R), 20, per_end=True)
+    surv, rounds, _, _ = brute.dense_tr(R["n"], brute.graph_to_dict(R), 20, per_end=True)
     S, it = oracle.transitive_reduce(R, fuzz=20, mode=oracle.PER_END)
     assert brute.graph_to_dict(S) == surv and it == rounds
 
@@ -246,3 +246,60 @@ def test_per_end_first_round_removes_subset_of_whole_row():
     for sem in (oracle.DIRMATCH, oracle.LITERAL):
         per, _ = oracle.transitive_reduce(R, fuzz=100, mode=sem | oracle.PER_END)
         assert set(brute.graph_to_dict(per)) <= ent
+
+
+# ------------------------------------------------------- LITERAL semiring reading (mode bit 0)
+RANDOM_GRAPHS = [(1, 12, 3.0, 0), (2, 20, 4.0, 50), (3, 30, 2.5, 200), (4, 25, 6.0, 10), (5, 16, 8.0, 1000)]
+
+
+@pytest.mark.parametrize("per_end", [False, True])
+@pytest.mark.parametrize("seed,n,deg,fuzz", RANDOM_GRAPHS)
+def test_literal_dense_brute_force(seed, n, deg, fuzz, per_end):
+    """LITERAL (Algorithm 3 carrying one (sum, composite) minimum per entry, endpoint rule after)
+    against the dense brute force that compares every valid walk as a tuple: N, its composite,
+    S and the round count, with and without per-end bounds."""
+    R = synth.random_graph(n, deg, hub_frac=0.1, max_suffix=300, seed=seed)
+    ent = brute.graph_to_dict(R)
+    surv, rounds, N1, D1 = brute.dense_tr(n, ent, fuzz, per_end=per_end, literal=True)
+    N, Nd = oracle.minplus(R, oracle.LITERAL)
+    for e, (i, k) in enumerate(sorted(ent)):
+        assert N[e] == N1[i, k], (i, k)
+        assert Nd[e] == D1[i, k], (i, k)
+    mode = oracle.LITERAL | (oracle.PER_END if per_end else 0)
+    S, it = oracle.transitive_reduce(R, fuzz=fuzz, mode=mode)
+    assert brute.graph_to_dict(S) == surv
+    assert it == rounds
+
+
+@pytest.mark.parametrize("per_end", [False, True])
+def test_literal_jittered_layout_brute_force(per_end):
+    w = synth.genome(3000, 5)
+    rd = synth.reads(w, 6.0, 400.0, 150.0, 50, 0, 0, 0, 6)
+    R = synth.overlap_graph(rd["start"], rd["end"], rd["strand"], 1, jitter=30, seed=7)
+    surv, rounds, _, _ = brute.dense_tr(R["n"], brute.graph_to_dict(R), 20, per_end=per_end, literal=True)
+    mode = oracle.LITERAL | (oracle.PER_END if per_end else 0)
+    S, it = oracle.transitive_reduce(R, fuzz=20, mode=mode)
+    assert brute.graph_to_dict(S) == surv and it == rounds
+
+
+def test_literal_keeps_edge_whose_min_walk_has_other_ends():
+    """Two walks 0 -> 1 -> 3 (suffixes 10 + 20, ends forward/forward: composite 0) and
+    0 -> 2 -> 3 (15 + 15, composite 3) tie at 30 under the entry 0 -> 3 (suffix 25, dir 3).
+    LITERAL keeps the walk with the smaller composite (0), which differs from d_03, so 0 -> 3
+    stays; DIRMATCH lets only the composite-3 walk compete and removes 0 -> 3 (25 + 10 >= 30)."""
+    ent = {(0, 1): (10, 0), (1, 3): (20, 0), (0, 2): (15, 2), (2, 3): (15, 1), (0, 3): (25, 3)}
+    R = brute.dict_to_graph(4, ent)
+    e03 = sorted(ent).index((0, 3))
+    N0, D0 = oracle.minplus(R, oracle.DIRMATCH)
+    N1, D1 = oracle.minplus(R, oracle.LITERAL)
+    assert (N0[e03], D0[e03]) == (30, 3)
+    assert (N1[e03], D1[e03]) == (30, 0)
+    dm, _ = oracle.transitive_reduce(R, fuzz=10)
+    lit, _ = oracle.transitive_reduce(R, fuzz=10, mode=oracle.LITERAL)
+    assert (0, 3) not in brute.graph_to_dict(dm)
+    assert (0, 3) in brute.graph_to_dict(lit)
+    # a strictly shorter walk with the right ends wins in both readings
+    ent2 = dict(ent)
+    ent2[(2, 3)] = (14, 1)
+    lit2, _ = oracle.transitive_reduce(brute.dict_to_graph(4, ent2), fuzz=10, mode=oracle.LITERAL)
+    assert (0, 3) not in brute.graph_to_dict(lit2)
