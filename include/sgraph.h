@@ -155,8 +155,10 @@ sg_status sg_minplus_square(const sg_graph_csr *R, int32_t mode, uint32_t *d_N, 
  * cudaMalloc when they need the product -- e.g. code running under a hard per-process memory
  * cap, while a memory pool is exhausted or being torn down, or on a host thread that may not
  * take the allocator's locks.
- *  - Limit: the workspace needs about 13 n + 16 nnz + 2 KB bytes; larger graphs are rejected with
- *    SG_ERR_BUDGET and a message naming the sizes (use sg_minplus_square for them).
+ *  - Limit: the workspace needs 17 n + 16 nnz bytes plus about 1.3 KB (row kinds 1 B, two row
+ *    lists 8 B and one prefix 8 B per row; one minimum and one prefix, 16 B, per entry); larger
+ *    graphs are rejected with SG_ERR_BUDGET and a message naming the sizes (use
+ *    sg_minplus_square for them).
  *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress);
  *    make that first call before any stream capture.
  *  - Every call on a device shares the one array, and it keeps the previous call's contents

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
     const int64_t nrows = (int64_t)*nrows_p;
     for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
         const int32_t i = rows[rb];
+        if (!SG_IN_BOUNDS(i >= 0 && i < g.n, 404, i)) continue;
         const int64_t r0 = g.rp[i], r1 = g.rp[i + 1], deg = r1 - r0;
         const int32_t *col = GMEM ? g.col + r0 : s_col;
         const uint32_t *suf = GMEM ? g.suf + r0 : s_suf;
@@ -240,18 +241,28 @@ static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; 
 // Buffers reused by every round (sized for the input graph; later rounds only shrink).
 struct TrWork {
     unsigned long long *counts;  // [6]: rows per kind, then fill cursors
-    int8_t *kind;                // [n]
-    int32_t *rows;               // [n]
-    unsigned long long *gbest;   // [nnz] per-entry minima of global-memory rows
+    int8_t *kind;                // [n + 1]
+    int32_t *rows;               // [2 (n + 1)]: shared-memory rows from 0, global-memory rows from n
+    unsigned long long *gbest;   // [nnz + 1] per-entry minima of global-memory rows
     int64_t *gpre;               // [nnz + n + 1] neighbour-degree prefixes of global-memory rows
 };
 
+// Element counts of TrWork's arrays for a graph of n rows and nnz entries, in field order. Both
+// the allocating path and the fixed-workspace path size their buffers from this one table.
+struct TrWorkSizes {
+    int64_t counts, kind, rows, gbest, gpre;
+};
+static TrWorkSizes tr_work_sizes(int64_t n, int64_t nnz) {
+    return TrWorkSizes{6, n + 1, 2 * (n + 1), nnz + 1, nnz + n + 1};
+}
+
 static sg_status tr_work_alloc(TrWork *w, int64_t n, int64_t nnz, Scratch &sc) {
-    w->counts = sc.get<unsigned long long>(6);
-    w->kind = sc.get<int8_t>(n + 1);
-    w->rows = sc.get<int32_t>(2 * (n + 1));
-    w->gbest = sc.get<unsigned long long>(nnz + 1);
-    w->gpre = sc.get<int64_t>(nnz + n + 1);
+    const TrWorkSizes z = tr_work_sizes(n, nnz);
+    w->counts = sc.get<unsigned long long>(z.counts);
+    w->kind = sc.get<int8_t>(z.kind);
+    w->rows = sc.get<int32_t>(z.rows);
+    w->gbest = sc.get<unsigned long long>(z.gbest);
+    w->gpre = sc.get<int64_t>(z.gpre);
     return (w->counts && w->kind && w->rows && w->gbest && w->gpre) ? SG_OK : SG_ERR_OOM;
 }
 
@@ -516,14 +527,16 @@ extern "C" sg_status sg_minplus_square_noalloc(const sg_graph_csr *R, int32_t mo
         return SG_ERR_INVALID;
     }
     const int64_t n = R->n, nnz = R->nnz;
-    // workspace layout inside the scratch array
+    // workspace layout inside the scratch array: the error word, then TrWork's arrays with the
+    // sizes the allocating path uses
+    const sg::TrWorkSizes z = sg::tr_work_sizes(n, nnz);
     const size_t o_err = 0;
     const size_t o_cnt = sg::up256(o_err + sizeof(uint32_t));
-    const size_t o_kind = sg::up256(o_cnt + 6 * sizeof(unsigned long long));
-    const size_t o_rows = sg::up256(o_kind + (size_t)(n + 1));
-    const size_t o_best = sg::up256(o_rows + (size_t)(n + 1) * sizeof(int32_t));
-    const size_t o_pre = sg::up256(o_best + (size_t)(nnz + 1) * sizeof(unsigned long long));
-    const size_t need = o_pre + (size_t)(nnz + n + 1) * sizeof(int64_t);
+    const size_t o_kind = sg::up256(o_cnt + (size_t)z.counts * sizeof(unsigned long long));
+    const size_t o_rows = sg::up256(o_kind + (size_t)z.kind * sizeof(int8_t));
+    const size_t o_best = sg::up256(o_rows + (size_t)z.rows * sizeof(int32_t));
+    const size_t o_pre = sg::up256(o_best + (size_t)z.gbest * sizeof(unsigned long long));
+    const size_t need = o_pre + (size_t)z.gpre * sizeof(int64_t);
     if (need > (size_t)SG_NOALLOC_SCRATCH_BYTES) {
         sg::set_error("minplus_square_noalloc: a graph with n=%lld and nnz=%lld needs %zu bytes of workspace, "
                       "more than the fixed %zu-byte scratch array; use sg_minplus_square",
