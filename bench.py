@@ -3,8 +3,9 @@
 One step = the whole path over one seeded synthetic read set: build A and At from the reads
 (canonical k-mers, Bloom pass, exact count, reliable filter), C = A At over the overlap semiring,
 and the transitive reduction of the overlap graph R (Algorithm 1). The workload is the
-bacterial-scale read set (5 Mbp genome with 50 repeat copies, 30x, 10 kbp mean, 15% errors,
-k = 17, reliable range [2, 20], >= 2 shared k-mers, fuzz 1000).
+C. elegans-shaped read set (100 Mbp genome with 2% of it in repeat families, 40x, 10 kbp mean,
+15% errors, k = 17, reliable range [2, 30], >= 2 shared k-mers, fuzz 1000); the bacterial-scale
+set (5 Mbp, 30x) is timed beside it under "bacterial".
 
 value  = A A^T semiring products (sum_j nnz(At_j)^2) per second over whole steps, inputs resident
          in HBM, L2 flushed (256 MB write) between steps.
@@ -38,7 +39,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--workload", default="bacterial-5Mbp-30x")
+    p.add_argument("--workload", default="elegans-100Mbp-40x")
     p.add_argument("--scale", type=float, default=1.0,
                    help="genome length factor: a smaller case of the same workload, for profiling captures")
     p.add_argument("--no-e2e", action="store_true")
@@ -140,6 +141,9 @@ def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
         return (2.0 * k["sort_passes"] * k["candidates"] * (k["sort_key_bytes"] + k["sort_val_bytes"])
                 + 2.0 * k["a_sort_passes"] * k["nnz"] * (4 + 8))
     if kernel == "spgemm_numeric":
+        if sz.get("upper"):  # partners k > i only: half the off-diagonal products, half of C
+            return (8.0 * sz["nnzA"] + 8.0 * sz["products_half"] + (8.0 + 8.0 * sz["S"]) * sz["nnzC"] / 2
+                    + 8.0 * (sz["n"] + 1))
         return 8.0 * sz["nnzA"] + 8.0 * sz["products"] + (8.0 + 8.0 * sz["S"]) * sz["nnzC"] + 8.0 * (sz["n"] + 1)
     if kernel == "spgemm_symbolic":
         return 4.0 * sz["nnzA"] + 4.0 * sz["products"] + 8.0 * (sz["n"] + 1)
@@ -163,15 +167,22 @@ def by_family(prof: dict) -> dict:
     return {k: tuple(v) for k, v in out.items()}
 
 
-def measured_traffic(kernel: str):
+def measured_traffic(kernel: str, workload: str, launch_bytes: float | None = None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if that summary was taken
-    on the current source of the kernel (else None: the counters are stale)."""
+    on the current source of the kernel and on `workload` (else None: the counters are stale or
+    belong to another read set). A summary taken on a smaller case of the same workload states
+    its algorithmic bytes per launch; its traffic is then scaled by the ratio of this launch's
+    algorithmic bytes to those (traffic grows with the work done)."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         src = open(os.path.join(ROOT, "paper_2010_10055_gb300", "csrc", t["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != t["source_sha256_16"]:
             return None
-        return float(t["dram_bytes_per_launch"])
+        if t.get("workload") == workload:
+            return float(t["dram_bytes_per_launch"])
+        if t.get("small_case_of") == workload and launch_bytes and t.get("algorithmic_bytes_per_launch"):
+            return float(t["dram_bytes_per_launch"]) * launch_bytes / float(t["algorithmic_bytes_per_launch"])
+        return None
     except Exception:
         return None
 
@@ -232,6 +243,7 @@ def main():
     deg = np.diff(d["R"]["row_ptr"]).astype(np.int64)
     tr_products = int(deg[d["R"]["col"]].sum()) if d["R"]["col"].size else 0
     sz = dict(n=n, total=total, windows=max(total - (w.k - 1) * n, 0), nnzA=km.A.nnz, products=products,
+              products_half=int((a * (a - 1) // 2).sum()), upper=bool(sg.tunables().get("spgemm_upper", 0)),
               nnzC=C.nnz, S=w.max_seeds, nnzR=R.nnz, tr_products=tr_products, nnzS=S.nnz, rounds=it, m=km.m,
               kstats=sg.last_kmer_stats())
     del km, C, S
@@ -291,8 +303,9 @@ def main():
         ab = algorithmic_bytes(dom_name, sz)  # per step
         ms_step = ms / args.steps
         ach = (ab / (ms_step / 1e3) / 1e9) if ab else None
+        abl = (ab * args.steps / cnt) if ab else None
         roof = {"kernel": dom_name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": (ach / hbm) if ach else None, "traffic": measured_traffic(dom_name),
+                "frac": (ach / hbm) if ach else None, "traffic": measured_traffic(dom_name, w.name, abl),
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": (ab * args.steps / cnt) if ab else None,
                 "launch_ms": ms / max(cnt, 1), "launches_per_step": cnt / args.steps,
                 "share": fam_breakdown[dom_name][1] / ktot}
@@ -328,6 +341,7 @@ def main():
             "config": {"workload": w.name, "reads": n, "bases": total, "k": w.k, "reliable": [w.lo, w.hi],
                        "min_shared": w.min_shared, "max_seeds": w.max_seeds, "fuzz": w.fuzz,
                        "m": sz["m"], "nnz_A": sz["nnzA"], "products": products, "nnz_C": sz["nnzC"],
+                       "products_half": sz["products_half"], "spgemm_form": "upper" if sz["upper"] else "rows",
                        "nnz_R": sz["nnzR"], "nnz_S": sz["nnzS"], "tr_rounds": sz["rounds"],
                        "candidates": sz["kstats"]["candidates"],
                        "candidate_sort_bytes": sz["kstats"]["sort_key_bytes"] + sz["kstats"]["sort_val_bytes"],
@@ -337,16 +351,71 @@ def main():
             "e2e": e2e, "roofline": roof, "rooflines": rooflines, "kernels": kernels, "stages": stages,
             "clocks": clk,
             "gpu_launches": launches, "device_memory_peak_gb": mem_peak / 1e9, "from_seeds": from_seeds}
+    if w.name != "bacterial-5Mbp-30x" and args.scale == 1.0 and not args.no_forms:
+        try:
+            line["bacterial"] = measure_extra(sg, "bacterial-5Mbp-30x", args.steps, args.warmup, 1000 * rank)
+        except Exception as ex:
+            line["bacterial"] = {"error": str(ex)[:300]}
     if not args.no_forms:
         line["batched"] = measure_batched(sg, 512, 200e3)
         line["served"] = measure_served(sg, 400, 200.0)
     if rank == 0 and not args.no_cpu:
-        # a bounded sample: about 15 Mbp of reads (0.1 of the bacterial genome), ~5 s of oracle time
-        line["cpu_baseline"] = cpu_baseline(w, scale=min(1.0, 1.5e7 / (w.G * w.coverage)))
+        # a bounded sample: about 15 Mbp of reads (0.1 of the bacterial genome), ~5-10 s of oracle
+        # time on one thread; beside it the same oracle on every host core at once
+        cscale = min(1.0, 1.5e7 / (w.G * w.coverage))
+        line["cpu_baseline"] = cpu_baseline(w, scale=cscale)
+        try:
+            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(w, scale=cscale)
+        except Exception as ex:  # reported, not fatal: the one-thread figure stands
+            line["cpu_baseline"]["all_cores"] = {"error": str(ex)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_extra(sg, name: str, steps: int, warmup: int, seed_off: int = 0) -> dict:
+    """Another plain workload timed the same way as the headline (inputs resident, L2 flushed,
+    CUDA events per step): products/s, ms per step and TR edges/s."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    w = synth.WORKLOADS[name]
+    w = synth.Workload(**{**w.__dict__, "seed": w.seed + seed_off})
+    d = synth.make(w)
+    seq = torch.from_numpy(d["seq"]).cuda()
+    off = torch.from_numpy(d["offsets"]).cuda()
+    R = sg.DeviceGraph.from_numpy(d["R"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+        sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+        sg.transitive_reduce(R, w.fuzz)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    products = nnz_c = 0
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        km = sg.build_kmer_matrix(seq, off, w.k, w.lo, w.hi)
+        C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+        ev[i][1].record(stream)
+        S, it = sg.transitive_reduce(R, w.fuzz)
+        ev[i][2].record(stream)
+        if i == 0:
+            a = np.diff(km.At.to_numpy()["row_ptr"]).astype(np.int64)
+            products, nnz_c = int((a * a).sum()), C.nnz
+        del km, C, S
+    torch.cuda.synchronize()
+    step = [e[0].elapsed_time(e[2]) for e in ev]
+    tr = [e[1].elapsed_time(e[2]) for e in ev]
+    return {"workload": w.name, "steps": steps, "warmup": warmup, "ms_per_step": sum(step) / steps,
+            "value": products * steps / (sum(step) / 1e3), "unit": UNIT, "products": products, "nnz_C": nnz_c,
+            "nnz_R": R.nnz, "tr_edges_per_s": R.nnz * steps / (sum(tr) / 1e3),
+            "l2": "flushed between steps (256 MB write)"}
 
 
 def measure_e2e(sg, d, w, args):
@@ -501,6 +570,50 @@ def measure_from_seeds(sg, seq, off, w) -> dict:
         torch.cuda.synchronize()
     return {"min_overlap": w.min_overlap, "nnz_R": R.nnz, "nnz_S": S.nnz, "tr_rounds": it,
             "graph_ms": ev[0].elapsed_time(ev[1]), "tr_ms": ev[1].elapsed_time(ev[2])}
+
+
+def _oracle_worker(wdict, scale, seed_off, barrier, out):
+    """One host process of the all-cores oracle timing: draws its own sample of the workload
+    (seed offset per process), waits for the others, then times the three oracle operations."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    w = synth.Workload(**{**wdict, "seed": wdict["seed"] + 7919 * seed_off})
+    ws = w.scaled(scale)
+    d = synth.make(ws)
+    oracle.build()
+    barrier.wait()
+    t0 = time.perf_counter()
+    km = oracle.build_kmer_matrix(d["seq"], d["offsets"], ws.k, ws.lo, ws.hi)
+    oracle.overlap_spgemm(km["A"], km["At"], ws.min_shared, ws.max_seeds)
+    oracle.transitive_reduce(d["R"], ws.fuzz)
+    t1 = time.perf_counter()
+    a = np.diff(km["At"]["row_ptr"]).astype(np.int64)
+    out.put((int((a * a).sum()), t0, t1))
+
+
+def cpu_baseline_all_cores(w, scale: float, procs: int | None = None) -> dict:
+    """The oracle as it stands, one independent sample per host core, all running at once
+    (spawned processes, so no GPU state is inherited): products of all samples / the wall time
+    from the common start to the last finish."""
+    import multiprocessing as mp
+
+    procs = procs or len(os.sched_getaffinity(0))
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(dict(w.__dict__), scale, r, barrier, out)) for r in range(procs)]
+    for p in ps:
+        p.start()
+    res = [out.get(timeout=900) for _ in ps]
+    for p in ps:
+        p.join()
+    prod = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": prod / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} independent samples of {w.name} at {scale:.3g} of the genome, one process per "
+                      f"core, {wall:.1f} s wall for build_kmer_matrix + overlap_spgemm + transitive_reduce"}
 
 
 def cpu_baseline(w, scale: float):

@@ -47,10 +47,13 @@ def _time_ms(step, reps: int) -> float:
     return statistics.median(ts)
 
 
-def autotune(step, space: dict | None = None, reps: int = 3, rounds: int = 1, log=None) -> dict:
-    """Tunes in place and returns {"params": chosen values, "ms": best step time, "trials": n}."""
+def autotune(step, space: dict | None = None, reps: int = 3, rounds: int = 1, log=None, timer=None) -> dict:
+    """Tunes in place and returns {"params": chosen values, "ms": best step time, "trials": n}.
+    timer(step, reps) -> ms times one setting (default: CUDA events around `step`, median of reps
+    after a warm-up call)."""
     space = space or SPACE
-    best = _time_ms(step, reps)
+    _time = timer or _time_ms
+    best = _time(step, reps)
     trials = 1
     for _ in range(rounds):
         for name, cands in space.items():
@@ -60,7 +63,7 @@ def autotune(step, space: dict | None = None, reps: int = 3, rounds: int = 1, lo
                 if v == cur:
                     continue
                 sg.tune(name, v)
-                ms = _time_ms(step, reps)
+                ms = _time(step, reps)
                 trials += 1
                 if log:
                     log(f"{name}={v}: {ms:.3f} ms")
@@ -71,31 +74,47 @@ def autotune(step, space: dict | None = None, reps: int = 3, rounds: int = 1, lo
     return {"params": sg.tunables(), "ms": best, "trials": trials}
 
 
-def cache_key(signature: str) -> str:
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
+
+
+def device_id() -> str:
+    """GPU name and multiprocessor count of the current device (part of every cache key)."""
     import torch
     p = torch.cuda.get_device_properties(torch.cuda.current_device())
-    return f"{p.name}|{p.multi_processor_count}|{signature}"
+    return f"{p.name}|{p.multi_processor_count}"
 
 
-def load(path: str, signature: str) -> bool:
-    """Applies cached values for this GPU and workload signature; returns whether any were found."""
+def cache_key(signature: str, device: str | None = None) -> str:
+    return f"{device or device_id()}|{signature}"
+
+
+def load(path: str, signature: str, device: str | None = None) -> bool:
+    """Applies cached values for this GPU and workload signature; returns whether any were found.
+    Values of tunables this library does not know, or out of their range, are skipped."""
     try:
-        entry = json.load(open(path)).get(cache_key(signature))
+        entry = json.load(open(path)).get(cache_key(signature, device))
     except (OSError, ValueError):
         return False
     if not entry:
         return False
+    known = sg.tunables()
+    applied = False
     for k, v in entry["params"].items():
-        sg.tune(k, v)
-    return True
+        if k in known:
+            try:
+                sg.tune(k, v)
+                applied = True
+            except ValueError:
+                pass
+    return applied
 
 
-def store(path: str, signature: str, result: dict) -> None:
+def store(path: str, signature: str, result: dict, device: str | None = None) -> None:
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
         data = {}
-    data[cache_key(signature)] = result
+    data[cache_key(signature, device)] = result
     os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
     with open(path, "w") as f:
         json.dump(data, f, indent=1)
