@@ -136,6 +136,32 @@ sg_status sg_overlap_spgemm(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t 
                             int32_t max_seeds, sg_overlap_csr *C, sg_stream_t stream);
 
 /*
+ * Receives one tile of C from sg_overlap_spgemm_tiled: rows row_begin .. row_begin + tile->n of C
+ * as a CSR of tile->n rows (row_ptr from 0; columns are read ids 0 .. n - 1; seeds slot-major with
+ * stride tile->nnz). The arrays are device memory owned by the library, complete when the
+ * callback runs and freed when it returns (copy what you keep). Any status other than SG_OK
+ * stops the call, which returns that status.
+ */
+typedef sg_status (*sg_overlap_tile_fn)(const sg_overlap_csr *tile, int64_t row_begin, void *user);
+
+/*
+ * C = A At as sg_overlap_spgemm, formed in row tiles under a device-memory budget (the paper's
+ * closing remark, Sec. VIII: forming C partially, under a memory bound, instead of all at once).
+ * Rows of C are independent; each tile is a range of consecutive rows, sized so that what the
+ * call holds at once -- the tile's intermediates, one global-memory hash table for its largest
+ * row, and the tile of C -- stays within budget_bytes (on top of A and At, which the caller
+ * holds). Tiles are handed to fn in row order, one at a time, on the calling thread; the
+ * concatenated tiles equal sg_overlap_spgemm's C bit for bit.
+ *   budget_bytes  device bytes the call may hold at once (> 0).
+ *   n_tiles       out (may be NULL): tiles delivered.
+ * Errors: as sg_overlap_spgemm; SG_ERR_BUDGET when one row alone does not fit the budget (no tile
+ * delivered); the callback's own status if it stops the call.
+ */
+sg_status sg_overlap_spgemm_tiled(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared,
+                                  int32_t max_seeds, size_t budget_bytes, sg_overlap_tile_fn fn, void *user,
+                                  int64_t *n_tiles, sg_stream_t stream);
+
+/*
  * N = R^2 over the MinPlus semiring of Algorithm 3 (add = min, multiply = R_ij + R_jk when the
  * walk i->j->k is valid, i.e. the two heads at j point opposite ways, Sec. II and IV-E),
  * evaluated on the pattern of R only (Algorithm 1 compares M and N only where both exist).
@@ -402,6 +428,16 @@ void sg_debug_stall_lookback(int on);
 /* Checked builds (compiled with -DSG_CHECKED): the first out-of-bounds index any kernel detected
  * and skipped since the last call, as site << 40 | index, or 0. Always 0 in normal builds. */
 uint64_t sg_debug_check(void);
+
+/* Test hook: while on, each fused overlap product (sg_overlap_spgemm) on the calling thread
+ * records which numeric launch handled each row of C, for parity tests that sample rows per
+ * launch. sg_debug_spgemm_classes copies the last record (n entries) to host memory and returns
+ * the number of rows recorded, or -1 if there is none (off, or the two-pass form ran). Codes:
+ * log2 of the shared-memory table size (6..14), 16 + log2 for a filtered table, 32 for a row sent
+ * straight to a global-memory table, 33 for a filtered one, plus 64 when a guessed table overflowed
+ * and the row was redone in global memory; -1 for a row with no products. */
+void sg_debug_record_classes(int on);
+int64_t sg_debug_spgemm_classes(int32_t *host_out, int64_t n);
 
 /* Sizes of the calling thread's last k-mer matrix build (sg_build_kmer_matrix or a batch), for
  * profiling: windows = sequence positions, candidates = windows that passed the Bloom filters and

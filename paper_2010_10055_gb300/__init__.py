@@ -24,13 +24,14 @@ DIRMATCH, LITERAL = 0, 1
 PER_END = 2  # mode flag: per-read-end row maxima in the reduction (or-ed with the semiring)
 INF = 0xFFFFFFFF
 
-EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_minplus_square", "sg_transitive_reduce",
+EXPORTS = ("sg_build_kmer_matrix", "sg_overlap_spgemm", "sg_overlap_spgemm_tiled", "sg_minplus_square", "sg_transitive_reduce",
            "sg_transitive_reduce_rounds", "sg_overlap_graph_from_seeds",
            "sg_pipeline_host", "sg_host_arena_create", "sg_host_arena_destroy", "sg_run_batch", "sg_free_batch",
            "sg_server_create", "sg_server_submit", "sg_server_poll", "sg_server_wait", "sg_job_result_free",
            "sg_server_destroy", "sg_server_cancel",
            "sg_free_csr_u32", "sg_free_overlap", "sg_free_graph", "sg_free", "sg_last_error",
-           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_stall_lookback", "sg_debug_check", "sg_last_kmer_stats", "sg_launch_count", "sg_memory_stats", "sg_memory_reset_peak", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
+           "sg_set_allocator", "sg_debug_fail_alloc_after", "sg_debug_stall_lookback", "sg_debug_check",
+           "sg_debug_record_classes", "sg_debug_spgemm_classes", "sg_last_kmer_stats", "sg_launch_count", "sg_memory_stats", "sg_memory_reset_peak", "sg_prof_enable", "sg_prof_select", "sg_tune_set", "sg_tune_get", "sg_tune_name",
            "sg_prof_reset", "sg_prof_collect", "sg_prof_entry")
 
 
@@ -153,6 +154,9 @@ def lib():
         L.sg_overlap_spgemm.restype = ctypes.c_int
         L.sg_overlap_spgemm.argtypes = [ctypes.POINTER(CsrU32), ctypes.POINTER(CsrU32), u32, i32,
                                         ctypes.POINTER(OverlapCsr), vp]
+        L.sg_overlap_spgemm_tiled.restype = ctypes.c_int
+        L.sg_overlap_spgemm_tiled.argtypes = [ctypes.POINTER(CsrU32), ctypes.POINTER(CsrU32), u32, i32,
+                                              ctypes.c_size_t, TILE_FN, vp, ctypes.POINTER(i64), vp]
         L.sg_minplus_square.restype = ctypes.c_int
         L.sg_minplus_square.argtypes = [ctypes.POINTER(GraphCsr), i32, vp, vp, vp]
         L.sg_transitive_reduce.restype = ctypes.c_int
@@ -391,6 +395,58 @@ def build_kmer_matrix(seq, offsets, k: int = 17, lo: int = 2, hi: int = 8, strea
     return KmerMatrix(a, at, codes.value, int(A.n_cols), st)
 
 
+TILE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(OverlapCsr), ctypes.c_int64, ctypes.c_void_p)
+
+
+def overlap_spgemm_tiled(km: KmerMatrix, budget_bytes: int, min_shared: int = 2, max_seeds: int = 2,
+                         stream=None, on_tile=None):
+    """C = A At formed in row tiles under a device-memory budget (see sg_overlap_spgemm_tiled).
+    Each tile is copied to the host as it arrives; on_tile(row_begin, tile_dict) is called with it
+    if given. Returns (C on the host, as Overlap.to_numpy() gives it, and the number of tiles)."""
+    L = lib()
+    st = _stream(stream)
+    parts = []
+    failure = []
+
+    def cb(tile_p, row_begin, _user):
+        try:
+            t = tile_p.contents
+            S, nnz = int(t.max_seeds), int(t.nnz)
+            d = dict(row_ptr=_host(_view(t.row_ptr, t.n + 1, "i8", None), "i8"),
+                     col=_host(_view(t.col, nnz, "i4", None), "i4"),
+                     count=_host(_view(t.count, nnz, "u4", None), "u4"),
+                     seed_i=_host(_view(t.seed_i, S * nnz, "u4", None), "u4").reshape(S, nnz),
+                     seed_k=_host(_view(t.seed_k, S * nnz, "u4", None), "u4").reshape(S, nnz))
+            parts.append((int(row_begin), d))
+            if on_tile is not None:
+                on_tile(int(row_begin), d)
+            return SG_OK
+        except Exception as ex:  # reported after the call; the library stops at a non-OK status
+            failure.append(ex)
+            return SG_ERR_INVALID
+
+    fn = TILE_FN(cb)
+    nt = ctypes.c_int64(0)
+    rc = L.sg_overlap_spgemm_tiled(ctypes.byref(km.A.s), ctypes.byref(km.At.s), int(min_shared), int(max_seeds),
+                                   int(budget_bytes), fn, None, ctypes.byref(nt), st)
+    if failure:
+        raise failure[0]
+    _check(rc, "overlap_spgemm_tiled")
+    n = km.A.shape[0]
+    S = int(max_seeds)
+    rp = [np.zeros(1, np.int64)]
+    off = 0
+    for _, d in parts:
+        rp.append(d["row_ptr"][1:] + off)
+        off += int(d["row_ptr"][-1])
+    out = dict(n=n, row_ptr=np.concatenate(rp) if parts else np.zeros(n + 1, np.int64),
+               col=np.concatenate([d["col"] for _, d in parts]) if parts else np.zeros(0, np.int32),
+               count=np.concatenate([d["count"] for _, d in parts]) if parts else np.zeros(0, np.uint32),
+               seed_i=np.concatenate([d["seed_i"] for _, d in parts], axis=1) if parts else np.zeros((S, 0), np.uint32),
+               seed_k=np.concatenate([d["seed_k"] for _, d in parts], axis=1) if parts else np.zeros((S, 0), np.uint32))
+    return out, int(nt.value)
+
+
 def overlap_spgemm(km: KmerMatrix, min_shared: int = 2, max_seeds: int = 2, stream=None) -> Overlap:
     """C = A At over the overlap semiring (see sg_overlap_spgemm)."""
     L = lib()
@@ -544,6 +600,21 @@ def debug_check():
     since the last call, or None."""
     v = int(lib().sg_debug_check())
     return None if v == 0 else (v >> 40, v & ((1 << 40) - 1))
+
+
+def debug_record_classes(on: bool):
+    """Test hook: record which numeric launch handles each row of C (see sg_debug_record_classes)."""
+    lib().sg_debug_record_classes(1 if on else 0)
+
+
+def debug_spgemm_classes(n: int):
+    """Per-row launch codes of the last fused overlap product on this thread, or None."""
+    L = lib()
+    L.sg_debug_spgemm_classes.restype = ctypes.c_int64
+    L.sg_debug_spgemm_classes.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    out = np.zeros(max(int(n), 1), np.int32)
+    got = int(L.sg_debug_spgemm_classes(out.ctypes.data, int(n)))
+    return None if got < 0 else out[:min(got, int(n))]
 
 
 def debug_stall_lookback(on: bool):

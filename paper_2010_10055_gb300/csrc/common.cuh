@@ -82,6 +82,11 @@ size_t device_bytes_available();
 // The calling thread's last k-mer build sizes (sg_last_kmer_stats).
 sg_kmer_stats &kmer_stats();
 
+// Test hook (sg_debug_record_classes): whether to record, and the calling thread's record of,
+// the numeric launch that handled each row of the last fused overlap product.
+bool debug_record_classes();
+std::vector<int32_t> &debug_classes();
+
 // Current value of a tunable parameter (see sg_tune_set).
 int64_t tune(const char *name);
 

@@ -19,9 +19,18 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
                      uint32_t hi, sg_csr_u32 *A, sg_csr_u32 *At, uint64_t **codes_out, cudaStream_t s,
                      Scratch &sc, JobMap jm, const uint32_t *lohi, unsigned long long *job_ncols, uint32_t hmax);
 
+// Options of the overlap product. A row range of a larger A (memory-bounded tiles): A holds rows
+// row0 .. row0 + A->n_rows of the full matrix with its row pointers rebased to 0, partners are
+// all At->n_cols reads, and C's rows are the range's (columns stay read ids).
+struct OverlapOpts {
+    int64_t row0 = 0;
+    bool whole_rows = false;  // fused pass on whole rows, no mirror, never the two-pass form
+    size_t gmem_bytes = 0;    // > 0: cap on the global-memory table pool of the redo pass
+};
+
 // C = A At over the overlap semiring (spgemm.cu).
 sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S, sg_overlap_csr *C,
-                       cudaStream_t s, Scratch &sc);
+                       cudaStream_t s, Scratch &sc, const OverlapOpts &opt = OverlapOpts{});
 
 // Transitive reduction (tr.cu). With job_ro (device, njobs + 1 read offsets), job_last (device,
 // njobs, zeroed) receives for each job the last round that removed one of its entries.

@@ -286,6 +286,9 @@ static Tunable g_tunables[] = {
     {"kmer_sort_buckets", 3, 0, 3},       // at most this many top code bits become candidate buckets
     {"bloom_bin_room_pct", 112, 1, 1000}, // a bin's hash buffer, % of the mean (overflow: sliced)
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
+    {"spgemm_upper", 1, 0, 1},            // 1: the fused pass tabulates partners k > i only and
+                                          // mirrors them (C is symmetric); 0: whole rows
+    {"spgemm_lower_smem", 4096, 1, 4096}, // mirrored parts up to this long are ordered in shared memory
     {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)
     {"spgemm_sample_min_nnz", (int64_t)1 << 26, 0, (int64_t)1 << 50},  // ... when nnz(A) is at least this
     {"spgemm_guess_pct", 300, 25, 10000}, // guess = pct / 100 x sampled partners per product x products
@@ -313,6 +316,17 @@ int64_t tune(const char *name) {
     return 0;
 }
 
+}  // namespace sg
+
+namespace sg {
+static thread_local bool t_record_classes = false;
+static thread_local std::vector<int32_t> t_classes;
+static thread_local bool t_classes_valid = false;
+bool debug_record_classes() { return t_record_classes; }
+std::vector<int32_t> &debug_classes() {
+    t_classes_valid = true;
+    return t_classes;
+}
 }  // namespace sg
 
 extern "C" {
@@ -346,6 +360,19 @@ void sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx) {
 void sg_debug_fail_alloc_after(int64_t n) { sg::g_fail_after.store(n > 0 ? n : 0); }
 
 void sg_debug_stall_lookback(int on) { sg::g_debug_stall.store(on ? 1 : 0); }
+
+void sg_debug_record_classes(int on) {
+    sg::t_record_classes = on != 0;
+    sg::t_classes_valid = false;
+    sg::t_classes.clear();
+}
+
+int64_t sg_debug_spgemm_classes(int32_t *host_out, int64_t n) {
+    if (!sg::t_classes_valid) return -1;
+    const int64_t m = std::min<int64_t>(n, (int64_t)sg::t_classes.size());
+    if (host_out && m > 0) memcpy(host_out, sg::t_classes.data(), (size_t)m * sizeof(int32_t));
+    return (int64_t)sg::t_classes.size();
+}
 
 void sg_free(void *d_ptr, sg_stream_t stream) { sg::dfree(d_ptr, (cudaStream_t)stream); }
 

@@ -30,8 +30,10 @@
 // Products of a row are enumerated warp by warp: a warp takes 32 consecutive entries of A's row,
 // scans their At row lengths in registers, and walks the flattened product list 32 at a time,
 // each lane finding its entry with a 5-step shuffle search.
+#include <algorithm>
 #include <mutex>
 #include <optional>
+#include <vector>
 
 #include "check.cuh"
 #include "ops.cuh"
@@ -63,10 +65,12 @@ struct SpArgs {
     const int64_t *a_beg;     // per A entry (i, j): start of At row j
     const uint32_t *a_len;    // per A entry: length of At row j
     const uint64_t *t_pair;   // At entries as (val << 32 | col): one sector per product
-    int64_t n;
+    int64_t n;      // rows of A handled by this call
     uint32_t min_shared;
     int S;
     uint32_t *err;  // DEV_OVERFLOW if the numeric pass ever disagrees with the symbolic sizes
+    int64_t np;     // partners: columns of At (all reads); n = np unless A is a row range of a larger A
+    int64_t row0;   // read id of row 0 of A (nonzero only for a row range), for the diagonal
 };
 
 // One warp per row: w_i, and for every entry (i, j) the start and length of At row j, so that
@@ -111,12 +115,13 @@ __global__ void classify_kernel(const int64_t *__restrict__ need, int64_t n, Cla
 }
 
 // symbolic table request: nextpow2(max(64, w >> shift)), capped at the exact bound 2 * min(w, n - 1)
-__global__ void sym_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, int64_t *__restrict__ need) {
+__global__ void sym_need_kernel(const int64_t *__restrict__ work, int64_t n, int64_t np, int shift,
+                                int64_t *__restrict__ need) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t w = work[i];
     if (w <= 0) { need[i] = 0; return; }
-    int64_t exact = pow2_at_least(2 * (w < n - 1 ? w : n - 1));
+    int64_t exact = pow2_at_least(2 * (w < np - 1 ? w : np - 1));
     int64_t guess = pow2_at_least((w >> shift) > 64 ? (w >> shift) : 64);
     need[i] = guess < exact ? guess : exact;
 }
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(512) symbolic_kernel(SpArgs g, const int32_t *
         int32_t *keys = sym_tab;
         if (GSLICE) {
             const int64_t w = work[i];
-            const int64_t T = pow2_at_least(2 * (w < g.n - 1 ? w : g.n - 1));
+            const int64_t T = pow2_at_least(2 * (w < g.np - 1 ? w : g.np - 1));
             lT = 0;
             while (((int64_t)1 << lT) < T) lT++;
             keys = gpool + (int64_t)blockIdx.x * slice;
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(512) symbolic_kernel(SpArgs g, const int32_t *
         }
         __syncthreads();
         const uint32_t msk = (uint32_t)T - 1u;
-        for_each_product<false>(g, i, g.a_rp[i], g.a_rp[i + 1], GSLICE ? nullptr : &s_ovf,
+        for_each_product<false>(g, (int32_t)(g.row0 + i), g.a_rp[i], g.a_rp[i + 1], GSLICE ? nullptr : &s_ovf,
                                 [&](int32_t k, uint32_t, int64_t) {
             uint32_t h = hash_slot(k, lT);
             for (int probe = 0; probe < T; probe++) {
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(1024) numeric_kernel(SpArgs g, const int32_t *
             int64_t T;
             if (FUSED) {
                 const int64_t w = work[i];
-                T = pow2_at_least(2 * (w < g.n - 1 ? w : g.n - 1));
+                T = pow2_at_least(2 * (w < g.np - 1 ? w : g.np - 1));
             } else {
                 T = need[i];
             }
@@ -378,12 +383,12 @@ __global__ void __launch_bounds__(1024) numeric_kernel(SpArgs g, const int32_t *
         __syncthreads();
         const int64_t r0 = g.a_rp[i], r1 = g.a_rp[i + 1];
         const uint32_t msk = (uint32_t)T - 1u;
-        const bool fid = g.n <= ((int64_t)1 << log2F);
+        const bool fid = g.np <= ((int64_t)1 << log2F);
         auto fbit = [&](int32_t k) -> uint32_t {
             return fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
         };
         if (FILT) {  // seen once -> F1, seen again -> F2 (bits are only ever set)
-            for_each_product<false>(g, i, r0, r1, nullptr, [&](int32_t k, uint32_t, int64_t) {
+            for_each_product<false>(g, (int32_t)(g.row0 + i), r0, r1, nullptr, [&](int32_t k, uint32_t, int64_t) {
                 const uint32_t b = fbit(k), m = 1u << (b & 31u);
                 if (((volatile uint32_t *)F2)[b >> 5] & m) return;
                 if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(1024) numeric_kernel(SpArgs g, const int32_t *
             __syncthreads();
         }
         const int cap = (T >> 1) + (T >> 2);  // guessed tables: at most 3/4 T partners
-        for_each_product<false>(g, i, r0, r1, guessed ? &s_ovf : nullptr, [&](int32_t k, uint32_t, int64_t idx) {
+        for_each_product<false>(g, (int32_t)(g.row0 + i), r0, r1, guessed ? &s_ovf : nullptr, [&](int32_t k, uint32_t, int64_t idx) {
             if (guessed && *(volatile int *)&s_ovf) return;  // the row is abandoned
             if (FILT) {  // seen once only: count 1 < min_shared
                 const uint32_t b = fbit(k);
@@ -501,6 +506,494 @@ __global__ void __launch_bounds__(1024) numeric_kernel(SpArgs g, const int32_t *
     }
 }
 
+// ------------------------------------------------------------------ upper-triangle numeric pass
+// C is symmetric (the shared set of (i, k) is that of (k, i); C_ki's seeds are C_ik's with the two
+// positions swapped and the same rc bit), so the fused path tabulates only partners k > i: for an
+// entry (i, j) of A these are the entries of At row j after read i (At rows are sorted by read),
+// which row_work_upper_kernel locates once. That halves the products and the table work; C is
+// then assembled from the upper triangle U by writing each U row in place and its mirror into the
+// lower part of the partner's row (mirror_c_kernel), whose entries are put in column order by a
+// sort per row (sort_lower_kernel).
+//
+// Table slot (64 bits): partner << 32 | count; empty = ~0. A product whose partner is present
+// costs one 64-bit atomicAdd on the slot; a new partner claims an empty slot and counts itself
+// with one atomicCAS. Seeds, by max_seeds: 1 -> one u32 slot kept by atomicMin; 2 -> one u64 word
+// (smallest << 32 | second smallest) replaced by atomicCAS only while the new index is smaller
+// than the second (later indices, the common case, cost one load); more -> the atomicMin chain.
+
+// One warp per row: w_i = products of row i with partners k > i, and for every entry (i, j) the
+// start (one past read i) and length of the tail of At row j.
+__global__ void row_work_upper_kernel(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
+                                      const int64_t *__restrict__ t_rp, const int32_t *__restrict__ t_col,
+                                      int64_t n, int64_t row0, int64_t *__restrict__ work,
+                                      int64_t *__restrict__ a_beg, uint32_t *__restrict__ a_len) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    int64_t w = 0;
+    for (int64_t a = a_rp[row] + lane; a < a_rp[row + 1]; a += 32) {
+        const int32_t j = a_col[a];
+        int64_t lo = t_rp[j], hi = t_rp[j + 1];
+        const int64_t e = hi;
+        while (lo < hi) {  // first entry of At row j with read > this row's read
+            const int64_t mid = (lo + hi) >> 1;
+            if (t_col[mid] <= (int32_t)(row0 + row)) lo = mid + 1; else hi = mid;
+        }
+        a_beg[a] = lo;
+        a_len[a] = (uint32_t)(e - lo);
+        w += e - lo;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) work[row] = w;
+}
+
+// Calls f(k, idx) for every product of row i (k = partner, idx = index of the A entry within the
+// row), skipping k == i. Warp-cooperative: a warp takes 32 consecutive entries of A's row, scans
+// their tail lengths (32-bit) and walks the flattened products TU_U x 32 at a time, each lane
+// finding its entry by a 5-step shuffle search; the gathers of the next step are issued before the
+// current step's table updates. Stops (per warp, at a chunk boundary) once *stop is nonzero.
+constexpr int TU_U = 2;
+
+template <class F>
+__device__ __forceinline__ void enum_products(const SpArgs &g, int32_t i, int64_t r0, int64_t r1,
+                                              const volatile int *stop, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t a0 = r0 + (int64_t)warp * 32; a0 < r1; a0 += (int64_t)nwarps * 32) {
+        if (stop && __any_sync(0xffffffffu, *stop != 0)) return;
+        const int64_t a = a0 + lane;
+        int64_t beg = 0;
+        uint32_t len = 0;
+        if (a < r1) {
+            beg = g.a_beg[a];
+            len = g.a_len[a];
+        }
+        uint32_t inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t excl = inc - len;
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        if (total == 0) continue;
+        int32_t kk[TU_U];
+        uint32_t ix[TU_U];
+        // step s covers products [s * 32 TU_U, (s + 1) * 32 TU_U)
+        auto gather = [&](uint32_t base) {
+#pragma unroll
+            for (int u = 0; u < TU_U; u++) {
+                const uint32_t p = base + u * 32 + lane;
+                int ow = 0;  // largest lane whose exclusive prefix is <= p
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const uint32_t v = __shfl_sync(0xffffffffu, excl, (ow + s) & 31);
+                    if (ow + s < 32 && v <= p) ow += s;
+                }
+                const int64_t ob = __shfl_sync(0xffffffffu, beg, ow);
+                const uint32_t oe = __shfl_sync(0xffffffffu, excl, ow);
+                ix[u] = (uint32_t)(a0 - r0) + (uint32_t)ow;
+                kk[u] = p < total ? g.t_col[ob + (p - oe)] : i;
+            }
+        };
+        gather(0);
+        for (uint32_t base = 0; base < total; base += 32 * TU_U) {
+            int32_t k_cur[TU_U];
+            uint32_t i_cur[TU_U];
+#pragma unroll
+            for (int u = 0; u < TU_U; u++) {
+                k_cur[u] = kk[u];
+                i_cur[u] = ix[u];
+            }
+            if (base + 32 * TU_U < total) gather(base + 32 * TU_U);
+#pragma unroll
+            for (int u = 0; u < TU_U; u++)
+                if (k_cur[u] != i) f(k_cur[u], i_cur[u]);
+        }
+    }
+}
+
+constexpr uint64_t SLOT_EMPTY = ~0ull;
+
+// At value of partner k in At row [b, b + len) (ascending reads), from the col and val arrays.
+__device__ __forceinline__ uint32_t at_value_cv(const int32_t *__restrict__ t_col, const uint32_t *__restrict__ t_val,
+                                                int64_t b, int64_t len, int32_t k) {
+    int64_t lo = b, hi = b + len;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (t_col[mid] <= k) lo = mid; else hi = mid;
+    }
+    return t_val[lo];
+}
+
+// Bytes of one table of T slots with S seeds: slots u64[T] | seeds | sort buffer u64[T / 2].
+__host__ __device__ inline size_t tab_seed_bytes(int64_t T, int S) {
+    return S == 0 ? 0 : (S == 2 ? (size_t)T * 8 : (size_t)T * 4 * (size_t)S);
+}
+__host__ __device__ inline size_t tab_bytes(int64_t T, int S) {
+    return (size_t)T * 8 + tab_seed_bytes(T, S) + (size_t)(T / 2) * 8;
+}
+
+// Numeric pass over the fused path's guessed tables (GSLICE == false: shared memory, a table
+// filling past 3/4, or a row keeping more than T / 2 partners, ends the row, which is appended to
+// ovf_list) or exact-bound tables in this block's global slice (GSLICE == true: 2 min(w_i, n - 1)
+// slots, never overflows). A finished row is written to the temporary arrays at c_rp[i] and its
+// length to nnz_row[i]; with colcnt, every kept partner k also counts one entry in colcnt[k] (the
+// mirrored entries of the upper-triangle form). SK: 0, 1, 2 seeds as above; 3 = the chain.
+// FILT: as in numeric_kernel (seen-once / seen-twice filters before the table).
+template <bool GSLICE, int SK, bool FILT>
+__global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
+                                                         const unsigned long long *__restrict__ nrows_p, int log2T,
+                                                         int log2F, unsigned char *__restrict__ gpool,
+                                                         int64_t slice_bytes, const int64_t *__restrict__ c_rp,
+                                                         int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
+                                                         uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
+                                                         int64_t c_nnz, const int64_t *__restrict__ work,
+                                                         int32_t *__restrict__ ovf_list,
+                                                         unsigned long long *__restrict__ ovf_count,
+                                                         int64_t *__restrict__ nnz_row, uint32_t *__restrict__ colcnt) {
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    __shared__ int s_ctr, s_ins, s_ovf, s_full;
+    const int S = g.S;
+    const int64_t nrows = (int64_t)*nrows_p;
+    for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
+        const int32_t i = rows[rb];
+        if (!SG_IN_BOUNDS(i >= 0 && i < g.n, 308, i)) continue;
+        int lT = log2T;
+        unsigned char *tb = FILT ? tab_raw + ((size_t)2 << log2F) / 8 : tab_raw;
+        uint32_t *F1 = (uint32_t *)tab_raw, *F2 = F1 + ((1 << log2F) >> 5);
+        if (GSLICE) {
+            const int64_t w = work[i];
+            const int64_t T = pow2_at_least(2 * (w < g.np - 1 ? w : g.np - 1));
+            lT = 0;
+            while (lT < 31 && ((int64_t)1 << lT) < T) lT++;
+            if (!SG_IN_BOUNDS(tab_bytes((int64_t)1 << lT, S) <= (size_t)slice_bytes, 309, T)) continue;
+            tb = gpool + (int64_t)blockIdx.x * slice_bytes;
+        }
+        const int32_t T = 1 << lT;
+        const int ob_cap = T >> 1;
+        uint64_t *slot = (uint64_t *)tb;
+        unsigned char *sd = tb + (size_t)T * 8;
+        uint64_t *seed2 = (uint64_t *)sd;
+        uint32_t *seed1 = (uint32_t *)sd;
+        uint64_t *obuf = (uint64_t *)(sd + tab_seed_bytes(T, S));
+        for (int x = threadIdx.x; x < T; x += blockDim.x) slot[x] = SLOT_EMPTY;
+        if (SK == 2)
+            for (int x = threadIdx.x; x < T; x += blockDim.x) seed2[x] = ~0ull;
+        else if (SK != 0)
+            for (int x = threadIdx.x; x < T * S; x += blockDim.x) seed1[x] = SEED_NONE;
+        if (FILT)
+            for (int x = threadIdx.x; x < (2 << log2F) >> 5; x += blockDim.x) F1[x] = 0u;
+        if (threadIdx.x == 0) {
+            s_ctr = 0;
+            s_ins = 0;
+            s_ovf = 0;
+            s_full = 0;
+        }
+        __syncthreads();
+        const int64_t r0 = g.a_rp[i], r1 = g.a_rp[i + 1];
+        const uint32_t msk = (uint32_t)T - 1u;
+        const bool fid = g.np <= ((int64_t)1 << log2F);
+        auto fbit = [&](int32_t k) -> uint32_t {
+            return fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
+        };
+        if (FILT) {
+            enum_products(g, (int32_t)(g.row0 + i), r0, r1, nullptr, [&](int32_t k, uint32_t) {
+                const uint32_t b = fbit(k), m = 1u << (b & 31u);
+                if (((volatile uint32_t *)F2)[b >> 5] & m) return;
+                if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
+            });
+            __syncthreads();
+        }
+        const int cap = (T >> 1) + (T >> 2);
+        enum_products(g, (int32_t)(g.row0 + i), r0, r1, GSLICE ? nullptr : &s_ovf, [&](int32_t k, uint32_t idx) {
+            if (!GSLICE && *(volatile int *)&s_ovf) return;
+            if (FILT) {
+                const uint32_t b = fbit(k);
+                if (!((F2[b >> 5] >> (b & 31u)) & 1u)) return;
+            }
+            uint32_t h = hash_slot(k, lT);
+            int probe = 0;
+            for (;;) {
+                uint64_t v = ((volatile uint64_t *)slot)[h];
+                if (v == SLOT_EMPTY) {
+                    v = atomicCAS((unsigned long long *)(slot + h), SLOT_EMPTY, ((uint64_t)(uint32_t)k << 32) | 1ull);
+                    if (v == SLOT_EMPTY) {
+                        if (!GSLICE && atomicAdd(&s_ins, 1) >= cap) s_ovf = 1;
+                        break;
+                    }
+                }
+                if ((int32_t)(v >> 32) == k) {
+                    atomicAdd((unsigned long long *)(slot + h), 1ull);
+                    break;
+                }
+                h = (h + 1) & msk;
+                if (++probe == T) {  // went round the whole table
+                    s_ovf = 1;
+                    return;
+                }
+            }
+            if (SK == 1) {
+                atomicMin(seed1 + h, idx);
+            } else if (SK == 2) {
+                uint64_t w = ((volatile uint64_t *)seed2)[h];
+                for (;;) {
+                    const uint32_t m1 = (uint32_t)(w >> 32), m2 = (uint32_t)w;
+                    if (idx >= m2) break;  // indices of one partner are distinct
+                    const uint64_t nw = idx < m1 ? (((uint64_t)idx << 32) | m1) : (((uint64_t)m1 << 32) | idx);
+                    const uint64_t old = atomicCAS((unsigned long long *)(seed2 + h), w, nw);
+                    if (old == w) break;
+                    w = old;
+                }
+            } else if (SK == 3) {
+                uint32_t v = idx;
+                uint32_t *sl = seed1 + (int64_t)h * S;
+                for (int q = 0; q < S; q++) {
+                    const uint32_t old = atomicMin(sl + q, v);
+                    if (old > v) v = old;
+                    if (v == SEED_NONE) break;
+                }
+            }
+        });
+        __syncthreads();
+        // kept partners -> sort buffer; a guessed table may keep more than it holds (s_full), an
+        // exact one (T >= 2 x partners) never does. s_ovf is not written past the barrier above.
+        if (GSLICE || !s_ovf) {
+            for (int x = threadIdx.x; x < T; x += blockDim.x) {
+                const uint64_t v = slot[x];
+                if (v != SLOT_EMPTY && (uint32_t)v >= g.min_shared) {
+                    const int p = atomicAdd(&s_ctr, 1);
+                    if (SG_IN_BOUNDS(!GSLICE || p < ob_cap, 310, p) && p < ob_cap)
+                        obuf[p] = (v & 0xFFFFFFFF00000000ull) | (uint32_t)x;
+                    else
+                        s_full = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (!GSLICE && (s_ovf || s_full)) {  // the global-memory pass redoes the row
+            if (threadIdx.x == 0) {
+                const unsigned long long q = atomicAdd(ovf_count, 1ull);
+                if (SG_IN_BOUNDS((int64_t)q < g.n, 311, q)) ovf_list[q] = i;
+            }
+            __syncthreads();
+            continue;
+        }
+        const int nv = s_ctr < ob_cap ? s_ctr : ob_cap;
+        int P2 = 1;
+        while (P2 < nv) P2 <<= 1;
+        for (int x = nv + threadIdx.x; x < P2; x += blockDim.x) obuf[x] = ~0ull;
+        __syncthreads();
+        for (int kk = 2; kk <= P2; kk <<= 1) {
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int x = threadIdx.x; x < P2; x += blockDim.x) {
+                    const int y = x ^ jj;
+                    if (y > x) {
+                        const uint64_t a = obuf[x], b = obuf[y];
+                        const bool up = (x & kk) == 0;
+                        if ((a > b) == up) {
+                            obuf[x] = b;
+                            obuf[y] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const int64_t e0 = c_rp[i];
+        const int64_t room = c_rp[i + 1] - e0;
+        if (nv > room && threadIdx.x == 0) atomicOr(g.err, (uint32_t)DEV_OVERFLOW);
+        const int nw = nv < room ? nv : (int)room;
+        if (threadIdx.x == 0) nnz_row[i] = nw;
+        for (int q = threadIdx.x; q < nw; q += blockDim.x) {
+            const uint64_t wq = obuf[q];
+            const uint32_t x = (uint32_t)wq;
+            const int32_t k = (int32_t)(wq >> 32);
+            const int64_t e = e0 + q;
+            c_col[e] = k;
+            c_cnt[e] = (uint32_t)slot[x];
+            if (colcnt) atomicAdd(colcnt + k, 1u);
+            for (int s = 0; s < S; s++) {
+                uint32_t sdx;
+                if (SK == 2) sdx = s == 0 ? (uint32_t)(seed2[x] >> 32) : (uint32_t)seed2[x];
+                else sdx = seed1[(int64_t)x * S + s];
+                uint32_t si = SEED_NONE, sk = SEED_NONE;
+                if (sdx != SEED_NONE) {
+                    const int64_t a = r0 + sdx;
+                    const uint32_t vi = g.a_val[a];
+                    const uint32_t vk = at_value_cv(g.t_col, g.t_val, g.a_beg[a], g.a_len[a], k);
+                    si = vi & 0x7FFFFFFFu;
+                    sk = (vk & 0x7FFFFFFFu) | ((vi ^ vk) & 0x80000000u);
+                }
+                c_si[(int64_t)s * c_nnz + e] = si;
+                c_sk[(int64_t)s * c_nnz + e] = sk;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// C from the upper triangle U (rows at tmp_off, lengths nnz_row, seeds slot-major with stride
+// tmp_n). One warp per row i of U: its entries go to C row i after the lower part (colcnt[i]
+// entries), in order; each entry (i, k) also goes, mirrored (seed positions swapped, same rc bit),
+// to a free place (cursor[k], zeroed) of row k's part of the lower scratch arrays (from lrp[k]);
+// sort_lower_kernel moves those into C in column order.
+__global__ void mirror_c_kernel(const int64_t *__restrict__ tmp_off, const int64_t *__restrict__ nnz_row,
+                                int64_t tmp_n, const int32_t *__restrict__ t_col, const uint32_t *__restrict__ t_cnt,
+                                const uint32_t *__restrict__ t_si, const uint32_t *__restrict__ t_sk, int S,
+                                const uint32_t *__restrict__ colcnt, const int64_t *__restrict__ c_rp,
+                                const int64_t *__restrict__ lrp, int64_t n, int64_t nnz, int64_t nnz_l,
+                                uint32_t *__restrict__ cursor, int32_t *__restrict__ c_col,
+                                uint32_t *__restrict__ c_cnt, uint32_t *__restrict__ c_si,
+                                uint32_t *__restrict__ c_sk, int32_t *__restrict__ l_col,
+                                uint32_t *__restrict__ l_cnt, uint32_t *__restrict__ l_si,
+                                uint32_t *__restrict__ l_sk) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int64_t src = tmp_off[row], len = nnz_row[row], dst = c_rp[row] + colcnt[row];
+    for (int64_t e = lane; e < len; e += 32) {
+        const int32_t k = t_col[src + e];
+        const uint32_t cnt = t_cnt[src + e];
+        c_col[dst + e] = k;
+        c_cnt[dst + e] = cnt;
+        if (!SG_IN_BOUNDS(k > row && k < n, 312, k)) continue;
+        const uint32_t p = atomicAdd(cursor + k, 1u);
+        const int64_t m = lrp[k] + p;
+        if (!SG_IN_BOUNDS(p < colcnt[k] && m < nnz_l, 313, p)) continue;
+        l_col[m] = (int32_t)row;
+        l_cnt[m] = cnt;
+        for (int q = 0; q < S; q++) {
+            const uint32_t si = t_si[(int64_t)q * tmp_n + src + e], sk = t_sk[(int64_t)q * tmp_n + src + e];
+            c_si[(int64_t)q * nnz + dst + e] = si;
+            c_sk[(int64_t)q * nnz + dst + e] = sk;
+            const bool none = si == SEED_NONE;
+            l_si[(int64_t)q * nnz_l + m] = none ? SEED_NONE : (sk & 0x7FFFFFFFu);
+            l_sk[(int64_t)q * nnz_l + m] = none ? SEED_NONE : (si | (sk & 0x80000000u));
+        }
+    }
+}
+
+// Moves each row's lower part (colcnt[i] entries from lrp[i] in the scratch arrays, distinct
+// columns < i, in arbitrary order) into C at c_rp[i] in column order. One block per row of up to
+// lmax (<= LOWER_SMEM) entries: keys (column << 32 | offset) bitonic-sorted in shared memory, then
+// each entry copied from its offset. Longer parts are listed for lower_big_kernel.
+constexpr int LOWER_SMEM = 4096;
+constexpr int LOWER_NT = 256;
+
+__device__ __forceinline__ void lower_copy(int64_t from, int64_t to, int S, int64_t nnz, int64_t nnz_l,
+                                           const int32_t *__restrict__ l_col, const uint32_t *__restrict__ l_cnt,
+                                           const uint32_t *__restrict__ l_si, const uint32_t *__restrict__ l_sk,
+                                           int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
+                                           uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk) {
+    c_col[to] = l_col[from];
+    c_cnt[to] = l_cnt[from];
+    for (int q = 0; q < S; q++) {
+        c_si[(int64_t)q * nnz + to] = l_si[(int64_t)q * nnz_l + from];
+        c_sk[(int64_t)q * nnz + to] = l_sk[(int64_t)q * nnz_l + from];
+    }
+}
+
+template <class K>
+__device__ __forceinline__ void block_bitonic(K *key, int64_t P2) {
+    for (int64_t kk = 2; kk <= P2; kk <<= 1) {
+        for (int64_t jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int64_t x = threadIdx.x; x < P2; x += blockDim.x) {
+                const int64_t y = x ^ jj;
+                if (y > x) {
+                    const K a = key[x], c = key[y];
+                    if ((a > c) == ((x & kk) == 0)) {
+                        key[x] = c;
+                        key[y] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(LOWER_NT) sort_lower_kernel(const uint32_t *__restrict__ colcnt,
+                                                           const int64_t *__restrict__ lrp,
+                                                           const int64_t *__restrict__ c_rp, int64_t n, int64_t nnz,
+                                                           int64_t nnz_l, int S, const int32_t *__restrict__ l_col,
+                                                           const uint32_t *__restrict__ l_cnt,
+                                                           const uint32_t *__restrict__ l_si,
+                                                           const uint32_t *__restrict__ l_sk,
+                                                           int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
+                                                           uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
+                                                           unsigned long long *__restrict__ big_count,
+                                                           int32_t *__restrict__ big_rows, int lmax) {
+    __shared__ uint64_t key[LOWER_SMEM];
+    for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
+        const int64_t L = colcnt[row];
+        if (L == 0) continue;
+        const int64_t lb = lrp[row], b = c_rp[row];
+        if (L > lmax) {
+            if (threadIdx.x == 0) {
+                const unsigned long long q = atomicAdd(big_count, 1ull);
+                if (SG_IN_BOUNDS((int64_t)q < n, 314, q)) big_rows[q] = (int32_t)row;
+            }
+            continue;
+        }
+        if (L == 1) {
+            if (threadIdx.x == 0) lower_copy(lb, b, S, nnz, nnz_l, l_col, l_cnt, l_si, l_sk, c_col, c_cnt, c_si, c_sk);
+            continue;
+        }
+        int64_t P2 = 1;
+        while (P2 < L) P2 <<= 1;
+        for (int64_t x = threadIdx.x; x < P2; x += blockDim.x)
+            key[x] = x < L ? (((uint64_t)(uint32_t)l_col[lb + x] << 32) | (uint32_t)x) : ~0ull;
+        __syncthreads();
+        block_bitonic(key, P2);
+        for (int64_t x = threadIdx.x; x < L; x += blockDim.x)
+            lower_copy(lb + (uint32_t)key[x], b + x, S, nnz, nnz_l, l_col, l_cnt, l_si, l_sk, c_col, c_cnt, c_si,
+                       c_sk);
+        __syncthreads();
+    }
+}
+
+// Lower parts longer than LOWER_SMEM: one block per listed row, its keys sorted in this block's
+// slice of global scratch (P2 = the next power of two of the length, 8 bytes each).
+__global__ void __launch_bounds__(1024) lower_big_kernel(const uint32_t *__restrict__ colcnt,
+                                                       const int64_t *__restrict__ lrp,
+                                                       const int64_t *__restrict__ c_rp, int64_t nnz, int64_t nnz_l,
+                                                       int S, const int32_t *__restrict__ rows,
+                                                       const unsigned long long *__restrict__ nrows_p,
+                                                       uint64_t *__restrict__ gpool, int64_t slice,
+                                                       const int32_t *__restrict__ l_col,
+                                                       const uint32_t *__restrict__ l_cnt,
+                                                       const uint32_t *__restrict__ l_si,
+                                                       const uint32_t *__restrict__ l_sk, int32_t *__restrict__ c_col,
+                                                       uint32_t *__restrict__ c_cnt, uint32_t *__restrict__ c_si,
+                                                       uint32_t *__restrict__ c_sk) {
+    const int64_t nrows = (int64_t)*nrows_p;
+    uint64_t *key = gpool + (int64_t)blockIdx.x * slice;
+    for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
+        const int32_t row = rows[rb];
+        const int64_t L = colcnt[row], lb = lrp[row], b = c_rp[row];
+        int64_t P2 = 1;
+        while (P2 < L) P2 <<= 1;
+        if (!SG_IN_BOUNDS(P2 <= slice, 315, L)) continue;
+        for (int64_t x = threadIdx.x; x < P2; x += blockDim.x)
+            key[x] = x < L ? (((uint64_t)(uint32_t)l_col[lb + x] << 32) | (uint32_t)x) : ~0ull;
+        __syncthreads();
+        block_bitonic(key, P2);
+        for (int64_t x = threadIdx.x; x < L; x += blockDim.x)
+            lower_copy(lb + (uint32_t)key[x], b + x, S, nnz, nnz_l, l_col, l_cnt, l_si, l_sk, c_col, c_cnt, c_si,
+                       c_sk);
+        __syncthreads();
+    }
+}
+
+// nnz of C's rows in the upper-triangle form: U row i plus its mirrored entries.
+__global__ void c_rowlen_kernel(const int64_t *__restrict__ nnz_row, const uint32_t *__restrict__ colcnt, int64_t n,
+                                int64_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = nnz_row[i] + colcnt[i];
+}
+
 static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
 
 // Sampled rows (every stride-th row, one block each): the products w, and the bits set in the
@@ -517,8 +1010,8 @@ __global__ void __launch_bounds__(512) sample_kernel(SpArgs g, const int64_t *__
     for (int x = threadIdx.x; x < 2 * nw; x += blockDim.x) smp_f[x] = 0u;
     if (threadIdx.x < 2) s_c[threadIdx.x] = 0ull;
     __syncthreads();
-    const bool fid = g.n <= ((int64_t)1 << log2F);
-    for_each_product<false>(g, (int32_t)i, g.a_rp[i], g.a_rp[i + 1], nullptr, [&](int32_t k, uint32_t, int64_t) {
+    const bool fid = g.np <= ((int64_t)1 << log2F);
+    for_each_product<false>(g, (int32_t)(g.row0 + i), g.a_rp[i], g.a_rp[i + 1], nullptr, [&](int32_t k, uint32_t, int64_t) {
         const uint32_t b = fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
         const uint32_t m = 1u << (b & 31u);
         if (((volatile uint32_t *)F2)[b >> 5] & m) return;
@@ -546,8 +1039,9 @@ __global__ void __launch_bounds__(512) sample_kernel(SpArgs g, const int64_t *__
 // w >> fshift, at most fcap = the largest filtered shared-memory table) goes to need_f and need is
 // 0, else need_f is 0.
 __global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, uint64_t fu, uint32_t t,
-                                  int64_t fwork, int fshift, uint64_t ff, int64_t fcap, int64_t *__restrict__ need,
-                                  int64_t *__restrict__ need_f, int64_t *__restrict__ room) {
+                                  int64_t fwork, int fshift, uint64_t ff, int64_t fcap, int upper, int64_t np,
+                                  int64_t row0, int64_t *__restrict__ need, int64_t *__restrict__ need_f,
+                                  int64_t *__restrict__ room) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t w = work[i];
@@ -560,13 +1054,13 @@ __global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, i
     const bool filt = fwork > 0 && w >= fwork;
     const uint64_t mul = filt ? ff : fu;
     const int64_t g0 = mul ? (int64_t)(((unsigned __int128)w * mul) >> 16) : (w >> (filt ? fshift : shift));
-    const int64_t exact = pow2_at_least(2 * (w < n - 1 ? w : n - 1));
+    const int64_t exact = pow2_at_least(2 * (w < np - 1 ? w : np - 1));
     int64_t guess = pow2_at_least(g0 > 64 ? g0 : 64);
     if (filt && guess > fcap) guess = fcap;  // kept partners are few: try the largest table first
     (filt ? need_f : need)[i] = guess < exact ? guess : exact;
     if (filt) need[i] = 0;
-    const int64_t r = w / t;
-    room[i] = r < n - 1 ? r : n - 1;
+    const int64_t r = w / t, rmax = upper ? np - 1 - (row0 + i) : np - 1;  // upper: partners k > i only
+    room[i] = r < rmax ? r : rmax;
 }
 
 // Fused path: copies each row's entries from the temporary arrays (row i at tmp_off[i], seeds
@@ -618,9 +1112,21 @@ static const char *const FIL_NAMES[] = {"spgemm_numeric_f64", "spgemm_numeric_f1
                                         "spgemm_numeric_f512", "spgemm_numeric_f1k", "spgemm_numeric_f2k",
                                         "spgemm_numeric_f4k", "spgemm_numeric_f8k", "spgemm_numeric_f16k"};
 
+// Largest row work: sizes the global-memory tables of the redo pass.
+__global__ void work_max_kernel(const int64_t *__restrict__ work, int64_t n, unsigned long long *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t w = i < n ? work[i] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t y = __shfl_xor_sync(0xffffffffu, w, o);
+        w = y > w ? y : w;
+    }
+    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(out, (unsigned long long)w);
+}
+
 sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S,
-                       sg_overlap_csr *C, cudaStream_t s, Scratch &sc) {
-    const int64_t n = A->n_rows;
+                       sg_overlap_csr *C, cudaStream_t s, Scratch &sc, const OverlapOpts &opt) {
+    const int64_t n = A->n_rows, np = At->n_cols;
     const int NT = 256;
     constexpr int NCNT = SP_NCLS + 2;  // classes + global class + overflow counter
     uint32_t *err = sc.get<uint32_t>(1);
@@ -628,7 +1134,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     int64_t *need = sc.get<int64_t>(n + 1);
     int64_t *nnz_row = sc.get<int64_t>(n + 1);
     int64_t *dist = sc.get<int64_t>(n + 1);
-    unsigned long long *counts = sc.get<unsigned long long>(4 * NCNT + 4);
+    unsigned long long *counts = sc.get<unsigned long long>(4 * NCNT + 6);
     int32_t *lists = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
     int32_t *ovf = sc.get<int32_t>(2 * (n + 1));  // overflow list | unused list of the re-run
     if (!err || !work || !need || !nnz_row || !dist || !counts || !lists || !ovf) return SG_ERR_OOM;
@@ -637,32 +1143,40 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     unsigned long long *fz_counts = counts + 2 * NCNT + 1, *fz_ovf = fz_counts + SP_NCLS + 1;
     unsigned long long *ff_counts = counts + 3 * NCNT + 1;  // filtered rows' classes + global class
     SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (4 * NCNT + 4) * sizeof(unsigned long long), s));
+    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (4 * NCNT + 6) * sizeof(unsigned long long), s));
     SG_CUDA_TRY(cudaMemsetAsync(nnz_row, 0, (n + 1) * sizeof(int64_t), s));
     SG_CUDA_TRY(cudaMemsetAsync(dist, 0, (n + 1) * sizeof(int64_t), s));
     int64_t *a_beg = sc.get<int64_t>(A->nnz + 1);
     uint32_t *a_len = sc.get<uint32_t>(A->nnz + 1);
-    uint64_t *t_pair = sc.get<uint64_t>(At->nnz + 1);
-    if (!a_beg || !a_len || !t_pair) return SG_ERR_OOM;
+    if (!a_beg || !a_len) return SG_ERR_OOM;
+    uint64_t *t_pair = nullptr;  // only the two-pass kernels read At as (val << 32 | col) pairs
     SpArgs g{A->row_ptr, A->col, A->val, At->row_ptr, At->col, At->val, a_beg, a_len, t_pair,
-             n, min_shared, S, err};
+             n, min_shared, S, err, np, opt.row0};
+    const bool fused = opt.whole_rows || tune("spgemm_fused") != 0;
+    const bool upper = fused && !opt.whole_rows && tune("spgemm_upper") != 0;
+    unsigned long long *wmax_d = counts + 4 * NCNT + 5;
     std::optional<StageScope> stage;
     stage.emplace("SpGEMMSymbolic", s);
-    SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr, n,
-              work, a_beg, a_len);
-    SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
+    if (upper)
+        SG_LAUNCH("row_work", row_work_upper_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col,
+                  At->row_ptr, At->col, n, opt.row0, work, a_beg, a_len);
+    else
+        SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr,
+                  n, work, a_beg, a_len);
+    SG_LAUNCH("work_max", work_max_kernel, blocks_for(n, 256), 256, 0, s, (const int64_t *)work, n, wmax_d);
     const int nsm = sm_count();
     const int grid = (int)(nsm * tune("spgemm_blocks_per_sm"));
-    // numeric: one class per table size from 2^6 while the table and its sort buffer fit in 160 KB
+    // numeric (two-pass form): one class per table size from 2^6 while table and sort buffer fit in 160 KB
     Classes num{};
     num.ncls = 0;
     while (num.ncls < SP_NCLS && num_table_bytes((int64_t)1 << (SP_MINLOG + num.ncls), S) <= (160u << 10)) {
         num.log2T[num.ncls] = SP_MINLOG + num.ncls;
         num.ncls++;
     }
-    Classes fz{};  // the fused pass's guessed tables (larger sort buffer; up to 220 KB: one block per SM)
+    // the fused pass's guessed tables (up to 220 KB: one block per SM)
+    Classes fz{};
     fz.ncls = 0;
-    while (fz.ncls < SP_NCLS && num_table_bytes((int64_t)1 << (SP_MINLOG + fz.ncls), S, true) <= (220u << 10)) {
+    while (fz.ncls < SP_NCLS && tab_bytes((int64_t)1 << (SP_MINLOG + fz.ncls), S) <= (220u << 10)) {
         fz.log2T[fz.ncls] = SP_MINLOG + fz.ncls;
         fz.ncls++;
     }
@@ -672,21 +1186,25 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     const size_t fbytes = ((size_t)2 << log2F) / 8;
     Classes ff{};
     ff.ncls = 0;
-    while (ff.ncls < SP_NCLS &&
-           num_table_bytes((int64_t)1 << (SP_MINLOG + ff.ncls), S, true) + fbytes <= (220u << 10)) {
+    while (ff.ncls < SP_NCLS && tab_bytes((int64_t)1 << (SP_MINLOG + ff.ncls), S) + fbytes <= (220u << 10)) {
         ff.log2T[ff.ncls] = SP_MINLOG + ff.ncls;
         ff.ncls++;
     }
-    // global-memory tables of the exact bound 2 min(w, n - 1) (rows beyond shared memory)
-    const int64_t Tmax = pow2_at_least(2 * (n > 1 ? n - 1 : 1));
+    // global-memory tables of the exact bound 2 min(w, np - 1) (rows beyond shared memory), sized
+    // for the largest row; the fused pass's pool may be capped by opt.gmem_bytes
+    const int64_t Tmax = pow2_at_least(2 * (np > 1 ? np - 1 : 1));
     const int64_t gslice_bytes = (int64_t)((num_table_bytes(Tmax, S) + 255) & ~(size_t)255);
+    int64_t tslice_bytes = 0;
+    const int SK = S <= 2 ? S : 3;
 
     // ---- fused path (no symbolic pass): guessed tables, rows written to a temporary region
-    if (tune("spgemm_fused")) {
+    if (fused) {
         stage.emplace("SpGEMMNumeric", s);
         int64_t *room = sc.get<int64_t>(n + 1), *tmp_off = sc.get<int64_t>(n + 1), *need_f = sc.get<int64_t>(n + 1);
         int32_t *lists_f = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
-        if (!room || !tmp_off || !need_f || !lists_f) return SG_ERR_OOM;
+        uint32_t *colcnt = upper ? sc.get<uint32_t>(n + 1) : nullptr;
+        if (!room || !tmp_off || !need_f || !lists_f || (upper && !colcnt)) return SG_ERR_OOM;
+        if (upper) SG_CUDA_TRY(cudaMemsetAsync(colcnt, 0, (n + 1) * sizeof(uint32_t), s));
         // filtered rows: mode 2 always, mode 1 when the sample finds under half the partners recur
         const int64_t fmode = tune("spgemm_filter_mode");
         int64_t fwork = min_shared >= 2 && ff.ncls > 0 && fmode > 0 ? tune("spgemm_filter_work") : 0;
@@ -715,7 +1233,8 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         if (fmode == 1 && recur) fwork = 0;
         SG_LAUNCH("fused_need", fused_need_kernel, blocks_for(n, NT), NT, 0, s, (const int64_t *)work, n,
                   (int)tune("num_guess_shift"), fu, min_shared, fwork, (int)tune("spgemm_filter_shift"), ffq,
-                  ff.ncls > 0 ? (int64_t)1 << ff.log2T[ff.ncls - 1] : (int64_t)64, need, need_f, room);
+                  ff.ncls > 0 ? (int64_t)1 << ff.log2T[ff.ncls - 1] : (int64_t)64, (int)upper, np, opt.row0, need,
+                  need_f, room);
         SG_TRY(exclusive_scan<int64_t>(room, tmp_off, n, s, err));
         SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, fz, fz_counts, lists);
         if (fwork)
@@ -723,38 +1242,73 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         unsigned long long h_fz[NCNT], h_ff[NCNT];
         int64_t tmp_n = 0;
         uint32_t herr = 0;
+        unsigned long long wmax = 0;
         SG_CUDA_TRY(cudaMemcpyAsync(h_ff, ff_counts, sizeof(h_ff), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(cudaMemcpyAsync(h_fz, fz_counts, sizeof(h_fz), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(&wmax, wmax_d, sizeof(wmax), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(read_back(&tmp_n, tmp_off + n, sizeof(int64_t), s));
         if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
+        tslice_bytes = (int64_t)((tab_bytes(pow2_at_least(2 * std::min<int64_t>((int64_t)wmax, np > 1 ? np - 1 : 1)), S) +
+                                  255) & ~(size_t)255);
         const double tmp_bytes = (double)tmp_n * (8.0 + 8.0 * S);
         // the region is reserved, mostly untouched: at most half of what the device can still give
+        // (a row range was sized for its budget before the call)
         const double avail = (double)device_bytes_available();
-        if (tmp_bytes <= (double)tune("spgemm_fused_max_mb") * 1048576.0 && tmp_bytes <= 0.5 * avail) {
+        if (opt.whole_rows ||
+            (tmp_bytes <= (double)tune("spgemm_fused_max_mb") * 1048576.0 && tmp_bytes <= 0.5 * avail)) {
             int32_t *t_col = sc.get<int32_t>(tmp_n + 1);
             uint32_t *t_cnt = sc.get<uint32_t>(tmp_n + 1);
             uint32_t *t_si = sc.get<uint32_t>((size_t)S * tmp_n + 1), *t_sk = sc.get<uint32_t>((size_t)S * tmp_n + 1);
             if (!t_col || !t_cnt || !t_si || !t_sk) return SG_ERR_OOM;
+            // one launch per table class; the seed form (SK) and the filter pick the instantiation
+            auto launch_tab = [&](bool filt, int log2T, const int32_t *rl, const unsigned long long *cnt,
+                                  const char *name) -> sg_status {
+                const size_t sm = tab_bytes((int64_t)1 << log2T, S) + (filt ? fbytes : 0);
+                const int nt = pick_numeric_threads(log2T, filt);
+#define SG_TAB_LAUNCH(SKV, FV)                                                                              \
+    do {                                                                                                    \
+        SG_CUDA_TRY(ensure_smem(tab_numeric_kernel<false, SKV, FV>, sm));                                   \
+        SG_LAUNCH(name, (tab_numeric_kernel<false, SKV, FV>), grid, nt, sm, s, g, rl, cnt, log2T, log2F,    \
+                  (unsigned char *)nullptr, (int64_t)0, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, \
+                  tmp_n, (const int64_t *)work, ovf, fz_ovf, nnz_row, colcnt);                              \
+    } while (0)
+                if (filt) {
+                    if (SK == 0) SG_TAB_LAUNCH(0, true);
+                    else if (SK == 1) SG_TAB_LAUNCH(1, true);
+                    else if (SK == 2) SG_TAB_LAUNCH(2, true);
+                    else SG_TAB_LAUNCH(3, true);
+                } else {
+                    if (SK == 0) SG_TAB_LAUNCH(0, false);
+                    else if (SK == 1) SG_TAB_LAUNCH(1, false);
+                    else if (SK == 2) SG_TAB_LAUNCH(2, false);
+                    else SG_TAB_LAUNCH(3, false);
+                }
+#undef SG_TAB_LAUNCH
+                return SG_OK;
+            };
+            auto launch_gtab = [&](const int32_t *rl, const unsigned long long *cnt, int ggrid,
+                                   unsigned char *pool) -> sg_status {
+#define SG_GTAB_LAUNCH(SKV)                                                                                   \
+    SG_LAUNCH("spgemm_numeric_gmem", (tab_numeric_kernel<true, SKV, false>), ggrid, 512, 0, s, g, rl, cnt, 0, \
+              0, pool, tslice_bytes, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n,               \
+              (const int64_t *)work, ovf + n + 1, unused, nnz_row, colcnt)
+                if (SK == 0) SG_GTAB_LAUNCH(0);
+                else if (SK == 1) SG_GTAB_LAUNCH(1);
+                else if (SK == 2) SG_GTAB_LAUNCH(2);
+                else SG_GTAB_LAUNCH(3);
+#undef SG_GTAB_LAUNCH
+                return SG_OK;
+            };
             for (int c = 0; c < fz.ncls; c++) {
                 if (!h_fz[c]) continue;
-                const size_t sm = num_table_bytes((int64_t)1 << fz.log2T[c], S, true);
-                SG_CUDA_TRY(ensure_smem(numeric_kernel<false, true>, sm));
-                SG_LAUNCH(NUM_NAMES[fz.log2T[c] - SP_MINLOG], (numeric_kernel<false, true>), grid,
-                          pick_numeric_threads(fz.log2T[c], false), sm, s, g, lists + (int64_t)c * n, fz_counts + c,
-                          fz.log2T[c], 0,
-                          (const int64_t *)need, (unsigned char *)nullptr, (int64_t)0, (const int64_t *)tmp_off,
-                          t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work, ovf, fz_ovf, nnz_row);
+                SG_TRY(launch_tab(false, fz.log2T[c], lists + (int64_t)c * n, fz_counts + c,
+                                  NUM_NAMES[fz.log2T[c] - SP_MINLOG]));
             }
             for (int c = 0; fwork && c < ff.ncls; c++) {  // rows with many products: filtered first
                 if (!h_ff[c]) continue;
-                const size_t sm = num_table_bytes((int64_t)1 << ff.log2T[c], S, true) + fbytes;
-                SG_CUDA_TRY(ensure_smem(numeric_kernel<false, true, true>, sm));
-                SG_LAUNCH(FIL_NAMES[ff.log2T[c] - SP_MINLOG], (numeric_kernel<false, true, true>), grid,
-                          pick_numeric_threads(ff.log2T[c], true), sm, s, g, lists_f + (int64_t)c * n, ff_counts + c,
-                          ff.log2T[c], log2F, (const int64_t *)need_f, (unsigned char *)nullptr, (int64_t)0,
-                          (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work, ovf,
-                          fz_ovf, nnz_row);
+                SG_TRY(launch_tab(true, ff.log2T[c], lists_f + (int64_t)c * n, ff_counts + c,
+                                  FIL_NAMES[ff.log2T[c] - SP_MINLOG]));
             }
             unsigned long long n_ovf = 0;
             SG_CUDA_TRY(read_back(&n_ovf, fz_ovf, sizeof(n_ovf), s));
@@ -762,27 +1316,39 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
             if (n_big + n_big_f + n_ovf > 0) {
                 unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
                 rows_g = rows_g > n_big_f ? rows_g : n_big_f;
-                const int ggrid = (int)(rows_g < (unsigned long long)nsm * 2 ? rows_g : (unsigned long long)nsm * 2);
-                unsigned char *pool = sc.get<unsigned char>((size_t)gslice_bytes * ggrid);
+                int ggrid = (int)(rows_g < (unsigned long long)nsm * 2 ? rows_g : (unsigned long long)nsm * 2);
+                if (opt.gmem_bytes)
+                    ggrid = (int)std::max<int64_t>(1, std::min<int64_t>(ggrid, (int64_t)opt.gmem_bytes / tslice_bytes));
+                unsigned char *pool = sc.get<unsigned char>((size_t)tslice_bytes * ggrid);
                 if (!pool) return SG_ERR_OOM;
-                if (n_big)
-                    SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
-                              lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, 0, 0, (const int64_t *)need, pool,
-                              gslice_bytes, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n,
-                              (const int64_t *)work, ovf + n + 1, unused, nnz_row);
-                if (n_big_f)
-                    SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
-                              lists_f + (int64_t)ff.ncls * n, ff_counts + ff.ncls, 0, 0, (const int64_t *)need_f,
-                              pool, gslice_bytes, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n,
-                              (const int64_t *)work, ovf + n + 1, unused, nnz_row);
-                if (n_ovf)
-                    SG_LAUNCH("spgemm_numeric_gmem", (numeric_kernel<true, true>), ggrid, 512, 0, s, g,
-                              (const int32_t *)ovf, fz_ovf, 0, 0, (const int64_t *)need, pool, gslice_bytes,
-                              (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n, (const int64_t *)work,
-                              ovf + n + 1, unused, nnz_row);
+                if (n_big) SG_TRY(launch_gtab(lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, ggrid, pool));
+                if (n_big_f) SG_TRY(launch_gtab(lists_f + (int64_t)ff.ncls * n, ff_counts + ff.ncls, ggrid, pool));
+                if (n_ovf) SG_TRY(launch_gtab((const int32_t *)ovf, fz_ovf, ggrid, pool));
+                sc.release(pool);
             }
+            if (debug_record_classes()) {  // test hook: which launch handled each row
+                std::vector<int32_t> &rec = debug_classes();
+                rec.assign(n, -1);
+                std::vector<int32_t> h;
+                auto mark = [&](const int32_t *dl, unsigned long long cnt, int code, bool add) -> sg_status {
+                    h.resize(cnt);
+                    if (cnt) SG_CUDA_TRY(read_back(h.data(), dl, cnt * sizeof(int32_t), s));
+                    for (int32_t r : h)
+                        if (r >= 0 && r < n) rec[r] = add ? rec[r] + code : code;
+                    return SG_OK;
+                };
+                for (int c = 0; c <= fz.ncls; c++)
+                    SG_TRY(mark(lists + (int64_t)c * n, h_fz[c], c < fz.ncls ? fz.log2T[c] : 32, false));
+                for (int c = 0; fwork && c <= ff.ncls; c++)
+                    SG_TRY(mark(lists_f + (int64_t)c * n, h_ff[c], c < ff.ncls ? 16 + ff.log2T[c] : 33, false));
+                SG_TRY(mark(ovf, n_ovf, 64, true));
+            }
+            int64_t *clen = upper ? need_f : nnz_row;  // need_f is free once the classes have run
+            if (upper)
+                SG_LAUNCH("c_rowlen", c_rowlen_kernel, blocks_for(n, NT), NT, 0, s, (const int64_t *)nnz_row,
+                          (const uint32_t *)colcnt, n, need_f);
             SG_ALLOC(C->row_ptr, int64_t, n + 1, s);
-            SG_TRY(exclusive_scan<int64_t>(nnz_row, C->row_ptr, n, s, err));
+            SG_TRY(exclusive_scan<int64_t>(clen, C->row_ptr, n, s, err));
             int64_t nnz = 0;
             SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             SG_CUDA_TRY(read_back(&nnz, C->row_ptr + n, sizeof(int64_t), s));
@@ -798,20 +1364,68 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
             SG_ALLOC(C->count, uint32_t, nnz, s);
             SG_ALLOC(C->seed_i, uint32_t, (int64_t)S * nnz, s);
             SG_ALLOC(C->seed_k, uint32_t, (int64_t)S * nnz, s);
-            SG_LAUNCH("compact_c", compact_c_kernel, blocks_for(n * 32, 256), 256, 0, s, (const int64_t *)tmp_off,
-                      tmp_n, (const int32_t *)t_col, (const uint32_t *)t_cnt, (const uint32_t *)t_si,
-                      (const uint32_t *)t_sk, S, (const int64_t *)C->row_ptr, n, nnz, C->col, C->count, C->seed_i,
-                      C->seed_k);
+            if (!upper) {
+                SG_LAUNCH("compact_c", compact_c_kernel, blocks_for(n * 32, 256), 256, 0, s, (const int64_t *)tmp_off,
+                          tmp_n, (const int32_t *)t_col, (const uint32_t *)t_cnt, (const uint32_t *)t_si,
+                          (const uint32_t *)t_sk, S, (const int64_t *)C->row_ptr, n, nnz, C->col, C->count,
+                          C->seed_i, C->seed_k);
+                return SG_OK;
+            }
+            // C = U + U^T: U rows in place, mirrored entries through the lower scratch arrays
+            int64_t *lrp = room;  // free once the scan of tmp_off has run
+            SG_TRY(exclusive_scan<uint32_t>(colcnt, lrp, n, s, err));
+            int64_t nnz_l = 0;
+            SG_CUDA_TRY(read_back(&nnz_l, lrp + n, sizeof(int64_t), s));
+            uint32_t *cursor = sc.get<uint32_t>(n + 1);
+            int32_t *l_col = sc.get<int32_t>(nnz_l + 1);
+            uint32_t *l_cnt = sc.get<uint32_t>(nnz_l + 1);
+            uint32_t *l_si = sc.get<uint32_t>((size_t)S * nnz_l + 1), *l_sk = sc.get<uint32_t>((size_t)S * nnz_l + 1);
+            if (!cursor || !l_col || !l_cnt || !l_si || !l_sk) return SG_ERR_OOM;
+            SG_CUDA_TRY(cudaMemsetAsync(cursor, 0, (n + 1) * sizeof(uint32_t), s));
+            SG_LAUNCH("mirror_c", mirror_c_kernel, blocks_for(n * 32, 256), 256, 0, s, (const int64_t *)tmp_off,
+                      (const int64_t *)nnz_row, tmp_n, (const int32_t *)t_col, (const uint32_t *)t_cnt,
+                      (const uint32_t *)t_si, (const uint32_t *)t_sk, S, (const uint32_t *)colcnt,
+                      (const int64_t *)C->row_ptr, (const int64_t *)lrp, n, nnz, nnz_l, cursor, C->col, C->count,
+                      C->seed_i, C->seed_k, l_col, l_cnt, l_si, l_sk);
+            for (const void *p : {(const void *)t_col, (const void *)t_cnt, (const void *)t_si, (const void *)t_sk})
+                sc.release(p);
+            unsigned long long *big_count = counts + 4 * NCNT + 4;  // zeroed with the counters
+            int32_t *big_rows = ovf;                                // free once the redo passes have run
+            SG_LAUNCH("sort_lower", sort_lower_kernel, (int64_t)nsm * 8, LOWER_NT, 0, s, (const uint32_t *)colcnt,
+                      (const int64_t *)lrp, (const int64_t *)C->row_ptr, n, nnz, nnz_l, S, (const int32_t *)l_col,
+                      (const uint32_t *)l_cnt, (const uint32_t *)l_si, (const uint32_t *)l_sk, C->col, C->count,
+                      C->seed_i, C->seed_k, big_count, big_rows,
+                      (int)std::min<int64_t>(tune("spgemm_lower_smem"), LOWER_SMEM));
+            unsigned long long n_lbig = 0;
+            SG_CUDA_TRY(read_back(&n_lbig, big_count, sizeof(n_lbig), s));
+            if (n_lbig) {
+                int64_t slice = 1;
+                while (slice < n) slice <<= 1;  // a lower part holds fewer than n entries
+                const int lgrid = (int)(n_lbig < (unsigned long long)nsm ? n_lbig : (unsigned long long)nsm);
+                uint64_t *kpool = sc.get<uint64_t>((size_t)slice * lgrid);
+                if (!kpool) return SG_ERR_OOM;
+                SG_LAUNCH("sort_lower_big", lower_big_kernel, lgrid, 1024, 0, s, (const uint32_t *)colcnt,
+                          (const int64_t *)lrp, (const int64_t *)C->row_ptr, nnz, nnz_l, S, (const int32_t *)big_rows,
+                          (const unsigned long long *)big_count, kpool, slice, (const int32_t *)l_col,
+                          (const uint32_t *)l_cnt, (const uint32_t *)l_si, (const uint32_t *)l_sk, C->col, C->count,
+                          C->seed_i, C->seed_k);
+            }
             return SG_OK;
         }
-        // the temporary region would exceed its budget: the two-pass path below
+        // the temporary region would exceed its budget: the two-pass path below, on full rows
+        if (upper)
+            SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col,
+                      At->row_ptr, n, work, a_beg, a_len);
     }
+    g.t_pair = t_pair = sc.get<uint64_t>(At->nnz + 1);
+    if (!t_pair) return SG_ERR_OOM;
+    SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
 
     // ---- symbolic: guessed shared-memory tables of 2^6 .. 2^14 slots, one class per size
     Classes sym{};
     sym.ncls = SP_NCLS;
     for (int c = 0; c < SP_NCLS; c++) sym.log2T[c] = SP_MINLOG + c;
-    SG_LAUNCH("sym_need", sym_need_kernel, blocks_for(n, NT), NT, 0, s, work, n, (int)tune("sym_guess_shift"),
+    SG_LAUNCH("sym_need", sym_need_kernel, blocks_for(n, NT), NT, 0, s, work, n, np, (int)tune("sym_guess_shift"),
               need);
     SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, sym, sym_counts, lists);
     for (int c = 0; c < sym.ncls; c++) {
@@ -827,7 +1441,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     SG_CUDA_TRY(read_back(h_sym, sym_counts, sizeof(h_sym), s));
     const unsigned long long n_big = h_sym[sym.ncls], n_ovf = h_sym[SP_NCLS + 1];
     if (n_big + n_ovf > 0) {
-        const int64_t slice = 2 * pow2_at_least(2 * (n > 1 ? n - 1 : 1));  // keys + counts of the largest row
+        const int64_t slice = 2 * pow2_at_least(2 * (np > 1 ? np - 1 : 1));  // keys + counts of the largest row
         const unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
         const int grid = (int)(rows_g < (unsigned long long)nsm * 2 ? rows_g : (unsigned long long)nsm * 2);
         int32_t *pool = sc.get<int32_t>((size_t)slice * grid);
@@ -926,4 +1540,125 @@ extern "C" void sg_free_overlap(sg_overlap_csr *c, sg_stream_t stream) {
     sg::dfree(c->seed_i, s);
     sg::dfree(c->seed_k, s);
     *c = sg_overlap_csr{};
+}
+
+// ------------------------------------------------------------------------------------------
+// Memory-bounded formation of C in row tiles (the paper's closing remark, Sec. VIII: form C in
+// parts under a memory bound instead of all at once). Rows of C are independent, so C is formed
+// for a range of A's rows at a time -- A's row pointers of the range rebased to 0, partners still
+// every read of At, whole rows (the mirrored form needs every earlier row) -- and each finished
+// tile is handed to the caller and freed before the next one starts.
+namespace sg {
+
+constexpr int64_t TILE_ROW_BYTES = 256;           // per-row arrays of one tile (row pointers, classes...)
+constexpr int64_t TILE_FIXED_BYTES = 4ll << 20;   // counters and allocation rounding of one tile
+
+// Per row: the bytes the row adds to a tile (its A entries' At tails, 12 B each; the temporary
+// and final room for its entries of C, min(w / t, np - 1) each, twice; and the per-row arrays)
+// and its products w (whole row, diagonal excluded). One warp per row.
+__global__ void tile_est_kernel(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
+                                const int64_t *__restrict__ t_rp, int64_t n, int64_t np, uint32_t t, int S,
+                                int64_t *__restrict__ bytes, int64_t *__restrict__ work) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    int64_t w = 0;
+    for (int64_t a = a_rp[row] + lane; a < a_rp[row + 1]; a += 32) {
+        const int32_t j = a_col[a];
+        w += t_rp[j + 1] - t_rp[j] - 1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) {
+        const int64_t room = std::min<int64_t>(w / t, np - 1);
+        bytes[row] = 12 * (a_rp[row + 1] - a_rp[row]) + 2 * (8 + 8 * (int64_t)S) * room + TILE_ROW_BYTES;
+        work[row] = w;
+    }
+}
+
+__global__ void rebase_rows_kernel(const int64_t *__restrict__ rp, int64_t r0, int64_t nr, int64_t *__restrict__ out) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x <= nr) out[x] = rp[r0 + x] - rp[r0];
+}
+
+}  // namespace sg
+
+extern "C" sg_status sg_overlap_spgemm_tiled(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared,
+                                             int32_t max_seeds, size_t budget_bytes, sg_overlap_tile_fn fn,
+                                             void *user, int64_t *n_tiles, sg_stream_t stream) {
+    using namespace sg;
+    if (n_tiles) *n_tiles = 0;
+    if (!A || !At || !fn || max_seeds < 0 || max_seeds > SP_MAX_SEEDS || min_shared < 1 || A->n_rows != At->n_cols ||
+        A->n_cols != At->n_rows || A->nnz != At->nnz || A->n_rows < 0 || A->n_rows >= ((int64_t)1 << 31) ||
+        !A->row_ptr || !At->row_ptr || budget_bytes == 0) {
+        set_error("overlap_spgemm_tiled: invalid arguments");
+        return SG_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = A->n_rows, np = At->n_cols;
+    const int S = max_seeds;
+    if (n == 0) return SG_OK;
+    // per-row bytes and products, and A's row pointers, on the host
+    std::vector<int64_t> hb(n), hw(n), hrp(n + 1);
+    {
+        Scratch sc(s);
+        int64_t *db = sc.get<int64_t>(n), *dw = sc.get<int64_t>(n);
+        if (!db || !dw) return SG_ERR_OOM;
+        SG_LAUNCH("tile_est", tile_est_kernel, (n * 32 + 255) / 256, 256, 0, s, A->row_ptr, A->col, At->row_ptr, n,
+                  np, min_shared, S, db, dw);
+        SG_CUDA_TRY(cudaMemcpyAsync(hb.data(), db, n * 8, cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(hw.data(), dw, n * 8, cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaMemcpyAsync(hrp.data(), A->row_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, s));
+        SG_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // the redo pass's global table for a tile whose largest row has w products
+    auto gslice = [&](int64_t w) -> int64_t {
+        const int64_t T = pow2_at_least(2 * std::min<int64_t>(std::max<int64_t>(w, 1), np > 1 ? np - 1 : 1));
+        return (int64_t)((tab_bytes(T, S) + 255) & ~(size_t)255);
+    };
+    int64_t tiles = 0;
+    for (int64_t r0 = 0; r0 < n;) {
+        // the longest range from r0 whose rows, one global table for its largest row and the fixed
+        // part fit the budget
+        int64_t acc = TILE_FIXED_BYTES, wmax = 0, r1 = r0;
+        while (r1 < n) {
+            const int64_t wm = std::max(wmax, hw[r1]);
+            if (acc + hb[r1] + gslice(wm) > (int64_t)budget_bytes) break;
+            acc += hb[r1];
+            wmax = wm;
+            r1++;
+        }
+        if (r1 == r0) {
+            set_error("overlap_spgemm_tiled: row %lld alone needs about %lld bytes, more than the budget of %zu",
+                      (long long)r0, (long long)(TILE_FIXED_BYTES + hb[r0] + gslice(hw[r0])), budget_bytes);
+            return SG_ERR_BUDGET;
+        }
+        const int64_t nr = r1 - r0, base = hrp[r0];
+        sg_overlap_csr Ct{};
+        sg_status st;
+        {
+            Scratch sc(s);
+            int64_t *rp = sc.get<int64_t>(nr + 1);
+            if (!rp) return SG_ERR_OOM;
+            SG_LAUNCH("rebase_rows", rebase_rows_kernel, (nr + 256) / 256, 256, 0, s, A->row_ptr, r0, nr, rp);
+            sg_csr_u32 At_{*At};
+            sg_csr_u32 Ar{nr, A->n_cols, hrp[r1] - base, rp, A->col + base, A->val + base};
+            OverlapOpts opt;
+            opt.row0 = r0;
+            opt.whole_rows = true;
+            opt.gmem_bytes = (size_t)((int64_t)budget_bytes - acc);  // >= one table for the largest row
+            st = overlap_impl(&Ar, &At_, min_shared, S, &Ct, s, sc, opt);
+        }
+        if (st == SG_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("overlap_spgemm_tiled: tile of rows %lld..%lld failed", (long long)r0, (long long)r1);
+            st = SG_ERR_CUDA;
+        }
+        if (st == SG_OK) st = fn(&Ct, r0, user);
+        sg_free_overlap(&Ct, stream);
+        if (st != SG_OK) return st;
+        tiles++;
+        if (n_tiles) *n_tiles = tiles;
+        r0 = r1;
+    }
+    return SG_OK;
 }

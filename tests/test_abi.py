@@ -14,6 +14,7 @@ def declared():
         if f.endswith(".h"):
             txt = open(os.path.join(HDR, f)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            txt = re.sub(r"typedef\s+sg_status\s*\(\*[^;]*;", "", txt)  # callback types, not functions
             names |= set(re.findall(r"\b(sg_[a-z0-9_]+)\s*\(", txt))
     return names
 

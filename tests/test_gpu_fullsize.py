@@ -13,7 +13,9 @@ slow for the k-mer stage and C:
 - properties that hold at any size: codes strictly ascending, A and At transposes, no diagonal in
   C and counts >= t, S a subgraph of R.
 
-Workloads: the bacterial one (the benchmark's) and the C. elegans-shaped one at full size (4.1 Gbp
+On the bacterial workload the whole codes, A, At and C are also compared with the whole oracle.
+
+Workloads: the bacterial one and the C. elegans-shaped one (the benchmark's) at full size (4.1 Gbp
 of reads, 1.8e9 nonzeros in A; about 2.5 minutes, mostly generation and the census; skipped with
 SG_SKIP_ELEGANS=1).
 """
@@ -144,6 +146,23 @@ def test_fullsize_sampled_c_rows(full):
             ka, kb = C["row_ptr"][k], C["row_ptr"][k + 1]
             t = ka + np.searchsorted(C["col"][ka:kb], i)
             assert t < kb and C["col"][t] == i and C["count"][t] == cnt, (i, k)
+
+
+def test_fullsize_whole_matrices_bacterial(full):
+    """On the bacterial workload (the smaller one) the whole oracle runs: codes, A, At and C are
+    compared with it element by element, no sampling (about 2.5 minutes of host time, mostly the
+    oracle's k-mer count)."""
+    w, d, km, C = full["w"], full["d"], full["km"], full["C"]
+    if w.name != synth.BACTERIAL.name:
+        pytest.skip("whole-matrix oracle only on the bacterial workload")
+    ekm = oracle.build_kmer_matrix(d["seq"], d["offsets"], w.k, w.lo, w.hi)
+    assert np.array_equal(km["codes"], ekm["codes"])
+    for name in ("A", "At"):
+        for key in ("row_ptr", "col", "val"):
+            assert np.array_equal(km[name][key], ekm[name][key]), f"{name}.{key}"
+    eC = oracle.overlap_spgemm(ekm["A"], ekm["At"], w.min_shared, w.max_seeds)
+    for key in ("row_ptr", "col", "count", "seed_i", "seed_k"):
+        assert np.array_equal(C[key], eC[key]), f"C.{key}"
 
 
 def test_fullsize_graph_from_seeds(full):

@@ -60,6 +60,12 @@ CONFIGS = [
     {"spgemm_sample_min_nnz": 0, "spgemm_sample_rows": 1, "spgemm_guess_pct": 25},  # tables too small
     {"spgemm_sample_min_nnz": 0, "spgemm_guess_pct": 10000},         # tables at the exact bound
     {"spgemm_sample_min_nnz": 0, "spgemm_filter_mode": 2, "spgemm_filter_work": 1},  # sampled, filtered
+    {"spgemm_upper": 0},                                             # whole rows, no mirror
+    {"spgemm_upper": 0, "num_guess_shift": 8},                       # whole rows, most rows overflow
+    {"spgemm_upper": 0, "spgemm_filter_mode": 2, "spgemm_filter_work": 1},  # whole rows, filtered
+    {"spgemm_lower_smem": 1},                                        # every mirrored part > 1: global sort
+    {"spgemm_lower_smem": 16, "num_guess_shift": 8},                 # mixed sort paths, overflowing tables
+    {"spgemm_blocks_per_sm": 1, "spgemm_big_threads": 512, "spgemm_lower_smem": 64},
 ]
 
 
