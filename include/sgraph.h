@@ -294,7 +294,11 @@ void sg_free_batch(sg_batch_result *r, sg_stream_t stream);
  * sg_run_batch and publishes each job's C and S. Jobs arriving while batches run are admitted as
  * workers and memory free up, and batches of different workers overlap on the device. A job's
  * result is the same alone and in any mix (the batch is block-diagonal). A job whose own device
- * estimate (about 64 B per base + 48 B per R entry) exceeds hbm_budget completes with
+ * estimate (about 64 B per base + 48 B per R entry) exceeds hbm_budget waits until nothing else
+ * is admitted and runs alone with C formed in row tiles (sg_overlap_spgemm_tiled) under what the
+ * budget leaves once its inputs, A, At and R are resident (about 24 B per base + 48 B per R
+ * entry); its result is the same. A job that does not fit even so (the k-mer stage, about 40 B
+ * per base, or the resident part plus 64 MB of tiles, above hbm_budget) completes with
  * SG_ERR_BUDGET. All calls are thread-safe.
  */
 typedef struct sg_server sg_server;

@@ -22,7 +22,9 @@ SPACE = {
     "bloom_unroll": [4, 8],
     "bloom_bits": [6, 8, 10, 12],
     "spgemm_fused": [0, 1],
-    "num_guess_shift": [1, 2, 3, 4],
+    "spgemm_upper": [0, 1],
+    "spgemm_tab_warps": [0, 32, 48, 64],
+    "spgemm_tmp_pct": [110, 125, 200],
     "spgemm_filter_mode": [0, 1, 2],
     "spgemm_filter_work": [1024, 2048, 4096, 8192],
     "spgemm_guess_pct": [150, 200, 300, 400],

@@ -26,6 +26,7 @@ struct OverlapOpts {
     int64_t row0 = 0;
     bool whole_rows = false;  // fused pass on whole rows, no mirror, never the two-pass form
     size_t gmem_bytes = 0;    // > 0: cap on the global-memory table pool of the redo pass
+    int64_t tmp_cap = 0;      // > 0: entries of the fused pass's temporary region (else from a sample)
 };
 
 // C = A At over the overlap semiring (spgemm.cu).

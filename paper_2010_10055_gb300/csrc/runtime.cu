@@ -289,17 +289,18 @@ static Tunable g_tunables[] = {
     {"spgemm_upper", 1, 0, 1},            // 1: the fused pass tabulates partners k > i only and
                                           // mirrors them (C is symmetric); 0: whole rows
     {"spgemm_lower_smem", 4096, 1, 4096}, // mirrored parts up to this long are ordered in shared memory
+    {"spgemm_tab_warps", 64, 0, 64},      // fused-pass blocks: threads for about this many warps per SM
+                                          // across the blocks that fit (0: fixed threads per table size)
     {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)
-    {"spgemm_sample_min_nnz", (int64_t)1 << 26, 0, (int64_t)1 << 50},  // ... when nnz(A) is at least this
-    {"spgemm_guess_pct", 300, 25, 10000}, // guess = pct / 100 x sampled partners per product x products
-    {"num_guess_shift", 2, 0, 8},         // fused numeric table guess = products >> shift (no sample)
+    {"spgemm_guess_pct", 300, 1, 10000},  // guess = pct / 100 x sampled partners per A entry x entries
+    {"spgemm_tmp_pct", 125, 1, 10000},    // fused temporary region = pct / 100 x sampled kept entries
+                                          // (+ 4 per row); rows that find it full are redone
     {"spgemm_fused_max_mb", 65536, 0, 1 << 30},  // temporary C region above which the two passes run
                                                   // (also when it exceeds half the free memory)
     {"spgemm_filter_mode", 1, 0, 2},      // seen-twice filter: 0 never, 1 where the sample finds it
                                           // pays, 2 always (rows of spgemm_filter_work products or more)
-    {"spgemm_filter_work", 2048, 0, (int64_t)1 << 40},  // fused rows with this many products or more
+    {"spgemm_filter_work", 1024, 0, (int64_t)1 << 40},  // fused rows with this many A entries or more
                                           // may first mark partners seen twice (0: never)
-    {"spgemm_filter_shift", 2, 0, 8},     // their table guess = products >> shift (no sample)
     {"spgemm_filter_log2", 17, 10, 19},   // at most 2^this bits per seen-once / seen-twice filter
     {"sym_guess_shift", 2, 0, 8},         // symbolic table guess = products >> shift
     {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch

@@ -6,8 +6,9 @@
 // jobs as one sg_run_batch (block-diagonal, so every job's result equals its result alone), copies
 // the results back and publishes them. A job arriving while other batches are on the GPU is
 // admitted by the next idle worker as soon as memory frees up, and batches on different workers
-// overlap on the device. A job whose estimate alone exceeds the budget completes with
-// SG_ERR_BUDGET.
+// overlap on the device. A job whose estimate alone exceeds the budget runs alone, once nothing
+// else is on the device, with C formed in row tiles under what the budget leaves
+// (sg_overlap_spgemm_tiled); one that does not fit even so completes with SG_ERR_BUDGET.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -37,7 +38,7 @@ struct Job {
     std::vector<uint8_t> rdir;
     uint32_t lo, hi;
     bool has_r;
-    size_t est;
+    size_t est, est_tiled;
     double t_submit;
 };
 
@@ -48,6 +49,20 @@ struct Done {
 // Device bytes a job may need while its batch runs (inputs, filters, candidates, matrices).
 size_t estimate_bytes(const Job &j) {
     return (size_t)64 * j.seq.size() + (size_t)48 * j.rcol.size() + (size_t)64 * j.off.size() + (1u << 20);
+}
+
+// Device bytes of the parts of a job that are not C: inputs, A and At, R and the reduction.
+size_t resident_bytes(const Job &j) {
+    return (size_t)24 * j.seq.size() + (size_t)48 * j.rcol.size() + (size_t)64 * j.off.size() + (1u << 20);
+}
+
+// ... and with C formed in row tiles (sg_overlap_spgemm_tiled): the k-mer stage's peak (about
+// 40 B per base) or the resident part plus the smallest useful tile budget, whichever is larger.
+constexpr size_t MIN_TILE_BUDGET = (size_t)64 << 20;
+size_t estimate_tiled_bytes(const Job &j) {
+    const size_t kmer = (size_t)40 * j.seq.size() + (size_t)64 * j.off.size() + (1u << 20);
+    const size_t rest = resident_bytes(j) + MIN_TILE_BUDGET;
+    return kmer > rest ? kmer : rest;
 }
 
 }  // namespace
@@ -202,6 +217,174 @@ static void run_batch_on(sg_server *srv, std::vector<Job *> &jobs, cudaStream_t 
     sg_free_batch(&br, (sg_stream_t)s);
 }
 
+// A job too large for the budget in one piece, run alone: A and At as usual, C formed in row
+// tiles under what the budget leaves once the rest of the job is resident (each tile copied to
+// the host as it completes), then the reduction of R.
+struct TileSink {
+    cudaStream_t s;
+    int S;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> col;
+    std::vector<uint32_t> cnt;
+    std::vector<std::vector<uint32_t>> si, sk;  // per seed slot
+};
+
+static sg_status tile_to_host(const sg_overlap_csr *t, int64_t row_begin, void *user) {
+    TileSink &k = *(TileSink *)user;
+    (void)row_begin;  // tiles arrive in row order
+    const int64_t base = (int64_t)k.col.size(), nt = t->nnz;
+    std::vector<int64_t> rp(t->n + 1);
+    k.col.resize(base + nt);
+    k.cnt.resize(base + nt);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), t->row_ptr, (t->n + 1) * 8, cudaMemcpyDeviceToHost, k.s);
+    if (e == cudaSuccess && nt) e = cudaMemcpyAsync(k.col.data() + base, t->col, nt * 4, cudaMemcpyDeviceToHost, k.s);
+    if (e == cudaSuccess && nt) e = cudaMemcpyAsync(k.cnt.data() + base, t->count, nt * 4, cudaMemcpyDeviceToHost, k.s);
+    for (int q = 0; q < k.S && e == cudaSuccess; q++) {
+        k.si[q].resize(base + nt);
+        k.sk[q].resize(base + nt);
+        if (nt) e = cudaMemcpyAsync(k.si[q].data() + base, t->seed_i + (int64_t)q * nt, nt * 4, cudaMemcpyDeviceToHost, k.s);
+        if (e == cudaSuccess && nt)
+            e = cudaMemcpyAsync(k.sk[q].data() + base, t->seed_k + (int64_t)q * nt, nt * 4, cudaMemcpyDeviceToHost, k.s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(k.s);
+    if (e != cudaSuccess) {
+        set_error("server: tile download failed: %s", cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+    }
+    for (int64_t i = 1; i <= t->n; i++) k.rp.push_back(base + rp[i]);
+    return SG_OK;
+}
+
+static void run_large_on(sg_server *srv, Job *jp, cudaStream_t s, Done *&out) {
+    const double t_start = now_s();
+    out = new Done();
+    Job &j = *jp;
+    const sg_batch_params &p = srv->cfg.params;
+    const int64_t n = (int64_t)j.off.size() - 1;
+    sg_status st = SG_OK;
+    sg_csr_u32 A{}, At{};
+    uint64_t *codes = nullptr;
+    sg_graph_csr Sg{};
+    int32_t iters = 0;
+    int64_t m_cols = 0;
+    TileSink sink;
+    sink.s = s;
+    sink.S = p.max_seeds;
+    sink.rp.push_back(0);
+    sink.si.resize(p.max_seeds);
+    sink.sk.resize(p.max_seeds);
+    std::vector<int64_t> srp;
+    std::vector<int32_t> scol;
+    std::vector<uint32_t> ssuf;
+    std::vector<uint8_t> sdir;
+    {
+        Scratch sc(s);
+        uint8_t *dseq = sc.get<uint8_t>(j.seq.size() + 16);
+        int64_t *doff = sc.get<int64_t>(j.off.size());
+        if (!dseq || !doff) st = SG_ERR_OOM;
+        if (st == SG_OK && (cudaMemcpyAsync(dseq, j.seq.data(), j.seq.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                            cudaMemcpyAsync(doff, j.off.data(), j.off.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+            set_error("server: input upload failed");
+            st = SG_ERR_CUDA;
+        }
+        if (st == SG_OK)
+            st = sg_build_kmer_matrix(dseq, doff, n, (int64_t)j.seq.size(), p.k, j.lo, j.hi, &A, &At, &codes,
+                                      (sg_stream_t)s);
+        dfree(codes, s);
+        codes = nullptr;
+        if (st == SG_OK) {
+            const size_t res = resident_bytes(j), budget = srv->cfg.hbm_budget;
+            const size_t tb = budget > res + MIN_TILE_BUDGET ? budget - res : MIN_TILE_BUDGET;
+            int64_t ntiles = 0;
+            st = sg_overlap_spgemm_tiled(&A, &At, p.min_shared, p.max_seeds, tb, tile_to_host, &sink, &ntiles,
+                                         (sg_stream_t)s);
+        }
+        m_cols = A.n_cols;
+        sg_free_csr_u32(&A, (sg_stream_t)s);
+        sg_free_csr_u32(&At, (sg_stream_t)s);
+        if (st == SG_OK && j.has_r) {
+            const int64_t nnz = (int64_t)j.rcol.size();
+            int64_t *rp = sc.get<int64_t>(n + 1);
+            int32_t *rc = sc.get<int32_t>(nnz + 1);
+            uint32_t *rs = sc.get<uint32_t>(nnz + 1);
+            uint8_t *rd = sc.get<uint8_t>(nnz + 1);
+            if (!rp || !rc || !rs || !rd) st = SG_ERR_OOM;
+            cudaError_t e = cudaSuccess;
+            if (st == SG_OK) e = cudaMemcpyAsync(rp, j.rrp.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s);
+            if (st == SG_OK && e == cudaSuccess && nnz) e = cudaMemcpyAsync(rc, j.rcol.data(), nnz * 4, cudaMemcpyHostToDevice, s);
+            if (st == SG_OK && e == cudaSuccess && nnz) e = cudaMemcpyAsync(rs, j.rsuf.data(), nnz * 4, cudaMemcpyHostToDevice, s);
+            if (st == SG_OK && e == cudaSuccess && nnz) e = cudaMemcpyAsync(rd, j.rdir.data(), nnz, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                set_error("server: R upload failed");
+                st = SG_ERR_CUDA;
+            }
+            sg_graph_csr R{n, nnz, rp, rc, rs, rd};
+            if (st == SG_OK) st = sg_transitive_reduce(&R, p.fuzz, p.tr_mode, &Sg, &iters, (sg_stream_t)s);
+            if (st == SG_OK) {
+                srp.resize(n + 1);
+                scol.resize(Sg.nnz);
+                ssuf.resize(Sg.nnz);
+                sdir.resize(Sg.nnz);
+                e = cudaMemcpyAsync(srp.data(), Sg.row_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess && Sg.nnz) e = cudaMemcpyAsync(scol.data(), Sg.col, Sg.nnz * 4, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess && Sg.nnz) e = cudaMemcpyAsync(ssuf.data(), Sg.suffix, Sg.nnz * 4, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess && Sg.nnz) e = cudaMemcpyAsync(sdir.data(), Sg.dir, Sg.nnz, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) {
+                    set_error("server: result download failed: %s", cudaGetErrorString(e));
+                    st = SG_ERR_CUDA;
+                }
+            }
+            sg_free_graph(&Sg, (sg_stream_t)s);
+        }
+    }
+    sg_job_result &r = out->r;
+    memset(&r, 0, sizeof(r));
+    r.status = st;
+    r.t_submit = j.t_submit;
+    r.t_start = t_start;
+    r.t_done = now_s();
+    r.batch_size = 1;
+    if (st != SG_OK) {
+        snprintf(r.error, sizeof(r.error), "%s", sg_last_error());
+        return;
+    }
+    const int64_t cn = (int64_t)sink.col.size(), S = p.max_seeds;
+    r.n = n;
+    r.m = m_cols;
+    r.nnz_c = cn;
+    r.max_seeds = (int32_t)S;
+    r.c_row_ptr = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+    r.c_col = (int32_t *)malloc(sizeof(int32_t) * (cn ? cn : 1));
+    r.c_count = (uint32_t *)malloc(sizeof(uint32_t) * (cn ? cn : 1));
+    r.c_seed_i = (uint32_t *)malloc(sizeof(uint32_t) * (cn * S > 0 ? cn * S : 1));
+    r.c_seed_k = (uint32_t *)malloc(sizeof(uint32_t) * (cn * S > 0 ? cn * S : 1));
+    memcpy(r.c_row_ptr, sink.rp.data(), sizeof(int64_t) * (n + 1));
+    if (cn) {
+        memcpy(r.c_col, sink.col.data(), sizeof(int32_t) * cn);
+        memcpy(r.c_count, sink.cnt.data(), sizeof(uint32_t) * cn);
+        for (int64_t q = 0; q < S; q++) {
+            memcpy(r.c_seed_i + q * cn, sink.si[q].data(), sizeof(uint32_t) * cn);
+            memcpy(r.c_seed_k + q * cn, sink.sk[q].data(), sizeof(uint32_t) * cn);
+        }
+    }
+    if (j.has_r) {
+        const int64_t sn = (int64_t)scol.size();
+        r.nnz_s = sn;
+        r.iterations = iters;
+        r.s_row_ptr = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+        r.s_col = (int32_t *)malloc(sizeof(int32_t) * (sn ? sn : 1));
+        r.s_suffix = (uint32_t *)malloc(sizeof(uint32_t) * (sn ? sn : 1));
+        r.s_dir = (uint8_t *)malloc(sn ? sn : 1);
+        memcpy(r.s_row_ptr, srp.data(), sizeof(int64_t) * (n + 1));
+        if (sn) {
+            memcpy(r.s_col, scol.data(), sizeof(int32_t) * sn);
+            memcpy(r.s_suffix, ssuf.data(), sizeof(uint32_t) * sn);
+            memcpy(r.s_dir, sdir.data(), sn);
+        }
+    }
+}
+
 static void worker_main(sg_server *srv) {
     if (cudaSetDevice(srv->cfg.device) != cudaSuccess) return;
     cudaStream_t s = nullptr;
@@ -209,25 +392,40 @@ static void worker_main(sg_server *srv) {
     const size_t budget = srv->cfg.hbm_budget;
     for (;;) {
         std::vector<Job *> batch;
+        Job *large = nullptr;
         size_t bytes = 0;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             for (;;) {
                 if (srv->stop) break;
-                // jobs that can never fit are answered right away
-                while (!srv->pending.empty() && srv->pending.front()->est > budget) {
+                // jobs that can never fit, not even with C in tiles, are answered right away
+                while (!srv->pending.empty() && srv->pending.front()->est > budget &&
+                       srv->pending.front()->est_tiled > budget) {
                     Job *j = srv->pending.front();
                     srv->pending.pop_front();
                     Done *d = new Done();
-                    char msg[128];
-                    snprintf(msg, sizeof(msg), "job needs about %zu bytes of device memory, the budget is %zu",
-                             j->est, budget);
+                    char msg[160];
+                    snprintf(msg, sizeof(msg),
+                             "job needs about %zu bytes of device memory (%zu with C in tiles), the budget is %zu",
+                             j->est, j->est_tiled, budget);
                     fill_error(&d->r, SG_ERR_BUDGET, j->t_submit, msg);
                     srv->done[j->ticket] = d;
                     delete j;
                     srv->cv_done.notify_all();
                 }
+                // a job that fits only with C in tiles runs alone, with the whole budget
+                if (!srv->pending.empty() && srv->pending.front()->est > budget) {
+                    if (srv->budget_used == 0) {
+                        large = srv->pending.front();
+                        srv->pending.pop_front();
+                        bytes = budget;
+                        break;
+                    }
+                    srv->cv_work.wait(lk);
+                    continue;
+                }
                 while (!srv->pending.empty() && (int)batch.size() < srv->cfg.max_batch &&
+                       srv->pending.front()->est <= budget &&
                        srv->budget_used + bytes + srv->pending.front()->est <= budget) {
                     bytes += srv->pending.front()->est;
                     batch.push_back(srv->pending.front());
@@ -236,11 +434,17 @@ static void worker_main(sg_server *srv) {
                 if (!batch.empty()) break;
                 srv->cv_work.wait(lk);
             }
-            if (batch.empty()) break;  // stopping
+            if (batch.empty() && !large) break;  // stopping
             srv->budget_used += bytes;
         }
         std::vector<Done *> res;
-        run_batch_on(srv, batch, s, res);
+        if (large) {
+            res.resize(1);
+            run_large_on(srv, large, s, res[0]);
+            batch.push_back(large);
+        } else {
+            run_batch_on(srv, batch, s, res);
+        }
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             srv->budget_used -= bytes;
@@ -290,6 +494,7 @@ extern "C" sg_status sg_server_submit(sg_server *srv, const sg_job *job, uint64_
         j->rdir.assign(job->r_dir, job->r_dir + job->r_nnz);
     }
     j->est = estimate_bytes(*j);
+    j->est_tiled = estimate_tiled_bytes(*j);
     j->t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(srv->mu);

@@ -297,8 +297,9 @@ __global__ void __launch_bounds__(512) symbolic_kernel(SpArgs g, const int32_t *
 // One table of T slots: sort buffer [T/2] u64 | keys [T] i32 | counts [T] u32 | seeds [T][S] u32,
 // in shared memory (GSLICE == false) or in this block's global slice. A seed is the index of the
 // A entry (i, j) within row i; its order is the order of j, so the S smallest indices are the
-// S shared k-mers with the smallest columns (reading r4). The positions are looked up when the
-// row is written: pos_i from A's entry, pos_k from At's row j (sorted by read).
+// S shared k-mers with the smallest columns, the seeds kept (a choice that does not depend on the
+// order of the updates). The positions are looked up when the row is written: pos_i from A's
+// entry, pos_k from At's row j (sorted by read).
 constexpr uint32_t SEED_NONE = 0xFFFFFFFFu;
 
 // guessed: a table sized from a guess may hold up to 3/4 T partners, so its sort buffer has T
@@ -506,58 +507,58 @@ __global__ void __launch_bounds__(1024) numeric_kernel(SpArgs g, const int32_t *
     }
 }
 
-// ------------------------------------------------------------------ upper-triangle numeric pass
-// C is symmetric (the shared set of (i, k) is that of (k, i); C_ki's seeds are C_ik's with the two
-// positions swapped and the same rc bit), so the fused path tabulates only partners k > i: for an
-// entry (i, j) of A these are the entries of At row j after read i (At rows are sorted by read),
-// which row_work_upper_kernel locates once. That halves the products and the table work; C is
-// then assembled from the upper triangle U by writing each U row in place and its mirror into the
-// lower part of the partner's row (mirror_c_kernel), whose entries are put in column order by a
-// sort per row (sort_lower_kernel).
+// ------------------------------------------------------------------------ fused numeric pass
+// The default numeric pass. Each block takes a row i of C and walks A's row: for an entry (i, j)
+// it reads the extent of At row j and, in the upper-triangle form, finds read i in it (At rows
+// are sorted by read); the products are the At entries after i (upper) or all but i (whole
+// rows). No per-entry table of At extents is stored beforehand: the extent is read where it is
+// used, so each A entry costs one gather of At's row pointers and one of its (short) row.
+//
+// Upper-triangle form: C is symmetric (the shared set of (i, k) is that of (k, i); C_ki's seeds
+// are C_ik's with the two positions swapped and the same rc bit), so only partners k > i are
+// tabulated, which halves the table work. C is then assembled from the upper triangle U by
+// writing each U row in place and its mirror into the lower part of the partner's row
+// (mirror_c_kernel, packed records), whose entries are put in column order by a sort per row
+// (sort_lower_kernel).
 //
 // Table slot (64 bits): partner << 32 | count; empty = ~0. A product whose partner is present
 // costs one 64-bit atomicAdd on the slot; a new partner claims an empty slot and counts itself
 // with one atomicCAS. Seeds, by max_seeds: 1 -> one u32 slot kept by atomicMin; 2 -> one u64 word
 // (smallest << 32 | second smallest) replaced by atomicCAS only while the new index is smaller
 // than the second (later indices, the common case, cost one load); more -> the atomicMin chain.
+//
+// Finished rows reserve their entries in a temporary region by one atomicAdd on a cursor (row i
+// at tmp_off[i]); a row that finds the region full is listed for a retry in a grown region.
 
-// One warp per row: w_i = products of row i with partners k > i, and for every entry (i, j) the
-// start (one past read i) and length of the tail of At row j.
-__global__ void row_work_upper_kernel(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
-                                      const int64_t *__restrict__ t_rp, const int32_t *__restrict__ t_col,
-                                      int64_t n, int64_t row0, int64_t *__restrict__ work,
-                                      int64_t *__restrict__ a_beg, uint32_t *__restrict__ a_len) {
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    int64_t w = 0;
-    for (int64_t a = a_rp[row] + lane; a < a_rp[row + 1]; a += 32) {
-        const int32_t j = a_col[a];
-        int64_t lo = t_rp[j], hi = t_rp[j + 1];
-        const int64_t e = hi;
-        while (lo < hi) {  // first entry of At row j with read > this row's read
+// Extent [beg, beg + len) of the products of A entry a of row gi (read id): the tail of At row
+// j = a_col[a] after read gi (UPPER), or the whole row (gi itself is skipped by the caller).
+template <bool UPPER>
+__device__ __forceinline__ void at_extent(const SpArgs &g, int64_t a, int32_t gi, int64_t &beg, uint32_t &len) {
+    const int32_t j = g.a_col[a];
+    const int64_t b = g.t_rp[j], e = g.t_rp[j + 1];
+    int64_t lo = b;
+    if (UPPER) {
+        int64_t hi = e;
+        while (lo < hi) {  // first entry of At row j with read > gi
             const int64_t mid = (lo + hi) >> 1;
-            if (t_col[mid] <= (int32_t)(row0 + row)) lo = mid + 1; else hi = mid;
+            if (g.t_col[mid] <= gi) lo = mid + 1; else hi = mid;
         }
-        a_beg[a] = lo;
-        a_len[a] = (uint32_t)(e - lo);
-        w += e - lo;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (lane == 0) work[row] = w;
+    beg = lo;
+    len = (uint32_t)(e - lo);
 }
 
-// Calls f(k, idx) for every product of row i (k = partner, idx = index of the A entry within the
-// row), skipping k == i. Warp-cooperative: a warp takes 32 consecutive entries of A's row, scans
-// their tail lengths (32-bit) and walks the flattened products TU_U x 32 at a time, each lane
-// finding its entry by a 5-step shuffle search; the gathers of the next step are issued before the
-// current step's table updates. Stops (per warp, at a chunk boundary) once *stop is nonzero.
+// Products of row i (read id gi) with their partner counts: f(k, idx) for every product, k = the
+// partner, idx = index of the A entry within the row; k == gi is skipped. Warp-cooperative: a warp
+// takes 32 consecutive entries of A's row, finds their extents, scans their lengths (32-bit) and
+// walks the flattened products TU_U x 32 at a time, each lane finding its entry by a 5-step
+// shuffle search; the gathers of the next step are issued before the current step's table
+// updates. Stops (per warp, at a chunk boundary) once *stop is nonzero.
 constexpr int TU_U = 2;
 
-template <class F>
-__device__ __forceinline__ void enum_products(const SpArgs &g, int32_t i, int64_t r0, int64_t r1,
-                                              const volatile int *stop, F &&f) {
+template <bool UPPER, class F>
+__device__ __forceinline__ void enum_fused(const SpArgs &g, int32_t gi, int64_t r0, int64_t r1,
+                                           const volatile int *stop, F &&f) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int64_t a0 = r0 + (int64_t)warp * 32; a0 < r1; a0 += (int64_t)nwarps * 32) {
@@ -565,10 +566,7 @@ __device__ __forceinline__ void enum_products(const SpArgs &g, int32_t i, int64_
         const int64_t a = a0 + lane;
         int64_t beg = 0;
         uint32_t len = 0;
-        if (a < r1) {
-            beg = g.a_beg[a];
-            len = g.a_len[a];
-        }
+        if (a < r1) at_extent<UPPER>(g, a, gi, beg, len);
         uint32_t inc = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -580,7 +578,6 @@ __device__ __forceinline__ void enum_products(const SpArgs &g, int32_t i, int64_
         if (total == 0) continue;
         int32_t kk[TU_U];
         uint32_t ix[TU_U];
-        // step s covers products [s * 32 TU_U, (s + 1) * 32 TU_U)
         auto gather = [&](uint32_t base) {
 #pragma unroll
             for (int u = 0; u < TU_U; u++) {
@@ -594,7 +591,7 @@ __device__ __forceinline__ void enum_products(const SpArgs &g, int32_t i, int64_
                 const int64_t ob = __shfl_sync(0xffffffffu, beg, ow);
                 const uint32_t oe = __shfl_sync(0xffffffffu, excl, ow);
                 ix[u] = (uint32_t)(a0 - r0) + (uint32_t)ow;
-                kk[u] = p < total ? g.t_col[ob + (p - oe)] : i;
+                kk[u] = p < total ? g.t_col[ob + (p - oe)] : gi;
             }
         };
         gather(0);
@@ -609,7 +606,7 @@ __device__ __forceinline__ void enum_products(const SpArgs &g, int32_t i, int64_
             if (base + 32 * TU_U < total) gather(base + 32 * TU_U);
 #pragma unroll
             for (int u = 0; u < TU_U; u++)
-                if (k_cur[u] != i) f(k_cur[u], i_cur[u]);
+                if (k_cur[u] != gi) f(k_cur[u], i_cur[u]);
         }
     }
 }
@@ -635,36 +632,47 @@ __host__ __device__ inline size_t tab_bytes(int64_t T, int S) {
     return (size_t)T * 8 + tab_seed_bytes(T, S) + (size_t)(T / 2) * 8;
 }
 
-// Numeric pass over the fused path's guessed tables (GSLICE == false: shared memory, a table
-// filling past 3/4, or a row keeping more than T / 2 partners, ends the row, which is appended to
-// ovf_list) or exact-bound tables in this block's global slice (GSLICE == true: 2 min(w_i, n - 1)
-// slots, never overflows). A finished row is written to the temporary arrays at c_rp[i] and its
-// length to nnz_row[i]; with colcnt, every kept partner k also counts one entry in colcnt[k] (the
-// mirrored entries of the upper-triangle form). SK: 0, 1, 2 seeds as above; 3 = the chain.
-// FILT: as in numeric_kernel (seen-once / seen-twice filters before the table).
-template <bool GSLICE, int SK, bool FILT>
+// Where finished rows go: the temporary region (capacity cap entries, seeds slot-major with stride
+// cap), its cursor, each row's offset and length, the rows to retry, and (upper form) the number of
+// mirrored entries each row of C will receive.
+struct TmpOut {
+    int32_t *col;
+    uint32_t *cnt, *si, *sk;
+    int64_t cap;
+    unsigned long long *cursor;
+    int64_t *off, *len;
+    int32_t *retry;
+    unsigned long long *n_retry;
+    uint32_t *colcnt;
+};
+
+// The numeric pass. GSLICE == false: a guessed table in shared memory; a table filling past 3/4,
+// or keeping more than T / 2 partners, ends the row, which is appended to ovf_list. GSLICE ==
+// true: a table of the exact bound 2 min(w, np - 1) slots in this block's slice of global memory,
+// where w = wl[rb] is the row's product count (never overflows). SK: 0, 1, 2 seeds as above; 3 =
+// the chain. FILT: the seen-once / seen-twice filters (2^log2F bits each) mark the partners of
+// the row first, and only partners seen twice reach the table (min_shared >= 2).
+template <bool GSLICE, int SK, bool FILT, bool UPPER>
 __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
                                                          const unsigned long long *__restrict__ nrows_p, int log2T,
                                                          int log2F, unsigned char *__restrict__ gpool,
-                                                         int64_t slice_bytes, const int64_t *__restrict__ c_rp,
-                                                         int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
-                                                         uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
-                                                         int64_t c_nnz, const int64_t *__restrict__ work,
-                                                         int32_t *__restrict__ ovf_list,
-                                                         unsigned long long *__restrict__ ovf_count,
-                                                         int64_t *__restrict__ nnz_row, uint32_t *__restrict__ colcnt) {
+                                                         int64_t slice_bytes, const int64_t *__restrict__ wl,
+                                                         TmpOut o, int32_t *__restrict__ ovf_list,
+                                                         unsigned long long *__restrict__ ovf_count) {
     extern __shared__ __align__(16) unsigned char tab_raw[];
-    __shared__ int s_ctr, s_ins, s_ovf, s_full;
+    __shared__ int s_ctr, s_ins, s_ovf, s_full, s_fail;
+    __shared__ unsigned long long s_e0;
     const int S = g.S;
     const int64_t nrows = (int64_t)*nrows_p;
     for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
         const int32_t i = rows[rb];
         if (!SG_IN_BOUNDS(i >= 0 && i < g.n, 308, i)) continue;
+        const int32_t gi = (int32_t)(g.row0 + i);
         int lT = log2T;
         unsigned char *tb = FILT ? tab_raw + ((size_t)2 << log2F) / 8 : tab_raw;
         uint32_t *F1 = (uint32_t *)tab_raw, *F2 = F1 + ((1 << log2F) >> 5);
         if (GSLICE) {
-            const int64_t w = work[i];
+            const int64_t w = wl[rb];
             const int64_t T = pow2_at_least(2 * (w < g.np - 1 ? w : g.np - 1));
             lT = 0;
             while (lT < 31 && ((int64_t)1 << lT) < T) lT++;
@@ -698,8 +706,8 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
         auto fbit = [&](int32_t k) -> uint32_t {
             return fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
         };
-        if (FILT) {
-            enum_products(g, (int32_t)(g.row0 + i), r0, r1, nullptr, [&](int32_t k, uint32_t) {
+        if (FILT) {  // seen once -> F1, seen again -> F2 (bits are only ever set)
+            enum_fused<UPPER>(g, gi, r0, r1, nullptr, [&](int32_t k, uint32_t) {
                 const uint32_t b = fbit(k), m = 1u << (b & 31u);
                 if (((volatile uint32_t *)F2)[b >> 5] & m) return;
                 if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
@@ -707,7 +715,7 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
             __syncthreads();
         }
         const int cap = (T >> 1) + (T >> 2);
-        enum_products(g, (int32_t)(g.row0 + i), r0, r1, GSLICE ? nullptr : &s_ovf, [&](int32_t k, uint32_t idx) {
+        enum_fused<UPPER>(g, gi, r0, r1, GSLICE ? nullptr : &s_ovf, [&](int32_t k, uint32_t idx) {
             if (!GSLICE && *(volatile int *)&s_ovf) return;
             if (FILT) {
                 const uint32_t b = fbit(k);
@@ -715,16 +723,19 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
             }
             uint32_t h = hash_slot(k, lT);
             int probe = 0;
+            uint64_t w2 = 0;
             for (;;) {
                 uint64_t v = ((volatile uint64_t *)slot)[h];
                 if (v == SLOT_EMPTY) {
                     v = atomicCAS((unsigned long long *)(slot + h), SLOT_EMPTY, ((uint64_t)(uint32_t)k << 32) | 1ull);
                     if (v == SLOT_EMPTY) {
                         if (!GSLICE && atomicAdd(&s_ins, 1) >= cap) s_ovf = 1;
+                        w2 = ~0ull;  // a new partner's seeds are still empty, or being filled
                         break;
                     }
                 }
                 if ((int32_t)(v >> 32) == k) {
+                    if (SK == 2) w2 = seed2[h];  // issued before the count update; the CAS below checks it
                     atomicAdd((unsigned long long *)(slot + h), 1ull);
                     break;
                 }
@@ -737,10 +748,10 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
             if (SK == 1) {
                 atomicMin(seed1 + h, idx);
             } else if (SK == 2) {
-                uint64_t w = ((volatile uint64_t *)seed2)[h];
+                uint64_t w = w2;
                 for (;;) {
                     const uint32_t m1 = (uint32_t)(w >> 32), m2 = (uint32_t)w;
-                    if (idx >= m2) break;  // indices of one partner are distinct
+                    if (idx >= m2 && w != ~0ull) break;  // indices of one partner are distinct
                     const uint64_t nw = idx < m1 ? (((uint64_t)idx << 32) | m1) : (((uint64_t)m1 << 32) | idx);
                     const uint64_t old = atomicCAS((unsigned long long *)(seed2 + h), w, nw);
                     if (old == w) break;
@@ -781,10 +792,23 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
             continue;
         }
         const int nv = s_ctr < ob_cap ? s_ctr : ob_cap;
+        if (threadIdx.x == 0) {  // reserve the row's entries in the temporary region
+            const unsigned long long e0 = atomicAdd(o.cursor, (unsigned long long)nv);
+            s_e0 = e0;
+            s_fail = e0 + (unsigned long long)nv > (unsigned long long)o.cap;
+            if (s_fail) {
+                const unsigned long long q = atomicAdd(o.n_retry, 1ull);
+                if (SG_IN_BOUNDS((int64_t)q < g.n, 316, q)) o.retry[q] = i;
+            } else {
+                o.off[i] = (int64_t)e0;
+                o.len[i] = nv;
+            }
+        }
         int P2 = 1;
         while (P2 < nv) P2 <<= 1;
         for (int x = nv + threadIdx.x; x < P2; x += blockDim.x) obuf[x] = ~0ull;
         __syncthreads();
+        if (s_fail) continue;  // the region is full: the row is redone in a grown one
         for (int kk = 2; kk <= P2; kk <<= 1) {
             for (int jj = kk >> 1; jj > 0; jj >>= 1) {
                 for (int x = threadIdx.x; x < P2; x += blockDim.x) {
@@ -801,19 +825,15 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
                 __syncthreads();
             }
         }
-        const int64_t e0 = c_rp[i];
-        const int64_t room = c_rp[i + 1] - e0;
-        if (nv > room && threadIdx.x == 0) atomicOr(g.err, (uint32_t)DEV_OVERFLOW);
-        const int nw = nv < room ? nv : (int)room;
-        if (threadIdx.x == 0) nnz_row[i] = nw;
-        for (int q = threadIdx.x; q < nw; q += blockDim.x) {
+        const int64_t e0 = (int64_t)s_e0;
+        for (int q = threadIdx.x; q < nv; q += blockDim.x) {
             const uint64_t wq = obuf[q];
             const uint32_t x = (uint32_t)wq;
             const int32_t k = (int32_t)(wq >> 32);
             const int64_t e = e0 + q;
-            c_col[e] = k;
-            c_cnt[e] = (uint32_t)slot[x];
-            if (colcnt) atomicAdd(colcnt + k, 1u);
+            o.col[e] = k;
+            o.cnt[e] = (uint32_t)slot[x];
+            if (o.colcnt) atomicAdd(o.colcnt + k, 1u);
             for (int s = 0; s < S; s++) {
                 uint32_t sdx;
                 if (SK == 2) sdx = s == 0 ? (uint32_t)(seed2[x] >> 32) : (uint32_t)seed2[x];
@@ -822,23 +842,117 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
                 if (sdx != SEED_NONE) {
                     const int64_t a = r0 + sdx;
                     const uint32_t vi = g.a_val[a];
-                    const uint32_t vk = at_value_cv(g.t_col, g.t_val, g.a_beg[a], g.a_len[a], k);
+                    const int32_t j = g.a_col[a];
+                    const int64_t tb0 = g.t_rp[j];
+                    const uint32_t vk = at_value_cv(g.t_col, g.t_val, tb0, g.t_rp[j + 1] - tb0, k);
                     si = vi & 0x7FFFFFFFu;
                     sk = (vk & 0x7FFFFFFFu) | ((vi ^ vk) & 0x80000000u);
                 }
-                c_si[(int64_t)s * c_nnz + e] = si;
-                c_sk[(int64_t)s * c_nnz + e] = sk;
+                o.si[(int64_t)s * o.cap + e] = si;
+                o.sk[(int64_t)s * o.cap + e] = sk;
             }
         }
         __syncthreads();
     }
 }
 
+// Products of listed rows (one warp each), for the exact global-memory tables and the retry
+// region's size: wl[q] = w of row rows[q], *wmax = the largest, *room = sum of min(w / t, np - 1).
+template <bool UPPER>
+__global__ void rows_work_kernel(SpArgs g, const int32_t *__restrict__ rows, const unsigned long long *__restrict__ cnt_p,
+                                 int64_t *__restrict__ wl, unsigned long long *__restrict__ wmax,
+                                 unsigned long long *__restrict__ room) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= (int64_t)*cnt_p) return;
+    const int32_t i = rows[q];
+    if (!SG_IN_BOUNDS(i >= 0 && i < g.n, 317, i)) return;
+    const int32_t gi = (int32_t)(g.row0 + i);
+    int64_t w = 0;
+    for (int64_t a = g.a_rp[i] + lane; a < g.a_rp[i + 1]; a += 32) {
+        int64_t beg;
+        uint32_t len;
+        at_extent<UPPER>(g, a, gi, beg, len);
+        w += len;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (!UPPER) w -= g.a_rp[i + 1] - g.a_rp[i];  // the diagonal: one product per entry
+    if (lane == 0) {
+        wl[q] = w;
+        atomicMax(wmax, (unsigned long long)w);
+        const int64_t r = std::min<int64_t>(w / g.min_shared, UPPER ? g.np - 1 - gi : g.np - 1);
+        atomicAdd(room, (unsigned long long)(r > 0 ? r : 0));
+    }
+}
+
+// Sampled rows (every stride-th row, one block each): the row's A entries, and the bits set in the
+// seen-once and seen-twice filters after its products -- about its distinct partners and its
+// partners seen at least twice. sums = {sum of A entries, sum F1 bits, sum F2 bits}.
+template <bool UPPER>
+__global__ void __launch_bounds__(512) sample_fx_kernel(SpArgs g, int64_t stride, int log2F,
+                                                       unsigned long long *__restrict__ sums) {
+    extern __shared__ __align__(16) uint32_t smp_f[];
+    __shared__ unsigned long long s_c[2];
+    const int64_t i = (int64_t)blockIdx.x * stride;
+    if (i >= g.n) return;
+    const int nw = (1 << log2F) >> 5;
+    uint32_t *F1 = smp_f, *F2 = smp_f + nw;
+    for (int x = threadIdx.x; x < 2 * nw; x += blockDim.x) smp_f[x] = 0u;
+    if (threadIdx.x < 2) s_c[threadIdx.x] = 0ull;
+    __syncthreads();
+    const bool fid = g.np <= ((int64_t)1 << log2F);
+    enum_fused<UPPER>(g, (int32_t)(g.row0 + i), g.a_rp[i], g.a_rp[i + 1], nullptr, [&](int32_t k, uint32_t) {
+        const uint32_t b = fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
+        const uint32_t m = 1u << (b & 31u);
+        if (((volatile uint32_t *)F2)[b >> 5] & m) return;
+        if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
+    });
+    __syncthreads();
+    unsigned long long c1 = 0, c2 = 0;
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) {
+        c1 += __popc(F1[x]);
+        c2 += __popc(F2[x]);
+    }
+    atomicAdd(&s_c[0], c1);
+    atomicAdd(&s_c[1], c2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(sums, (unsigned long long)(g.a_rp[i + 1] - g.a_rp[i]));
+        atomicAdd(sums + 1, s_c[0]);
+        atomicAdd(sums + 2, s_c[1]);
+    }
+}
+
+// Table requests of the fused pass, from each row's number of A entries L: a guess of
+// (L * fu) >> 16 partners (fu = sampled partners per A entry, fixed point), at least 64 slots.
+// Rows with L >= fwork (fwork > 0) take the filtered pass: their guess ((L * ff) >> 16, at most
+// fcap = the largest filtered shared-memory table) goes to need_f and need is 0, else need_f is 0.
+__global__ void fx_need_kernel(const int64_t *__restrict__ a_rp, int64_t n, uint64_t fu, int64_t fwork, uint64_t ff,
+                               int64_t fcap, int64_t tcap, int64_t *__restrict__ need, int64_t *__restrict__ need_f) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t L = a_rp[i + 1] - a_rp[i];
+    need_f[i] = 0;
+    if (L <= 0) {
+        need[i] = 0;
+        return;
+    }
+    const bool filt = fwork > 0 && L >= fwork;
+    const int64_t g0 = (int64_t)(((unsigned __int128)L * (filt ? ff : fu)) >> 16);
+    int64_t guess = pow2_at_least(g0 > 64 ? g0 : 64);
+    if (guess > tcap) guess = tcap;  // no row has more partners than the table bound for all reads
+    if (filt && guess > fcap) guess = fcap;
+    (filt ? need_f : need)[i] = guess;
+    if (filt) need[i] = 0;
+}
+
 // C from the upper triangle U (rows at tmp_off, lengths nnz_row, seeds slot-major with stride
 // tmp_n). One warp per row i of U: its entries go to C row i after the lower part (colcnt[i]
 // entries), in order; each entry (i, k) also goes, mirrored (seed positions swapped, same rc bit),
-// to a free place (cursor[k], zeroed) of row k's part of the lower scratch arrays (from lrp[k]);
-// sort_lower_kernel moves those into C in column order.
+// as one packed record (col, count, then si, sk per seed slot: 2 + 2S words) to a free place
+// (cursor[k], zeroed) of row k's part of the lower record array (from lrp[k]); sort_lower_kernel
+// moves those into C in column order.
 __global__ void mirror_c_kernel(const int64_t *__restrict__ tmp_off, const int64_t *__restrict__ nnz_row,
                                 int64_t tmp_n, const int32_t *__restrict__ t_col, const uint32_t *__restrict__ t_cnt,
                                 const uint32_t *__restrict__ t_si, const uint32_t *__restrict__ t_sk, int S,
@@ -846,13 +960,14 @@ __global__ void mirror_c_kernel(const int64_t *__restrict__ tmp_off, const int64
                                 const int64_t *__restrict__ lrp, int64_t n, int64_t nnz, int64_t nnz_l,
                                 uint32_t *__restrict__ cursor, int32_t *__restrict__ c_col,
                                 uint32_t *__restrict__ c_cnt, uint32_t *__restrict__ c_si,
-                                uint32_t *__restrict__ c_sk, int32_t *__restrict__ l_col,
-                                uint32_t *__restrict__ l_cnt, uint32_t *__restrict__ l_si,
-                                uint32_t *__restrict__ l_sk) {
+                                uint32_t *__restrict__ c_sk, uint32_t *__restrict__ lrec) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
-    const int64_t src = tmp_off[row], len = nnz_row[row], dst = c_rp[row] + colcnt[row];
+    const int64_t len = nnz_row[row];
+    if (len == 0) return;
+    const int64_t src = tmp_off[row], dst = c_rp[row] + colcnt[row];
+    const int RS = 2 + 2 * S;
     for (int64_t e = lane; e < len; e += 32) {
         const int32_t k = t_col[src + e];
         const uint32_t cnt = t_cnt[src + e];
@@ -862,36 +977,35 @@ __global__ void mirror_c_kernel(const int64_t *__restrict__ tmp_off, const int64
         const uint32_t p = atomicAdd(cursor + k, 1u);
         const int64_t m = lrp[k] + p;
         if (!SG_IN_BOUNDS(p < colcnt[k] && m < nnz_l, 313, p)) continue;
-        l_col[m] = (int32_t)row;
-        l_cnt[m] = cnt;
+        uint32_t *r = lrec + m * RS;
+        r[0] = (uint32_t)row;
+        r[1] = cnt;
         for (int q = 0; q < S; q++) {
             const uint32_t si = t_si[(int64_t)q * tmp_n + src + e], sk = t_sk[(int64_t)q * tmp_n + src + e];
             c_si[(int64_t)q * nnz + dst + e] = si;
             c_sk[(int64_t)q * nnz + dst + e] = sk;
             const bool none = si == SEED_NONE;
-            l_si[(int64_t)q * nnz_l + m] = none ? SEED_NONE : (sk & 0x7FFFFFFFu);
-            l_sk[(int64_t)q * nnz_l + m] = none ? SEED_NONE : (si | (sk & 0x80000000u));
+            r[2 + 2 * q] = none ? SEED_NONE : (sk & 0x7FFFFFFFu);
+            r[3 + 2 * q] = none ? SEED_NONE : (si | (sk & 0x80000000u));
         }
     }
 }
 
-// Moves each row's lower part (colcnt[i] entries from lrp[i] in the scratch arrays, distinct
-// columns < i, in arbitrary order) into C at c_rp[i] in column order. One block per row of up to
-// lmax (<= LOWER_SMEM) entries: keys (column << 32 | offset) bitonic-sorted in shared memory, then
-// each entry copied from its offset. Longer parts are listed for lower_big_kernel.
+// Moves each row's lower part (colcnt[i] packed records from lrp[i], distinct columns < i, in
+// arbitrary order) into C at c_rp[i] in column order. One block per row of up to lmax (<=
+// LOWER_SMEM) entries: keys (column << 32 | offset) bitonic-sorted in shared memory, then each
+// record copied from its offset. Longer parts are listed for lower_big_kernel.
 constexpr int LOWER_SMEM = 4096;
 constexpr int LOWER_NT = 256;
 
-__device__ __forceinline__ void lower_copy(int64_t from, int64_t to, int S, int64_t nnz, int64_t nnz_l,
-                                           const int32_t *__restrict__ l_col, const uint32_t *__restrict__ l_cnt,
-                                           const uint32_t *__restrict__ l_si, const uint32_t *__restrict__ l_sk,
+__device__ __forceinline__ void lower_copy(const uint32_t *__restrict__ r, int64_t to, int S, int64_t nnz,
                                            int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
                                            uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk) {
-    c_col[to] = l_col[from];
-    c_cnt[to] = l_cnt[from];
+    c_col[to] = (int32_t)r[0];
+    c_cnt[to] = r[1];
     for (int q = 0; q < S; q++) {
-        c_si[(int64_t)q * nnz + to] = l_si[(int64_t)q * nnz_l + from];
-        c_sk[(int64_t)q * nnz + to] = l_sk[(int64_t)q * nnz_l + from];
+        c_si[(int64_t)q * nnz + to] = r[2 + 2 * q];
+        c_sk[(int64_t)q * nnz + to] = r[3 + 2 * q];
     }
 }
 
@@ -917,15 +1031,13 @@ __device__ __forceinline__ void block_bitonic(K *key, int64_t P2) {
 __global__ void __launch_bounds__(LOWER_NT) sort_lower_kernel(const uint32_t *__restrict__ colcnt,
                                                            const int64_t *__restrict__ lrp,
                                                            const int64_t *__restrict__ c_rp, int64_t n, int64_t nnz,
-                                                           int64_t nnz_l, int S, const int32_t *__restrict__ l_col,
-                                                           const uint32_t *__restrict__ l_cnt,
-                                                           const uint32_t *__restrict__ l_si,
-                                                           const uint32_t *__restrict__ l_sk,
+                                                           int S, const uint32_t *__restrict__ lrec,
                                                            int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
                                                            uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
                                                            unsigned long long *__restrict__ big_count,
                                                            int32_t *__restrict__ big_rows, int lmax) {
     __shared__ uint64_t key[LOWER_SMEM];
+    const int RS = 2 + 2 * S;
     for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
         const int64_t L = colcnt[row];
         if (L == 0) continue;
@@ -938,18 +1050,17 @@ __global__ void __launch_bounds__(LOWER_NT) sort_lower_kernel(const uint32_t *__
             continue;
         }
         if (L == 1) {
-            if (threadIdx.x == 0) lower_copy(lb, b, S, nnz, nnz_l, l_col, l_cnt, l_si, l_sk, c_col, c_cnt, c_si, c_sk);
+            if (threadIdx.x == 0) lower_copy(lrec + lb * RS, b, S, nnz, c_col, c_cnt, c_si, c_sk);
             continue;
         }
         int64_t P2 = 1;
         while (P2 < L) P2 <<= 1;
         for (int64_t x = threadIdx.x; x < P2; x += blockDim.x)
-            key[x] = x < L ? (((uint64_t)(uint32_t)l_col[lb + x] << 32) | (uint32_t)x) : ~0ull;
+            key[x] = x < L ? (((uint64_t)lrec[(lb + x) * RS] << 32) | (uint32_t)x) : ~0ull;
         __syncthreads();
         block_bitonic(key, P2);
         for (int64_t x = threadIdx.x; x < L; x += blockDim.x)
-            lower_copy(lb + (uint32_t)key[x], b + x, S, nnz, nnz_l, l_col, l_cnt, l_si, l_sk, c_col, c_cnt, c_si,
-                       c_sk);
+            lower_copy(lrec + (lb + (uint32_t)key[x]) * RS, b + x, S, nnz, c_col, c_cnt, c_si, c_sk);
         __syncthreads();
     }
 }
@@ -958,17 +1069,15 @@ __global__ void __launch_bounds__(LOWER_NT) sort_lower_kernel(const uint32_t *__
 // slice of global scratch (P2 = the next power of two of the length, 8 bytes each).
 __global__ void __launch_bounds__(1024) lower_big_kernel(const uint32_t *__restrict__ colcnt,
                                                        const int64_t *__restrict__ lrp,
-                                                       const int64_t *__restrict__ c_rp, int64_t nnz, int64_t nnz_l,
-                                                       int S, const int32_t *__restrict__ rows,
+                                                       const int64_t *__restrict__ c_rp, int64_t nnz, int S,
+                                                       const int32_t *__restrict__ rows,
                                                        const unsigned long long *__restrict__ nrows_p,
                                                        uint64_t *__restrict__ gpool, int64_t slice,
-                                                       const int32_t *__restrict__ l_col,
-                                                       const uint32_t *__restrict__ l_cnt,
-                                                       const uint32_t *__restrict__ l_si,
-                                                       const uint32_t *__restrict__ l_sk, int32_t *__restrict__ c_col,
+                                                       const uint32_t *__restrict__ lrec, int32_t *__restrict__ c_col,
                                                        uint32_t *__restrict__ c_cnt, uint32_t *__restrict__ c_si,
                                                        uint32_t *__restrict__ c_sk) {
     const int64_t nrows = (int64_t)*nrows_p;
+    const int RS = 2 + 2 * S;
     uint64_t *key = gpool + (int64_t)blockIdx.x * slice;
     for (int64_t rb = blockIdx.x; rb < nrows; rb += gridDim.x) {
         const int32_t row = rows[rb];
@@ -977,12 +1086,11 @@ __global__ void __launch_bounds__(1024) lower_big_kernel(const uint32_t *__restr
         while (P2 < L) P2 <<= 1;
         if (!SG_IN_BOUNDS(P2 <= slice, 315, L)) continue;
         for (int64_t x = threadIdx.x; x < P2; x += blockDim.x)
-            key[x] = x < L ? (((uint64_t)(uint32_t)l_col[lb + x] << 32) | (uint32_t)x) : ~0ull;
+            key[x] = x < L ? (((uint64_t)lrec[(lb + x) * RS] << 32) | (uint32_t)x) : ~0ull;
         __syncthreads();
         block_bitonic(key, P2);
         for (int64_t x = threadIdx.x; x < L; x += blockDim.x)
-            lower_copy(lb + (uint32_t)key[x], b + x, S, nnz, nnz_l, l_col, l_cnt, l_si, l_sk, c_col, c_cnt, c_si,
-                       c_sk);
+            lower_copy(lrec + (lb + (uint32_t)key[x]) * RS, b + x, S, nnz, c_col, c_cnt, c_si, c_sk);
         __syncthreads();
     }
 }
@@ -995,73 +1103,6 @@ __global__ void c_rowlen_kernel(const int64_t *__restrict__ nnz_row, const uint3
 }
 
 static inline int64_t blocks_for(int64_t n, int nt) { return (n + nt - 1) / nt; }
-
-// Sampled rows (every stride-th row, one block each): the products w, and the bits set in the
-// seen-once and seen-twice filters after the row's products -- about its distinct partners and
-// its partners seen at least twice. sums = {sum w, sum F1 bits, sum F2 bits}.
-__global__ void __launch_bounds__(512) sample_kernel(SpArgs g, const int64_t *__restrict__ work, int64_t stride,
-                                                    int log2F, unsigned long long *__restrict__ sums) {
-    extern __shared__ __align__(16) uint32_t smp_f[];
-    __shared__ unsigned long long s_c[2];
-    const int64_t i = (int64_t)blockIdx.x * stride;
-    if (i >= g.n) return;
-    const int nw = (1 << log2F) >> 5;
-    uint32_t *F1 = smp_f, *F2 = smp_f + nw;
-    for (int x = threadIdx.x; x < 2 * nw; x += blockDim.x) smp_f[x] = 0u;
-    if (threadIdx.x < 2) s_c[threadIdx.x] = 0ull;
-    __syncthreads();
-    const bool fid = g.np <= ((int64_t)1 << log2F);
-    for_each_product<false>(g, (int32_t)(g.row0 + i), g.a_rp[i], g.a_rp[i + 1], nullptr, [&](int32_t k, uint32_t, int64_t) {
-        const uint32_t b = fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
-        const uint32_t m = 1u << (b & 31u);
-        if (((volatile uint32_t *)F2)[b >> 5] & m) return;
-        if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
-    });
-    __syncthreads();
-    unsigned long long c1 = 0, c2 = 0;
-    for (int x = threadIdx.x; x < nw; x += blockDim.x) {
-        c1 += __popc(F1[x]);
-        c2 += __popc(F2[x]);
-    }
-    atomicAdd(&s_c[0], c1);
-    atomicAdd(&s_c[1], c2);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(sums, (unsigned long long)(work[i] > 0 ? work[i] : 0));
-        atomicAdd(sums + 1, s_c[0]);
-        atomicAdd(sums + 2, s_c[1]);
-    }
-}
-
-// Fused path: guessed table size and the row's output room min(w / t, n - 1). The guess is
-// (w * fu) >> 16 for a sampled partner ratio fu (fixed point), or w >> shift without a sample.
-// Rows with w >= fwork (fwork > 0) take the filtered pass: their guess ((w * ff) >> 16, or
-// w >> fshift, at most fcap = the largest filtered shared-memory table) goes to need_f and need is
-// 0, else need_f is 0.
-__global__ void fused_need_kernel(const int64_t *__restrict__ work, int64_t n, int shift, uint64_t fu, uint32_t t,
-                                  int64_t fwork, int fshift, uint64_t ff, int64_t fcap, int upper, int64_t np,
-                                  int64_t row0, int64_t *__restrict__ need, int64_t *__restrict__ need_f,
-                                  int64_t *__restrict__ room) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t w = work[i];
-    need_f[i] = 0;
-    if (w <= 0) {
-        need[i] = 0;
-        room[i] = 0;
-        return;
-    }
-    const bool filt = fwork > 0 && w >= fwork;
-    const uint64_t mul = filt ? ff : fu;
-    const int64_t g0 = mul ? (int64_t)(((unsigned __int128)w * mul) >> 16) : (w >> (filt ? fshift : shift));
-    const int64_t exact = pow2_at_least(2 * (w < np - 1 ? w : np - 1));
-    int64_t guess = pow2_at_least(g0 > 64 ? g0 : 64);
-    if (filt && guess > fcap) guess = fcap;  // kept partners are few: try the largest table first
-    (filt ? need_f : need)[i] = guess < exact ? guess : exact;
-    if (filt) need[i] = 0;
-    const int64_t r = w / t, rmax = upper ? np - 1 - (row0 + i) : np - 1;  // upper: partners k > i only
-    room[i] = r < rmax ? r : rmax;
-}
 
 // Fused path: copies each row's entries from the temporary arrays (row i at tmp_off[i], seeds
 // slot-major with stride tmp_n) to C (row i at c_rp[i], stride nnz). One warp per row.
@@ -1101,6 +1142,18 @@ static int pick_numeric_threads(int log2T, bool filtered) {
     return filtered ? (log2T <= 11 ? 256 : 512) : pick_threads(log2T);
 }
 
+// threads per block of the fused pass: enough warps that the blocks shared memory lets reside on
+// one SM bring about spgemm_tab_warps warps (64 = the SM's limit) between them
+static int pick_tab_threads(int log2T, int S, bool filtered) {
+    const int64_t want = tune("spgemm_tab_warps");
+    if (want <= 0) return pick_numeric_threads(log2T, filtered);
+    const size_t bytes = tab_bytes((int64_t)1 << log2T, S) + (filtered ? (size_t)32 << 10 : 0);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(32, (int64_t)((227u << 10) / bytes)));
+    int64_t threads = 64;
+    while (threads < 1024 && blocks * (threads / 32) < want) threads <<= 1;
+    return (int)threads;
+}
+
 // Launch names by table size, so that per-kernel timing separates the classes.
 static const char *const SYM_NAMES[] = {"spgemm_symbolic_t64", "spgemm_symbolic_t128", "spgemm_symbolic_t256",
                                         "spgemm_symbolic_t512", "spgemm_symbolic_t1k", "spgemm_symbolic_t2k",
@@ -1112,18 +1165,6 @@ static const char *const FIL_NAMES[] = {"spgemm_numeric_f64", "spgemm_numeric_f1
                                         "spgemm_numeric_f512", "spgemm_numeric_f1k", "spgemm_numeric_f2k",
                                         "spgemm_numeric_f4k", "spgemm_numeric_f8k", "spgemm_numeric_f16k"};
 
-// Largest row work: sizes the global-memory tables of the redo pass.
-__global__ void work_max_kernel(const int64_t *__restrict__ work, int64_t n, unsigned long long *__restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t w = i < n ? work[i] : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const int64_t y = __shfl_xor_sync(0xffffffffu, w, o);
-        w = y > w ? y : w;
-    }
-    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(out, (unsigned long long)w);
-}
-
 sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_shared, int S,
                        sg_overlap_csr *C, cudaStream_t s, Scratch &sc, const OverlapOpts &opt) {
     const int64_t n = A->n_rows, np = At->n_cols;
@@ -1134,7 +1175,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     int64_t *need = sc.get<int64_t>(n + 1);
     int64_t *nnz_row = sc.get<int64_t>(n + 1);
     int64_t *dist = sc.get<int64_t>(n + 1);
-    unsigned long long *counts = sc.get<unsigned long long>(4 * NCNT + 6);
+    unsigned long long *counts = sc.get<unsigned long long>(4 * NCNT + 10);
     int32_t *lists = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
     int32_t *ovf = sc.get<int32_t>(2 * (n + 1));  // overflow list | unused list of the re-run
     if (!err || !work || !need || !nnz_row || !dist || !counts || !lists || !ovf) return SG_ERR_OOM;
@@ -1143,27 +1184,15 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     unsigned long long *fz_counts = counts + 2 * NCNT + 1, *fz_ovf = fz_counts + SP_NCLS + 1;
     unsigned long long *ff_counts = counts + 3 * NCNT + 1;  // filtered rows' classes + global class
     SG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (4 * NCNT + 6) * sizeof(unsigned long long), s));
+    SG_CUDA_TRY(cudaMemsetAsync(counts, 0, (4 * NCNT + 10) * sizeof(unsigned long long), s));
     SG_CUDA_TRY(cudaMemsetAsync(nnz_row, 0, (n + 1) * sizeof(int64_t), s));
     SG_CUDA_TRY(cudaMemsetAsync(dist, 0, (n + 1) * sizeof(int64_t), s));
-    int64_t *a_beg = sc.get<int64_t>(A->nnz + 1);
-    uint32_t *a_len = sc.get<uint32_t>(A->nnz + 1);
-    if (!a_beg || !a_len) return SG_ERR_OOM;
     uint64_t *t_pair = nullptr;  // only the two-pass kernels read At as (val << 32 | col) pairs
-    SpArgs g{A->row_ptr, A->col, A->val, At->row_ptr, At->col, At->val, a_beg, a_len, t_pair,
+    SpArgs g{A->row_ptr, A->col, A->val, At->row_ptr, At->col, At->val, nullptr, nullptr, t_pair,
              n, min_shared, S, err, np, opt.row0};
     const bool fused = opt.whole_rows || tune("spgemm_fused") != 0;
     const bool upper = fused && !opt.whole_rows && tune("spgemm_upper") != 0;
-    unsigned long long *wmax_d = counts + 4 * NCNT + 5;
     std::optional<StageScope> stage;
-    stage.emplace("SpGEMMSymbolic", s);
-    if (upper)
-        SG_LAUNCH("row_work", row_work_upper_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col,
-                  At->row_ptr, At->col, n, opt.row0, work, a_beg, a_len);
-    else
-        SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr,
-                  n, work, a_beg, a_len);
-    SG_LAUNCH("work_max", work_max_kernel, blocks_for(n, 256), 256, 0, s, (const int64_t *)work, n, wmax_d);
     const int nsm = sm_count();
     const int grid = (int)(nsm * tune("spgemm_blocks_per_sm"));
     // numeric (two-pass form): one class per table size from 2^6 while table and sort buffer fit in 160 KB
@@ -1180,9 +1209,9 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         fz.log2T[fz.ncls] = SP_MINLOG + fz.ncls;
         fz.ncls++;
     }
-    // filtered rows (fused path): two filters of 2^log2F bits, one bit per read while n fits
+    // filtered rows (fused path): two filters of 2^log2F bits, one bit per read while np fits
     int log2F = 10;
-    while (log2F < (int)tune("spgemm_filter_log2") && ((int64_t)1 << log2F) < n) log2F++;
+    while (log2F < (int)tune("spgemm_filter_log2") && ((int64_t)1 << log2F) < np) log2F++;
     const size_t fbytes = ((size_t)2 << log2F) / 8;
     Classes ff{};
     ff.ncls = 0;
@@ -1190,114 +1219,151 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         ff.log2T[ff.ncls] = SP_MINLOG + ff.ncls;
         ff.ncls++;
     }
-    // global-memory tables of the exact bound 2 min(w, np - 1) (rows beyond shared memory), sized
-    // for the largest row; the fused pass's pool may be capped by opt.gmem_bytes
+    // global-memory tables of the exact bound 2 min(w, np - 1) for the two-pass form's largest row
     const int64_t Tmax = pow2_at_least(2 * (np > 1 ? np - 1 : 1));
     const int64_t gslice_bytes = (int64_t)((num_table_bytes(Tmax, S) + 255) & ~(size_t)255);
-    int64_t tslice_bytes = 0;
     const int SK = S <= 2 ? S : 3;
 
     // ---- fused path (no symbolic pass): guessed tables, rows written to a temporary region
     if (fused) {
         stage.emplace("SpGEMMNumeric", s);
-        int64_t *room = sc.get<int64_t>(n + 1), *tmp_off = sc.get<int64_t>(n + 1), *need_f = sc.get<int64_t>(n + 1);
+        int64_t *tmp_off = sc.get<int64_t>(n + 1), *need_f = sc.get<int64_t>(n + 1), *lrp = sc.get<int64_t>(n + 1);
         int32_t *lists_f = sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1));
+        int32_t *retry = sc.get<int32_t>(n + 1);
         uint32_t *colcnt = upper ? sc.get<uint32_t>(n + 1) : nullptr;
-        if (!room || !tmp_off || !need_f || !lists_f || (upper && !colcnt)) return SG_ERR_OOM;
+        if (!tmp_off || !need_f || !lrp || !lists_f || !retry || (upper && !colcnt)) return SG_ERR_OOM;
         if (upper) SG_CUDA_TRY(cudaMemsetAsync(colcnt, 0, (n + 1) * sizeof(uint32_t), s));
-        // filtered rows: mode 2 always, mode 1 when the sample finds under half the partners recur
+        // counters after the class counts (4 NCNT + 1 of them), all zeroed above
+        unsigned long long *tcur = counts + 4 * NCNT + 1;     // temporary region cursor
+        unsigned long long *n_retry = counts + 4 * NCNT + 2;  // rows that found the region full
+        unsigned long long *gw = counts + 4 * NCNT + 3;       // {largest w, room} of listed rows (2)
+        unsigned long long *big_count = counts + 4 * NCNT + 5;  // long mirrored parts
+        unsigned long long *sums = counts + 4 * NCNT + 6;     // sample sums (3)
+        // sampled rows: distinct partners (r1) and partners seen at least twice (r2) per A entry
         const int64_t fmode = tune("spgemm_filter_mode");
         int64_t fwork = min_shared >= 2 && ff.ncls > 0 && fmode > 0 ? tune("spgemm_filter_work") : 0;
-        // table guesses from a sample of rows (large inputs only): partners per product, r1 distinct
-        // and r2 seen at least twice
-        uint64_t fu = 0, ffq = 0;
-        const int64_t nsamp = A->nnz >= tune("spgemm_sample_min_nnz") ? tune("spgemm_sample_rows") : 0;
-        bool recur = true;  // without a sample, mode 1 does not filter
-        if (nsamp > 0 && n > 0) {
+        double r1 = 0.0, r2 = 0.0;
+        const int64_t nsamp = tune("spgemm_sample_rows");
+        if (nsamp > 0 && n > 0 && A->nnz > 0) {
             const int64_t stride = n > nsamp ? n / nsamp : 1;
             const int64_t nb = (n + stride - 1) / stride;
-            unsigned long long *sums = counts + 4 * NCNT + 1;  // zeroed with the counters
-            SG_CUDA_TRY(ensure_smem(sample_kernel, fbytes));
-            SG_LAUNCH("spgemm_sample", sample_kernel, nb, 256, fbytes, s, g, (const int64_t *)work, stride, log2F,
-                      sums);
+            if (upper) {
+                SG_CUDA_TRY(ensure_smem(sample_fx_kernel<true>, fbytes));
+                SG_LAUNCH("spgemm_sample", sample_fx_kernel<true>, nb, 256, fbytes, s, g, stride, log2F, sums);
+            } else {
+                SG_CUDA_TRY(ensure_smem(sample_fx_kernel<false>, fbytes));
+                SG_LAUNCH("spgemm_sample", sample_fx_kernel<false>, nb, 256, fbytes, s, g, stride, log2F, sums);
+            }
             unsigned long long h[3] = {0, 0, 0};
             SG_CUDA_TRY(read_back(h, sums, sizeof(h), s));
             if (h[0] > 0) {
-                const double pct = (double)tune("spgemm_guess_pct") / 100.0;
-                const double r1 = (double)h[1] / (double)h[0], r2 = (double)h[2] / (double)h[0];
-                fu = (uint64_t)(pct * r1 * 65536.0) + 1;
-                ffq = (uint64_t)(pct * r2 * 65536.0) + 1;
-                recur = r1 < 2.0 * r2;  // most partners recur: the filter would keep nearly all
+                r1 = (double)h[1] / (double)h[0];
+                r2 = (double)h[2] / (double)h[0];
             }
         }
+        if (r1 == 0.0) r1 = r2 = 1.0;  // no sample: a partner per A entry
+        const bool recur = r1 < 2.0 * r2;  // most partners recur: the filter would keep nearly all
         if (fmode == 1 && recur) fwork = 0;
-        SG_LAUNCH("fused_need", fused_need_kernel, blocks_for(n, NT), NT, 0, s, (const int64_t *)work, n,
-                  (int)tune("num_guess_shift"), fu, min_shared, fwork, (int)tune("spgemm_filter_shift"), ffq,
-                  ff.ncls > 0 ? (int64_t)1 << ff.log2T[ff.ncls - 1] : (int64_t)64, (int)upper, np, opt.row0, need,
-                  need_f, room);
-        SG_TRY(exclusive_scan<int64_t>(room, tmp_off, n, s, err));
+        const double pct = (double)tune("spgemm_guess_pct") / 100.0;
+        const uint64_t fu = (uint64_t)(pct * r1 * 65536.0) + 1, ffq = (uint64_t)(pct * r2 * 65536.0) + 1;
+        SG_LAUNCH("fused_need", fx_need_kernel, blocks_for(n, NT), NT, 0, s, A->row_ptr, n, fu, fwork, ffq,
+                  ff.ncls > 0 ? (int64_t)1 << ff.log2T[ff.ncls - 1] : (int64_t)64, Tmax, need, need_f);
         SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need, n, fz, fz_counts, lists);
         if (fwork)
             SG_LAUNCH("classify", classify_kernel, blocks_for(n, NT), NT, 0, s, need_f, n, ff, ff_counts, lists_f);
         unsigned long long h_fz[NCNT], h_ff[NCNT];
-        int64_t tmp_n = 0;
         uint32_t herr = 0;
-        unsigned long long wmax = 0;
         SG_CUDA_TRY(cudaMemcpyAsync(h_ff, ff_counts, sizeof(h_ff), cudaMemcpyDeviceToHost, s));
         SG_CUDA_TRY(cudaMemcpyAsync(h_fz, fz_counts, sizeof(h_fz), cudaMemcpyDeviceToHost, s));
-        SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        SG_CUDA_TRY(cudaMemcpyAsync(&wmax, wmax_d, sizeof(wmax), cudaMemcpyDeviceToHost, s));
-        SG_CUDA_TRY(read_back(&tmp_n, tmp_off + n, sizeof(int64_t), s));
+        SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));
         if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
-        tslice_bytes = (int64_t)((tab_bytes(pow2_at_least(2 * std::min<int64_t>((int64_t)wmax, np > 1 ? np - 1 : 1)), S) +
-                                  255) & ~(size_t)255);
-        const double tmp_bytes = (double)tmp_n * (8.0 + 8.0 * S);
-        // the region is reserved, mostly untouched: at most half of what the device can still give
-        // (a row range was sized for its budget before the call)
+        // the temporary region: the sampled kept partners per A entry (r2 for min_shared >= 2, r1
+        // for 1) times nnz(A), with room to spare; rows that find it full are redone in a grown one
+        int64_t cap = opt.tmp_cap;
+        if (cap <= 0) {
+            const double kept = (min_shared >= 2 ? r2 : r1) * (double)A->nnz + 4.0 * (double)n;
+            cap = (int64_t)((double)tune("spgemm_tmp_pct") / 100.0 * kept) + 64;
+        }
+        const double tmp_bytes = (double)cap * (8.0 + 8.0 * S);
+        // at most half of what the device can still give (a row range was sized for its budget)
         const double avail = (double)device_bytes_available();
         if (opt.whole_rows ||
             (tmp_bytes <= (double)tune("spgemm_fused_max_mb") * 1048576.0 && tmp_bytes <= 0.5 * avail)) {
-            int32_t *t_col = sc.get<int32_t>(tmp_n + 1);
-            uint32_t *t_cnt = sc.get<uint32_t>(tmp_n + 1);
-            uint32_t *t_si = sc.get<uint32_t>((size_t)S * tmp_n + 1), *t_sk = sc.get<uint32_t>((size_t)S * tmp_n + 1);
-            if (!t_col || !t_cnt || !t_si || !t_sk) return SG_ERR_OOM;
-            // one launch per table class; the seed form (SK) and the filter pick the instantiation
+            TmpOut o{};
+            o.col = sc.get<int32_t>(cap + 1);
+            o.cnt = sc.get<uint32_t>(cap + 1);
+            o.si = sc.get<uint32_t>((size_t)S * cap + 1);
+            o.sk = sc.get<uint32_t>((size_t)S * cap + 1);
+            if (!o.col || !o.cnt || !o.si || !o.sk) return SG_ERR_OOM;
+            o.cap = cap;
+            o.cursor = tcur;
+            o.off = tmp_off;
+            o.len = nnz_row;
+            o.retry = retry;
+            o.n_retry = n_retry;
+            o.colcnt = colcnt;
+            // one launch per table class; the seed form (SK), the filter and the form pick the kernel
             auto launch_tab = [&](bool filt, int log2T, const int32_t *rl, const unsigned long long *cnt,
                                   const char *name) -> sg_status {
                 const size_t sm = tab_bytes((int64_t)1 << log2T, S) + (filt ? fbytes : 0);
-                const int nt = pick_numeric_threads(log2T, filt);
-#define SG_TAB_LAUNCH(SKV, FV)                                                                              \
+                const int nt = pick_tab_threads(log2T, S, filt);
+#define SG_TAB_LAUNCH(SKV, FV, UV)                                                                          \
     do {                                                                                                    \
-        SG_CUDA_TRY(ensure_smem(tab_numeric_kernel<false, SKV, FV>, sm));                                   \
-        SG_LAUNCH(name, (tab_numeric_kernel<false, SKV, FV>), grid, nt, sm, s, g, rl, cnt, log2T, log2F,    \
-                  (unsigned char *)nullptr, (int64_t)0, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, \
-                  tmp_n, (const int64_t *)work, ovf, fz_ovf, nnz_row, colcnt);                              \
+        SG_CUDA_TRY(ensure_smem(tab_numeric_kernel<false, SKV, FV, UV>, sm));                               \
+        SG_LAUNCH(name, (tab_numeric_kernel<false, SKV, FV, UV>), grid, nt, sm, s, g, rl, cnt, log2T, log2F, \
+                  (unsigned char *)nullptr, (int64_t)0, (const int64_t *)nullptr, o, ovf, fz_ovf);         \
     } while (0)
-                if (filt) {
-                    if (SK == 0) SG_TAB_LAUNCH(0, true);
-                    else if (SK == 1) SG_TAB_LAUNCH(1, true);
-                    else if (SK == 2) SG_TAB_LAUNCH(2, true);
-                    else SG_TAB_LAUNCH(3, true);
-                } else {
-                    if (SK == 0) SG_TAB_LAUNCH(0, false);
-                    else if (SK == 1) SG_TAB_LAUNCH(1, false);
-                    else if (SK == 2) SG_TAB_LAUNCH(2, false);
-                    else SG_TAB_LAUNCH(3, false);
-                }
+#define SG_TAB_SK(FV, UV)                      \
+    do {                                       \
+        if (SK == 0) SG_TAB_LAUNCH(0, FV, UV); \
+        else if (SK == 1) SG_TAB_LAUNCH(1, FV, UV); \
+        else if (SK == 2) SG_TAB_LAUNCH(2, FV, UV); \
+        else SG_TAB_LAUNCH(3, FV, UV);         \
+    } while (0)
+                if (filt && upper) SG_TAB_SK(true, true);
+                else if (filt) SG_TAB_SK(true, false);
+                else if (upper) SG_TAB_SK(false, true);
+                else SG_TAB_SK(false, false);
+#undef SG_TAB_SK
 #undef SG_TAB_LAUNCH
                 return SG_OK;
             };
-            auto launch_gtab = [&](const int32_t *rl, const unsigned long long *cnt, int ggrid,
-                                   unsigned char *pool) -> sg_status {
-#define SG_GTAB_LAUNCH(SKV)                                                                                   \
-    SG_LAUNCH("spgemm_numeric_gmem", (tab_numeric_kernel<true, SKV, false>), ggrid, 512, 0, s, g, rl, cnt, 0, \
-              0, pool, tslice_bytes, (const int64_t *)tmp_off, t_col, t_cnt, t_si, t_sk, tmp_n,               \
-              (const int64_t *)work, ovf + n + 1, unused, nnz_row, colcnt)
-                if (SK == 0) SG_GTAB_LAUNCH(0);
-                else if (SK == 1) SG_GTAB_LAUNCH(1);
-                else if (SK == 2) SG_GTAB_LAUNCH(2);
-                else SG_GTAB_LAUNCH(3);
+            // rows in exact global-memory tables: their products first (table sizes), then the pass
+            int64_t *wl = sc.get<int64_t>(n + 1);
+            if (!wl) return SG_ERR_OOM;
+            auto launch_gtab = [&](const int32_t *rl, const unsigned long long *cnt, unsigned long long nrows)
+                -> sg_status {
+                SG_CUDA_TRY(cudaMemsetAsync(gw, 0, 2 * sizeof(unsigned long long), s));
+                if (upper)
+                    SG_LAUNCH("spgemm_rows_work", rows_work_kernel<true>, blocks_for((int64_t)nrows * 32, 256), 256, 0,
+                              s, g, rl, cnt, wl, gw, gw + 1);
+                else
+                    SG_LAUNCH("spgemm_rows_work", rows_work_kernel<false>, blocks_for((int64_t)nrows * 32, 256), 256,
+                              0, s, g, rl, cnt, wl, gw, gw + 1);
+                unsigned long long wmax = 0;
+                SG_CUDA_TRY(read_back(&wmax, gw, sizeof(wmax), s));
+                const int64_t T = pow2_at_least(2 * std::min<int64_t>(std::max<int64_t>((int64_t)wmax, 1),
+                                                                      np > 1 ? np - 1 : 1));
+                const int64_t slice = (int64_t)((tab_bytes(T, S) + 255) & ~(size_t)255);
+                int ggrid = (int)std::min<unsigned long long>(nrows, (unsigned long long)nsm * 2);
+                if (opt.gmem_bytes) ggrid = (int)std::max<int64_t>(1, std::min<int64_t>(ggrid, (int64_t)opt.gmem_bytes / slice));
+                unsigned char *pool = sc.get<unsigned char>((size_t)slice * ggrid);
+                if (!pool) return SG_ERR_OOM;
+#define SG_GTAB_LAUNCH(SKV, UV)                                                                                \
+    SG_LAUNCH("spgemm_numeric_gmem", (tab_numeric_kernel<true, SKV, false, UV>), ggrid, 512, 0, s, g, rl, cnt, \
+              0, 0, pool, slice, (const int64_t *)wl, o, ovf + n + 1, unused)
+#define SG_GTAB_SK(UV)                     \
+    do {                                   \
+        if (SK == 0) SG_GTAB_LAUNCH(0, UV); \
+        else if (SK == 1) SG_GTAB_LAUNCH(1, UV); \
+        else if (SK == 2) SG_GTAB_LAUNCH(2, UV); \
+        else SG_GTAB_LAUNCH(3, UV);        \
+    } while (0)
+                if (upper) SG_GTAB_SK(true);
+                else SG_GTAB_SK(false);
+#undef SG_GTAB_SK
 #undef SG_GTAB_LAUNCH
+                sc.release(pool);
                 return SG_OK;
             };
             for (int c = 0; c < fz.ncls; c++) {
@@ -1305,7 +1371,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 SG_TRY(launch_tab(false, fz.log2T[c], lists + (int64_t)c * n, fz_counts + c,
                                   NUM_NAMES[fz.log2T[c] - SP_MINLOG]));
             }
-            for (int c = 0; fwork && c < ff.ncls; c++) {  // rows with many products: filtered first
+            for (int c = 0; fwork && c < ff.ncls; c++) {  // rows with many entries: filtered first
                 if (!h_ff[c]) continue;
                 SG_TRY(launch_tab(true, ff.log2T[c], lists_f + (int64_t)c * n, ff_counts + c,
                                   FIL_NAMES[ff.log2T[c] - SP_MINLOG]));
@@ -1313,18 +1379,56 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
             unsigned long long n_ovf = 0;
             SG_CUDA_TRY(read_back(&n_ovf, fz_ovf, sizeof(n_ovf), s));
             const unsigned long long n_big = h_fz[fz.ncls], n_big_f = fwork ? h_ff[ff.ncls] : 0;
-            if (n_big + n_big_f + n_ovf > 0) {
-                unsigned long long rows_g = n_big > n_ovf ? n_big : n_ovf;
-                rows_g = rows_g > n_big_f ? rows_g : n_big_f;
-                int ggrid = (int)(rows_g < (unsigned long long)nsm * 2 ? rows_g : (unsigned long long)nsm * 2);
-                if (opt.gmem_bytes)
-                    ggrid = (int)std::max<int64_t>(1, std::min<int64_t>(ggrid, (int64_t)opt.gmem_bytes / tslice_bytes));
-                unsigned char *pool = sc.get<unsigned char>((size_t)tslice_bytes * ggrid);
-                if (!pool) return SG_ERR_OOM;
-                if (n_big) SG_TRY(launch_gtab(lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, ggrid, pool));
-                if (n_big_f) SG_TRY(launch_gtab(lists_f + (int64_t)ff.ncls * n, ff_counts + ff.ncls, ggrid, pool));
-                if (n_ovf) SG_TRY(launch_gtab((const int32_t *)ovf, fz_ovf, ggrid, pool));
-                sc.release(pool);
+            if (n_big) SG_TRY(launch_gtab(lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, n_big));
+            if (n_big_f) SG_TRY(launch_gtab(lists_f + (int64_t)ff.ncls * n, ff_counts + ff.ncls, n_big_f));
+            if (n_ovf) SG_TRY(launch_gtab((const int32_t *)ovf, fz_ovf, n_ovf));
+            // rows that found the region full: grow it by their exact room and redo them
+            unsigned long long n_rt = 0;
+            SG_CUDA_TRY(read_back(&n_rt, n_retry, sizeof(n_rt), s));
+            if (n_rt) {
+                int32_t *rl = sc.get<int32_t>(n_rt + 1);
+                unsigned long long *rc = sc.get<unsigned long long>(1);
+                if (!rl || !rc) return SG_ERR_OOM;
+                SG_CUDA_TRY(cudaMemcpyAsync(rl, retry, n_rt * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+                SG_CUDA_TRY(cudaMemcpyAsync(rc, n_retry, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+                SG_CUDA_TRY(cudaMemsetAsync(gw, 0, 2 * sizeof(unsigned long long), s));
+                if (upper)
+                    SG_LAUNCH("spgemm_rows_work", rows_work_kernel<true>, blocks_for((int64_t)n_rt * 32, 256), 256, 0,
+                              s, g, (const int32_t *)rl, (const unsigned long long *)rc, wl, gw, gw + 1);
+                else
+                    SG_LAUNCH("spgemm_rows_work", rows_work_kernel<false>, blocks_for((int64_t)n_rt * 32, 256), 256,
+                              0, s, g, (const int32_t *)rl, (const unsigned long long *)rc, wl, gw, gw + 1);
+                unsigned long long hroom = 0;
+                SG_CUDA_TRY(read_back(&hroom, gw + 1, sizeof(hroom), s));
+                TmpOut o2 = o;
+                o2.cap = cap + (int64_t)hroom;
+                o2.col = sc.get<int32_t>(o2.cap + 1);
+                o2.cnt = sc.get<uint32_t>(o2.cap + 1);
+                o2.si = sc.get<uint32_t>((size_t)S * o2.cap + 1);
+                o2.sk = sc.get<uint32_t>((size_t)S * o2.cap + 1);
+                if (!o2.col || !o2.cnt || !o2.si || !o2.sk) return SG_ERR_OOM;
+                SG_CUDA_TRY(cudaMemcpyAsync(o2.col, o.col, cap * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+                SG_CUDA_TRY(cudaMemcpyAsync(o2.cnt, o.cnt, cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+                for (int q = 0; q < S; q++) {
+                    SG_CUDA_TRY(cudaMemcpyAsync(o2.si + (int64_t)q * o2.cap, o.si + (int64_t)q * cap,
+                                                cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+                    SG_CUDA_TRY(cudaMemcpyAsync(o2.sk + (int64_t)q * o2.cap, o.sk + (int64_t)q * cap,
+                                                cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+                }
+                for (const void *p : {(const void *)o.col, (const void *)o.cnt, (const void *)o.si, (const void *)o.sk})
+                    sc.release(p);
+                const unsigned long long c0 = (unsigned long long)cap;  // successful rows lie below cap
+                SG_CUDA_TRY(cudaMemcpyAsync(tcur, &c0, sizeof(c0), cudaMemcpyHostToDevice, s));
+                SG_CUDA_TRY(cudaMemsetAsync(n_retry, 0, sizeof(unsigned long long), s));
+                o = o2;
+                cap = o2.cap;
+                SG_TRY(launch_gtab((const int32_t *)rl, (const unsigned long long *)rc, n_rt));
+                unsigned long long n_rt2 = 0;
+                SG_CUDA_TRY(read_back(&n_rt2, n_retry, sizeof(n_rt2), s));
+                if (n_rt2) {
+                    set_error("overlap_spgemm: %llu rows did not fit the grown region (internal error)", n_rt2);
+                    return SG_ERR_OVERFLOW;
+                }
             }
             if (debug_record_classes()) {  // test hook: which launch handled each row
                 std::vector<int32_t> &rec = debug_classes();
@@ -1366,35 +1470,30 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
             SG_ALLOC(C->seed_k, uint32_t, (int64_t)S * nnz, s);
             if (!upper) {
                 SG_LAUNCH("compact_c", compact_c_kernel, blocks_for(n * 32, 256), 256, 0, s, (const int64_t *)tmp_off,
-                          tmp_n, (const int32_t *)t_col, (const uint32_t *)t_cnt, (const uint32_t *)t_si,
-                          (const uint32_t *)t_sk, S, (const int64_t *)C->row_ptr, n, nnz, C->col, C->count,
+                          cap, (const int32_t *)o.col, (const uint32_t *)o.cnt, (const uint32_t *)o.si,
+                          (const uint32_t *)o.sk, S, (const int64_t *)C->row_ptr, n, nnz, C->col, C->count,
                           C->seed_i, C->seed_k);
                 return SG_OK;
             }
-            // C = U + U^T: U rows in place, mirrored entries through the lower scratch arrays
-            int64_t *lrp = room;  // free once the scan of tmp_off has run
+            // C = U + U^T: U rows in place, mirrored entries through packed lower records
             SG_TRY(exclusive_scan<uint32_t>(colcnt, lrp, n, s, err));
             int64_t nnz_l = 0;
             SG_CUDA_TRY(read_back(&nnz_l, lrp + n, sizeof(int64_t), s));
             uint32_t *cursor = sc.get<uint32_t>(n + 1);
-            int32_t *l_col = sc.get<int32_t>(nnz_l + 1);
-            uint32_t *l_cnt = sc.get<uint32_t>(nnz_l + 1);
-            uint32_t *l_si = sc.get<uint32_t>((size_t)S * nnz_l + 1), *l_sk = sc.get<uint32_t>((size_t)S * nnz_l + 1);
-            if (!cursor || !l_col || !l_cnt || !l_si || !l_sk) return SG_ERR_OOM;
+            uint32_t *lrec = sc.get<uint32_t>((size_t)(2 + 2 * S) * nnz_l + 1);
+            if (!cursor || !lrec) return SG_ERR_OOM;
             SG_CUDA_TRY(cudaMemsetAsync(cursor, 0, (n + 1) * sizeof(uint32_t), s));
             SG_LAUNCH("mirror_c", mirror_c_kernel, blocks_for(n * 32, 256), 256, 0, s, (const int64_t *)tmp_off,
-                      (const int64_t *)nnz_row, tmp_n, (const int32_t *)t_col, (const uint32_t *)t_cnt,
-                      (const uint32_t *)t_si, (const uint32_t *)t_sk, S, (const uint32_t *)colcnt,
+                      (const int64_t *)nnz_row, cap, (const int32_t *)o.col, (const uint32_t *)o.cnt,
+                      (const uint32_t *)o.si, (const uint32_t *)o.sk, S, (const uint32_t *)colcnt,
                       (const int64_t *)C->row_ptr, (const int64_t *)lrp, n, nnz, nnz_l, cursor, C->col, C->count,
-                      C->seed_i, C->seed_k, l_col, l_cnt, l_si, l_sk);
-            for (const void *p : {(const void *)t_col, (const void *)t_cnt, (const void *)t_si, (const void *)t_sk})
+                      C->seed_i, C->seed_k, lrec);
+            for (const void *p : {(const void *)o.col, (const void *)o.cnt, (const void *)o.si, (const void *)o.sk})
                 sc.release(p);
-            unsigned long long *big_count = counts + 4 * NCNT + 4;  // zeroed with the counters
-            int32_t *big_rows = ovf;                                // free once the redo passes have run
+            int32_t *big_rows = ovf;  // free once the redo passes have run
             SG_LAUNCH("sort_lower", sort_lower_kernel, (int64_t)nsm * 8, LOWER_NT, 0, s, (const uint32_t *)colcnt,
-                      (const int64_t *)lrp, (const int64_t *)C->row_ptr, n, nnz, nnz_l, S, (const int32_t *)l_col,
-                      (const uint32_t *)l_cnt, (const uint32_t *)l_si, (const uint32_t *)l_sk, C->col, C->count,
-                      C->seed_i, C->seed_k, big_count, big_rows,
+                      (const int64_t *)lrp, (const int64_t *)C->row_ptr, n, nnz, S, (const uint32_t *)lrec, C->col,
+                      C->count, C->seed_i, C->seed_k, big_count, big_rows,
                       (int)std::min<int64_t>(tune("spgemm_lower_smem"), LOWER_SMEM));
             unsigned long long n_lbig = 0;
             SG_CUDA_TRY(read_back(&n_lbig, big_count, sizeof(n_lbig), s));
@@ -1405,18 +1504,23 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 uint64_t *kpool = sc.get<uint64_t>((size_t)slice * lgrid);
                 if (!kpool) return SG_ERR_OOM;
                 SG_LAUNCH("sort_lower_big", lower_big_kernel, lgrid, 1024, 0, s, (const uint32_t *)colcnt,
-                          (const int64_t *)lrp, (const int64_t *)C->row_ptr, nnz, nnz_l, S, (const int32_t *)big_rows,
-                          (const unsigned long long *)big_count, kpool, slice, (const int32_t *)l_col,
-                          (const uint32_t *)l_cnt, (const uint32_t *)l_si, (const uint32_t *)l_sk, C->col, C->count,
-                          C->seed_i, C->seed_k);
+                          (const int64_t *)lrp, (const int64_t *)C->row_ptr, nnz, S, (const int32_t *)big_rows,
+                          (const unsigned long long *)big_count, kpool, slice, (const uint32_t *)lrec, C->col,
+                          C->count, C->seed_i, C->seed_k);
             }
             return SG_OK;
         }
-        // the temporary region would exceed its budget: the two-pass path below, on full rows
-        if (upper)
-            SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col,
-                      At->row_ptr, n, work, a_beg, a_len);
+        // the temporary region would exceed its budget: the two-pass path below
     }
+    // ---- two-pass form: row work and At extents per A entry, symbolic sizes, exact tables
+    int64_t *a_beg = sc.get<int64_t>(A->nnz + 1);
+    uint32_t *a_len = sc.get<uint32_t>(A->nnz + 1);
+    if (!a_beg || !a_len) return SG_ERR_OOM;
+    g.a_beg = a_beg;
+    g.a_len = a_len;
+    stage.emplace("SpGEMMSymbolic", s);
+    SG_LAUNCH("row_work", row_work_kernel, blocks_for(n * 32, 256), 256, 0, s, A->row_ptr, A->col, At->row_ptr, n,
+              work, a_beg, a_len);
     g.t_pair = t_pair = sc.get<uint64_t>(At->nnz + 1);
     if (!t_pair) return SG_ERR_OOM;
     SG_LAUNCH("at_pairs", pair_kernel, blocks_for(At->nnz, 256), 256, 0, s, At->col, At->val, At->nnz, t_pair);
@@ -1553,9 +1657,9 @@ namespace sg {
 constexpr int64_t TILE_ROW_BYTES = 256;           // per-row arrays of one tile (row pointers, classes...)
 constexpr int64_t TILE_FIXED_BYTES = 4ll << 20;   // counters and allocation rounding of one tile
 
-// Per row: the bytes the row adds to a tile (its A entries' At tails, 12 B each; the temporary
-// and final room for its entries of C, min(w / t, np - 1) each, twice; and the per-row arrays)
-// and its products w (whole row, diagonal excluded). One warp per row.
+// Per row: the bytes the row adds to a tile (the temporary and the final room for its entries of
+// C, min(w / t, np - 1) each, twice; and the per-row arrays) and its products w (whole row,
+// diagonal excluded). One warp per row.
 __global__ void tile_est_kernel(const int64_t *__restrict__ a_rp, const int32_t *__restrict__ a_col,
                                 const int64_t *__restrict__ t_rp, int64_t n, int64_t np, uint32_t t, int S,
                                 int64_t *__restrict__ bytes, int64_t *__restrict__ work) {
@@ -1571,7 +1675,7 @@ __global__ void tile_est_kernel(const int64_t *__restrict__ a_rp, const int32_t 
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if (lane == 0) {
         const int64_t room = std::min<int64_t>(w / t, np - 1);
-        bytes[row] = 12 * (a_rp[row + 1] - a_rp[row]) + 2 * (8 + 8 * (int64_t)S) * room + TILE_ROW_BYTES;
+        bytes[row] = 2 * (8 + 8 * (int64_t)S) * room + TILE_ROW_BYTES;
         work[row] = w;
     }
 }
@@ -1620,11 +1724,12 @@ extern "C" sg_status sg_overlap_spgemm_tiled(const sg_csr_u32 *A, const sg_csr_u
     for (int64_t r0 = 0; r0 < n;) {
         // the longest range from r0 whose rows, one global table for its largest row and the fixed
         // part fit the budget
-        int64_t acc = TILE_FIXED_BYTES, wmax = 0, r1 = r0;
+        int64_t acc = TILE_FIXED_BYTES, wmax = 0, r1 = r0, room = 0;
         while (r1 < n) {
             const int64_t wm = std::max(wmax, hw[r1]);
             if (acc + hb[r1] + gslice(wm) > (int64_t)budget_bytes) break;
             acc += hb[r1];
+            room += std::min<int64_t>(hw[r1] / min_shared, np - 1);
             wmax = wm;
             r1++;
         }
@@ -1647,6 +1752,7 @@ extern "C" sg_status sg_overlap_spgemm_tiled(const sg_csr_u32 *A, const sg_csr_u
             opt.row0 = r0;
             opt.whole_rows = true;
             opt.gmem_bytes = (size_t)((int64_t)budget_bytes - acc);  // >= one table for the largest row
+            opt.tmp_cap = room + 1;  // exact bound: no row of the tile finds the region full
             st = overlap_impl(&Ar, &At_, min_shared, S, &Ct, s, sc, opt);
         }
         if (st == SG_OK && cudaStreamSynchronize(s) != cudaSuccess) {

@@ -199,39 +199,65 @@ def make(w: Workload, with_graph: bool = True) -> dict:
 
 
 # ------------------------------------------------------------------ batched / served job mixes
-def batched_sets(count: int = 512, g_lo: float = 20e3, g_hi: float = 2e6, seed: int = 2013) -> list:
+def _parallel(fn, args, workers: int):
+    """fn over args in order; the generator's C calls release the GIL, so threads run in parallel."""
+    if workers <= 1 or len(args) <= 1:
+        return [fn(*a) for a in args]
+    import concurrent.futures
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(lambda a: fn(*a), args))
+
+
+def _default_workers() -> int:
+    try:
+        return max(1, min(16, len(os.sched_getaffinity(0))))
+    except (AttributeError, OSError):
+        return 1
+
+
+def batched_sets(count: int = 512, g_lo: float = 20e3, g_hi: float = 2e6, seed: int = 2013,
+                 workers: int | None = None) -> list:
     """Independent read sets of the batched workload: genome log-uniform in [g_lo, g_hi], coverage
     U[10, 40], mean read length U[2, 10] kbp (sd 0.4 x mean), errors U[12, 15] % split 3:2:1
     (ins:del:sub), k = 17, reliable range [2, max(8, round(0.75 x coverage))], R from true
-    coordinates (overlaps >= 500 bp). Set b is seeded from (seed, b)."""
+    coordinates (overlaps >= 500 bp). Set b is seeded from (seed, b); the sets are drawn on
+    `workers` host threads with the same result."""
     rng = np.random.default_rng(seed)
-    out = []
+    params = []
     for b in range(count):
         G = int(np.exp(rng.uniform(np.log(g_lo), np.log(g_hi))))
         cov = float(rng.uniform(10, 40))
         mean = float(rng.uniform(2000, 10000))
         err = float(rng.uniform(0.12, 0.15))
+        params.append((b, G, cov, mean, err))
+
+    def one(b, G, cov, mean, err):
         g = genome(G, seed * 100003 + b)
         rd = reads(g, cov, mean, 0.4 * mean, 500, err / 2, err / 3, err / 6, seed * 100003 + b + 1)
         R = overlap_graph(rd["start"], rd["end"], rd["strand"], 500)
-        out.append(dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=max(8, int(round(0.75 * cov))), R=R,
-                        genome=G))
-    return out
+        return dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=max(8, int(round(0.75 * cov))), R=R, genome=G)
+
+    return _parallel(one, params, _default_workers() if workers is None else workers)
 
 
 def served_jobs(count: int = 500, rate: float = 200.0, g_min: float = 20e3, g_max: float = 20e6,
-                alpha: float = 1.5, seed: int = 2014) -> list:
+                alpha: float = 1.5, seed: int = 2014, workers: int | None = None) -> list:
     """Jobs of the served workload: Poisson arrivals at `rate` per second; genome size Pareto(alpha)
     from g_min, truncated at g_max; 30x, mean read length 10 kbp (sd 4 kbp), 15 % errors (3:2:1),
-    range [2, 20], R from true coordinates (overlaps >= 500 bp). Each job has an arrival time."""
+    range [2, 20], R from true coordinates (overlaps >= 500 bp). Each job has an arrival time.
+    Drawn on `workers` host threads with the same result."""
     rng = np.random.default_rng(seed)
     t = 0.0
-    out = []
+    params = []
     for b in range(count):
         t += float(rng.exponential(1.0 / rate))
         G = int(min(g_max, g_min * (1.0 - rng.uniform()) ** (-1.0 / alpha)))
+        params.append((b, G, t))
+
+    def one(b, G, t):
         g = genome(G, seed * 100003 + b)
         rd = reads(g, 30.0, 10000.0, 4000.0, 500, 0.075, 0.05, 0.025, seed * 100003 + b + 1)
         R = overlap_graph(rd["start"], rd["end"], rd["strand"], 500)
-        out.append(dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=20, R=R, genome=G, arrival=t))
-    return out
+        return dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=20, R=R, genome=G, arrival=t)
+
+    return _parallel(one, params, _default_workers() if workers is None else workers)

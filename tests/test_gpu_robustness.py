@@ -49,22 +49,24 @@ CONFIGS = [
     {"bloom_scatter_cfg": 2, "kmer_sort_buckets": 0},                # 256 x 32 tiles, one bucket
     {"spgemm_fused": 0, "sym_guess_shift": 8},                      # two passes, tiny symbolic guesses
     {"spgemm_fused": 0, "sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
-    {"num_guess_shift": 8},                                          # fused, most rows overflow
-    {"num_guess_shift": 0},                                          # fused, exact-bound guesses
-    {"num_guess_shift": 0, "spgemm_big_threads": 512},               # 4 K+ tables, 512 threads
+    {"spgemm_guess_pct": 25},                                        # fused, most rows overflow
+    {"spgemm_guess_pct": 10000},                                     # fused, guesses past shared memory
+    {"spgemm_guess_pct": 100, "spgemm_big_threads": 512},            # 4 K+ tables, 512 threads
     {"spgemm_fused_max_mb": 0},                                      # fused path over budget: fallback
     {"spgemm_filter_work": 0},                                       # no seen-twice filter
     {"spgemm_filter_mode": 2, "spgemm_filter_work": 1},              # every row filtered first
-    {"spgemm_filter_mode": 2, "spgemm_filter_work": 1, "spgemm_filter_shift": 8},  # filtered rows overflow
-    {"spgemm_sample_min_nnz": 0},                                    # sampled guesses
-    {"spgemm_sample_min_nnz": 0, "spgemm_sample_rows": 1, "spgemm_guess_pct": 25},  # tables too small
-    {"spgemm_sample_min_nnz": 0, "spgemm_guess_pct": 10000},         # tables at the exact bound
-    {"spgemm_sample_min_nnz": 0, "spgemm_filter_mode": 2, "spgemm_filter_work": 1},  # sampled, filtered
+    {"spgemm_filter_mode": 2, "spgemm_filter_work": 1, "spgemm_guess_pct": 5},  # filtered rows overflow
+    {"spgemm_sample_rows": 0},                                       # no sample: a partner per A entry
+    {"spgemm_sample_rows": 1, "spgemm_guess_pct": 25},               # one sampled row, tables too small
+    {"spgemm_tmp_pct": 1},                                           # temporary region full: retries
+    {"spgemm_tmp_pct": 1, "spgemm_upper": 0},                        # ... for whole rows
+    {"spgemm_tab_warps": 0},                                         # fixed threads per table size
+    {"spgemm_tab_warps": 8, "spgemm_blocks_per_sm": 1},              # few warps, small grid
     {"spgemm_upper": 0},                                             # whole rows, no mirror
-    {"spgemm_upper": 0, "num_guess_shift": 8},                       # whole rows, most rows overflow
+    {"spgemm_upper": 0, "spgemm_guess_pct": 25},                     # whole rows, most rows overflow
     {"spgemm_upper": 0, "spgemm_filter_mode": 2, "spgemm_filter_work": 1},  # whole rows, filtered
     {"spgemm_lower_smem": 1},                                        # every mirrored part > 1: global sort
-    {"spgemm_lower_smem": 16, "num_guess_shift": 8},                 # mixed sort paths, overflowing tables
+    {"spgemm_lower_smem": 16, "spgemm_guess_pct": 25},               # mixed sort paths, overflowing tables
     {"spgemm_blocks_per_sm": 1, "spgemm_big_threads": 512, "spgemm_lower_smem": 64},
 ]
 
@@ -100,7 +102,7 @@ def test_tunables_never_change_results(medium, cfg):
 
 @pytest.mark.parametrize("cfg", [{"spgemm_filter_mode": 2, "spgemm_filter_work": 1, "spgemm_filter_log2": 10},
                                  {"spgemm_filter_mode": 2, "spgemm_filter_work": 1, "spgemm_filter_log2": 10,
-                                  "spgemm_filter_shift": 6}],
+                                  "spgemm_guess_pct": 10}],
                          ids=["hashed-filter", "hashed-filter-small-tables"])
 def test_hashed_seen_twice_filter(cfg):
     """More reads (about 1500) than filter bits (2^10): partners share filter bits, count-1

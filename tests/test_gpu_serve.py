@@ -118,3 +118,30 @@ def test_server_cancel_queued_job():
         _check(res[2], jobs[2], 300)
     finally:
         srv.close()
+
+
+def test_server_admits_job_over_budget_with_c_in_tiles():
+    """A job whose one-piece estimate exceeds the budget, but whose resident part (inputs, A, At,
+    R) plus a tile budget fits, runs alone with C formed in row tiles: its result equals the
+    oracle's, and a small job queued behind it still completes."""
+    g = synth.genome(100_000, 41)
+    rd = synth.reads(g, 60.0, 10000.0, 3000.0, 500, 0.075, 0.05, 0.025, 42)
+    R = synth.overlap_graph(rd["start"], rd["end"], rd["strand"], 500)
+    job = dict(seq=rd["seq"], offsets=rd["offsets"], lo=2, hi=40, R=R)
+    L, n1, rn = rd["seq"].size, rd["offsets"].size, R["col"].size
+    est = 64 * L + 48 * rn + 64 * n1 + (1 << 20)
+    est_tiled = max(40 * L + 64 * n1 + (1 << 20), 24 * L + 48 * rn + 64 * n1 + (1 << 20) + (64 << 20))
+    budget = est_tiled + (1 << 20)
+    assert est > budget
+    small = _jobs(9, 1)[0]
+    srv = sg.Server(hbm_budget=budget, max_batch=4, workers=2, fuzz=300)
+    try:
+        t_big = srv.submit(job["seq"], job["offsets"], job["lo"], job["hi"], job["R"])
+        t_small = srv.submit(small["seq"], small["offsets"], small["lo"], small["hi"], small["R"])
+        r = srv.wait(t_big)
+        assert r["status"] == sg.SG_OK, r["error"]
+        assert r["batch_size"] == 1
+        _check(r, job, 300)
+        _check(srv.wait(t_small), small, 300)
+    finally:
+        srv.close()
