@@ -207,6 +207,10 @@ def main():
         w = w.scaled(args.scale)
         w.name = f"{w.name}@{args.scale:g}"
     w = synth.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})  # independent replica per rank
+    from paper_2010_10055_gb300 import autotune
+    defaults = sg.tunables()
+    tuned = autotune.load(autotune.DEFAULT_CACHE, w.name.split("@")[0])  # this GPU's cached choice, if any
+    tuned_params = {k: v for k, v in sg.tunables().items() if defaults.get(k) != v}
     d = synth.make(w)
     n = int(d["offsets"].size - 1)
     total = int(d["seq"].size)
@@ -350,7 +354,8 @@ def main():
             "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
             "e2e": e2e, "roofline": roof, "rooflines": rooflines, "kernels": kernels, "stages": stages,
             "clocks": clk,
-            "gpu_launches": launches, "device_memory_peak_gb": mem_peak / 1e9, "from_seeds": from_seeds}
+            "gpu_launches": launches, "device_memory_peak_gb": mem_peak / 1e9, "from_seeds": from_seeds,
+            "tunables_from_cache": tuned_params if tuned else None}
     if w.name != "bacterial-5Mbp-30x" and args.scale == 1.0 and not args.no_forms:
         try:
             line["bacterial"] = measure_extra(sg, "bacterial-5Mbp-30x", args.steps, args.warmup, 1000 * rank)
@@ -483,6 +488,9 @@ def measure_batched(sg, count: int, g_hi: float, reps: int = 3) -> dict:
             sg.overlap_spgemm(km, 2, 2)
             sg.transitive_reduce(it["R"], 1000)
 
+    from paper_2010_10055_gb300 import autotune
+    saved = sg.tunables()
+
     def batched():
         return sg.run_batch(items, k=17, min_shared=2, max_seeds=2, fuzz=1000)
 
@@ -501,12 +509,19 @@ def measure_batched(sg, count: int, g_hi: float, reps: int = 3) -> dict:
             del out
         return statistics.median(ts)
 
-    plain_ms, batched_ms = timed(plain), timed(batched)
-    res = batched()
+    plain_ms = timed(plain)
+    tuned = autotune.load(autotune.DEFAULT_CACHE, f"batched-{count}")  # this GPU's cached choice, if any
+    try:
+        batched_ms = timed(batched)
+        res = batched()
+    finally:
+        for k, v in saved.items():
+            sg.tune(k, v)
     a = np.diff(res.to_numpy()["At"]["row_ptr"]).astype(np.int64)
     prod = int((a * a).sum())
     return {"sets": count, "genome_bp": [20000, int(g_hi)], "bases": int(sum(x["seq"].size for x in sets)),
             "generation_s": t_gen, "device_memory_peak_gb": sg.memory_stats()[2] / 1e9,
+            "tunables_from_cache": bool(tuned),
             "products": prod, "plain_ms": plain_ms, "batched_ms": batched_ms, "speedup": plain_ms / batched_ms,
             "products_per_s_batched": prod / (batched_ms / 1e3), "products_per_s_plain": prod / (plain_ms / 1e3)}
 

@@ -439,7 +439,9 @@ uint64_t sg_debug_check(void);
  * the number of rows recorded, or -1 if there is none (off, or the two-pass form ran). Codes:
  * log2 of the shared-memory table size (6..14), 16 + log2 for a filtered table, 32 for a row sent
  * straight to a global-memory table, 33 for a filtered one, plus 64 when a guessed table overflowed
- * and the row was redone in global memory; -1 for a row with no products. */
+ * and the row was redone in global memory; 96 + log2 for a row redone in a larger shared-memory
+ * table after an overflow (128: in global memory; plus 64 if that one overflowed too); -1 for a
+ * row with no products. */
 void sg_debug_record_classes(int on);
 int64_t sg_debug_spgemm_classes(int32_t *host_out, int64_t n);
 

@@ -288,16 +288,22 @@ static Tunable g_tunables[] = {
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
     {"spgemm_upper", 1, 0, 1},            // 1: the fused pass tabulates partners k > i only and
                                           // mirrors them (C is symmetric); 0: whole rows
-    {"spgemm_lower_smem", 4096, 1, 4096}, // mirrored parts up to this long are ordered in shared memory
+    {"spgemm_at_records", 1, 0, 1},       // 1: the fused pass reads At rows as 32-byte records
+    {"spgemm_smem_carveout", -1, -1, 100},// fused-pass shared-memory carveout, % (-1: the driver's)
+    {"spgemm_escalate", 1, 0, 8},         // a guessed table that overflows is tried once more
+                                          // 2^this times larger in shared memory (0: global memory)
+    {"spgemm_mirror_sort", 1, 0, 1},      // 1: mirrored entries ordered by a stable radix sort by column;
+                                          // 0: scattered by atomics and sorted per row
+    {"spgemm_lower_smem", 4096, 1, 4096}, // (0 above) parts up to this long are sorted in shared memory
     {"spgemm_tab_warps", 64, 0, 64},      // fused-pass blocks: threads for about this many warps per SM
                                           // across the blocks that fit (0: fixed threads per table size)
     {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)
-    {"spgemm_guess_pct", 300, 1, 10000},  // guess = pct / 100 x sampled partners per A entry x entries
+    {"spgemm_guess_pct", 200, 1, 10000},  // guess = pct / 100 x sampled partners per A entry x entries
     {"spgemm_tmp_pct", 125, 1, 10000},    // fused temporary region = pct / 100 x sampled kept entries
                                           // (+ 4 per row); rows that find it full are redone
     {"spgemm_fused_max_mb", 65536, 0, 1 << 30},  // temporary C region above which the two passes run
                                                   // (also when it exceeds half the free memory)
-    {"spgemm_filter_mode", 1, 0, 2},      // seen-twice filter: 0 never, 1 where the sample finds it
+    {"spgemm_filter_mode", 0, 0, 2},      // seen-twice filter: 0 never, 1 where the sample finds it
                                           // pays, 2 always (rows of spgemm_filter_work products or more)
     {"spgemm_filter_work", 1024, 0, (int64_t)1 << 40},  // fused rows with this many A entries or more
                                           // may first mark partners seen twice (0: never)

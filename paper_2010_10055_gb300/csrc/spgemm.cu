@@ -71,7 +71,55 @@ struct SpArgs {
     uint32_t *err;  // DEV_OVERFLOW if the numeric pass ever disagrees with the symbolic sizes
     int64_t np;     // partners: columns of At (all reads); n = np unless A is a row range of a larger A
     int64_t row0;   // read id of row 0 of A (nonzero only for a row range), for the diagonal
+    const struct AtRec *t_rec;  // At rows as 32-byte records (fused pass), or nullptr
 };
+
+// One At row as a 32-byte record: its start in At, its length and, when it has at most AT_INL
+// entries, their reads. An A entry's products then cost one aligned 32-byte load -- one DRAM
+// sector -- instead of a row-pointer gather plus a gather of the row.
+constexpr int AT_INL = 5;
+struct __align__(32) AtRec {
+    int64_t b;
+    uint32_t len;
+    int32_t r[AT_INL];
+};
+static_assert(sizeof(AtRec) == 32, "one sector per record");
+
+__device__ __forceinline__ AtRec load_rec(const AtRec *p) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint4 y = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+    AtRec r;
+    r.b = (int64_t)(((uint64_t)x.y << 32) | x.x);
+    r.len = x.z;
+    r.r[0] = (int32_t)x.w;
+    r.r[1] = (int32_t)y.x;
+    r.r[2] = (int32_t)y.y;
+    r.r[3] = (int32_t)y.z;
+    r.r[4] = (int32_t)y.w;
+    return r;
+}
+
+// One thread per row j of At: its record.
+__global__ void at_rec_kernel(const int64_t *__restrict__ t_rp, const int32_t *__restrict__ t_col, int64_t m,
+                              AtRec *__restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t b = t_rp[j], len = t_rp[j + 1] - b;
+    uint4 x, y;
+    x.x = (uint32_t)b;
+    x.y = (uint32_t)((uint64_t)b >> 32);
+    x.z = len > 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)len;
+    int32_t r[AT_INL];
+#pragma unroll
+    for (int t = 0; t < AT_INL; t++) r[t] = (len <= AT_INL && t < len) ? t_col[b + t] : -1;
+    x.w = (uint32_t)r[0];
+    y.x = (uint32_t)r[1];
+    y.y = (uint32_t)r[2];
+    y.z = (uint32_t)r[3];
+    y.w = (uint32_t)r[4];
+    reinterpret_cast<uint4 *>(out + j)[0] = x;
+    reinterpret_cast<uint4 *>(out + j)[1] = y;
+}
 
 // One warp per row: w_i, and for every entry (i, j) the start and length of At row j, so that
 // the two passes stream these instead of gathering At's row pointers at random.
@@ -531,11 +579,36 @@ __global__ void __launch_bounds__(1024) numeric_kernel(SpArgs g, const int32_t *
 // at tmp_off[i]); a row that finds the region full is listed for a retry in a grown region.
 
 // Extent [beg, beg + len) of the products of A entry a of row gi (read id): the tail of At row
-// j = a_col[a] after read gi (UPPER), or the whole row (gi itself is skipped by the caller).
+// j = a_col[a] after read gi (UPPER), or the whole row (gi itself is skipped by the caller). With
+// records, a row of at most AT_INL entries is read from its record: *rec receives it and *t0 the
+// index of the first product within it; *t0 = -1 otherwise (the products are read from t_col).
 template <bool UPPER>
-__device__ __forceinline__ void at_extent(const SpArgs &g, int64_t a, int32_t gi, int64_t &beg, uint32_t &len) {
+__device__ __forceinline__ void at_extent(const SpArgs &g, int64_t a, int32_t gi, int64_t &beg, uint32_t &len,
+                                          AtRec *rec = nullptr, int *t0 = nullptr) {
     const int32_t j = g.a_col[a];
-    const int64_t b = g.t_rp[j], e = g.t_rp[j + 1];
+    int64_t b, e;
+    if (g.t_rec) {
+        const AtRec r = load_rec(g.t_rec + j);
+        b = r.b;
+        if (r.len <= AT_INL) {
+            int t = 0;
+            if (UPPER) {
+#pragma unroll
+                for (int q = 0; q < AT_INL; q++)
+                    if (q < (int)r.len && r.r[q] <= gi) t = q + 1;
+            }
+            beg = b + t;
+            len = r.len - (uint32_t)t;
+            if (rec) *rec = r;
+            if (t0) *t0 = t;
+            return;
+        }
+        e = b + (int64_t)r.len;
+    } else {
+        b = g.t_rp[j];
+        e = g.t_rp[j + 1];
+    }
+    if (t0) *t0 = -1;
     int64_t lo = b;
     if (UPPER) {
         int64_t hi = e;
@@ -556,17 +629,37 @@ __device__ __forceinline__ void at_extent(const SpArgs &g, int64_t a, int32_t gi
 // updates. Stops (per warp, at a chunk boundary) once *stop is nonzero.
 constexpr int TU_U = 2;
 
+// With records (g.t_rec), wb is this block's buffer of AT_INL x 32 ints per warp: each lane puts
+// its record's reads there, and a product of a short row is read from it instead of from t_col.
+constexpr int WB_PER_WARP = 32 * AT_INL;
+
 template <bool UPPER, class F>
 __device__ __forceinline__ void enum_fused(const SpArgs &g, int32_t gi, int64_t r0, int64_t r1,
-                                           const volatile int *stop, F &&f) {
+                                           const volatile int *stop, int32_t *wb, F &&f) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int32_t *wbw = wb ? wb + warp * WB_PER_WARP : nullptr;
     for (int64_t a0 = r0 + (int64_t)warp * 32; a0 < r1; a0 += (int64_t)nwarps * 32) {
         if (stop && __any_sync(0xffffffffu, *stop != 0)) return;
         const int64_t a = a0 + lane;
         int64_t beg = 0;
         uint32_t len = 0;
-        if (a < r1) at_extent<UPPER>(g, a, gi, beg, len);
+        int wsrc = -1;  // index in wbw of this lane's first product, or -1: products in t_col
+        AtRec rec;
+        int t0 = -1;
+        if (a < r1) {
+            if (wbw) at_extent<UPPER>(g, a, gi, beg, len, &rec, &t0);
+            else at_extent<UPPER>(g, a, gi, beg, len);
+        }
+        if (wbw) {
+            __syncwarp();  // the previous chunk's reads of wbw are done
+            if (t0 >= 0) {
+#pragma unroll
+                for (int q = 0; q < AT_INL; q++) wbw[lane * AT_INL + q] = rec.r[q];
+                wsrc = lane * AT_INL + t0;
+            }
+            __syncwarp();  // every lane's reads are in wbw
+        }
         uint32_t inc = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -590,8 +683,9 @@ __device__ __forceinline__ void enum_fused(const SpArgs &g, int32_t gi, int64_t 
                 }
                 const int64_t ob = __shfl_sync(0xffffffffu, beg, ow);
                 const uint32_t oe = __shfl_sync(0xffffffffu, excl, ow);
+                const int os = __shfl_sync(0xffffffffu, wsrc, ow);
                 ix[u] = (uint32_t)(a0 - r0) + (uint32_t)ow;
-                kk[u] = p < total ? g.t_col[ob + (p - oe)] : gi;
+                kk[u] = p >= total ? gi : (os >= 0 ? wbw[os + (int)(p - oe)] : g.t_col[ob + (p - oe)]);
             }
         };
         gather(0);
@@ -652,14 +746,22 @@ struct TmpOut {
 // where w = wl[rb] is the row's product count (never overflows). SK: 0, 1, 2 seeds as above; 3 =
 // the chain. FILT: the seen-once / seen-twice filters (2^log2F bits each) mark the partners of
 // the row first, and only partners seen twice reach the table (min_shared >= 2).
+// Registers of the numeric pass: at most 40 per thread, so that 48 warps fit an SM (64 registers
+// would allow 32); the compiler spills a few bytes to stay under it.
+#ifndef SG_TAB_BOUNDS
+#define SG_TAB_BOUNDS __maxnreg__(40)
+#endif
+
 template <bool GSLICE, int SK, bool FILT, bool UPPER>
-__global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
+__global__ void SG_TAB_BOUNDS tab_numeric_kernel(SpArgs g, const int32_t *__restrict__ rows,
                                                          const unsigned long long *__restrict__ nrows_p, int log2T,
                                                          int log2F, unsigned char *__restrict__ gpool,
                                                          int64_t slice_bytes, const int64_t *__restrict__ wl,
                                                          TmpOut o, int32_t *__restrict__ ovf_list,
-                                                         unsigned long long *__restrict__ ovf_count) {
+                                                         unsigned long long *__restrict__ ovf_count, int64_t wb_off,
+                                                         int8_t *__restrict__ ovf_lt) {
     extern __shared__ __align__(16) unsigned char tab_raw[];
+    int32_t *wb = g.t_rec ? (int32_t *)(tab_raw + wb_off) : nullptr;  // record reads, per warp
     __shared__ int s_ctr, s_ins, s_ovf, s_full, s_fail;
     __shared__ unsigned long long s_e0;
     const int S = g.S;
@@ -707,7 +809,7 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
             return fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
         };
         if (FILT) {  // seen once -> F1, seen again -> F2 (bits are only ever set)
-            enum_fused<UPPER>(g, gi, r0, r1, nullptr, [&](int32_t k, uint32_t) {
+            enum_fused<UPPER>(g, gi, r0, r1, nullptr, wb, [&](int32_t k, uint32_t) {
                 const uint32_t b = fbit(k), m = 1u << (b & 31u);
                 if (((volatile uint32_t *)F2)[b >> 5] & m) return;
                 if (atomicOr(F1 + (b >> 5), m) & m) atomicOr(F2 + (b >> 5), m);
@@ -715,7 +817,7 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
             __syncthreads();
         }
         const int cap = (T >> 1) + (T >> 2);
-        enum_fused<UPPER>(g, gi, r0, r1, GSLICE ? nullptr : &s_ovf, [&](int32_t k, uint32_t idx) {
+        enum_fused<UPPER>(g, gi, r0, r1, GSLICE ? nullptr : &s_ovf, wb, [&](int32_t k, uint32_t idx) {
             if (!GSLICE && *(volatile int *)&s_ovf) return;
             if (FILT) {
                 const uint32_t b = fbit(k);
@@ -786,7 +888,10 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
         if (!GSLICE && (s_ovf || s_full)) {  // the global-memory pass redoes the row
             if (threadIdx.x == 0) {
                 const unsigned long long q = atomicAdd(ovf_count, 1ull);
-                if (SG_IN_BOUNDS((int64_t)q < g.n, 311, q)) ovf_list[q] = i;
+                if (SG_IN_BOUNDS((int64_t)q < g.n, 311, q)) {
+                    ovf_list[q] = i;
+                    if (ovf_lt) ovf_lt[q] = (int8_t)lT;  // the table that was too small
+                }
             }
             __syncthreads();
             continue;
@@ -843,8 +948,22 @@ __global__ void __launch_bounds__(1024) tab_numeric_kernel(SpArgs g, const int32
                     const int64_t a = r0 + sdx;
                     const uint32_t vi = g.a_val[a];
                     const int32_t j = g.a_col[a];
-                    const int64_t tb0 = g.t_rp[j];
-                    const uint32_t vk = at_value_cv(g.t_col, g.t_val, tb0, g.t_rp[j + 1] - tb0, k);
+                    uint32_t vk;
+                    if (g.t_rec) {
+                        const AtRec rr = load_rec(g.t_rec + j);
+                        if (rr.len <= AT_INL) {
+                            int q = 0;
+#pragma unroll
+                            for (int t = 1; t < AT_INL; t++)
+                                if (t < (int)rr.len && rr.r[t] <= k) q = t;
+                            vk = g.t_val[rr.b + q];
+                        } else {
+                            vk = at_value_cv(g.t_col, g.t_val, rr.b, rr.len, k);
+                        }
+                    } else {
+                        const int64_t tb0 = g.t_rp[j];
+                        vk = at_value_cv(g.t_col, g.t_val, tb0, g.t_rp[j + 1] - tb0, k);
+                    }
                     si = vi & 0x7FFFFFFFu;
                     sk = (vk & 0x7FFFFFFFu) | ((vi ^ vk) & 0x80000000u);
                 }
@@ -902,7 +1021,8 @@ __global__ void __launch_bounds__(512) sample_fx_kernel(SpArgs g, int64_t stride
     if (threadIdx.x < 2) s_c[threadIdx.x] = 0ull;
     __syncthreads();
     const bool fid = g.np <= ((int64_t)1 << log2F);
-    enum_fused<UPPER>(g, (int32_t)(g.row0 + i), g.a_rp[i], g.a_rp[i + 1], nullptr, [&](int32_t k, uint32_t) {
+    int32_t *wb = g.t_rec ? (int32_t *)(smp_f + 2 * nw) : nullptr;
+    enum_fused<UPPER>(g, (int32_t)(g.row0 + i), g.a_rp[i], g.a_rp[i + 1], nullptr, wb, [&](int32_t k, uint32_t) {
         const uint32_t b = fid ? (uint32_t)k & ((1u << log2F) - 1u) : ((uint32_t)k * 2654435761u) >> (32 - log2F);
         const uint32_t m = 1u << (b & 31u);
         if (((volatile uint32_t *)F2)[b >> 5] & m) return;
@@ -1095,6 +1215,66 @@ __global__ void __launch_bounds__(1024) lower_big_kernel(const uint32_t *__restr
     }
 }
 
+// C from the upper triangle U (rows at tmp_off, lengths nnz_row, seeds slot-major with stride
+// tmp_n). One warp per row i of U: its entries go to C row i after the lower part (colcnt[i]
+// entries), in order; every entry (i, k) also writes, at its row-major rank rpu[i] + e, a sort key
+// (the partner k) and a value (i << 33 | its position in C). A stable sort by key then lists each
+// column's entries by ascending row, which is the order of the mirrored entries in the lower part
+// of row k (lower_fill_kernel).
+constexpr int MIRROR_POS_BITS = 33;
+
+__global__ void mirror_keys_kernel(const int64_t *__restrict__ tmp_off, const int64_t *__restrict__ nnz_row,
+                                   int64_t tmp_n, const int32_t *__restrict__ t_col,
+                                   const uint32_t *__restrict__ t_cnt, const uint32_t *__restrict__ t_si,
+                                   const uint32_t *__restrict__ t_sk, int S, const uint32_t *__restrict__ colcnt,
+                                   const int64_t *__restrict__ c_rp, const int64_t *__restrict__ rpu, int64_t n,
+                                   int64_t nnz, int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
+                                   uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
+                                   uint32_t *__restrict__ mkey, uint64_t *__restrict__ mval) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int64_t len = nnz_row[row];
+    if (len == 0) return;
+    const int64_t src = tmp_off[row], dst = c_rp[row] + colcnt[row], u0 = rpu[row];
+    for (int64_t e = lane; e < len; e += 32) {
+        const int32_t k = t_col[src + e];
+        c_col[dst + e] = k;
+        c_cnt[dst + e] = t_cnt[src + e];
+        for (int q = 0; q < S; q++) {
+            c_si[(int64_t)q * nnz + dst + e] = t_si[(int64_t)q * tmp_n + src + e];
+            c_sk[(int64_t)q * nnz + dst + e] = t_sk[(int64_t)q * tmp_n + src + e];
+        }
+        mkey[u0 + e] = (uint32_t)k;
+        mval[u0 + e] = ((uint64_t)row << MIRROR_POS_BITS) | (uint64_t)(dst + e);
+    }
+}
+
+// Sorted mirror list -> lower parts: entry q of the list (partner k, row i, position p of C_ik)
+// is the (q - lrp[k])-th entry of row k's lower part: C_ki with the count of C_ik and its seeds'
+// positions swapped (same rc bit).
+__global__ void lower_fill_kernel(const uint32_t *__restrict__ mkey, const uint64_t *__restrict__ mval, int64_t nu,
+                                  const int64_t *__restrict__ lrp, const int64_t *__restrict__ c_rp, int64_t n,
+                                  int64_t nnz, int S, int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
+                                  uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nu) return;
+    const uint32_t k = mkey[q];
+    const uint64_t v = mval[q];
+    const int64_t i = (int64_t)(v >> MIRROR_POS_BITS), p = (int64_t)(v & ((1ull << MIRROR_POS_BITS) - 1));
+    if (!SG_IN_BOUNDS(k < n && p < nnz, 312, q)) return;
+    const int64_t d = c_rp[k] + (q - lrp[k]);
+    if (!SG_IN_BOUNDS(d >= c_rp[k] && d < c_rp[k + 1], 313, d)) return;
+    c_col[d] = (int32_t)i;
+    c_cnt[d] = c_cnt[p];
+    for (int s = 0; s < S; s++) {
+        const uint32_t si = c_si[(int64_t)s * nnz + p], sk = c_sk[(int64_t)s * nnz + p];
+        const bool none = si == SEED_NONE;
+        c_si[(int64_t)s * nnz + d] = none ? SEED_NONE : (sk & 0x7FFFFFFFu);
+        c_sk[(int64_t)s * nnz + d] = none ? SEED_NONE : (si | (sk & 0x80000000u));
+    }
+}
+
 // nnz of C's rows in the upper-triangle form: U row i plus its mirrored entries.
 __global__ void c_rowlen_kernel(const int64_t *__restrict__ nnz_row, const uint32_t *__restrict__ colcnt, int64_t n,
                                 int64_t *__restrict__ out) {
@@ -1125,6 +1305,21 @@ __global__ void compact_c_kernel(const int64_t *__restrict__ tmp_off, int64_t tm
     }
 }
 
+// Rows whose guessed table overflowed (ovf[0 .. *cnt_p), with the log2 size that was too small
+// in lt) go to the smallest class at least 2^shift times larger, or to the global class.
+__global__ void escalate_kernel(const int32_t *__restrict__ ovf, const int8_t *__restrict__ lt,
+                                const unsigned long long *__restrict__ cnt_p, int shift, Classes cl, int64_t n,
+                                unsigned long long *__restrict__ counts, int32_t *__restrict__ lists) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)*cnt_p) return;
+    const int want = lt[q] + shift;
+    int c = cl.ncls;
+    for (int x = 0; x < cl.ncls; x++)
+        if (cl.log2T[x] >= want) { c = x; break; }
+    const unsigned long long p = atomicAdd(counts + c, 1ull);
+    if (SG_IN_BOUNDS((int64_t)p < n, 318, p)) lists[(int64_t)c * n + (int64_t)p] = ovf[q];
+}
+
 __global__ void pair_kernel(const int32_t *__restrict__ col, const uint32_t *__restrict__ val, int64_t nnz,
                             uint64_t *__restrict__ pair) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1144,13 +1339,18 @@ static int pick_numeric_threads(int log2T, bool filtered) {
 
 // threads per block of the fused pass: enough warps that the blocks shared memory lets reside on
 // one SM bring about spgemm_tab_warps warps (64 = the SM's limit) between them
-static int pick_tab_threads(int log2T, int S, bool filtered) {
+// tsm = the table's (and filters') shared memory, warp_bytes = each warp's record buffer; code =
+// log2T, negated for unfiltered tables (for the fixed choice when spgemm_tab_warps is 0)
+static int pick_tab_threads(size_t tsm, size_t warp_bytes, int code) {
     const int64_t want = tune("spgemm_tab_warps");
-    if (want <= 0) return pick_numeric_threads(log2T, filtered);
-    const size_t bytes = tab_bytes((int64_t)1 << log2T, S) + (filtered ? (size_t)32 << 10 : 0);
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(32, (int64_t)((227u << 10) / bytes)));
+    if (want <= 0) return pick_numeric_threads(code < 0 ? -code : code, code > 0);
     int64_t threads = 64;
-    while (threads < 1024 && blocks * (threads / 32) < want) threads <<= 1;
+    for (;;) {
+        const size_t bytes = tsm + warp_bytes * (size_t)(threads / 32);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(32, (int64_t)((227u << 10) / bytes)));
+        if (threads >= 1024 || blocks * (threads / 32) >= want) break;
+        threads <<= 1;
+    }
     return (int)threads;
 }
 
@@ -1189,12 +1389,26 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     SG_CUDA_TRY(cudaMemsetAsync(dist, 0, (n + 1) * sizeof(int64_t), s));
     uint64_t *t_pair = nullptr;  // only the two-pass kernels read At as (val << 32 | col) pairs
     SpArgs g{A->row_ptr, A->col, A->val, At->row_ptr, At->col, At->val, nullptr, nullptr, t_pair,
-             n, min_shared, S, err, np, opt.row0};
+             n, min_shared, S, err, np, opt.row0, nullptr};
     const bool fused = opt.whole_rows || tune("spgemm_fused") != 0;
     const bool upper = fused && !opt.whole_rows && tune("spgemm_upper") != 0;
     std::optional<StageScope> stage;
     const int nsm = sm_count();
     const int grid = (int)(nsm * tune("spgemm_blocks_per_sm"));
+    // the fused pass reads At through 32-byte row records when they fit beside everything else
+    // (not for row ranges: every range would build them again, outside its budget)
+    const int64_t m = At->n_rows;
+    AtRec *recs = nullptr;
+    if (fused && !opt.whole_rows && tune("spgemm_at_records") && m > 0 &&
+        (double)m * sizeof(AtRec) <= 0.25 * (double)device_bytes_available()) {
+        recs = sc.get<AtRec>(m);
+        if (!recs) return SG_ERR_OOM;
+        stage.emplace("SpGEMMSymbolic", s);
+        SG_LAUNCH("at_records", at_rec_kernel, blocks_for(m, 256), 256, 0, s, At->row_ptr, At->col, m, recs);
+        g.t_rec = recs;
+    }
+    // shared memory of the per-warp record buffers, for a block of `threads`
+    auto wbb = [&](int threads) -> size_t { return recs ? (size_t)(threads / 32) * WB_PER_WARP * 4 : 0; };
     // numeric (two-pass form): one class per table size from 2^6 while table and sort buffer fit in 160 KB
     Classes num{};
     num.ncls = 0;
@@ -1202,10 +1416,12 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         num.log2T[num.ncls] = SP_MINLOG + num.ncls;
         num.ncls++;
     }
-    // the fused pass's guessed tables (up to 220 KB: one block per SM)
+    // the fused pass's guessed tables (up to 220 KB with the record buffers of 1024 threads: one
+    // block per SM)
+    const size_t tab_limit = (220u << 10) - wbb(1024);
     Classes fz{};
     fz.ncls = 0;
-    while (fz.ncls < SP_NCLS && tab_bytes((int64_t)1 << (SP_MINLOG + fz.ncls), S) <= (220u << 10)) {
+    while (fz.ncls < SP_NCLS && tab_bytes((int64_t)1 << (SP_MINLOG + fz.ncls), S) <= tab_limit) {
         fz.log2T[fz.ncls] = SP_MINLOG + fz.ncls;
         fz.ncls++;
     }
@@ -1215,7 +1431,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
     const size_t fbytes = ((size_t)2 << log2F) / 8;
     Classes ff{};
     ff.ncls = 0;
-    while (ff.ncls < SP_NCLS && tab_bytes((int64_t)1 << (SP_MINLOG + ff.ncls), S) + fbytes <= (220u << 10)) {
+    while (ff.ncls < SP_NCLS && tab_bytes((int64_t)1 << (SP_MINLOG + ff.ncls), S) + fbytes <= tab_limit) {
         ff.log2T[ff.ncls] = SP_MINLOG + ff.ncls;
         ff.ncls++;
     }
@@ -1247,12 +1463,13 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
         if (nsamp > 0 && n > 0 && A->nnz > 0) {
             const int64_t stride = n > nsamp ? n / nsamp : 1;
             const int64_t nb = (n + stride - 1) / stride;
+            const size_t ssm = fbytes + wbb(256);
             if (upper) {
-                SG_CUDA_TRY(ensure_smem(sample_fx_kernel<true>, fbytes));
-                SG_LAUNCH("spgemm_sample", sample_fx_kernel<true>, nb, 256, fbytes, s, g, stride, log2F, sums);
+                SG_CUDA_TRY(ensure_smem(sample_fx_kernel<true>, ssm));
+                SG_LAUNCH("spgemm_sample", sample_fx_kernel<true>, nb, 256, ssm, s, g, stride, log2F, sums);
             } else {
-                SG_CUDA_TRY(ensure_smem(sample_fx_kernel<false>, fbytes));
-                SG_LAUNCH("spgemm_sample", sample_fx_kernel<false>, nb, 256, fbytes, s, g, stride, log2F, sums);
+                SG_CUDA_TRY(ensure_smem(sample_fx_kernel<false>, ssm));
+                SG_LAUNCH("spgemm_sample", sample_fx_kernel<false>, nb, 256, ssm, s, g, stride, log2F, sums);
             }
             unsigned long long h[3] = {0, 0, 0};
             SG_CUDA_TRY(read_back(h, sums, sizeof(h), s));
@@ -1303,15 +1520,21 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
             o.n_retry = n_retry;
             o.colcnt = colcnt;
             // one launch per table class; the seed form (SK), the filter and the form pick the kernel
+            const int carve = (int)tune("spgemm_smem_carveout");
             auto launch_tab = [&](bool filt, int log2T, const int32_t *rl, const unsigned long long *cnt,
-                                  const char *name) -> sg_status {
-                const size_t sm = tab_bytes((int64_t)1 << log2T, S) + (filt ? fbytes : 0);
-                const int nt = pick_tab_threads(log2T, S, filt);
+                                  const char *name, int32_t *ol, unsigned long long *oc, int8_t *olt) -> sg_status {
+                const size_t tsm = tab_bytes((int64_t)1 << log2T, S) + (filt ? fbytes : 0);
+                const int nt = pick_tab_threads(tsm, wbb(32), filt ? log2T : -log2T);
+                const size_t sm = tsm + wbb(nt);
+                const int64_t wb_off = (int64_t)tsm;
 #define SG_TAB_LAUNCH(SKV, FV, UV)                                                                          \
     do {                                                                                                    \
         SG_CUDA_TRY(ensure_smem(tab_numeric_kernel<false, SKV, FV, UV>, sm));                               \
+        if (carve >= 0)                                                                                     \
+            SG_CUDA_TRY(cudaFuncSetAttribute(tab_numeric_kernel<false, SKV, FV, UV>,                        \
+                                             cudaFuncAttributePreferredSharedMemoryCarveout, carve));       \
         SG_LAUNCH(name, (tab_numeric_kernel<false, SKV, FV, UV>), grid, nt, sm, s, g, rl, cnt, log2T, log2F, \
-                  (unsigned char *)nullptr, (int64_t)0, (const int64_t *)nullptr, o, ovf, fz_ovf);         \
+                  (unsigned char *)nullptr, (int64_t)0, (const int64_t *)nullptr, o, ol, oc, wb_off, olt);  \
     } while (0)
 #define SG_TAB_SK(FV, UV)                      \
     do {                                       \
@@ -1349,9 +1572,10 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 if (opt.gmem_bytes) ggrid = (int)std::max<int64_t>(1, std::min<int64_t>(ggrid, (int64_t)opt.gmem_bytes / slice));
                 unsigned char *pool = sc.get<unsigned char>((size_t)slice * ggrid);
                 if (!pool) return SG_ERR_OOM;
-#define SG_GTAB_LAUNCH(SKV, UV)                                                                                \
-    SG_LAUNCH("spgemm_numeric_gmem", (tab_numeric_kernel<true, SKV, false, UV>), ggrid, 512, 0, s, g, rl, cnt, \
-              0, 0, pool, slice, (const int64_t *)wl, o, ovf + n + 1, unused)
+                const size_t gsm = wbb(512);
+#define SG_GTAB_LAUNCH(SKV, UV)                                                                                  \
+    SG_LAUNCH("spgemm_numeric_gmem", (tab_numeric_kernel<true, SKV, false, UV>), ggrid, 512, gsm, s, g, rl, cnt, \
+              0, 0, pool, slice, (const int64_t *)wl, o, ovf + n + 1, unused, (int64_t)0, (int8_t *)nullptr)
 #define SG_GTAB_SK(UV)                     \
     do {                                   \
         if (SK == 0) SG_GTAB_LAUNCH(0, UV); \
@@ -1366,22 +1590,53 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 sc.release(pool);
                 return SG_OK;
             };
+            // rows whose guessed table overflows are tried once more in a table 4 x larger while
+            // one fits in shared memory (esc: second-round class lists and counts, their overflow
+            // list), else redone in global memory
+            const int esc_shift = (int)tune("spgemm_escalate");
+            int8_t *ovf_lt = esc_shift > 0 ? sc.get<int8_t>(n + 1) : nullptr;
+            unsigned long long *esc_counts = esc_shift > 0 ? sc.get<unsigned long long>(NCNT + 1) : nullptr;
+            int32_t *esc_lists = esc_shift > 0 ? sc.get<int32_t>((size_t)(SP_NCLS + 1) * (n + 1)) : nullptr;
+            int32_t *esc_ovf = esc_shift > 0 ? sc.get<int32_t>(n + 1) : nullptr;
+            if (esc_shift > 0 && (!ovf_lt || !esc_counts || !esc_lists || !esc_ovf)) return SG_ERR_OOM;
+            if (esc_shift > 0) SG_CUDA_TRY(cudaMemsetAsync(esc_counts, 0, (NCNT + 1) * sizeof(unsigned long long), s));
             for (int c = 0; c < fz.ncls; c++) {
                 if (!h_fz[c]) continue;
                 SG_TRY(launch_tab(false, fz.log2T[c], lists + (int64_t)c * n, fz_counts + c,
-                                  NUM_NAMES[fz.log2T[c] - SP_MINLOG]));
+                                  NUM_NAMES[fz.log2T[c] - SP_MINLOG], ovf, fz_ovf, ovf_lt));
             }
             for (int c = 0; fwork && c < ff.ncls; c++) {  // rows with many entries: filtered first
                 if (!h_ff[c]) continue;
                 SG_TRY(launch_tab(true, ff.log2T[c], lists_f + (int64_t)c * n, ff_counts + c,
-                                  FIL_NAMES[ff.log2T[c] - SP_MINLOG]));
+                                  FIL_NAMES[ff.log2T[c] - SP_MINLOG], ovf, fz_ovf, nullptr));
             }
-            unsigned long long n_ovf = 0;
+            unsigned long long n_ovf = 0, h_esc[NCNT + 1] = {};
             SG_CUDA_TRY(read_back(&n_ovf, fz_ovf, sizeof(n_ovf), s));
+            // filtered rows' overflows (no size recorded) are escalated past every class
+            const bool escalate = esc_shift > 0 && n_ovf > 0 && !fwork;
+            if (escalate) {
+                SG_LAUNCH("escalate", escalate_kernel, blocks_for((int64_t)n_ovf, NT), NT, 0, s, (const int32_t *)ovf,
+                          (const int8_t *)ovf_lt, (const unsigned long long *)fz_ovf, esc_shift, fz, n, esc_counts,
+                          esc_lists);
+                SG_CUDA_TRY(read_back(h_esc, esc_counts, sizeof(h_esc), s));
+                for (int c = 0; c < fz.ncls; c++) {
+                    if (!h_esc[c]) continue;
+                    SG_TRY(launch_tab(false, fz.log2T[c], esc_lists + (int64_t)c * n, esc_counts + c,
+                                      NUM_NAMES[fz.log2T[c] - SP_MINLOG], esc_ovf, esc_counts + NCNT, nullptr));
+                }
+            }
             const unsigned long long n_big = h_fz[fz.ncls], n_big_f = fwork ? h_ff[ff.ncls] : 0;
             if (n_big) SG_TRY(launch_gtab(lists + (int64_t)fz.ncls * n, fz_counts + fz.ncls, n_big));
             if (n_big_f) SG_TRY(launch_gtab(lists_f + (int64_t)ff.ncls * n, ff_counts + ff.ncls, n_big_f));
-            if (n_ovf) SG_TRY(launch_gtab((const int32_t *)ovf, fz_ovf, n_ovf));
+            if (escalate) {
+                unsigned long long n_ovf2 = 0;
+                SG_CUDA_TRY(read_back(&n_ovf2, esc_counts + NCNT, sizeof(n_ovf2), s));
+                if (h_esc[fz.ncls])
+                    SG_TRY(launch_gtab(esc_lists + (int64_t)fz.ncls * n, esc_counts + fz.ncls, h_esc[fz.ncls]));
+                if (n_ovf2) SG_TRY(launch_gtab((const int32_t *)esc_ovf, esc_counts + NCNT, n_ovf2));
+            } else if (n_ovf) {
+                SG_TRY(launch_gtab((const int32_t *)ovf, fz_ovf, n_ovf));
+            }
             // rows that found the region full: grow it by their exact room and redo them
             unsigned long long n_rt = 0;
             SG_CUDA_TRY(read_back(&n_rt, n_retry, sizeof(n_rt), s));
@@ -1446,6 +1701,13 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 for (int c = 0; fwork && c <= ff.ncls; c++)
                     SG_TRY(mark(lists_f + (int64_t)c * n, h_ff[c], c < ff.ncls ? 16 + ff.log2T[c] : 33, false));
                 SG_TRY(mark(ovf, n_ovf, 64, true));
+                if (escalate) {  // second round: 96 + log2 of the larger table, 32 + 96 global
+                    for (int c = 0; c <= fz.ncls; c++)
+                        SG_TRY(mark(esc_lists + (int64_t)c * n, h_esc[c], c < fz.ncls ? 96 + fz.log2T[c] : 128, false));
+                    unsigned long long n_ovf2 = 0;
+                    SG_CUDA_TRY(read_back(&n_ovf2, esc_counts + NCNT, sizeof(n_ovf2), s));
+                    SG_TRY(mark(esc_ovf, n_ovf2, 64, true));
+                }
             }
             int64_t *clen = upper ? need_f : nnz_row;  // need_f is free once the classes have run
             if (upper)
@@ -1475,10 +1737,35 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                           C->seed_i, C->seed_k);
                 return SG_OK;
             }
-            // C = U + U^T: U rows in place, mirrored entries through packed lower records
+            // C = U + U^T: U rows in place; the mirrored entries of each column, in row order
             SG_TRY(exclusive_scan<uint32_t>(colcnt, lrp, n, s, err));
             int64_t nnz_l = 0;
             SG_CUDA_TRY(read_back(&nnz_l, lrp + n, sizeof(int64_t), s));
+            if (tune("spgemm_mirror_sort") && nnz < ((int64_t)1 << MIRROR_POS_BITS)) {
+                int64_t *rpu = need;  // free once the classes have run
+                SG_TRY(exclusive_scan<int64_t>(nnz_row, rpu, n, s, err));
+                uint32_t *mk0 = sc.get<uint32_t>(nnz_l + 1), *mk1 = sc.get<uint32_t>(nnz_l + 1);
+                uint64_t *mv0 = sc.get<uint64_t>(nnz_l + 1), *mv1 = sc.get<uint64_t>(nnz_l + 1);
+                if (!mk0 || !mk1 || !mv0 || !mv1) return SG_ERR_OOM;
+                SG_LAUNCH("mirror_c", mirror_keys_kernel, blocks_for(n * 32, 256), 256, 0, s,
+                          (const int64_t *)tmp_off, (const int64_t *)nnz_row, cap, (const int32_t *)o.col,
+                          (const uint32_t *)o.cnt, (const uint32_t *)o.si, (const uint32_t *)o.sk, S,
+                          (const uint32_t *)colcnt, (const int64_t *)C->row_ptr, (const int64_t *)rpu, n, nnz, C->col,
+                          C->count, C->seed_i, C->seed_k, mk0, mv0);
+                for (const void *p : {(const void *)o.col, (const void *)o.cnt, (const void *)o.si, (const void *)o.sk})
+                    sc.release(p);
+                int kbits = 1;
+                while (kbits < 32 && ((int64_t)1 << kbits) < n) kbits++;
+                bool alt = false;
+                SG_TRY((radix_sort_pairs<uint32_t, uint64_t>(mk0, mv0, mk1, mv1, nnz_l, kbits, &alt, s, err)));
+                SG_LAUNCH("lower_fill", lower_fill_kernel, blocks_for(nnz_l, 256), 256, 0, s,
+                          (const uint32_t *)(alt ? mk1 : mk0), (const uint64_t *)(alt ? mv1 : mv0), nnz_l,
+                          (const int64_t *)lrp, (const int64_t *)C->row_ptr, n, nnz, S, C->col, C->count, C->seed_i,
+                          C->seed_k);
+                SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));  // the sort waits between tiles
+                if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
+                return SG_OK;
+            }
             uint32_t *cursor = sc.get<uint32_t>(n + 1);
             uint32_t *lrec = sc.get<uint32_t>((size_t)(2 + 2 * S) * nnz_l + 1);
             if (!cursor || !lrec) return SG_ERR_OOM;

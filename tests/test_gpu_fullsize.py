@@ -9,7 +9,8 @@ slow for the k-mer stage and C:
 - sampled rows of A: the read's own windows (oracle) and their census give the read's reliable
   k-mers, which must be A's row (columns by code rank, lowest position, strand) exactly;
 - sampled rows of C: the oracle's single-row product on the same A and At, and the mirrored
-  entries C_ki;
+  entries C_ki; the sample takes at least 10 rows from every numeric launch that ran (each table
+  size, the global-memory tables, the rows redone after an overflow) beside uniform ones;
 - properties that hold at any size: codes strictly ascending, A and At transposes, no diagonal in
   C and counts >= t, S a subgraph of R.
 
@@ -44,9 +45,15 @@ def full(request):
     d = synth.make(w)
     off = dev(d["offsets"], np.int64)
     km = sg.build_kmer_matrix(dev(d["seq"], np.uint8), off, w.k, w.lo, w.hi)
-    C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+    sg.debug_record_classes(True)  # which numeric launch handled each row, for the stratified sample
+    try:
+        C = sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
+        classes = sg.debug_spgemm_classes(km.A.shape[0])
+    finally:
+        sg.debug_record_classes(False)
     S, it = sg.transitive_reduce(sg.DeviceGraph.from_numpy(d["R"]), w.fuzz)
-    out = dict(w=w, d=d, km=km.to_numpy(), C=C.to_numpy(), S=S.to_numpy(), it=it, C_dev=C, off_dev=off)
+    out = dict(w=w, d=d, km=km.to_numpy(), C=C.to_numpy(), S=S.to_numpy(), it=it, C_dev=C, off_dev=off,
+               classes=classes)
     del km, S
     return out
 
@@ -131,11 +138,26 @@ def test_fullsize_sampled_a_rows(full, census):
             assert t < tb and At["col"][t] == i and At["val"][t] == v, (i, j)
 
 
+def _stratified_rows(full, rng, per_class=10, uniform=100):
+    """Rows of C to check: uniform ones, the first and last, and per_class from every numeric
+    launch the product ran (each shared-memory table size, the global-memory tables, rows redone
+    after an overflow), read back through the class-record hook."""
+    n = full["C"]["n"]
+    rows = [rng.choice(n, uniform, replace=False), [0, n - 1]]
+    cls = full["classes"]
+    assert cls is not None and cls.size == n
+    for code in np.unique(cls):
+        idx = np.nonzero(cls == code)[0]
+        rows.append(rng.choice(idx, min(per_class, idx.size), replace=False))
+    return np.unique(np.concatenate(rows)).tolist(), np.unique(cls).tolist()
+
+
 def test_fullsize_sampled_c_rows(full):
     w, km, C = full["w"], full["km"], full["C"]
     rng = np.random.default_rng(2012)
-    n = C["n"]
-    for i in np.unique(np.concatenate([rng.choice(n, 100, replace=False), [0, n - 1]])).tolist():
+    rows, codes = _stratified_rows(full, rng)
+    print(f"C rows checked: {len(rows)} across launch codes {codes}")
+    for i in rows:
         r = oracle.overlap_row(km["A"], km["At"], i, w.min_shared, w.max_seeds)
         a, b = C["row_ptr"][i], C["row_ptr"][i + 1]
         assert np.array_equal(C["col"][a:b], r["col"]), i

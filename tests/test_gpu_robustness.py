@@ -65,9 +65,13 @@ CONFIGS = [
     {"spgemm_upper": 0},                                             # whole rows, no mirror
     {"spgemm_upper": 0, "spgemm_guess_pct": 25},                     # whole rows, most rows overflow
     {"spgemm_upper": 0, "spgemm_filter_mode": 2, "spgemm_filter_work": 1},  # whole rows, filtered
-    {"spgemm_lower_smem": 1},                                        # every mirrored part > 1: global sort
-    {"spgemm_lower_smem": 16, "spgemm_guess_pct": 25},               # mixed sort paths, overflowing tables
+    {"spgemm_mirror_sort": 0, "spgemm_lower_smem": 16, "spgemm_guess_pct": 25},  # mixed row sorts
     {"spgemm_blocks_per_sm": 1, "spgemm_big_threads": 512, "spgemm_lower_smem": 64},
+    {"spgemm_at_records": 0},                                        # At rows gathered, no records
+    {"spgemm_at_records": 0, "spgemm_upper": 0},
+    {"spgemm_filter_mode": 1},                                       # filter where the sample says
+    {"spgemm_mirror_sort": 0},                                       # mirror by atomics + row sorts
+    {"spgemm_mirror_sort": 0, "spgemm_lower_smem": 1},               # ... all in global memory
 ]
 
 
