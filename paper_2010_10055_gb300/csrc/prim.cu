@@ -1,6 +1,8 @@
 // prim.cu -- single-pass exclusive scan and stable LSD radix sort, both with decoupled look-back
 // between tiles (the radix sort: one upfront digit count for all passes, then one kernel per pass
 // that ranks keys per warp with ballots and scatters from shared memory in digit order).
+#include <algorithm>
+
 #include "check.cuh"
 #include "prim.cuh"
 
@@ -143,6 +145,7 @@ constexpr int RS_WARPS = RS_NT / 32;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_NT * RS_ITEMS;
 constexpr int RS_MAXP = 8;
+constexpr int RS_LBW = 8;  // predecessors read per look-back step, at most
 
 template <class K>
 __global__ void __launch_bounds__(RS_NT) radix_upfront_kernel(const K *__restrict__ keys, int64_t n, int lo_bit,
@@ -174,13 +177,13 @@ struct RsSmem {
 
 // ghist: this pass's 256 digit totals; status: [ntiles][256] look-back words, zeroed; tile_ctr:
 // zeroed. Without values (HAS_V == false) vin / vout are not touched.
-template <class K, class V, bool HAS_V>
+template <class K, class V, bool HAS_V, bool MATCH>
 __global__ void __launch_bounds__(RS_NT, HAS_V ? 3 : 4) radix_onesweep_kernel(const K *__restrict__ kin, const V *__restrict__ vin,
                                                               K *__restrict__ kout, V *__restrict__ vout,
                                                               int64_t n, int shift,
                                                               const unsigned long long *__restrict__ ghist,
                                                               unsigned long long *status, unsigned int *tile_ctr,
-                                                              uint32_t *err) {
+                                                              uint32_t *err, int lbw) {
     extern __shared__ __align__(16) unsigned char rs_raw[];
     RsSmem<K, V, HAS_V> &sm = *reinterpret_cast<RsSmem<K, V, HAS_V> *>(rs_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -201,13 +204,19 @@ __global__ void __launch_bounds__(RS_NT, HAS_V ? 3 : 4) radix_onesweep_kernel(co
         key[it] = valid ? kin[idx] : K(0);
         if (HAS_V) val[HAS_V ? it : 0] = valid ? vin[idx] : V(0);
         const uint32_t d = (uint32_t)(key[it] >> shift) & (RS_RADIX - 1);
-        // lanes holding the same digit: intersect the ballots of the digit's 8 bits
-        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+        // lanes holding the same digit: one match instruction, or the intersection of the ballots
+        // of the digit's 8 bits (invalid lanes carry a digit value no valid lane has)
+        uint32_t peers;
+        if (MATCH) {
+            peers = __match_any_sync(0xffffffffu, valid ? d : RS_RADIX);
+        } else {
+            peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-        for (int b = 0; b < RS_BITS; b++) {
-            const bool bit = (d >> b) & 1u;
-            const uint32_t bb = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? bb : ~bb;
+            for (int b = 0; b < RS_BITS; b++) {
+                const bool bit = (d >> b) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bb : ~bb;
+            }
         }
         const uint32_t base_cnt = valid ? sm.wcnt[w][d] : 0u;
         __syncwarp();
@@ -234,10 +243,24 @@ __global__ void __launch_bounds__(RS_NT, HAS_V ? 3 : 4) radix_onesweep_kernel(co
         lb_store(mine, LB_P | tot);
     } else {
         lb_store(mine, LB_A | tot);
-        for (int64_t t = tile - 1; t >= 0; t--) {
-            const unsigned long long v = lb_wait(status + t * RS_RADIX + d, err);
-            excl += (int64_t)(v & LB_VAL);
-            if ((v >> 62) == 2) break;
+        // walk back lbw predecessors at a time: their words are read together, and only a word not
+        // yet published is waited on
+        bool done = false;
+        for (int64_t t = tile - 1; t >= 0 && !done; t -= lbw) {
+            unsigned long long v[RS_LBW];
+#pragma unroll
+            for (int q = 0; q < RS_LBW; q++)
+                v[q] = (q < lbw && t - q >= 0)
+                           ? *reinterpret_cast<const volatile unsigned long long *>(status + (t - q) * RS_RADIX + d)
+                           : 0ull;
+#pragma unroll
+            for (int q = 0; q < RS_LBW; q++) {
+                if (done || q >= lbw || t - q < 0) continue;
+                unsigned long long x = v[q];
+                if ((x >> 62) == 0) x = lb_wait(status + (t - q) * RS_RADIX + d, err);
+                excl += (int64_t)(x & LB_VAL);
+                if ((x >> 62) == 2) done = true;
+            }
         }
         lb_store(mine, LB_P | (unsigned long long)(excl + tot));
     }
@@ -295,13 +318,23 @@ static sg_status radix_sort_impl(K *k0, V *v0, K *k1, V *v1, int64_t n, int lo_b
     const int64_t hgrid = ntiles < hmax ? ntiles : hmax;
     SG_LAUNCH("radix_upfront", radix_upfront_kernel<K>, hgrid, RS_NT, 0, s, (const K *)k0, n, lo_bit, npass, ghist);
     const size_t smem = sizeof(RsSmem<K, V, HAS_V>);
-    SG_CUDA_TRY(ensure_smem(radix_onesweep_kernel<K, V, HAS_V>, smem));
+    const bool match = tune("radix_match") != 0;
+    const int lbw = (int)std::min<int64_t>(std::max<int64_t>(tune("radix_lookback"), 1), RS_LBW);
+    if (match) SG_CUDA_TRY(ensure_smem(radix_onesweep_kernel<K, V, HAS_V, true>, smem));
+    else SG_CUDA_TRY(ensure_smem(radix_onesweep_kernel<K, V, HAS_V, false>, smem));
     K *ki = k0, *ko = k1;
     V *vi = v0, *vo = v1;
     for (int p = 0; p < npass; p++) {
-        SG_LAUNCH("radix_onesweep", (radix_onesweep_kernel<K, V, HAS_V>), ntiles, RS_NT, smem, s, (const K *)ki,
-                  (const V *)vi, ko, vo, n, lo_bit + RS_BITS * p, (const unsigned long long *)(ghist + p * RS_RADIX),
-                  status + (size_t)p * ntiles * RS_RADIX, ctr + p, err);
+        if (match)
+            SG_LAUNCH("radix_onesweep", (radix_onesweep_kernel<K, V, HAS_V, true>), ntiles, RS_NT, smem, s,
+                      (const K *)ki, (const V *)vi, ko, vo, n, lo_bit + RS_BITS * p,
+                      (const unsigned long long *)(ghist + p * RS_RADIX), status + (size_t)p * ntiles * RS_RADIX,
+                      ctr + p, err, lbw);
+        else
+            SG_LAUNCH("radix_onesweep", (radix_onesweep_kernel<K, V, HAS_V, false>), ntiles, RS_NT, smem, s,
+                      (const K *)ki, (const V *)vi, ko, vo, n, lo_bit + RS_BITS * p,
+                      (const unsigned long long *)(ghist + p * RS_RADIX), status + (size_t)p * ntiles * RS_RADIX,
+                      ctr + p, err, lbw);
         K *tk = ki; ki = ko; ko = tk;
         V *tv = vi; vi = vo; vo = tv;
         *in_alt = !*in_alt;

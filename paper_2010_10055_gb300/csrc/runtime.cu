@@ -284,6 +284,8 @@ static Tunable g_tunables[] = {
     {"bloom_scatter_cfg", 0, 0, 2},       // bin scatter tile: 0 512x16, 1 256x16, 2 256x32 hashes
     {"bloom_scatter_levels", 0, 0, 2},    // passes grouping hashes by bin (0: two beyond 4096 bins)
     {"kmer_sort_buckets", 3, 0, 3},       // at most this many top code bits become candidate buckets
+    {"radix_match", 0, 0, 1},             // radix sort ranking: 1 one match instruction per key, 0 ballots
+    {"radix_lookback", 8, 1, 8},          // radix sort look-back: predecessors read per step
     {"bloom_bin_room_pct", 112, 1, 1000}, // a bin's hash buffer, % of the mean (overflow: sliced)
     {"spgemm_fused", 1, 0, 1},            // 1: numeric pass with guessed tables, no symbolic pass
     {"spgemm_upper", 1, 0, 1},            // 1: the fused pass tabulates partners k > i only and

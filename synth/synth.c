@@ -281,12 +281,14 @@ static int quads_to_csr(quad_t *q, int64_t nq, int64_t n, synth_graph_t *g) {
     return 0;
 }
 
-static const int64_t *g_sort_start, *g_sort_end;
-static int cmp_by_start(const void *a, const void *b) {
-    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
-    if (g_sort_start[i] != g_sort_start[j]) return g_sort_start[i] < g_sort_start[j] ? -1 : 1;
-    if (g_sort_end[i] != g_sort_end[j]) return g_sort_end[i] < g_sort_end[j] ? -1 : 1;
-    return i < j ? -1 : (i > j);
+/* reads in (start, end, index) order; the comparator reads only its two records, so concurrent
+ * calls (the batched and served sets are drawn on several host threads) do not interfere */
+typedef struct { int64_t start, end, idx; } span_t;
+static int cmp_span(const void *a, const void *b) {
+    const span_t *x = (const span_t *)a, *y = (const span_t *)b;
+    if (x->start != y->start) return x->start < y->start ? -1 : 1;
+    if (x->end != y->end) return x->end < y->end ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
 }
 
 /*
@@ -304,10 +306,12 @@ int synth_overlap_graph(const int64_t *start, const int64_t *end, const uint8_t 
     memset(g, 0, sizeof(*g));
     if (min_overlap < 1) min_overlap = 1;
     int64_t *ord = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
-    if (!ord) return -1;
-    for (int64_t i = 0; i < n; i++) ord[i] = i;
-    g_sort_start = start; g_sort_end = end;
-    qsort(ord, (size_t)n, sizeof(int64_t), cmp_by_start);
+    span_t *sp = (span_t *)malloc((size_t)(n ? n : 1) * sizeof(span_t));
+    if (!ord || !sp) { free(ord); free(sp); return -1; }
+    for (int64_t i = 0; i < n; i++) { sp[i].start = start[i]; sp[i].end = end[i]; sp[i].idx = i; }
+    qsort(sp, (size_t)n, sizeof(span_t), cmp_span);
+    for (int64_t i = 0; i < n; i++) ord[i] = sp[i].idx;
+    free(sp);
     int64_t cap = 1024, nq = 0;
     quad_t *q = (quad_t *)malloc(cap * sizeof(quad_t));
     if (!q) { free(ord); return -1; }
