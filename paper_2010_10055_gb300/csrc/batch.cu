@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ops.cuh"
@@ -63,7 +64,8 @@ __global__ void batch_concat_kernel(const ItemDesc *__restrict__ items, uint8_t 
     }
 }
 
-static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg_batch_params *p,
+// One group of items as one block-diagonal union (the whole batch when it is one group).
+static sg_status union_impl(const sg_batch_item *items, int32_t nitems, const sg_batch_params *p,
                             sg_batch_result *out, cudaStream_t s, Scratch &sc) {
     std::vector<ItemDesc> d(nitems);
     std::vector<int64_t> ro(nitems + 1, 0), co(nitems + 1, 0);
@@ -174,6 +176,177 @@ static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg
     memcpy(out->read_off, ro.data(), sizeof(int64_t) * (nitems + 1));
     memcpy(out->col_off, co.data(), sizeof(int64_t) * (nitems + 1));
     for (int b = 0; b < nitems; b++) out->iterations[b] = items[b].R ? last[b] + 1 : 0;
+    return SG_OK;
+}
+
+// dst[i] = src[i] + add (i < n): a group's indices moved to their place in the whole batch
+template <class T>
+__global__ void copy_add_kernel(const T *__restrict__ src, int64_t n, T add, T *__restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] + add;
+}
+
+template <class T>
+__global__ void fill_kernel(T *__restrict__ dst, int64_t n, T v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = v;
+}
+
+template <class T>
+static sg_status copy_add(const T *src, int64_t n, T add, T *dst, cudaStream_t s) {
+    if (n <= 0) return SG_OK;
+    if (add == T(0)) {
+        SG_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        return SG_OK;
+    }
+    SG_LAUNCH("batch_merge", copy_add_kernel<T>, (n + 255) / 256, 256, 0, s, src, n, add, dst);
+    return SG_OK;
+}
+
+// Runs of the batch: an item of at least batch_alone_kb kilobases runs on its own (alone it
+// already fills the GPU, and in a union its k-mer keys would carry more bits); consecutive
+// smaller items share a union of at most batch_group_kb kilobases, which saves their per-call
+// launches. Every group's results are then moved, indices offset, into the one batch result,
+// so the result is the same whatever the grouping.
+static sg_status batch_impl(const sg_batch_item *items, int32_t nitems, const sg_batch_params *p,
+                            sg_batch_result *out, cudaStream_t s, Scratch &sc) {
+    const int64_t alone = tune("batch_alone_kb") * 1000, gmax = tune("batch_group_kb") * 1000;
+    std::vector<int32_t> cut{0};  // group g = items cut[g] .. cut[g + 1]
+    int64_t acc = 0;
+    for (int32_t b = 0; b < nitems; b++) {
+        const int64_t t = items[b].total_len;
+        const bool big = alone > 0 && t >= alone;
+        if (b > cut.back() && (big || acc + t > gmax || (alone > 0 && items[b - 1].total_len >= alone))) {
+            cut.push_back(b);
+            acc = 0;
+        }
+        acc += t;
+    }
+    cut.push_back(nitems);
+    const int ng = (int)cut.size() - 1;
+    if (ng == 1) return union_impl(items, nitems, p, out, s, sc);
+    std::vector<sg_batch_result> gr(ng);
+    for (int g = 0; g < ng; g++) {
+        Scratch sg_(s);
+        const sg_status st = union_impl(items + cut[g], cut[g + 1] - cut[g], p, &gr[g], s, sg_);
+        if (st != SG_OK) {
+            for (int h = 0; h <= g; h++) sg_free_batch(&gr[h], (sg_stream_t)s);
+            return st;
+        }
+    }
+    // sizes and bases of every group in the whole batch
+    int64_t N = 0, M = 0, nA = 0, nC = 0, nS = 0;
+    bool any_s = false;
+    std::vector<int64_t> RB(ng), CB(ng), AB(ng), CCB(ng), SB(ng);
+    for (int g = 0; g < ng; g++) {
+        RB[g] = N; CB[g] = M; AB[g] = nA; CCB[g] = nC; SB[g] = nS;
+        N += gr[g].A.n_rows;
+        M += gr[g].A.n_cols;
+        nA += gr[g].A.nnz;
+        nC += gr[g].C.nnz;
+        nS += gr[g].S.nnz;
+        any_s |= gr[g].S.row_ptr != nullptr;
+    }
+    const int S = p->max_seeds;
+    sg_status st = SG_OK;
+    auto fail = [&](sg_status e) {
+        for (int g = 0; g < ng; g++) sg_free_batch(&gr[g], (sg_stream_t)s);
+        return e;
+    };
+#define SG_MERGE_TRY(expr)                  \
+    do {                                    \
+        st = (expr);                        \
+        if (st != SG_OK) return fail(st);   \
+    } while (0)
+#define SG_MERGE_ALLOC(ptr, type, count)                                \
+    do {                                                                \
+        ptr = (type *)dalloc((size_t)(count) * sizeof(type), s);        \
+        if (!ptr) return fail(SG_ERR_OOM);                              \
+    } while (0)
+    out->A = sg_csr_u32{N, M, nA, nullptr, nullptr, nullptr};
+    out->At = sg_csr_u32{M, N, nA, nullptr, nullptr, nullptr};
+    SG_MERGE_ALLOC(out->A.row_ptr, int64_t, N + 1);
+    SG_MERGE_ALLOC(out->A.col, int32_t, nA);
+    SG_MERGE_ALLOC(out->A.val, uint32_t, nA);
+    SG_MERGE_ALLOC(out->At.row_ptr, int64_t, M + 1);
+    SG_MERGE_ALLOC(out->At.col, int32_t, nA);
+    SG_MERGE_ALLOC(out->At.val, uint32_t, nA);
+    SG_MERGE_ALLOC(out->d_kmer_codes, uint64_t, M);
+    out->C = sg_overlap_csr{N, nC, S, nullptr, nullptr, nullptr, nullptr, nullptr};
+    SG_MERGE_ALLOC(out->C.row_ptr, int64_t, N + 1);
+    SG_MERGE_ALLOC(out->C.col, int32_t, nC);
+    SG_MERGE_ALLOC(out->C.count, uint32_t, nC);
+    SG_MERGE_ALLOC(out->C.seed_i, uint32_t, (int64_t)S * nC);
+    SG_MERGE_ALLOC(out->C.seed_k, uint32_t, (int64_t)S * nC);
+    if (any_s) {
+        out->S = sg_graph_csr{N, nS, nullptr, nullptr, nullptr, nullptr};
+        SG_MERGE_ALLOC(out->S.row_ptr, int64_t, N + 1);
+        SG_MERGE_ALLOC(out->S.col, int32_t, nS);
+        SG_MERGE_ALLOC(out->S.suffix, uint32_t, nS);
+        SG_MERGE_ALLOC(out->S.dir, uint8_t, nS);
+    }
+    for (int g = 0; g < ng; g++) {
+        const sg_batch_result &r = gr[g];
+        const int64_t n = r.A.n_rows, m = r.A.n_cols;
+        SG_MERGE_TRY(copy_add<int64_t>(r.A.row_ptr, n, AB[g], out->A.row_ptr + RB[g], s));
+        SG_MERGE_TRY(copy_add<int32_t>(r.A.col, r.A.nnz, (int32_t)CB[g], out->A.col + AB[g], s));
+        SG_MERGE_TRY(copy_add<uint32_t>(r.A.val, r.A.nnz, 0u, out->A.val + AB[g], s));
+        SG_MERGE_TRY(copy_add<int64_t>(r.At.row_ptr, m, AB[g], out->At.row_ptr + CB[g], s));
+        SG_MERGE_TRY(copy_add<int32_t>(r.At.col, r.At.nnz, (int32_t)RB[g], out->At.col + AB[g], s));
+        SG_MERGE_TRY(copy_add<uint32_t>(r.At.val, r.At.nnz, 0u, out->At.val + AB[g], s));
+        SG_MERGE_TRY(copy_add<uint64_t>(r.d_kmer_codes, m, 0ull, out->d_kmer_codes + CB[g], s));
+        SG_MERGE_TRY(copy_add<int64_t>(r.C.row_ptr, n, CCB[g], out->C.row_ptr + RB[g], s));
+        SG_MERGE_TRY(copy_add<int32_t>(r.C.col, r.C.nnz, (int32_t)RB[g], out->C.col + CCB[g], s));
+        SG_MERGE_TRY(copy_add<uint32_t>(r.C.count, r.C.nnz, 0u, out->C.count + CCB[g], s));
+        for (int q = 0; q < S; q++) {
+            SG_MERGE_TRY(copy_add<uint32_t>(r.C.seed_i + (int64_t)q * r.C.nnz, r.C.nnz, 0u,
+                                            out->C.seed_i + (int64_t)q * nC + CCB[g], s));
+            SG_MERGE_TRY(copy_add<uint32_t>(r.C.seed_k + (int64_t)q * r.C.nnz, r.C.nnz, 0u,
+                                            out->C.seed_k + (int64_t)q * nC + CCB[g], s));
+        }
+        if (any_s) {
+            if (r.S.row_ptr) {
+                SG_MERGE_TRY(copy_add<int64_t>(r.S.row_ptr, n, SB[g], out->S.row_ptr + RB[g], s));
+                SG_MERGE_TRY(copy_add<int32_t>(r.S.col, r.S.nnz, (int32_t)RB[g], out->S.col + SB[g], s));
+                SG_MERGE_TRY(copy_add<uint32_t>(r.S.suffix, r.S.nnz, 0u, out->S.suffix + SB[g], s));
+                SG_MERGE_TRY(copy_add<uint8_t>(r.S.dir, r.S.nnz, (uint8_t)0, out->S.dir + SB[g], s));
+            } else if (n > 0) {  // no item of this group has R: its rows of S are empty
+                SG_LAUNCH("batch_merge", fill_kernel<int64_t>, (n + 255) / 256, 256, 0, s, out->S.row_ptr + RB[g],
+                          n, SB[g]);
+            }
+        }
+    }
+    // the closing row pointers
+    SG_CUDA_TRY(cudaMemcpyAsync(out->A.row_ptr + N, &nA, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    SG_CUDA_TRY(cudaMemcpyAsync(out->At.row_ptr + M, &nA, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    SG_CUDA_TRY(cudaMemcpyAsync(out->C.row_ptr + N, &nC, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (any_s) SG_CUDA_TRY(cudaMemcpyAsync(out->S.row_ptr + N, &nS, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+#undef SG_MERGE_ALLOC
+#undef SG_MERGE_TRY
+    out->n_items = nitems;
+    out->read_off = (int64_t *)malloc(sizeof(int64_t) * (nitems + 1));
+    out->col_off = (int64_t *)malloc(sizeof(int64_t) * (nitems + 1));
+    out->iterations = (int32_t *)malloc(sizeof(int32_t) * (nitems > 0 ? nitems : 1));
+    if (!out->read_off || !out->col_off || !out->iterations) {
+        set_error("run_batch: host allocation failed");
+        return fail(SG_ERR_OOM);
+    }
+    out->iterations_all = 0;
+    for (int g = 0; g < ng; g++) {
+        const sg_batch_result &r = gr[g];
+        for (int32_t b = cut[g]; b < cut[g + 1]; b++) {
+            const int32_t lb = b - cut[g];
+            out->read_off[b] = RB[g] + r.read_off[lb];
+            out->col_off[b] = CB[g] + r.col_off[lb];
+            out->iterations[b] = r.iterations[lb];
+        }
+        out->iterations_all = std::max(out->iterations_all, r.iterations_all);
+    }
+    out->read_off[nitems] = N;
+    out->col_off[nitems] = M;
+    // the host copies of the closing row pointers must outlive the copies: wait for them
+    SG_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int g = 0; g < ng; g++) sg_free_batch(&gr[g], (sg_stream_t)s);
     return SG_OK;
 }
 

@@ -70,3 +70,36 @@ def test_batch_rejects_out_of_set_columns():
     with pytest.raises(sg.SgError) as e:
         sg.run_batch(_device(sets, [True, True]), k=17)
     assert e.value.status == sg.SG_ERR_INVALID
+
+
+@pytest.mark.parametrize("cfg", [{"batch_group_kb": 1200, "batch_alone_kb": 700},
+                                 {"batch_group_kb": 1200, "batch_alone_kb": 0},
+                                 {"batch_group_kb": 100000, "batch_alone_kb": 500}],
+                         ids=["groups+alone", "groups", "alone"])
+def test_batch_in_groups_matches_oracle(cfg):
+    """The batch split into several unions (and items that run on their own), their results moved
+    into one batch result: every slice still equals the oracle on its set alone. The first two
+    sets have no R, so a group without any R sits beside groups with one."""
+    sets = _sets(4, 10)
+    with_r = [b >= 2 for b in range(len(sets))]
+    saved = sg.tunables()
+    try:
+        for k, v in cfg.items():
+            sg.tune(k, v)
+        res = sg.run_batch(_device(sets, with_r), k=17, min_shared=2, max_seeds=2, fuzz=150)
+    finally:
+        for k, v in saved.items():
+            sg.tune(k, v)
+    for b, x in enumerate(sets):
+        got = res.item(b)
+        km = oracle.build_kmer_matrix(x["seq"], x["offsets"], 17, x["lo"], x["hi"])
+        assert np.array_equal(got["codes"], km["codes"]), b
+        assert_csr_equal(got["A"], km["A"], f"A[{b}]")
+        assert_csr_equal(got["At"], km["At"], f"At[{b}]")
+        assert_overlap_equal(got["C"], oracle.overlap_spgemm(km["A"], km["At"], 2, 2))
+        if with_r[b]:
+            eS, eit = oracle.transitive_reduce(x["R"], 150)
+            assert_graph_equal(got["S"], eS)
+            assert got["iterations"] == eit, b
+        else:
+            assert got["S"]["col"].size == 0 and got["iterations"] == 0
