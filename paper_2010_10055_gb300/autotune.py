@@ -18,20 +18,19 @@ SPACE = {
     "bloom_bin_kb": [64, 128],
     "bloom_scatter_cfg": [0, 1, 2],
     "kmer_sort_buckets": [0, 2, 3],
-    "bloom_slice_mb": [32, 48, 64, 96, 128],
-    "bloom_unroll": [4, 8],
     "bloom_bits": [6, 8, 10, 12],
-    "spgemm_fused": [0, 1],
+    "radix_lookback": [4, 8],
     "spgemm_upper": [0, 1],
-    "spgemm_tab_warps": [0, 32, 48, 64],
+    "spgemm_guess_pct": [150, 200, 250, 300],
+    "spgemm_escalate": [0, 1],
+    "spgemm_filter_mode": [0, 1],
+    "spgemm_tab_warps": [32, 48, 64],
     "spgemm_tmp_pct": [110, 125, 200],
-    "spgemm_filter_mode": [0, 1, 2],
-    "spgemm_filter_work": [1024, 2048, 4096, 8192],
-    "spgemm_guess_pct": [150, 200, 300, 400],
-    "sym_guess_shift": [0, 1, 2, 3],
-    "spgemm_blocks_per_sm": [2, 4, 8, 16],
-    "tr_blocks_per_sm": [4, 8, 16, 32],
+    "spgemm_blocks_per_sm": [4, 8, 16],
+    "tr_blocks_per_sm": [8, 16, 32],
 }
+# the batched form adds the planner's thresholds
+BATCH_SPACE = {"batch_alone_kb": [32000, 64000, 128000], "batch_group_kb": [100000, 250000, 500000, 1000000]}
 
 
 def _time_ms(step, reps: int) -> float:
@@ -140,10 +139,10 @@ def _main():
     p.add_argument("--cache", default=None)
     a = p.parse_args()
     if a.batched:
-        sets = synth.batched_sets(a.sets, 20e3, 200e3)
+        sets = synth.batched_sets(a.sets, 20e3, 2e6)
         items = [dict(seq=torch.from_numpy(x["seq"]).cuda(), offsets=torch.from_numpy(x["offsets"]).cuda(),
                       lo=x["lo"], hi=x["hi"], R=sg.DeviceGraph.from_numpy(x["R"])) for x in sets]
-        signature = f"batched-{a.sets}"
+        signature = f"batched-{a.sets}"  # the bench's batched measurement loads this key
 
         def step():
             sg.run_batch(items, k=17, min_shared=2, max_seeds=2, fuzz=1000)
@@ -159,7 +158,8 @@ def _main():
             sg.overlap_spgemm(km, w.min_shared, w.max_seeds)
             sg.transitive_reduce(R, w.fuzz)
     before = sg.tunables()
-    res = autotune(step, reps=a.reps, log=lambda s: print(s, flush=True))
+    space = {**SPACE, **BATCH_SPACE} if a.batched else SPACE
+    res = autotune(step, space=space, reps=a.reps, log=lambda s: print(s, flush=True))
     changed = {k: (before[k], v) for k, v in res["params"].items() if before.get(k) != v}
     print(json.dumps({"signature": signature, "ms": res["ms"], "trials": res["trials"], "changed": changed,
                       "params": res["params"]}), flush=True)

@@ -315,9 +315,9 @@ static Tunable g_tunables[] = {
     {"spgemm_big_threads", 1024, 512, 1024},  // threads of numeric blocks with 4 K table slots or more
     {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch
     {"pool_cross_stream_reuse", 1, 0, 1}, // pool may hand memory freed on one stream to another
-    {"batch_alone_kb", 16000, 0, 1 << 30},  // batched items of this many kilobases or more run on their
+    {"batch_alone_kb", 64000, 0, 1 << 30},  // batched items of this many kilobases or more run on their
                                             // own (0: every item shares the union)
-    {"batch_group_kb", 1000000, 1, 1 << 30},// ... the others share unions of at most this many kilobases
+    {"batch_group_kb", 500000, 1, 1 << 30}, // ... the others share unions of at most this many kilobases
 };
 static std::mutex g_tune_mu;
 

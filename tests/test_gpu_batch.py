@@ -103,3 +103,30 @@ def test_batch_in_groups_matches_oracle(cfg):
             assert got["iterations"] == eit, b
         else:
             assert got["S"]["col"].size == 0 and got["iterations"] == 0
+
+
+def test_batch_at_stated_sizes_equals_each_set_alone():
+    """Sets drawn from the batched workload's own distribution (genomes log-uniform 20 kbp - 2 Mbp,
+    coverage 10-40x), the largest of them included, under the default planner: every slice of the
+    batch equals the three calls on that set alone on the GPU, bit for bit (the plain calls are
+    the ones the oracle pins elsewhere), and the smallest sets also equal the oracle."""
+    sets = synth.batched_sets(512, 20e3, 2e6)
+    order = np.argsort([x["seq"].size for x in sets])
+    pick = sorted(set(order[:8].tolist()) | set(order[-4:].tolist()) | set(order[250:262].tolist()))
+    sub = [sets[b] for b in pick]
+    items = _device(sub, [True] * len(sub))
+    res = sg.run_batch(items, k=17, min_shared=2, max_seeds=2, fuzz=1000)
+    for b, (x, it) in enumerate(zip(sub, items)):
+        got = res.item(b)
+        km = sg.build_kmer_matrix(it["seq"], it["offsets"], 17, x["lo"], x["hi"])
+        kmn = km.to_numpy()
+        assert np.array_equal(got["codes"], kmn["codes"]), b
+        assert_csr_equal(got["A"], kmn["A"], f"A[{b}]")
+        assert_csr_equal(got["At"], kmn["At"], f"At[{b}]")
+        assert_overlap_equal(got["C"], sg.overlap_spgemm(km, 2, 2).to_numpy())
+        S, it_ = sg.transitive_reduce(it["R"], 1000)
+        assert_graph_equal(got["S"], S.to_numpy())
+        assert got["iterations"] == it_, b
+        if x["seq"].size < 400_000:
+            ekm = oracle.build_kmer_matrix(x["seq"], x["offsets"], 17, x["lo"], x["hi"])
+            assert_overlap_equal(got["C"], oracle.overlap_spgemm(ekm["A"], ekm["At"], 2, 2))

@@ -145,3 +145,27 @@ def test_server_admits_job_over_budget_with_c_in_tiles():
         _check(srv.wait(t_small), small, 300)
     finally:
         srv.close()
+
+
+def test_served_jobs_at_stated_sizes_equal_plain_calls():
+    """Jobs drawn from the served workload's own distribution (Pareto genome sizes from 20 kbp,
+    30x), submitted as a burst so that they share batches: each result equals the plain three
+    calls on that job alone, bit for bit."""
+    jobs = synth.served_jobs(60, 200.0)
+    srv = sg.Server(hbm_budget=150 << 30, max_batch=16, workers=2, fuzz=1000)
+    try:
+        res = [srv.wait(srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"])) for j in jobs[:4]]
+        tickets = [srv.submit(j["seq"], j["offsets"], j["lo"], j["hi"], j["R"]) for j in jobs[4:]]
+        res += [srv.wait(t) for t in tickets]
+    finally:
+        srv.close()
+    assert max(r["batch_size"] for r in res) > 1
+    import torch
+    for r, j in zip(res, jobs):
+        assert r["status"] == sg.SG_OK, r["error"]
+        km = sg.build_kmer_matrix(torch.from_numpy(j["seq"]).cuda(), torch.from_numpy(j["offsets"]).cuda(), 17,
+                                  j["lo"], j["hi"])
+        assert_overlap_equal(r["C"], sg.overlap_spgemm(km, 2, 2).to_numpy())
+        S, it = sg.transitive_reduce(sg.DeviceGraph.from_numpy(j["R"]), 1000)
+        assert_graph_equal(r["S"], S.to_numpy())
+        assert r["iterations"] == it
