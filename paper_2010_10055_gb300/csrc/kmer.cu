@@ -805,6 +805,309 @@ __global__ void emit_fused_kernel(const uint64_t *__restrict__ pre,
     }
 }
 
+// Segments straight from the sorted keys of the PK_POS form, in two passes over tiles of
+// DS_TILE sorted candidates (DS_ITEMS consecutive ones per thread), with no unpacked key/value
+// arrays and no per-candidate prefix array:
+//   mark: each tile stages its keys (and DS_HALO neighbours on each side) in shared memory, walks
+//         each candidate's run of equal keys there (as seg_flags_kernel does), and stores two bits
+//         per candidate -- heads a reliable segment | kept (first of its read in a reliable
+//         segment) << 1 -- and the tile's two totals;
+//   emit: after exclusive scans of the tile totals, each tile recovers every candidate's column
+//         and At slot from its tile's prefixes and a block scan of its flags, and writes At, the
+//         codes and the pairs sorted into A (emit_fused_kernel's outputs).
+// Keys are equal when they lie in the same bucket range and agree in their code bits. "First of
+// its read" tests whether the previous candidate's window lies in the extent [off[r], off[r + 1])
+// of the read r holding this one; the reads are found by searches that run for DS_GROUP
+// candidates at once, so that their loads overlap.
+constexpr int DS_NT = 256;
+constexpr int DS_ITEMS = 16;
+constexpr int DS_TILE = DS_NT * DS_ITEMS;
+constexpr int DS_HALO = SEG_WALK_MAX + 16;  // a walk reads at most SEG_WALK_MAX + 1 neighbours
+constexpr int DS_GROUP = 4;
+// Staged keys are padded by one slot every 16, so that the 32 lanes of a warp, reading 8-byte
+// keys DS_ITEMS apart, hit distinct banks.
+__device__ __forceinline__ int ds_pad(int j) { return j + (j >> 4); }
+constexpr int DS_SMEM = DS_TILE + 2 * DS_HALO + (DS_TILE + 2 * DS_HALO) / 16 + 1;
+
+// The bucket holding sorted index i, and the bucket's index range [s0, s1).
+__device__ __forceinline__ uint64_t bucket_range(const BucketStarts &bs, int64_t i, int64_t nc, int64_t &s0,
+                                                 int64_t &s1) {
+    uint64_t b = 0;
+    s0 = 0;
+    s1 = nc;
+#pragma unroll
+    for (int j = 1; j < 8; j++)  // constant indices: the ranges stay in parameter space
+        if (j < bs.nb) {
+            const int64_t st = bs.start[j];
+            if (i >= st) {
+                b++;
+                s0 = st;
+            } else if (st < s1) {
+                s1 = st;
+            }
+        }
+    return b;
+}
+
+// r[u] = the read holding window q[u] (the last r with off[r] <= q[u]) for the active u, found
+// together: every step issues the loads of all unfinished searches before using any.
+template <int G>
+__device__ __forceinline__ void reads_of(const int64_t (&q)[G], const bool (&act)[G], int64_t (&r)[G],
+                                         const int64_t *__restrict__ off, int64_t n,
+                                         const int32_t *__restrict__ lut, int64_t nb) {
+    int64_t lo[G], hi[G];
+#pragma unroll
+    for (int u = 0; u < G; u++) {
+        lo[u] = 0;
+        hi[u] = 1;
+        if (act[u]) {
+            const int64_t b = q[u] >> LUT_SHIFT;
+            lo[u] = lut[b];
+            hi[u] = b + 1 < nb ? (int64_t)lut[b + 1] + 1 : n;  // the read lies in [lo, hi)
+            if (hi[u] > n) hi[u] = n;
+        }
+    }
+    for (;;) {
+        bool any = false;
+        int64_t mid[G], om[G];
+#pragma unroll
+        for (int u = 0; u < G; u++) {
+            mid[u] = (lo[u] + hi[u]) >> 1;
+            if (hi[u] - lo[u] > 1) {
+                om[u] = off[mid[u]];
+                any = true;
+            }
+        }
+        if (!any) break;
+#pragma unroll
+        for (int u = 0; u < G; u++)
+            if (hi[u] - lo[u] > 1) {
+                if (om[u] <= q[u]) lo[u] = mid[u]; else hi[u] = mid[u];
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < G; u++) r[u] = lo[u];
+}
+
+// Stages sorted keys [base - DS_HALO, base + DS_TILE + DS_HALO) in sk, key base - DS_HALO + j at
+// sk[ds_pad(j)] (0 outside [0, nc)).
+__device__ __forceinline__ void stage_keys(uint64_t *sk, const uint64_t *__restrict__ packed, int64_t base,
+                                           int64_t nc) {
+    for (int j = threadIdx.x; j < DS_TILE + 2 * DS_HALO; j += DS_NT) {
+        const int64_t g = base - DS_HALO + j;
+        sk[ds_pad(j)] = (g >= 0 && g < nc) ? __ldg(packed + g) : 0ull;
+    }
+}
+
+struct SegArgs {
+    const uint64_t *packed;
+    int64_t nc;
+    int pb;
+    BucketStarts bs;
+    uint32_t lo, hi;
+    const uint32_t *lohi;
+    int kbits;
+    int hmax;
+    const int64_t *off;
+    int64_t n;
+    const int32_t *lut;
+    int64_t nb;
+};
+
+__global__ void __launch_bounds__(DS_NT) seg_mark_kernel(SegArgs a, uint32_t *__restrict__ flags,
+                                                        uint32_t *__restrict__ tseg, uint32_t *__restrict__ tkeep) {
+    __shared__ uint64_t sk[DS_SMEM];
+    __shared__ uint32_t red[2][DS_NT / 32];
+    const int64_t tile = blockIdx.x, base = tile * DS_TILE;
+    stage_keys(sk, a.packed, base, a.nc);
+    __syncthreads();
+    const int l0 = DS_HALO + threadIdx.x * DS_ITEMS;  // this thread's first item in sk (unpadded)
+    const int64_t i0 = base + threadIdx.x * DS_ITEMS;
+    const uint64_t lowmask = (1ull << a.pb) - 1;
+    uint32_t fw = 0, need = 0;
+    // the run of equal keys [rh, re) holding the last walked item, and whether it is a reliable
+    // segment; the items after it inside the run share both (a run cut short by the walk bound is
+    // longer than any hi, hence unreliable for all of its items)
+    int64_t rh = 0, re = 0;
+    bool rrel = false;
+#pragma unroll 1
+    for (int u = 0; u < DS_ITEMS; u++) {
+        const int64_t i = i0 + u;
+        if (i >= a.nc) break;
+        if (i >= re) {
+            int64_t s0, s1;
+            const uint64_t b = bucket_range(a.bs, i, a.nc, s0, s1);
+            const int li = l0 + u;
+            const uint64_t c = sk[ds_pad(li)] >> a.pb;
+            int back = 0, fwd = 0;
+            while (back <= a.hmax && i - back > s0 && (sk[ds_pad(li - back - 1)] >> a.pb) == c) back++;
+            while (fwd <= a.hmax && i + 1 + fwd < s1 && (sk[ds_pad(li + 1 + fwd)] >> a.pb) == c) fwd++;
+            uint32_t lo_i = a.lo, hi_i = a.hi;
+            if (a.lohi) {
+                const uint64_t job = ((b << a.bs.shift) | c) >> a.kbits;
+                lo_i = a.lohi[2 * job];
+                hi_i = a.lohi[2 * job + 1];
+            }
+            const int len = back + fwd + 1;
+            rrel = back <= a.hmax && fwd <= a.hmax && len >= (int64_t)lo_i && len <= (int64_t)hi_i;
+            rh = i - back;
+            re = i + 1 + fwd;
+        }
+        if (rrel && rh == i) fw |= 3u << (2 * u);  // heads its segment: first of its read too
+        else if (rrel) need |= 1u << u;            // kept if the previous window is of another read
+    }
+#pragma unroll 1
+    for (int u0 = 0; u0 < DS_ITEMS; u0 += DS_GROUP) {
+        if (((need >> u0) & ((1u << DS_GROUP) - 1)) == 0) continue;
+        int64_t q[DS_GROUP], r[DS_GROUP];
+        bool act[DS_GROUP];
+#pragma unroll
+        for (int u = 0; u < DS_GROUP; u++) {
+            act[u] = (need >> (u0 + u)) & 1u;
+            q[u] = (int64_t)((sk[ds_pad(l0 + u0 + u)] & lowmask) >> 1);
+        }
+        reads_of<DS_GROUP>(q, act, r, a.off, a.n, a.lut, a.nb);
+#pragma unroll
+        for (int u = 0; u < DS_GROUP; u++)
+            if (act[u]) {
+                const int64_t qp = (int64_t)((sk[ds_pad(l0 + u0 + u - 1)] & lowmask) >> 1);
+                if (!(qp >= a.off[r[u]] && qp < a.off[r[u] + 1])) fw |= 2u << (2 * (u0 + u));
+            }
+    }
+    flags[tile * DS_NT + threadIdx.x] = fw;
+    uint32_t ns = __popc(fw & 0x55555555u), nk = __popc(fw & 0xAAAAAAAAu);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        nk += __shfl_xor_sync(0xffffffffu, nk, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = ns;
+        red[1][threadIdx.x >> 5] = nk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ts = 0, tk = 0;
+        for (int w = 0; w < DS_NT / 32; w++) {
+            ts += red[0][w];
+            tk += red[1][w];
+        }
+        tseg[tile] = ts;
+        tkeep[tile] = tk;
+    }
+}
+
+// pseg / pkeep: exclusive prefixes of the tile totals (reliable segments, kept entries). The
+// tile's candidates are taken in DS_ITEMS rows of DS_NT (candidate base + row * DS_NT + thread),
+// so that a warp's outputs of one row are consecutive; a candidate's column and At slot are its
+// tile's prefix plus the counts of the rows before it and of the lanes before it (ballots).
+__global__ void __launch_bounds__(DS_NT, 4) seg_emit_kernel(SegArgs a, const uint32_t *__restrict__ flags,
+                                                        const int64_t *__restrict__ pseg,
+                                                        const int64_t *__restrict__ pkeep, int64_t m, int64_t nnz,
+                                                        int32_t *__restrict__ at_col, uint32_t *__restrict__ at_val,
+                                                        int64_t *__restrict__ at_rp, uint64_t *__restrict__ codes,
+                                                        uint32_t *__restrict__ a_key, uint64_t *__restrict__ a_val,
+                                                        unsigned long long *__restrict__ job_ncols) {
+    constexpr int NW = DS_NT / 32;
+    __shared__ uint64_t sk[DS_SMEM];
+    __shared__ uint32_t sf[DS_NT];                       // the tile's flag words (DS_ITEMS candidates each)
+    __shared__ uint32_t hmask[DS_ITEMS][NW], kmask[DS_ITEMS][NW];  // per row and warp: heads, kept
+    __shared__ uint32_t hpre[DS_ITEMS * NW], kpre[DS_ITEMS * NW];  // their exclusive prefixes in the tile
+    const int64_t tile = blockIdx.x, base = tile * DS_TILE;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (tile == 0 && threadIdx.x == 0) at_rp[m] = nnz;
+    stage_keys(sk, a.packed, base, a.nc);
+    sf[threadIdx.x] = flags[tile * DS_NT + threadIdx.x];
+    __syncthreads();
+    auto flag_of = [&](int j) { return (sf[j >> 4] >> (2 * (j & 15))) & 3u; };  // candidate base + j
+#pragma unroll
+    for (int u = 0; u < DS_ITEMS; u++) {
+        const uint32_t f = flag_of(u * DS_NT + threadIdx.x);
+        const uint32_t hb = __ballot_sync(0xffffffffu, f & 1u), kb = __ballot_sync(0xffffffffu, f & 2u);
+        if (lane == 0) {
+            hmask[u][w] = hb;
+            kmask[u][w] = kb;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scans of the DS_ITEMS * NW counts, row-major
+        constexpr int PER = DS_ITEMS * NW / 32;
+        uint32_t hc[PER], kc[PER], hs = 0, ks = 0;
+#pragma unroll
+        for (int x = 0; x < PER; x++) {
+            const int idx = lane * PER + x;
+            hc[x] = __popc(hmask[idx / NW][idx % NW]);
+            kc[x] = __popc(kmask[idx / NW][idx % NW]);
+            hs += hc[x];
+            ks += kc[x];
+        }
+        uint32_t hi = hs, ki = ks;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t hy = __shfl_up_sync(0xffffffffu, hi, o), ky = __shfl_up_sync(0xffffffffu, ki, o);
+            if (lane >= o) {
+                hi += hy;
+                ki += ky;
+            }
+        }
+        uint32_t hr = hi - hs, kr = ki - ks;
+#pragma unroll
+        for (int x = 0; x < PER; x++) {
+            hpre[lane * PER + x] = hr;
+            kpre[lane * PER + x] = kr;
+            hr += hc[x];
+            kr += kc[x];
+        }
+    }
+    __syncthreads();
+    const int64_t seg0 = pseg[tile], keep0 = pkeep[tile];
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint64_t lowmask = (1ull << a.pb) - 1;
+#pragma unroll 1
+    for (int u0 = 0; u0 < DS_ITEMS; u0 += DS_GROUP) {
+        int64_t q[DS_GROUP], r[DS_GROUP];
+        bool act[DS_GROUP];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < DS_GROUP; u++) {
+            const int j = (u0 + u) * DS_NT + threadIdx.x;
+            act[u] = (flag_of(j) & 2u) != 0;
+            any |= act[u];
+            q[u] = (int64_t)((sk[ds_pad(DS_HALO + j)] & lowmask) >> 1);
+        }
+        if (any) reads_of<DS_GROUP>(q, act, r, a.off, a.n, a.lut, a.nb);
+#pragma unroll
+        for (int u = 0; u < DS_GROUP; u++) {
+            const int row = u0 + u, j = row * DS_NT + threadIdx.x;
+            const uint32_t f = flag_of(j);
+            if (!f) continue;
+            const int64_t i = base + j;
+            const uint64_t p = sk[ds_pad(DS_HALO + j)];
+            // heads up to and including this candidate: its segment's column is that count - 1
+            const int64_t segs = seg0 + hpre[row * NW + w] + __popc(hmask[row][w] & lt) + (f & 1u);
+            const int64_t col = segs - 1;
+            const int64_t o = keep0 + kpre[row * NW + w] + __popc(kmask[row][w] & lt);
+            if (!SG_IN_BOUNDS(col >= 0 && col < m, 110, col)) continue;
+            if (f & 1u) {
+                int64_t s0, s1;
+                const uint64_t key = (bucket_range(a.bs, i, a.nc, s0, s1) << a.bs.shift) | (p >> a.pb);
+                at_rp[col] = o;
+                codes[col] = a.kbits < 64 ? key & ((1ull << a.kbits) - 1) : key;
+                if (job_ncols) atomicAdd(job_ncols + (key >> a.kbits), 1ull);
+            }
+            if (f & 2u) {
+                if (!SG_IN_BOUNDS(o >= 0 && o < nnz, 111, o)) continue;
+                const uint32_t rr = (uint32_t)r[u];
+                const uint32_t v = (uint32_t)(q[u] - a.off[r[u]]) | (uint32_t)((p & 1u) << 31);
+                at_col[o] = (int32_t)rr;
+                at_val[o] = v;
+                a_key[o] = rr;
+                a_val[o] = ((uint64_t)col << 32) | v;
+            }
+        }
+    }
+}
+
 // Row pointers of A from the read ids of its entries, sorted ascending.
 __global__ void rowptr_from_sorted_kernel(const uint32_t *__restrict__ rows, int64_t nnz, int64_t n,
                                           int64_t *__restrict__ rp) {
@@ -1058,11 +1361,20 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_LAUNCH("cand_emit", cand_emit_kernel<false>, nblk, KM_NT, 0, s, bk, (const uint32_t *)cmask,
                   (const int64_t *)wpos, mode, pb, key0, val0, nc);
     early.reset();
-    uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = sc.get<uint64_t>(nc);
-    if (!key1 || !val1) return SG_ERR_OOM;
+    uint64_t *key1 = sc.get<uint64_t>(nc), *val1 = mode == PK_PAIRS ? sc.get<uint64_t>(nc) : nullptr;
+    if (!key1 || (mode == PK_PAIRS && !val1)) return SG_ERR_OOM;
     bool alt = false;
-    const uint64_t *key;
-    uint64_t *val;
+    const uint64_t *key = nullptr;
+    uint64_t *val = nullptr;
+    // direct: segments, columns and At straight from the sorted PK_POS keys (seg_mark, scans of
+    // its tile totals, seg_emit); needs the walk bound of the fused flags
+    const bool direct = mode == PK_POS && nc > 0 && tune("kmer_direct_seg") && hmax <= (uint32_t)SEG_WALK_MAX;
+    const uint64_t *sorted = nullptr;  // direct: the sorted keys
+    uint32_t *dflags = nullptr;        // direct: two flag bits per candidate
+    int64_t *dpre = nullptr;           // direct: [ntiles + 1] segments before each tile, then kept entries
+    SegArgs dargs{};
+    uint64_t *pre = nullptr;
+    int64_t sizes[2] = {0, 0};  // m, nnz
     {
         sg_kmer_stats &ks = kmer_stats();
         ks = sg_kmer_stats{};
@@ -1095,11 +1407,33 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
             }
         }
         uint64_t *ks = alt ? key1 : key0, *kfree = alt ? key0 : key1;
-        SG_LAUNCH("unpack", unpack_kernel, blocks_for(nc, NT), NT, 0, s, (const uint64_t *)ks, (const uint64_t *)val0,
-                  nc, mode, pb, bs, off, n, (const int32_t *)lut, nlut, kfree, val1);
-        key = kfree;
-        val = val1;
-        sc.release(ks);
+        if (direct) {
+            sc.release(kfree);
+            sorted = ks;
+            const int64_t ntiles = (nc + DS_TILE - 1) / DS_TILE;
+            dflags = sc.get<uint32_t>(ntiles * DS_NT);
+            uint32_t *tcount = sc.get<uint32_t>(2 * ntiles);
+            dpre = sc.get<int64_t>(2 * (ntiles + 1));
+            if (!dflags || !tcount || !dpre) return SG_ERR_OOM;
+            dargs = SegArgs{sorted, nc, pb, bs, lo, hi, lohi, 2 * k, (int)hmax, off, n, (const int32_t *)lut, nlut};
+            SG_LAUNCH("seg_mark", seg_mark_kernel, ntiles, DS_NT, 0, s, dargs, dflags, tcount, tcount + ntiles);
+            SG_TRY(exclusive_scan<uint32_t>(tcount, dpre, ntiles, s, err));
+            SG_TRY(exclusive_scan<uint32_t>(tcount + ntiles, dpre + ntiles + 1, ntiles, s, err));
+            SG_CUDA_TRY(cudaMemcpyAsync(&sizes[0], dpre + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            SG_CUDA_TRY(cudaMemcpyAsync(&sizes[1], dpre + 2 * ntiles + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            SG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            SG_CUDA_TRY(cudaStreamSynchronize(s));
+            sc.release(tcount);
+        }
+        if (!direct) {
+            val1 = sc.get<uint64_t>(nc);
+            if (!val1) return SG_ERR_OOM;
+            SG_LAUNCH("unpack", unpack_kernel, blocks_for(nc, NT), NT, 0, s, (const uint64_t *)ks,
+                      (const uint64_t *)val0, nc, mode, pb, bs, off, n, (const int32_t *)lut, nlut, kfree, val1);
+            key = kfree;
+            val = val1;
+            sc.release(ks);
+        }
         if (val0) sc.release(val0);
     } else {
         SG_TRY((radix_sort_pairs<uint64_t, uint64_t>(key0, val0, key1, val1, nc, code_bits, &alt, s, err)));
@@ -1115,12 +1449,10 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     // The fused form packs (reliable segments, kept entries) into one scanned 64-bit word whose
     // look-back keeps 62 bits: segments < 2^31 (at most nc / 2 with the Bloom filter, each reliable
     // segment holding >= lo >= 2 entries) and kept entries < 2^31 (counted first).
-    bool fused = hmax <= (uint32_t)SEG_WALK_MAX && nc < ((int64_t)1 << 32) &&
+    bool fused = !direct && hmax <= (uint32_t)SEG_WALK_MAX && nc < ((int64_t)1 << 32) &&
                  (use_bloom || nc < ((int64_t)1 << PK_SHIFT));
     uint32_t *head = nullptr, *rel = nullptr, *keep = nullptr;
     int64_t *seg_excl = nullptr, *seg_start = nullptr, *col_of_seg = nullptr, *out_pos = nullptr;
-    uint64_t *pre = nullptr;
-    int64_t sizes[2] = {0, 0};  // m, nnz
     if (fused) {
         pre = sc.get<uint64_t>(nc + 1);
         unsigned long long *nkeep = sc.get<unsigned long long>(1);
@@ -1145,7 +1477,7 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_CUDA_TRY(cudaStreamSynchronize(s));
         sizes[0] = (int64_t)(tot & ((1ull << PK_SHIFT) - 1));
         sizes[1] = (int64_t)(tot >> PK_SHIFT);
-    } else {
+    } else if (!direct) {  // (direct: sizes and the error word were read back after its scan)
         head = sc.get<uint32_t>(nc + 1);
         seg_excl = sc.get<int64_t>(nc + 1);
         seg_start = sc.get<int64_t>(nc + 1);
@@ -1187,7 +1519,12 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     uint32_t *ak0 = sc.get<uint32_t>(nnz);
     uint64_t *av0 = sc.get<uint64_t>(nnz);
     if (!ak0 || !av0) return SG_ERR_OOM;
-    if (fused)
+    if (direct) {
+        const int64_t ntiles = (nc + DS_TILE - 1) / DS_TILE;
+        SG_LAUNCH("emit_at", seg_emit_kernel, ntiles, DS_NT, 0, s, dargs, (const uint32_t *)dflags,
+                  (const int64_t *)dpre, (const int64_t *)(dpre + ntiles + 1), m, nnz, At->col, At->val,
+                  At->row_ptr, *codes_out, ak0, av0, job_ncols);
+    } else if (fused)
         SG_LAUNCH("emit_at", emit_fused_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, (const uint64_t *)pre, key,
                   (const uint64_t *)val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0, av0, 2 * k,
                   job_ncols);
@@ -1195,7 +1532,8 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
         SG_LAUNCH("emit_at", emit_at_kernel, blocks_for(nc > 0 ? nc : 1, NT), NT, 0, s, head, seg_excl, rel,
                   col_of_seg, keep, out_pos, key, val, nc, m, nnz, At->col, At->val, At->row_ptr, *codes_out, ak0,
                   av0, 2 * k, job_ncols);
-    for (const void *p : {(const void *)key, (const void *)val, (const void *)pre,
+    for (const void *p : {(const void *)key, (const void *)val, (const void *)pre, (const void *)sorted,
+                          (const void *)dflags, (const void *)dpre,
                           (const void *)head, (const void *)seg_excl, (const void *)seg_start, (const void *)rel,
                           (const void *)col_of_seg, (const void *)keep, (const void *)out_pos})
         if (p) sc.release(p);

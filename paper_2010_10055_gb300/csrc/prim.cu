@@ -8,123 +8,9 @@
 
 namespace sg {
 
-// -------------------------------------------------------------------- decoupled look-back
-// A tile publishes a 64-bit status word per counter: flag in the top two bits (0 = nothing yet,
-// LB_A = this tile's own aggregate, LB_P = inclusive prefix through this tile), value in the low 62
-// bits. Tiles take their ids from an atomic counter in launch order, so every tile waited on has
-// already started and never waits on a later one. Each wait is bounded: after LB_SPIN_LIMIT polls
-// the waiter records DEV_TIMEOUT in *err (read back by the caller) and goes on with a zero.
-constexpr unsigned long long LB_A = 1ull << 62, LB_P = 2ull << 62, LB_VAL = (1ull << 62) - 1;
-constexpr int LB_SPIN_LIMIT = 1 << 20;  // at least 64 ms of polling; a real wait takes microseconds
-
-__device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long long v) {
-    *reinterpret_cast<volatile unsigned long long *>(p) = v;
-}
-
-__device__ __forceinline__ unsigned long long lb_wait(const unsigned long long *p, uint32_t *err) {
-    unsigned long long v = *reinterpret_cast<const volatile unsigned long long *>(p);
-    for (int it = 0; (v >> 62) == 0; it++) {
-        if (it >= LB_SPIN_LIMIT) {
-            if (err) atomicOr(err, (uint32_t)DEV_TIMEOUT);
-            return LB_P;
-        }
-        __nanosleep(64);
-        v = *reinterpret_cast<const volatile unsigned long long *>(p);
-    }
-    return v;
-}
-
-// ------------------------------------------------------------------------------- scan
-// One pass: each tile loads its items once, publishes its sum, finds the sum of all earlier tiles
-// by look-back (warp 0, 32 predecessors per step) and writes its outputs.
-constexpr int SCAN_NT = 256;
-constexpr int SCAN_ITEMS = 16;
-constexpr int SCAN_TILE = SCAN_NT * SCAN_ITEMS;
-
-// stall != 0 (test hook, sg_debug_stall_lookback): tile 0 withholds its prefix, so the waits of
-// the tiles after it run out.
-template <class T>
-__global__ void __launch_bounds__(SCAN_NT) scan_kernel(const T *in, int64_t n, int64_t *out,
-                                                      unsigned long long *status, unsigned int *tile_ctr,
-                                                      uint32_t *err, int stall) {
-    __shared__ int64_t vals[SCAN_TILE + SCAN_TILE / 32];
-    __shared__ int64_t tmp[SCAN_NT / 32 + 1];
-    __shared__ int64_t s_excl;
-    __shared__ unsigned int s_tile;
-    if (threadIdx.x == 0) s_tile = tile_ctr ? atomicAdd(tile_ctr, 1u) : 0u;
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int64_t base = tile * SCAN_TILE;
-    auto pad = [](int i) { return i + (i >> 5); };  // break the bank conflicts of blocked reads
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        const int idx = i * SCAN_NT + threadIdx.x;
-        vals[pad(idx)] = (base + idx < n) ? (int64_t)in[base + idx] : 0;
-    }
-    __syncthreads();
-    int64_t loc[SCAN_ITEMS];
-    int64_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        loc[i] = sum;
-        sum += vals[pad(threadIdx.x * SCAN_ITEMS + i)];
-    }
-    int64_t total;
-    const int64_t pre = block_exclusive_scan<SCAN_NT>(sum, tmp, &total);
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        int64_t excl = 0;
-        if (tile > 0) {
-            if (lane == 0) lb_store(status + tile, LB_A | (unsigned long long)total);
-            for (int64_t t = tile - 1;; t -= 32) {
-                const int64_t idx = t - lane;
-                const unsigned long long v = idx >= 0 ? lb_wait(status + idx, err) : LB_P;
-                const unsigned pm = __ballot_sync(0xffffffffu, (v >> 62) == 2);
-                const int stop = pm ? __ffs(pm) - 1 : 31;  // nearest inclusive prefix
-                int64_t c = lane <= stop ? (int64_t)(v & LB_VAL) : 0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                excl += c;
-                if (pm) break;
-            }
-        }
-        if (lane == 0) {
-            if (status && !(stall && tile == 0)) lb_store(status + tile, LB_P | (unsigned long long)(excl + total));
-            s_excl = excl;
-        }
-    }
-    __syncthreads();
-    const int64_t off = s_excl + pre;
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) vals[pad(threadIdx.x * SCAN_ITEMS + i)] = loc[i] + off;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        const int idx = i * SCAN_NT + threadIdx.x;
-        if (base + idx < n) out[base + idx] = vals[pad(idx)];
-    }
-    if (base + SCAN_TILE >= n && threadIdx.x == 0) out[n] = s_excl + total;
-}
-
 template <class T>
 sg_status exclusive_scan(const T *in, int64_t *out, int64_t n, cudaStream_t s, uint32_t *err) {
-    if (n <= 0) {
-        SG_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
-        return SG_OK;
-    }
-    const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (nt == 1) {
-        SG_LAUNCH("scan", scan_kernel<T>, 1, SCAN_NT, 0, s, in, n, out, (unsigned long long *)nullptr,
-                  (unsigned int *)nullptr, err, 0);
-        return SG_OK;
-    }
-    Scratch sc(s);
-    unsigned long long *status = sc.get<unsigned long long>(nt + 1);  // [nt] status, then the tile counter
-    if (!status) return SG_ERR_OOM;
-    SG_CUDA_TRY(cudaMemsetAsync(status, 0, (size_t)(nt + 1) * sizeof(unsigned long long), s));
-    SG_LAUNCH("scan", scan_kernel<T>, nt, SCAN_NT, 0, s, in, n, out, status, (unsigned int *)(status + nt), err,
-              debug_stall_lookback());
-    return SG_OK;
+    return exclusive_scan_fn(ScanLoad<T>{in}, out, n, s, err);
 }
 
 template sg_status exclusive_scan<int64_t>(const int64_t *, int64_t *, int64_t, cudaStream_t, uint32_t *);

@@ -42,13 +42,16 @@ def test_kmer_matrix_sort_forms(k, buckets, G):
     seq = rd["seq"].copy()
     seq[::997] = ord("N")
     exp = oracle.build_kmer_matrix(seq, rd["offsets"], k, 2, 12)
-    saved = sg.tunables()["kmer_sort_buckets"]
+    saved = sg.tunables()
     try:
         sg.tune("kmer_sort_buckets", buckets)
-        _, got = gpu_kmer(seq, rd["offsets"], k, 2, 12)
+        for direct in (1, 0):  # segments from the sorted packed keys, or from unpacked arrays
+            sg.tune("kmer_direct_seg", direct)
+            _, got = gpu_kmer(seq, rd["offsets"], k, 2, 12)
+            assert_kmer_equal(got, exp)
     finally:
-        sg.tune("kmer_sort_buckets", saved)
-    assert_kmer_equal(got, exp)
+        for name in ("kmer_sort_buckets", "kmer_direct_seg"):
+            sg.tune(name, saved[name])
 
 
 def test_kmer_matrix_edge_cases():

@@ -47,6 +47,8 @@ CONFIGS = [
     {"bloom_scatter_levels": 2, "bloom_bin_kb": 16},                 # two grouping passes
     {"bloom_scatter_levels": 2, "bloom_bin_room_pct": 50},           # superbins overflow: sliced redo
     {"bloom_scatter_cfg": 2, "kmer_sort_buckets": 0},                # 256 x 32 tiles, one bucket
+    {"kmer_direct_seg": 0},                                          # unpacked keys, then segments
+    {"kmer_direct_seg": 0, "kmer_sort_buckets": 0},
     {"spgemm_fused": 0, "sym_guess_shift": 8},                      # two passes, tiny symbolic guesses
     {"spgemm_fused": 0, "sym_guess_shift": 0, "spgemm_blocks_per_sm": 1, "tr_blocks_per_sm": 1},
     {"spgemm_guess_pct": 25},                                        # fused, most rows overflow
