@@ -284,6 +284,7 @@ static Tunable g_tunables[] = {
     {"bloom_scatter_cfg", 0, 0, 2},       // bin scatter tile: 0 512x16, 1 256x16, 2 256x32 hashes
     {"bloom_scatter_levels", 0, 0, 2},    // passes grouping hashes by bin (0: two beyond 4096 bins)
     {"kmer_sort_buckets", 3, 0, 3},       // at most this many top code bits become candidate buckets
+    {"kmer_direct_seg", 1, 0, 1},         // 1: segments and At straight from the sorted packed keys
     {"radix_match", 0, 0, 1},             // radix sort ranking: 1 one match instruction per key, 0 ballots
     {"radix_lookback", 8, 1, 8},          // radix sort look-back: predecessors read per step
     {"bloom_bin_room_pct", 112, 1, 1000}, // a bin's hash buffer, % of the mean (overflow: sliced)
@@ -299,6 +300,7 @@ static Tunable g_tunables[] = {
     {"spgemm_lower_smem", 4096, 1, 4096}, // (0 above) parts up to this long are sorted in shared memory
     {"spgemm_tab_warps", 64, 0, 64},      // fused-pass blocks: threads for about this many warps per SM
                                           // across the blocks that fit (0: fixed threads per table size)
+    {"spgemm_tab_max_threads", 1024, 64, 1024},  // ... but at most this many threads per block
     {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)
     {"spgemm_guess_pct", 200, 1, 10000},  // guess = pct / 100 x sampled partners per A entry x entries
     {"spgemm_tmp_pct", 125, 1, 10000},    // fused temporary region = pct / 100 x sampled kept entries
