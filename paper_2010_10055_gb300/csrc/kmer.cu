@@ -921,58 +921,74 @@ __global__ void __launch_bounds__(DS_NT) seg_mark_kernel(SegArgs a, uint32_t *__
     const int64_t tile = blockIdx.x, base = tile * DS_TILE;
     stage_keys(sk, a.packed, base, a.nc);
     __syncthreads();
-    const int l0 = DS_HALO + threadIdx.x * DS_ITEMS;  // this thread's first item in sk (unpadded)
-    const int64_t i0 = base + threadIdx.x * DS_ITEMS;
-    const uint64_t lowmask = (1ull << a.pb) - 1;
+    // indices below are local: candidate base - DS_HALO + x is staged at sk[ds_pad(x)]
+    const int l0 = DS_HALO + threadIdx.x * DS_ITEMS;
+    const int64_t g0 = base - DS_HALO;
+    const int64_t lrest = a.nc - g0;
+    const int lend = lrest < (int64_t)(l0 + DS_ITEMS) ? (int)lrest : l0 + DS_ITEMS;  // past this thread's last item
+    const uint64_t lowmask = (1ull << a.pb) - 1, codemask = ~lowmask;
     uint32_t fw = 0, need = 0;
+    // the bucket range [b0, b1) of the current item, clipped to the staged keys
+    int b0 = 0, b1 = 0;
+    uint64_t bkt = 0;
     // the run of equal keys [rh, re) holding the last walked item, and whether it is a reliable
     // segment; the items after it inside the run share both (a run cut short by the walk bound is
     // longer than any hi, hence unreliable for all of its items)
-    int64_t rh = 0, re = 0;
+    int rh = 0, re = 0;
     bool rrel = false;
 #pragma unroll 1
-    for (int u = 0; u < DS_ITEMS; u++) {
-        const int64_t i = i0 + u;
-        if (i >= a.nc) break;
-        if (i >= re) {
-            int64_t s0, s1;
-            const uint64_t b = bucket_range(a.bs, i, a.nc, s0, s1);
-            const int li = l0 + u;
-            const uint64_t c = sk[ds_pad(li)] >> a.pb;
-            int back = 0, fwd = 0;
-            while (back <= a.hmax && i - back > s0 && (sk[ds_pad(li - back - 1)] >> a.pb) == c) back++;
-            while (fwd <= a.hmax && i + 1 + fwd < s1 && (sk[ds_pad(li + 1 + fwd)] >> a.pb) == c) fwd++;
+    for (int li = l0; li < lend; li++) {
+        if (li >= re) {
+            if (li >= b1) {
+                int64_t s0, s1;
+                bkt = bucket_range(a.bs, g0 + li, a.nc, s0, s1);
+                b0 = s0 - g0 > 0 ? (int)(s0 - g0) : 0;
+                b1 = s1 - g0 < (int64_t)(DS_TILE + 2 * DS_HALO) ? (int)(s1 - g0) : DS_TILE + 2 * DS_HALO;
+            }
+            const uint64_t key = sk[ds_pad(li)];
+            int h = li, e = li + 1;
+            while (li - h <= a.hmax && h > b0 && ((sk[ds_pad(h - 1)] ^ key) & codemask) == 0) h--;
+            while (e - li - 1 <= a.hmax && e < b1 && ((sk[ds_pad(e)] ^ key) & codemask) == 0) e++;
             uint32_t lo_i = a.lo, hi_i = a.hi;
             if (a.lohi) {
-                const uint64_t job = ((b << a.bs.shift) | c) >> a.kbits;
+                const uint64_t job = ((bkt << a.bs.shift) | (key >> a.pb)) >> a.kbits;
                 lo_i = a.lohi[2 * job];
                 hi_i = a.lohi[2 * job + 1];
             }
-            const int len = back + fwd + 1;
-            rrel = back <= a.hmax && fwd <= a.hmax && len >= (int64_t)lo_i && len <= (int64_t)hi_i;
-            rh = i - back;
-            re = i + 1 + fwd;
+            const int len = e - h;
+            rrel = li - h <= a.hmax && e - li - 1 <= a.hmax && len >= (int)lo_i && (uint32_t)len <= hi_i;
+            rh = h;
+            re = e;
         }
-        if (rrel && rh == i) fw |= 3u << (2 * u);  // heads its segment: first of its read too
+        const int u = li - l0;
+        if (rrel && rh == li) fw |= 3u << (2 * u);  // heads its segment: first of its read too
         else if (rrel) need |= 1u << u;            // kept if the previous window is of another read
     }
+    // the previous window qp < q (position order within a segment) lies in another read when a
+    // read starts in (qp, q]: decided from the read table alone when the read holding q's bucket
+    // start comes after the read holding the start of the bucket after qp's; else searched
 #pragma unroll 1
     for (int u0 = 0; u0 < DS_ITEMS; u0 += DS_GROUP) {
         if (((need >> u0) & ((1u << DS_GROUP) - 1)) == 0) continue;
-        int64_t q[DS_GROUP], r[DS_GROUP];
+        int64_t q[DS_GROUP], qp[DS_GROUP], r[DS_GROUP];
         bool act[DS_GROUP];
 #pragma unroll
         for (int u = 0; u < DS_GROUP; u++) {
             act[u] = (need >> (u0 + u)) & 1u;
             q[u] = (int64_t)((sk[ds_pad(l0 + u0 + u)] & lowmask) >> 1);
+            qp[u] = (int64_t)((sk[ds_pad(l0 + u0 + u - 1)] & lowmask) >> 1);
+            if (act[u]) {
+                const int64_t bq = q[u] >> LUT_SHIFT, bp = (qp[u] >> LUT_SHIFT) + 1;
+                if (bp < a.nb && bq >= bp && a.lut[bq] > a.lut[bp]) {
+                    act[u] = false;
+                    fw |= 2u << (2 * (u0 + u));
+                }
+            }
         }
         reads_of<DS_GROUP>(q, act, r, a.off, a.n, a.lut, a.nb);
 #pragma unroll
         for (int u = 0; u < DS_GROUP; u++)
-            if (act[u]) {
-                const int64_t qp = (int64_t)((sk[ds_pad(l0 + u0 + u - 1)] & lowmask) >> 1);
-                if (!(qp >= a.off[r[u]] && qp < a.off[r[u] + 1])) fw |= 2u << (2 * (u0 + u));
-            }
+            if (act[u] && !(qp[u] >= a.off[r[u]] && qp[u] < a.off[r[u] + 1])) fw |= 2u << (2 * (u0 + u));
     }
     flags[tile * DS_NT + threadIdx.x] = fw;
     uint32_t ns = __popc(fw & 0x55555555u), nk = __popc(fw & 0xAAAAAAAAu);
@@ -1063,6 +1079,8 @@ __global__ void __launch_bounds__(DS_NT, 4) seg_emit_kernel(SegArgs a, const uin
     const int64_t seg0 = pseg[tile], keep0 = pkeep[tile];
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t lowmask = (1ull << a.pb) - 1;
+    int64_t s0 = 0, s1 = 0;  // the bucket range of the last head, and its bucket
+    uint64_t bkt = 0;
 #pragma unroll 1
     for (int u0 = 0; u0 < DS_ITEMS; u0 += DS_GROUP) {
         int64_t q[DS_GROUP], r[DS_GROUP];
@@ -1089,8 +1107,8 @@ __global__ void __launch_bounds__(DS_NT, 4) seg_emit_kernel(SegArgs a, const uin
             const int64_t o = keep0 + kpre[row * NW + w] + __popc(kmask[row][w] & lt);
             if (!SG_IN_BOUNDS(col >= 0 && col < m, 110, col)) continue;
             if (f & 1u) {
-                int64_t s0, s1;
-                const uint64_t key = (bucket_range(a.bs, i, a.nc, s0, s1) << a.bs.shift) | (p >> a.pb);
+                if (i < s0 || i >= s1) bkt = bucket_range(a.bs, i, a.nc, s0, s1);
+                const uint64_t key = (bkt << a.bs.shift) | (p >> a.pb);
                 at_rp[col] = o;
                 codes[col] = a.kbits < 64 ? key & ((1ull << a.kbits) - 1) : key;
                 if (job_ncols) atomicAdd(job_ncols + (key >> a.kbits), 1ull);

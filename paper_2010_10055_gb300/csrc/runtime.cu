@@ -300,7 +300,7 @@ static Tunable g_tunables[] = {
     {"spgemm_lower_smem", 4096, 1, 4096}, // (0 above) parts up to this long are sorted in shared memory
     {"spgemm_tab_warps", 64, 0, 64},      // fused-pass blocks: threads for about this many warps per SM
                                           // across the blocks that fit (0: fixed threads per table size)
-    {"spgemm_tab_max_threads", 1024, 64, 1024},  // ... but at most this many threads per block
+    {"spgemm_tab_warps_big", 32, 1, 64},  // ... the same for tables of 4 K slots and more
     {"spgemm_sample_rows", 256, 0, 1 << 20},  // rows sampled for the fused tables' guesses (0: none)
     {"spgemm_guess_pct", 200, 1, 10000},  // guess = pct / 100 x sampled partners per A entry x entries
     {"spgemm_tmp_pct", 125, 1, 10000},    // fused temporary region = pct / 100 x sampled kept entries

@@ -1338,19 +1338,20 @@ static int pick_numeric_threads(int log2T, bool filtered) {
 }
 
 // threads per block of the fused pass: enough warps that the blocks shared memory lets reside on
-// one SM bring about spgemm_tab_warps warps (64 = the SM's limit) between them, and at most
-// spgemm_tab_max_threads
+// one SM bring about spgemm_tab_warps warps (64 = the SM's limit) between them; for tables of 4 K
+// slots and more, spgemm_tab_warps_big
 // tsm = the table's (and filters') shared memory, warp_bytes = each warp's record buffer; code =
 // log2T, negated for unfiltered tables (for the fixed choice when spgemm_tab_warps is 0)
 static int pick_tab_threads(size_t tsm, size_t warp_bytes, int code) {
-    const int64_t want = tune("spgemm_tab_warps");
-    if (want <= 0) return pick_numeric_threads(code < 0 ? -code : code, code > 0);
-    const int64_t cap = tune("spgemm_tab_max_threads");
+    const int log2T = code < 0 ? -code : code;
+    int64_t want = tune("spgemm_tab_warps");
+    if (want <= 0) return pick_numeric_threads(log2T, code > 0);
+    if (log2T >= 12) want = tune("spgemm_tab_warps_big");
     int64_t threads = 64;
     for (;;) {
         const size_t bytes = tsm + warp_bytes * (size_t)(threads / 32);
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(32, (int64_t)((227u << 10) / bytes)));
-        if (threads >= 1024 || threads >= cap || blocks * (threads / 32) >= want) break;
+        if (threads >= 1024 || blocks * (threads / 32) >= want) break;
         threads <<= 1;
     }
     return (int)threads;
