@@ -14,6 +14,8 @@ struct sg_host_arena {
     size_t h_cap = 0;
     void *d = nullptr;  // device block for the inputs
     size_t d_cap = 0;
+    cudaStream_t cs = nullptr;  // copies C to the host while the reduction runs
+    cudaEvent_t ev = nullptr;   // C complete on the call's stream
 };
 
 namespace sg {
@@ -106,40 +108,68 @@ static sg_status pipeline_impl(const sg_pipeline_job *j, sg_host_arena *ar, sg_p
         }
         st = sg_overlap_spgemm(&A, &At, j->min_shared, j->max_seeds, &C, (sg_stream_t)s);
         if (st != SG_OK) break;
-        if (do_tr) {
-            st = sg_transitive_reduce(&R, j->fuzz, j->tr_mode, &S, &iters, (sg_stream_t)s);
-            if (st != SG_OK) break;
-        }
-        // host results: C then S, packed in the pinned arena
-        const int64_t cn = C.nnz, sn = S.nnz, Sd = C.max_seeds;
+        // host results: C then S (at most nnz(R) entries: S is a subgraph of R), packed in the
+        // pinned arena; C is copied on the arena's copy stream while the reduction runs
+        const int64_t cn = C.nnz, Sd = C.max_seeds, smax = do_tr ? j->r_nnz : 0;
         size_t h_crp = 0, h_ccol = align256(h_crp + (size_t)(n + 1) * 8);
         size_t h_ccnt = align256(h_ccol + (size_t)cn * 4);
         size_t h_csi = align256(h_ccnt + (size_t)cn * 4);
         size_t h_csk = align256(h_csi + (size_t)cn * Sd * 4);
         size_t h_srp = align256(h_csk + (size_t)cn * Sd * 4);
         size_t h_scol = align256(h_srp + (do_tr ? (size_t)(n + 1) * 8 : 0));
-        size_t h_ssuf = align256(h_scol + (size_t)sn * 4);
-        size_t h_sdir = align256(h_ssuf + (size_t)sn * 4);
-        size_t hbytes = h_sdir + (size_t)sn + 8;
-        st = grow_host(ar, hbytes);
+        size_t h_ssuf = align256(h_scol + (size_t)smax * 4);
+        size_t h_sdir = align256(h_ssuf + (size_t)smax * 4);
+        size_t hbytes = h_sdir + (size_t)smax + 8;
+        st = grow_host(ar, hbytes);  // no copy into the arena is in flight between calls
         if (st != SG_OK) break;
+        if (!ar->cs && cudaStreamCreateWithFlags(&ar->cs, cudaStreamNonBlocking) != cudaSuccess) {
+            ar->cs = nullptr;
+            set_error("pipeline: copy stream creation failed");
+            st = SG_ERR_CUDA;
+            break;
+        }
+        if (!ar->ev && cudaEventCreateWithFlags(&ar->ev, cudaEventDisableTiming) != cudaSuccess) {
+            ar->ev = nullptr;
+            set_error("pipeline: event creation failed");
+            st = SG_ERR_CUDA;
+            break;
+        }
         unsigned char *h = (unsigned char *)ar->h;
         unsigned long long hprod = 0;
         cudaError_t e = cudaMemcpyAsync(&hprod, prod, 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h + h_crp, C.row_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && cn) e = cudaMemcpyAsync(h + h_ccol, C.col, (size_t)cn * 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && cn) e = cudaMemcpyAsync(h + h_ccnt, C.count, (size_t)cn * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ar->ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ar->cs, ar->ev, 0);
+        cudaStream_t cs = ar->cs;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h + h_crp, C.row_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && cn) e = cudaMemcpyAsync(h + h_ccol, C.col, (size_t)cn * 4, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && cn) e = cudaMemcpyAsync(h + h_ccnt, C.count, (size_t)cn * 4, cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess && cn && Sd)
-            e = cudaMemcpyAsync(h + h_csi, C.seed_i, (size_t)cn * Sd * 4, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(h + h_csi, C.seed_i, (size_t)cn * Sd * 4, cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess && cn && Sd)
-            e = cudaMemcpyAsync(h + h_csk, C.seed_k, (size_t)cn * Sd * 4, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(h + h_csk, C.seed_k, (size_t)cn * Sd * 4, cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(cs);  // nothing of C is freed while a copy may still read it
+            set_error("pipeline: copying C to the host failed: %s", cudaGetErrorString(e));
+            st = SG_ERR_CUDA;
+            break;
+        }
+        if (do_tr) {
+            st = sg_transitive_reduce(&R, j->fuzz, j->tr_mode, &S, &iters, (sg_stream_t)s);
+            if (st != SG_OK) {
+                cudaStreamSynchronize(cs);
+                break;
+            }
+        }
+        const int64_t sn = S.nnz;
         if (do_tr) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(h + h_srp, S.row_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess && sn) e = cudaMemcpyAsync(h + h_scol, S.col, (size_t)sn * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess && sn) e = cudaMemcpyAsync(h + h_ssuf, S.suffix, (size_t)sn * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess && sn) e = cudaMemcpyAsync(h + h_sdir, S.dir, (size_t)sn, cudaMemcpyDeviceToHost, s);
         }
+        const cudaError_t ec = cudaStreamSynchronize(cs);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = ec;
         if (e != cudaSuccess) {
             set_error("pipeline: copying results to the host failed: %s", cudaGetErrorString(e));
             st = SG_ERR_CUDA;
@@ -180,6 +210,11 @@ extern "C" sg_status sg_host_arena_create(sg_host_arena **arena) {
 
 extern "C" void sg_host_arena_destroy(sg_host_arena *a) {
     if (!a) return;
+    if (a->cs) {
+        cudaStreamSynchronize(a->cs);
+        cudaStreamDestroy(a->cs);
+    }
+    if (a->ev) cudaEventDestroy(a->ev);
     if (a->h) cudaFreeHost(a->h);
     if (a->d) cudaFree(a->d);
     delete a;
