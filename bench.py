@@ -136,6 +136,12 @@ def algorithmic_bytes(kernel: str, sz: dict) -> float | None:
         return 4.0 * sz["total"] + 8.0 * sz["windows"]         # hashes in + filter word read and write
     if kernel == "cand_count":
         return 4.0 * sz["total"] + 4.0 * sz["windows"]         # hashes in + second-filter word probe
+    if kernel == "cand_emit" and k:                           # candidate masks and packed bases in, keys out
+        return 0.125 * sz["windows"] + 0.25 * sz["total"] + 8.0 * k["candidates"]
+    if kernel == "seg_mark" and k and sz.get("direct_seg"):  # sorted keys in, two flag bits out
+        return 8.25 * k["candidates"]
+    if kernel == "emit_at" and k and sz.get("direct_seg"):   # sorted keys and flags in; At, A pairs, codes out
+        return 8.25 * k["candidates"] + 20.0 * k["nnz"] + 16.0 * k["m"]
     if kernel == "radix_onesweep" and sz.get("kstats"):
         k = sz["kstats"]  # every pass reads and writes each record once (the histogram is its own kernel)
         return (2.0 * k["sort_passes"] * k["candidates"] * (k["sort_key_bytes"] + k["sort_val_bytes"])
@@ -249,7 +255,7 @@ def main():
     sz = dict(n=n, total=total, windows=max(total - (w.k - 1) * n, 0), nnzA=km.A.nnz, products=products,
               products_half=int((a * (a - 1) // 2).sum()), upper=bool(sg.tunables().get("spgemm_upper", 0)),
               nnzC=C.nnz, S=w.max_seeds, nnzR=R.nnz, tr_products=tr_products, nnzS=S.nnz, rounds=it, m=km.m,
-              kstats=sg.last_kmer_stats())
+              kstats=sg.last_kmer_stats(), direct_seg=bool(sg.tunables().get("kmer_direct_seg", 0)))
     del km, C, S
 
     # ---- timed region: K steps, per-step events, L2 flushed in between; only the dominant
