@@ -478,15 +478,17 @@ __global__ void __launch_bounds__(KM_NT) cand_count_kernel(const uint32_t *__res
             const uint32_t m = __ballot_sync(0xffffffffu, is_candidate(h[u], b2, use_bloom, bb));
             if (lane == g0u + u) mine = m;
             c += __popc(m);
-            if (BKT && m) {
+            if (BKT && m) {  // lane j < nb counts the candidates of bucket j, one ballot per bucket bit
                 const int64_t g = g0 + g0u + u;
                 const bool cand = (m >> lane) & 1u;
                 const uint32_t b = cand ? bucket_of(bk, window_key(bk.P[g], bk.P[g + 1], lane, bk.k, jc, g * 32 + lane))
                                         : 0u;
-                for (int j = 0; j < bk.nb; j++) {
-                    const uint32_t mb = __ballot_sync(0xffffffffu, cand && b == (uint32_t)j);
-                    if (lane == j) cb += __popc(mb);
+                uint32_t own = m;
+                for (int t = 0; (1 << t) < bk.nb; t++) {
+                    const uint32_t bt = __ballot_sync(0xffffffffu, cand && ((b >> t) & 1u));
+                    own &= ((lane >> t) & 1) ? bt : ~bt;
                 }
+                if (lane < bk.nb) cb += __popc(own);
             }
         }
     }
@@ -545,14 +547,18 @@ __global__ void __launch_bounds__(KM_NT) cand_emit_kernel(Buckets bk, const uint
         const uint64_t x = cand ? window_key(bk.P[g0 + g], bk.P[g0 + g + 1], lane, bk.k, jc, q) : 0ull;
         int64_t p;
         {
+            // peers (the lanes of this lane's bucket) and own (the lanes of bucket `lane`, for
+            // lane < nb) from one ballot per bucket bit; this lane's slot follows the base of its
+            // bucket (held by lane b) and the lanes below it in the bucket
             const uint32_t b = cand ? bucket_of(bk, x) : 0u;
-            p = 0;
-            for (int j = 0; j < bk.nb; j++) {
-                const uint32_t mb = __ballot_sync(0xffffffffu, cand && b == (uint32_t)j);
-                const int64_t base = __shfl_sync(0xffffffffu, o, j);
-                if (cand && b == (uint32_t)j) p = base + __popc(mb & below);
-                if (lane == j) o += __popc(mb);
+            uint32_t peers = m, own = m;
+            for (int t = 0; (1 << t) < bk.nb; t++) {
+                const uint32_t bt = __ballot_sync(0xffffffffu, cand && ((b >> t) & 1u));
+                peers &= ((b >> t) & 1u) ? bt : ~bt;
+                own &= ((lane >> t) & 1) ? bt : ~bt;
             }
+            p = __shfl_sync(0xffffffffu, o, (int)b) + __popc(peers & below);
+            if (lane < bk.nb) o += __popc(own);
         }
         if (cand && SG_IN_BOUNDS(p >= 0 && p < nc, 102, p))  // buckets: always PK_POS
             keys[p] = (((x & bk.kmask) & lowmask) << pb) | ((uint64_t)q << 1) | (x >> 63);
