@@ -319,7 +319,7 @@ static Tunable g_tunables[] = {
     {"pool_cross_stream_reuse", 1, 0, 1}, // pool may hand memory freed on one stream to another
     {"batch_alone_kb", 64000, 0, 1 << 30},  // batched items of this many kilobases or more run on their
                                             // own (0: every item shares the union)
-    {"batch_group_kb", 500000, 1, 1 << 30}, // ... the others share unions of at most this many kilobases
+    {"batch_group_kb", 250000, 1, 1 << 30}, // ... the others share unions of at most this many kilobases
 };
 static std::mutex g_tune_mu;
 
