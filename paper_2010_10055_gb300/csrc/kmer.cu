@@ -24,7 +24,8 @@
 //  5. segments -> exact frequency (segment length) -> reliable flag -> column = rank of the
 //     reliable code; within a reliable segment the first entry of each read is its lowest
 //     position: those entries are At's row, already sorted by read.
-//  6. A = At transposed by a stable radix sort on the read id (columns stay ascending).
+//  6. A = At transposed by a stable radix sort on the read id (columns stay ascending); its last
+//     pass writes A's column and value arrays.
 #include <optional>
 #include <type_traits>
 
@@ -1574,12 +1575,14 @@ sg_status build_impl(const uint8_t *seq, const int64_t *off, int64_t n, int64_t 
     kmer_stats().nnz = nnz;
     kmer_stats().a_sort_passes = nnz > 1 ? (rbits + 7) / 8 : 0;
     bool aalt = false;
-    SG_TRY((radix_sort_pairs<uint32_t, uint64_t>(ak0, av0, ak1, av1, nnz, rbits, &aalt, s, err)));
+    const bool split = nnz > 1 && rbits > 0;  // the sort's last pass writes A's columns and values
+    if (split)
+        SG_TRY(radix_sort_pairs_split(ak0, av0, ak1, av1, nnz, rbits, &aalt, (uint32_t *)A->col, A->val, s, err));
     const uint32_t *arow = aalt ? ak1 : ak0;
     const uint64_t *apv = aalt ? av1 : av0;
     SG_LAUNCH("rowptr_from_sorted", rowptr_from_sorted_kernel, blocks_for(nnz + 1, NT), NT, 0, s, arow, nnz, n,
               A->row_ptr);
-    SG_LAUNCH("split_pairs", split_pairs_kernel, blocks_for(nnz, NT), NT, 0, s, apv, nnz, A->col, A->val);
+    if (!split) SG_LAUNCH("split_pairs", split_pairs_kernel, blocks_for(nnz, NT), NT, 0, s, apv, nnz, A->col, A->val);
     SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));  // the sort of A waits between tiles
     if (herr) return timeout_error("build_kmer_matrix");
     return SG_OK;

@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(RS_NT, HAS_V ? 3 : 4) radix_onesweep_kernel(co
                                                               int64_t n, int shift,
                                                               const unsigned long long *__restrict__ ghist,
                                                               unsigned long long *status, unsigned int *tile_ctr,
-                                                              uint32_t *err, int lbw) {
+                                                              uint32_t *err, int lbw, uint32_t *__restrict__ vhi,
+                                                              uint32_t *__restrict__ vlo) {
     extern __shared__ __align__(16) unsigned char rs_raw[];
     RsSmem<K, V, HAS_V> &sm = *reinterpret_cast<RsSmem<K, V, HAS_V> *>(rs_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -176,13 +177,21 @@ __global__ void __launch_bounds__(RS_NT, HAS_V ? 3 : 4) radix_onesweep_kernel(co
         const int64_t o = sm.gbase[dd] + i;
         if (!SG_IN_BOUNDS(o >= 0 && o < n, 202, o)) continue;
         kout[o] = kk;
-        if (HAS_V) vout[o] = sm.vals[HAS_V ? i : 0];
+        if (HAS_V) {
+            const V v = sm.vals[HAS_V ? i : 0];
+            if (vhi) {  // 64-bit values written as their two halves
+                vhi[o] = (uint32_t)((uint64_t)v >> 32);
+                vlo[o] = (uint32_t)v;
+            } else {
+                vout[o] = v;
+            }
+        }
     }
 }
 
 template <class K, class V, bool HAS_V>
 static sg_status radix_sort_impl(K *k0, V *v0, K *k1, V *v1, int64_t n, int lo_bit, int hi_bit, bool *in_alt,
-                                 cudaStream_t s, uint32_t *err) {
+                                 cudaStream_t s, uint32_t *err, uint32_t *vhi = nullptr, uint32_t *vlo = nullptr) {
     static_assert(RS_NT == RS_RADIX, "one thread per digit");
     *in_alt = false;
     if (n <= 1 || hi_bit <= lo_bit) return SG_OK;
@@ -211,16 +220,17 @@ static sg_status radix_sort_impl(K *k0, V *v0, K *k1, V *v1, int64_t n, int lo_b
     K *ki = k0, *ko = k1;
     V *vi = v0, *vo = v1;
     for (int p = 0; p < npass; p++) {
+        uint32_t *hi = p == npass - 1 ? vhi : nullptr, *lo = p == npass - 1 ? vlo : nullptr;
         if (match)
             SG_LAUNCH("radix_onesweep", (radix_onesweep_kernel<K, V, HAS_V, true>), ntiles, RS_NT, smem, s,
                       (const K *)ki, (const V *)vi, ko, vo, n, lo_bit + RS_BITS * p,
                       (const unsigned long long *)(ghist + p * RS_RADIX), status + (size_t)p * ntiles * RS_RADIX,
-                      ctr + p, err, lbw);
+                      ctr + p, err, lbw, hi, lo);
         else
             SG_LAUNCH("radix_onesweep", (radix_onesweep_kernel<K, V, HAS_V, false>), ntiles, RS_NT, smem, s,
                       (const K *)ki, (const V *)vi, ko, vo, n, lo_bit + RS_BITS * p,
                       (const unsigned long long *)(ghist + p * RS_RADIX), status + (size_t)p * ntiles * RS_RADIX,
-                      ctr + p, err, lbw);
+                      ctr + p, err, lbw, hi, lo);
         K *tk = ki; ki = ko; ko = tk;
         V *tv = vi; vi = vo; vo = tv;
         *in_alt = !*in_alt;
@@ -232,6 +242,15 @@ template <class K, class V>
 sg_status radix_sort_pairs(K *k0, V *v0, K *k1, V *v1, int64_t n, int key_bits, bool *in_alt, cudaStream_t s,
                            uint32_t *err) {
     return radix_sort_impl<K, V, true>(k0, v0, k1, v1, n, 0, key_bits, in_alt, s, err);
+}
+
+sg_status radix_sort_pairs_split(uint32_t *k0, uint64_t *v0, uint32_t *k1, uint64_t *v1, int64_t n, int key_bits,
+                                 bool *in_alt, uint32_t *vhi, uint32_t *vlo, cudaStream_t s, uint32_t *err) {
+    if (n <= 1 || key_bits <= 0) {
+        set_error("internal: split radix sort of %lld pairs on %d bits", (long long)n, key_bits);
+        return SG_ERR_INVALID;
+    }
+    return radix_sort_impl<uint32_t, uint64_t, true>(k0, v0, k1, v1, n, 0, key_bits, in_alt, s, err, vhi, vlo);
 }
 
 sg_status radix_sort_keys(uint64_t *k0, uint64_t *k1, int64_t n, int lo_bit, int hi_bit, bool *in_alt,

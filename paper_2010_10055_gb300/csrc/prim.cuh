@@ -26,6 +26,12 @@ template <class K, class V>
 sg_status radix_sort_pairs(K *k0, V *v0, K *k1, V *v1, int64_t n, int key_bits, bool *in_alt,
                            cudaStream_t s, uint32_t *err);
 
+// radix_sort_pairs for 32-bit keys and 64-bit values whose last pass writes each value as two
+// 32-bit halves, vhi[i] = v >> 32 and vlo[i] = (uint32_t)v (n entries each), instead of to v0/v1;
+// the sorted keys end as radix_sort_pairs says. Needs n > 1 and key_bits > 0 (at least one pass).
+sg_status radix_sort_pairs_split(uint32_t *k0, uint64_t *v0, uint32_t *k1, uint64_t *v1, int64_t n, int key_bits,
+                                 bool *in_alt, uint32_t *vhi, uint32_t *vlo, cudaStream_t s, uint32_t *err);
+
 // Stable LSD radix sort of 64-bit keys by their bits [lo_bit, hi_bit) (other bits ride along;
 // bits above hi_bit up to the last digit's end must be zero).
 sg_status radix_sort_keys(uint64_t *k0, uint64_t *k1, int64_t n, int lo_bit, int hi_bit, bool *in_alt,
