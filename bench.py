@@ -468,6 +468,7 @@ def measure_e2e(sg, d, w, args):
         d2h = 8 * nrow * 2 + res.nnz_c * (8 + 8 * res.max_seeds) + res.nnz_s * 9 + 8
         return {"value": float(res.products) * args.steps / sum(times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(times) / args.steps,
+                "step_ms_min": 1e3 * min(times), "step_ms_max": 1e3 * max(times),
                 "nnz_C": int(res.nnz_c), "nnz_S": int(res.nnz_s)}
     finally:
         L.sg_host_arena_destroy(arena)
