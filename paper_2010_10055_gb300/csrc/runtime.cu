@@ -295,6 +295,8 @@ static Tunable g_tunables[] = {
     {"spgemm_smem_carveout", -1, -1, 100},// fused-pass shared-memory carveout, % (-1: the driver's)
     {"spgemm_escalate", 1, 0, 8},         // a guessed table that overflows is tried once more
                                           // 2^this times larger in shared memory (0: global memory)
+    {"spgemm_mirror_rec", 1, 0, 1},       // 1: (mirror sort) U's entries copied into 32-byte records that
+                                          // the mirror reads, instead of C's arrays (max_seeds <= 3)
     {"spgemm_mirror_sort", 1, 0, 1},      // 1: mirrored entries ordered by a stable radix sort by column;
                                           // 0: scattered by atomics and sorted per row
     {"spgemm_lower_smem", 4096, 1, 4096}, // (0 above) parts up to this long are sorted in shared memory

@@ -1222,6 +1222,12 @@ __global__ void __launch_bounds__(1024) lower_big_kernel(const uint32_t *__restr
 // column's entries by ascending row, which is the order of the mirrored entries in the lower part
 // of row k (lower_fill_kernel).
 constexpr int MIRROR_POS_BITS = 33;
+// An entry of U as one 32-byte record (count, then si, sk per seed slot) for max_seeds <= 3, so
+// that its mirror gathers one sector instead of 1 + 2 max_seeds words of C's arrays.
+constexpr int MIRROR_REC_SEEDS = 3;
+struct __align__(32) MirrorRec {
+    uint32_t w[8];
+};
 
 __global__ void mirror_keys_kernel(const int64_t *__restrict__ tmp_off, const int64_t *__restrict__ nnz_row,
                                    int64_t tmp_n, const int32_t *__restrict__ t_col,
@@ -1230,7 +1236,8 @@ __global__ void mirror_keys_kernel(const int64_t *__restrict__ tmp_off, const in
                                    const int64_t *__restrict__ c_rp, const int64_t *__restrict__ rpu, int64_t n,
                                    int64_t nnz, int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
                                    uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
-                                   uint32_t *__restrict__ mkey, uint64_t *__restrict__ mval) {
+                                   uint32_t *__restrict__ mkey, uint64_t *__restrict__ mval,
+                                   MirrorRec *__restrict__ mrec) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -1239,14 +1246,27 @@ __global__ void mirror_keys_kernel(const int64_t *__restrict__ tmp_off, const in
     const int64_t src = tmp_off[row], dst = c_rp[row] + colcnt[row], u0 = rpu[row];
     for (int64_t e = lane; e < len; e += 32) {
         const int32_t k = t_col[src + e];
+        const uint32_t cnt = t_cnt[src + e];
         c_col[dst + e] = k;
-        c_cnt[dst + e] = t_cnt[src + e];
+        c_cnt[dst + e] = cnt;
+        MirrorRec r = {};
+        r.w[0] = cnt;
         for (int q = 0; q < S; q++) {
-            c_si[(int64_t)q * nnz + dst + e] = t_si[(int64_t)q * tmp_n + src + e];
-            c_sk[(int64_t)q * nnz + dst + e] = t_sk[(int64_t)q * tmp_n + src + e];
+            const uint32_t si = t_si[(int64_t)q * tmp_n + src + e], sk = t_sk[(int64_t)q * tmp_n + src + e];
+            c_si[(int64_t)q * nnz + dst + e] = si;
+            c_sk[(int64_t)q * nnz + dst + e] = sk;
+            if (q < MIRROR_REC_SEEDS) {
+                r.w[1 + 2 * q] = si;
+                r.w[2 + 2 * q] = sk;
+            }
         }
         mkey[u0 + e] = (uint32_t)k;
-        mval[u0 + e] = ((uint64_t)row << MIRROR_POS_BITS) | (uint64_t)(dst + e);
+        if (mrec) {  // the mirror reads this record by its index in U instead of C's arrays at dst + e
+            mrec[u0 + e] = r;
+            mval[u0 + e] = ((uint64_t)row << MIRROR_POS_BITS) | (uint64_t)(u0 + e);
+        } else {
+            mval[u0 + e] = ((uint64_t)row << MIRROR_POS_BITS) | (uint64_t)(dst + e);
+        }
     }
 }
 
@@ -1256,19 +1276,29 @@ __global__ void mirror_keys_kernel(const int64_t *__restrict__ tmp_off, const in
 __global__ void lower_fill_kernel(const uint32_t *__restrict__ mkey, const uint64_t *__restrict__ mval, int64_t nu,
                                   const int64_t *__restrict__ lrp, const int64_t *__restrict__ c_rp, int64_t n,
                                   int64_t nnz, int S, int32_t *__restrict__ c_col, uint32_t *__restrict__ c_cnt,
-                                  uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk) {
+                                  uint32_t *__restrict__ c_si, uint32_t *__restrict__ c_sk,
+                                  const MirrorRec *__restrict__ mrec) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nu) return;
     const uint32_t k = mkey[q];
     const uint64_t v = mval[q];
+    // p: the U entry's position in C, or (records) its index in U
     const int64_t i = (int64_t)(v >> MIRROR_POS_BITS), p = (int64_t)(v & ((1ull << MIRROR_POS_BITS) - 1));
-    if (!SG_IN_BOUNDS(k < n && p < nnz, 312, q)) return;
+    if (!SG_IN_BOUNDS(k < n && p < (mrec ? nu : nnz), 312, q)) return;
     const int64_t d = c_rp[k] + (q - lrp[k]);
     if (!SG_IN_BOUNDS(d >= c_rp[k] && d < c_rp[k + 1], 313, d)) return;
     c_col[d] = (int32_t)i;
-    c_cnt[d] = c_cnt[p];
+    MirrorRec r = {};
+    if (mrec) {
+        const uint4 *pr = reinterpret_cast<const uint4 *>(mrec + p);
+        const uint4 a = __ldg(pr), b = __ldg(pr + 1);
+        r.w[0] = a.x; r.w[1] = a.y; r.w[2] = a.z; r.w[3] = a.w;
+        r.w[4] = b.x; r.w[5] = b.y; r.w[6] = b.z; r.w[7] = b.w;
+    }
+    c_cnt[d] = mrec ? r.w[0] : c_cnt[p];
     for (int s = 0; s < S; s++) {
-        const uint32_t si = c_si[(int64_t)s * nnz + p], sk = c_sk[(int64_t)s * nnz + p];
+        const uint32_t si = mrec ? r.w[1 + 2 * s] : c_si[(int64_t)s * nnz + p];
+        const uint32_t sk = mrec ? r.w[2 + 2 * s] : c_sk[(int64_t)s * nnz + p];
         const bool none = si == SEED_NONE;
         c_si[(int64_t)s * nnz + d] = none ? SEED_NONE : (sk & 0x7FFFFFFFu);
         c_sk[(int64_t)s * nnz + d] = none ? SEED_NONE : (si | (sk & 0x80000000u));
@@ -1750,11 +1780,17 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 uint32_t *mk0 = sc.get<uint32_t>(nnz_l + 1), *mk1 = sc.get<uint32_t>(nnz_l + 1);
                 uint64_t *mv0 = sc.get<uint64_t>(nnz_l + 1), *mv1 = sc.get<uint64_t>(nnz_l + 1);
                 if (!mk0 || !mk1 || !mv0 || !mv1) return SG_ERR_OOM;
+                // U's entries as records, where the seeds fit one (nnz_l = nnz(U): every U entry is mirrored)
+                MirrorRec *mrec = nullptr;
+                if (tune("spgemm_mirror_rec") && S <= MIRROR_REC_SEEDS) {
+                    mrec = sc.get<MirrorRec>(nnz_l + 1);
+                    if (!mrec) return SG_ERR_OOM;
+                }
                 SG_LAUNCH("mirror_c", mirror_keys_kernel, blocks_for(n * 32, 256), 256, 0, s,
                           (const int64_t *)tmp_off, (const int64_t *)nnz_row, cap, (const int32_t *)o.col,
                           (const uint32_t *)o.cnt, (const uint32_t *)o.si, (const uint32_t *)o.sk, S,
                           (const uint32_t *)colcnt, (const int64_t *)C->row_ptr, (const int64_t *)rpu, n, nnz, C->col,
-                          C->count, C->seed_i, C->seed_k, mk0, mv0);
+                          C->count, C->seed_i, C->seed_k, mk0, mv0, mrec);
                 for (const void *p : {(const void *)o.col, (const void *)o.cnt, (const void *)o.si, (const void *)o.sk})
                     sc.release(p);
                 int kbits = 1;
@@ -1764,7 +1800,7 @@ sg_status overlap_impl(const sg_csr_u32 *A, const sg_csr_u32 *At, uint32_t min_s
                 SG_LAUNCH("lower_fill", lower_fill_kernel, blocks_for(nnz_l, 256), 256, 0, s,
                           (const uint32_t *)(alt ? mk1 : mk0), (const uint64_t *)(alt ? mv1 : mv0), nnz_l,
                           (const int64_t *)lrp, (const int64_t *)C->row_ptr, n, nnz, S, C->col, C->count, C->seed_i,
-                          C->seed_k);
+                          C->seed_k, (const MirrorRec *)mrec);
                 SG_CUDA_TRY(read_back(&herr, err, sizeof(uint32_t), s));  // the sort waits between tiles
                 if (herr & DEV_TIMEOUT) return timeout_error("overlap_spgemm");
                 return SG_OK;

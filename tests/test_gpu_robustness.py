@@ -73,6 +73,7 @@ CONFIGS = [
     {"spgemm_at_records": 0, "spgemm_upper": 0},
     {"spgemm_filter_mode": 1},                                       # filter where the sample says
     {"spgemm_mirror_sort": 0},                                       # mirror by atomics + row sorts
+    {"spgemm_mirror_rec": 0},                                        # mirror gathers C's arrays
     {"spgemm_mirror_sort": 0, "spgemm_lower_smem": 1},               # ... all in global memory
 ]
 
