@@ -8,22 +8,25 @@
 // lowest such position).
 //
 // Pipeline (all on `stream`):
-//  0. pack           one walk over the reads packs the bases (2 bits each) and marks where a
-//                    valid window starts (1 bit each); every later pass recomputes a window's
-//                    canonical code and strand from two packed words.
+//  0. pack           one walk over the reads packs the bases (2 bits each) and stores each
+//                    window's 32-bit filter hash (H_NONE where no valid window starts); later
+//                    passes recompute a window's canonical code and strand from two packed words.
 //  1. bloom_insert   every code is OR-ed into the blocked Bloom filter B1 (all probe bits in one
 //                    32-bit word, so "already present" is decided by one atomic); a code found
-//                    present is OR-ed into B2 ("seen at least twice"). Skipped when lo == 1.
+//                    present is OR-ed into B2 ("seen at least twice"). Where they fit, the hashes
+//                    are first grouped by filter bin and each bin's filters live in shared memory.
+//                    Skipped when lo == 1.
 //  2. cand_count     per warp, a ballot mask of the windows whose code tests positive in B2.
 //                    Every occurrence of a k-mer with frequency >= 2 passes (false positives only
 //                    add singletons, which the exact count below drops).
 //  3. cand_emit      writes (code, position | strand) at scanned offsets, so the candidates stay
 //                    in position order, i.e. (read, pos) order.
-//  4. radix sort by code (stable): equal codes form segments in (read, pos) order; positions are
-//     then resolved to (read, pos).
+//  4. radix sort by code (stable): equal codes form segments in (read, pos) order.
 //  5. segments -> exact frequency (segment length) -> reliable flag -> column = rank of the
 //     reliable code; within a reliable segment the first entry of each read is its lowest
-//     position: those entries are At's row, already sorted by read.
+//     position: those entries are At's row, already sorted by read. For position-and-code keys
+//     this runs on the sorted keys themselves (seg_mark, scans of its tile totals, seg_emit,
+//     which resolves the kept windows to (read, pos)); other key forms are unpacked first.
 //  6. A = At transposed by a stable radix sort on the read id (columns stay ascending); its last
 //     pass writes A's column and value arrays.
 #include <optional>
