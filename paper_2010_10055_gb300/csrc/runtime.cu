@@ -318,6 +318,7 @@ static Tunable g_tunables[] = {
     {"spgemm_blocks_per_sm", 16, 1, 64},  // grid of each SpGEMM class launch
     {"spgemm_big_threads", 1024, 512, 1024},  // threads of numeric blocks with 4 K table slots or more
     {"tr_blocks_per_sm", 32, 1, 64},      // grid of the min-plus launch
+    {"tr_warp_rows", 1, 0, 1},            // 1: min-plus products of staged rows by a warp per neighbour
     {"pool_cross_stream_reuse", 1, 0, 1}, // pool may hand memory freed on one stream to another
     {"batch_alone_kb", 64000, 0, 1 << 30},  // batched items of this many kilobases or more run on their
                                             // own (0: every item shares the union)

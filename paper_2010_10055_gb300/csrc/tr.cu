@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
                                                             unsigned long long *__restrict__ gbest,
                                                             int64_t *__restrict__ gpre,
                                                             uint8_t *__restrict__ keep, int64_t *__restrict__ kept,
-                                                            uint32_t *__restrict__ outN, uint8_t *__restrict__ outD) {
+                                                            uint32_t *__restrict__ outN, uint8_t *__restrict__ outD,
+                                                            int warp_rows) {
     __shared__ int32_t s_col[GMEM ? 1 : TR_SMEM_ROW];
     __shared__ uint32_t s_suf[GMEM ? 1 : TR_SMEM_ROW];
     __shared__ uint8_t s_dir[GMEM ? 1 : TR_SMEM_ROW];
@@ -136,7 +137,29 @@ __global__ void __launch_bounds__(TR_NT) minplus_mark_kernel(TrGraph g, const in
         }
         __syncthreads();
         const int64_t P = pre[deg];
-        // N = R^2 on the pattern of row i
+        // N = R^2 on the pattern of row i: a warp per neighbour j walking j's row (staged rows,
+        // warp_rows), or every thread on the flattened products, each finding its neighbour by a
+        // search of the degree prefix
+        if (!GMEM && warp_rows) {
+            const int lane = threadIdx.x & 31;
+            for (int64_t a = threadIdx.x >> 5; a < deg; a += TR_NT / 32) {
+                const int32_t j = col[a];
+                const int64_t jb = g.rp[j], je = g.rp[j + 1];
+                const uint32_t dij = dir[a], sa = suf[a];
+                for (int64_t b = jb + lane; b < je; b += 32) {
+                    const int32_t k = g.col[b];
+                    if (k == i) continue;
+                    const int64_t t = find_col(col, deg, k);
+                    if (t < 0) continue;
+                    const uint32_t djk = g.dir[b];
+                    if ((dij & 1u) != (djk >> 1)) continue;  // heads at j must point opposite ways
+                    const uint32_t comp = (dij & 2u) | (djk & 1u);
+                    if ((mode & 1) == SG_TR_DIRMATCH && comp != dir[t]) continue;
+                    const unsigned long long key = ((unsigned long long)(sa + g.suf[b]) << 2) | comp;
+                    atomicMin(best + t, key);
+                }
+            }
+        } else
         for (int64_t p = threadIdx.x; p < P; p += TR_NT) {
             int64_t lo = 0, hi = deg;  // entry a with pre[a] <= p < pre[a + 1]
             while (hi - lo > 1) {
@@ -284,10 +307,10 @@ static sg_status minplus_round(const TrGraph &g, int64_t nnz, int mode, uint32_t
     const int64_t gs = n < gcap ? n : gcap;
     SG_LAUNCH("tr_minplus_mark", minplus_mark_kernel<false>, gs, TR_NT, 0, s, g, (const int32_t *)w.rows,
               counts + 1, err, mode, fuzz, (unsigned long long *)nullptr, (int64_t *)nullptr, keep, kept, outN,
-              outD);
+              outD, (int)tune("tr_warp_rows"));
     const int64_t gg = n < (int64_t)sm_count() * 2 ? n : (int64_t)sm_count() * 2;
     SG_LAUNCH("tr_minplus_mark_gmem", minplus_mark_kernel<true>, gg, TR_NT, 0, s, g, (const int32_t *)(w.rows + n),
-              counts + 2, err, mode, fuzz, w.gbest, w.gpre, keep, kept, outN, outD);
+              counts + 2, err, mode, fuzz, w.gbest, w.gpre, keep, kept, outN, outD, 0);
     return SG_OK;
 }
 

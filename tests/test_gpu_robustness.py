@@ -69,6 +69,7 @@ CONFIGS = [
     {"spgemm_upper": 0, "spgemm_filter_mode": 2, "spgemm_filter_work": 1},  # whole rows, filtered
     {"spgemm_mirror_sort": 0, "spgemm_lower_smem": 16, "spgemm_guess_pct": 25},  # mixed row sorts
     {"spgemm_blocks_per_sm": 1, "spgemm_big_threads": 512, "spgemm_lower_smem": 64},
+    {"tr_warp_rows": 0},                                             # min-plus over flattened products
     {"spgemm_at_records": 0},                                        # At rows gathered, no records
     {"spgemm_at_records": 0, "spgemm_upper": 0},
     {"spgemm_filter_mode": 1},                                       # filter where the sample says
