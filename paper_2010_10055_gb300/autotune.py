@@ -25,9 +25,13 @@ SPACE = {
     "spgemm_escalate": [0, 1],
     "spgemm_filter_mode": [0, 1],
     "spgemm_tab_warps": [32, 48, 64],
+    "spgemm_tab_warps_big": [16, 32, 64],
+    "spgemm_mirror_rec": [0, 1],
+    "kmer_direct_seg": [0, 1],
     "spgemm_tmp_pct": [110, 125, 200],
     "spgemm_blocks_per_sm": [4, 8, 16],
     "tr_blocks_per_sm": [8, 16, 32],
+    "tr_warp_rows": [0, 1],
 }
 # the batched form adds the planner's thresholds
 BATCH_SPACE = {"batch_alone_kb": [32000, 64000, 128000], "batch_group_kb": [100000, 250000, 500000, 1000000]}
