@@ -833,7 +833,7 @@ constexpr int DS_NT = 256;
 constexpr int DS_ITEMS = 16;
 constexpr int DS_TILE = DS_NT * DS_ITEMS;
 constexpr int DS_HALO = SEG_WALK_MAX + 16;  // a walk reads at most SEG_WALK_MAX + 1 neighbours
-constexpr int DS_GROUP = 4;
+constexpr int DS_GROUP = 2;  // 2: 20.6 / 34.8 ms for mark / emit, 4: 26.2 / 37.9 ms (registers, occupancy)
 // Staged keys are padded by one slot every 16, so that the 32 lanes of a warp, reading 8-byte
 // keys DS_ITEMS apart, hit distinct banks.
 __device__ __forceinline__ int ds_pad(int j) { return j + (j >> 4); }
